@@ -1,0 +1,205 @@
+"""FP64 CPU oracle for the explicit shallow-water step (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  It wraps ``bm_oracle.c`` (serial, edge loop, built with
+``-O2 -ffp-contract=off``) through ctypes and shares no code with the CUDA path.
+
+What the oracle computes follows BASEMENT v3 (arXiv 2102.12862): Eq. 1/Eq. 10
+unknowns (H, q_x, q_y), the update of Eq. 12 with an HLLC flux and the
+modified-state bed treatment (Section "Numerical solution", "Hydrodynamics"),
+Manning friction (Eq. 2, Table 1) split off with a semi-implicit two-stage RK,
+and the time step of Eq. 21.
+
+Parity unpinned: the discharge-inflow distribution and the wet/dry threshold
+heuristics are pinned only by mass balance and agreement with the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bm_oracle.c")
+_LIB_SERIAL = os.path.join(_HERE, "liboracle.so")
+# A test that plants a mistake in the oracle compiles a mutated copy of the source
+# (ORACLE_MUTANT_SRC) into a private library (ORACLE_MUTANT_LIB).
+if os.environ.get("ORACLE_MUTANT_SRC"):
+    _SRC = os.environ["ORACLE_MUTANT_SRC"]
+    _LIB_SERIAL = os.environ["ORACLE_MUTANT_LIB"]
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_lock = threading.Lock()
+_libs: dict = {}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2 -ffp-contract=off); returns the .so path."""
+    with _lock:
+        if force or not os.path.exists(_LIB_SERIAL) or os.path.getmtime(_LIB_SERIAL) < os.path.getmtime(_SRC):
+            tmp = _LIB_SERIAL + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                                   "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB_SERIAL)
+    return _LIB_SERIAL
+
+
+class _Params(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("g", C.c_double), ("h_min", C.c_double), ("dt_max", C.c_double),
+                ("cfl_mode", C.c_int), ("hydro_t", C.POINTER(C.c_double)), ("hydro_q", C.POINTER(C.c_double)),
+                ("hydro_n", C.c_int64)]
+
+
+def _lib():
+    if "serial" not in _libs:
+        lib = C.CDLL(build())
+        P = C.POINTER
+        d, i64 = C.c_double, C.c_int64
+        lib.orc_create.argtypes = [i64, P(d), i64, P(C.c_int32), P(d), P(d), P(C.c_uint8), P(_Params),
+                                   P(C.c_void_p)]
+        lib.orc_create.restype = C.c_int
+        lib.orc_destroy.argtypes = [C.c_void_p]
+        lib.orc_step.argtypes = [C.c_void_p, P(d), P(d), P(d), P(d), d, P(d)]
+        lib.orc_step.restype = d
+        lib.orc_run.argtypes = [C.c_void_p, P(d), P(d), P(d), P(d), d, i64, P(d)]
+        lib.orc_run.restype = i64
+        lib.orc_volume.argtypes = [C.c_void_p, P(d)]
+        lib.orc_volume.restype = d
+        lib.orc_next_dt.argtypes = [C.c_void_p, P(d), P(d), P(d), d]
+        lib.orc_next_dt.restype = d
+        lib.orc_hllc.argtypes = [d, d, d, d, d, d, d, P(d)]
+        lib.orc_wave_speeds.argtypes = [d, d, d, d, d, P(d), P(d)]
+        lib.orc_friction.argtypes = [d, d, d, d, d, P(d), P(d)]
+        lib.orc_hydrograph.argtypes = [P(_Params), d]
+        lib.orc_hydrograph.restype = d
+        lib.orc_n_edges.argtypes = [C.c_void_p]
+        lib.orc_n_edges.restype = i64
+        lib.orc_cell_area.argtypes = [C.c_void_p, P(d)]
+        lib.orc_edges.argtypes = [C.c_void_p, P(i64), P(i64), P(d), P(d), P(d)]
+        _libs["serial"] = lib
+    return _libs["serial"]
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+class Oracle:
+    """One mesh + one state, stepped on the CPU in FP64.
+
+    ``scenario`` is any object with the attributes of ``workloads.Scenario``
+    (xy, tri, z, manning, edge_tag, H, qx, qy, params).
+    """
+
+    def __init__(self, scenario, **overrides):
+        lib = _lib()
+        s = scenario
+        prm = dict(s.params)
+        prm.update(overrides)
+        self._hydro_t = np.ascontiguousarray(prm.get("hydro_t", np.zeros(0)), dtype=np.float64)
+        self._hydro_q = np.ascontiguousarray(prm.get("hydro_q", np.zeros(0)), dtype=np.float64)
+        self.params = _Params(prm.get("cfl", 0.9), prm.get("g", 9.81), prm.get("h_min", 1e-6),
+                              prm.get("dt_max", 1.0), int(prm.get("cfl_mode", 0)),
+                              _dp(self._hydro_t), _dp(self._hydro_q), len(self._hydro_t))
+        xy = np.ascontiguousarray(s.xy, dtype=np.float64)
+        tri = np.ascontiguousarray(s.tri, dtype=np.int32)
+        z = np.ascontiguousarray(s.z, dtype=np.float64)
+        man = np.ascontiguousarray(s.manning, dtype=np.float64)
+        tag = np.ascontiguousarray(s.edge_tag, dtype=np.uint8)
+        h = C.c_void_p()
+        rc = lib.orc_create(len(xy), _dp(xy), len(tri), tri.ctypes.data_as(C.POINTER(C.c_int32)), _dp(z), _dp(man),
+                            tag.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(self.params), C.byref(h))
+        if rc != 0:
+            raise OracleError(f"orc_create failed with code {rc}")
+        self._h = h
+        self.n_cells = len(tri)
+        self.z = z.copy()
+        self.H = np.array(s.H, dtype=np.float64, copy=True)
+        self.qx = np.array(s.qx if s.qx is not None else np.zeros(self.n_cells), dtype=np.float64, copy=True)
+        self.qy = np.array(s.qy if s.qy is not None else np.zeros(self.n_cells), dtype=np.float64, copy=True)
+        self.t = C.c_double(0.0)
+        self.bvol = C.c_double(0.0)
+        self.steps = 0
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib().orc_destroy(h)
+            self._h = None
+
+    def step(self, n: int = 1, t_end: float = math.inf) -> int:
+        lib = _lib()
+        k = lib.orc_run(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), C.byref(self.t), float(t_end), int(n),
+                        C.byref(self.bvol))
+        self.steps += k
+        return k
+
+    def run_until(self, t_end: float, max_steps: int = 10**9) -> int:
+        return self.step(max_steps, t_end)
+
+    def next_dt(self) -> float:
+        return _lib().orc_next_dt(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), self.t.value)
+
+    def volume(self) -> float:
+        return _lib().orc_volume(self._h, _dp(self.H))
+
+    @property
+    def time(self) -> float:
+        return self.t.value
+
+    @property
+    def boundary_volume(self) -> float:
+        return self.bvol.value
+
+    def area(self) -> np.ndarray:
+        a = np.empty(self.n_cells)
+        _lib().orc_cell_area(self._h, _dp(a))
+        return a
+
+    def edges(self):
+        lib = _lib()
+        ne = lib.orc_n_edges(self._h)
+        L = np.empty(ne, np.int64)
+        R = np.empty(ne, np.int64)
+        nx, ny, ln = np.empty(ne), np.empty(ne), np.empty(ne)
+        lib.orc_edges(self._h, L.ctypes.data_as(C.POINTER(C.c_int64)), R.ctypes.data_as(C.POINTER(C.c_int64)),
+                      _dp(nx), _dp(ny), _dp(ln))
+        return L, R, nx, ny, ln
+
+    def depth(self) -> np.ndarray:
+        return self.H - self.z
+
+
+def hllc(hL, uL, vL, hR, uR, vR, g=9.81):
+    """HLLC flux (F_h, F_n, F_t) in the edge frame, as the oracle computes it."""
+    out = (C.c_double * 3)()
+    _lib().orc_hllc(hL, uL, vL, hR, uR, vR, g, out)
+    return np.array(out[:])
+
+
+def wave_speeds(hL, uL, hR, uR, g=9.81):
+    """(S_L, S_R) wave-speed bounds the oracle's HLLC uses."""
+    a, b = C.c_double(), C.c_double()
+    _lib().orc_wave_speeds(hL, uL, hR, uR, g, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def friction(h, n, dt, qx, qy, g=9.81, h_min=1e-6):
+    """One split friction step on (qx, qy) with depth h frozen."""
+    a, b = C.c_double(qx), C.c_double(qy)
+    _lib().orc_friction(h, n, g, dt, h_min, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def hydrograph(t_pts, q_pts, t):
+    tt = np.ascontiguousarray(t_pts, dtype=np.float64)
+    qq = np.ascontiguousarray(q_pts, dtype=np.float64)
+    p = _Params(0.9, 9.81, 1e-6, 1.0, 0, _dp(tt), _dp(qq), len(tt))
+    return _lib().orc_hydrograph(C.byref(p), float(t))

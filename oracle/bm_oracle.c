@@ -1,0 +1,493 @@
+/*
+ * bm_oracle.c -- plain, serial, FP64 CPU oracle for the explicit finite-volume
+ * time step of the 2D shallow-water equations of BASEMENT v3 (arXiv 2102.12862,
+ * Section "Numerical solution", subsection "Hydrodynamics").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, import or call
+ * this file; only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark do.  It shares no code, header, table or helper with the CUDA path.
+ *
+ * It is written as an EDGE loop (each edge visited once, in the caller's cell
+ * numbering), deliberately unlike the tiled GPU kernel, and is compiled with
+ * -O2 -ffp-contract=off so every operation rounds once, in source order.
+ *
+ * What one step computes (all in the unknowns of Eq. 1 / Eq. 10: H, q_x, q_y):
+ *   0. dt from Eq. 21 on U^n (rho_ij = 4|Omega_i|/(3 l_ij), lambda = |u.n| + sqrt(g h)),
+ *      clipped by dt_max (parameter list of the hydrodynamic module) and t_end.
+ *   1. per edge: modified states (hydrostatic reconstruction on max(z_L, z_R),
+ *      the bed treatment named in the "Hydrodynamics" numerics subsection), HLLC
+ *      flux (Toro 2001 ch. 10, named in the same subsection) in the edge frame,
+ *      pre-balanced pressure correction 1/2 g h*^2 of each side.
+ *   2. boundary edges: wall (mirror), transmissive (zero gradient), discharge
+ *      inflow (Section "Boundary conditions": standard inflow / wall).
+ *   3. conservative update, Eq. 12.
+ *   4. Manning friction (Eq. 2, Table 1) split off and integrated with a
+ *      two-stage semi-implicit Runge-Kutta (Heun) step.
+ *   5. q := 0 on cells whose depth is below the minimum water depth.
+ *
+ * Readings where the paper is silent are the same as in the design notes:
+ * modified-state form, Toro wave speeds, h_min, friction stages, rho_ij, the
+ * inflow distribution, wall mass flux exactly zero.
+ *
+ * Pinned by tests/test_oracle_*.py (closed forms, invariants, paper values).
+ * The Q-inflow distribution and the threshold heuristics are "parity unpinned"
+ * beyond mass balance.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+
+/* parameters of one run (hydrodynamic module parameter list) */
+typedef struct {
+  double cfl;      /* Eq. 21 coefficient, default 0.9 */
+  double g;        /* gravity, 9.81 */
+  double h_min;    /* minimum water depth */
+  double dt_max;   /* upper limit of the time step */
+  int cfl_mode;    /* 0: Eq. 21 literally; 1: dt <= |Omega_i| / sum_j l_ij lambda_ij */
+  const double *hydro_t, *hydro_q; /* inflow hydrograph Q(t), piecewise linear */
+  int64_t hydro_n;
+} orc_params;
+
+typedef struct {
+  int64_t n_cells, n_edges;
+  /* per edge: left cell, right cell (>= 0) or boundary code -1 - tag; unit
+   * normal pointing from left to right; length. left < right for interior edges. */
+  int64_t *eL, *eR;
+  double *nx, *ny, *len;
+  /* per cell */
+  double *area, *z, *man;
+  int64_t *cedge;        /* 3 per cell: edge index of local edge k */
+  /* per edge, filled each step: flux contribution to the left and to the right
+   * cell, already multiplied by the edge length */
+  double *cL, *cR;       /* 3 per edge */
+  double *qin;           /* per edge: imposed unit discharge on inflow edges */
+  double inflow_len;     /* total length of the inflow boundary */
+  orc_params p;
+  double *ht, *hq;
+} orc_mesh;
+
+/* ---------- mesh topology (independent, plain) ---------- */
+
+typedef struct { int64_t a, b, t; int k; } orc_half;
+
+static int cmp_half(const void* x, const void* y) {
+  const orc_half* u = (const orc_half*)x;
+  const orc_half* v = (const orc_half*)y;
+  if (u->a != v->a) return u->a < v->a ? -1 : 1;
+  if (u->b != v->b) return u->b < v->b ? -1 : 1;
+  if (u->t != v->t) return u->t < v->t ? -1 : 1;
+  return u->k - v->k;
+}
+
+void orc_destroy(orc_mesh* m) {
+  if (!m) return;
+  free(m->eL); free(m->eR); free(m->nx); free(m->ny); free(m->len);
+  free(m->area); free(m->z); free(m->man); free(m->cedge);
+  free(m->cL); free(m->cR); free(m->qin); free(m->ht); free(m->hq);
+  free(m);
+}
+
+/*
+ * Build the finite-volume mesh of Section "Domain discretization": cells are
+ * triangles, l_ij and n_ij (unit, pointing from i to j) per edge, |Omega_i| per
+ * cell.  Clockwise triangles are reoriented; their edge tags follow the edges.
+ * edge_tag[3t+k] tags edge (v_k, v_{k+1}) of the triangle as given: 0 wall,
+ * 1 transmissive, 2 inflow.  Returns ORC_EINVAL on any malformed input.
+ */
+int orc_create(int64_t n_nodes, const double* xy, int64_t n_tri, const int32_t* tri,
+               const double* z, const double* man, const uint8_t* edge_tag,
+               const orc_params* p, orc_mesh** out) {
+  *out = NULL;
+  if (n_tri <= 0 || n_nodes < 3) return ORC_EINVAL;
+  orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
+  if (!m) return ORC_ENOMEM;
+  m->n_cells = n_tri;
+  m->p = *p;
+  int64_t N = n_tri;
+  m->area = (double*)malloc(N * sizeof(double));
+  m->z = (double*)malloc(N * sizeof(double));
+  m->man = (double*)malloc(N * sizeof(double));
+  m->cedge = (int64_t*)malloc(3 * N * sizeof(int64_t));
+  int32_t* v = (int32_t*)malloc(3 * N * sizeof(int32_t));
+  uint8_t* tg = (uint8_t*)malloc(3 * N);
+  orc_half* hs = (orc_half*)malloc(3 * N * sizeof(orc_half));
+  if (!m->area || !m->z || !m->man || !m->cedge || !v || !tg || !hs) {
+    free(v); free(tg); free(hs); orc_destroy(m); return ORC_ENOMEM;
+  }
+  int rc = ORC_OK;
+  for (int64_t t = 0; t < N && rc == ORC_OK; ++t) {
+    int32_t a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= n_nodes || b >= n_nodes || c >= n_nodes) { rc = ORC_EINVAL; break; }
+    double ax = xy[2 * a], ay = xy[2 * a + 1], bx = xy[2 * b], by = xy[2 * b + 1];
+    double cx = xy[2 * c], cy = xy[2 * c + 1];
+    double twice = (bx - ax) * (cy - ay) - (cx - ax) * (by - ay);
+    if (twice < 0) { /* clockwise: swap v1, v2; edge k of the new triangle is old edge 2,1,0 */
+      v[3 * t] = a; v[3 * t + 1] = c; v[3 * t + 2] = b;
+      tg[3 * t] = edge_tag[3 * t + 2]; tg[3 * t + 1] = edge_tag[3 * t + 1]; tg[3 * t + 2] = edge_tag[3 * t];
+      twice = -twice;
+    } else {
+      v[3 * t] = a; v[3 * t + 1] = b; v[3 * t + 2] = c;
+      tg[3 * t] = edge_tag[3 * t]; tg[3 * t + 1] = edge_tag[3 * t + 1]; tg[3 * t + 2] = edge_tag[3 * t + 2];
+    }
+    if (!(twice > 0)) { rc = ORC_EINVAL; break; }
+    m->area[t] = 0.5 * twice;
+    m->z[t] = z[t];
+    m->man[t] = man[t];
+    if (!(man[t] >= 0) || !isfinite(z[t])) { rc = ORC_EINVAL; break; }
+    for (int k = 0; k < 3; ++k) {
+      int64_t p0 = v[3 * t + k], p1 = v[3 * t + (k + 1) % 3];
+      hs[3 * t + k].a = p0 < p1 ? p0 : p1;
+      hs[3 * t + k].b = p0 < p1 ? p1 : p0;
+      hs[3 * t + k].t = t;
+      hs[3 * t + k].k = k;
+    }
+  }
+  if (rc != ORC_OK) { free(v); free(tg); free(hs); orc_destroy(m); return rc; }
+  qsort(hs, 3 * N, sizeof(orc_half), cmp_half);
+  /* count edges */
+  int64_t ne = 0;
+  for (int64_t i = 0; i < 3 * N;) {
+    int64_t j = i + 1;
+    while (j < 3 * N && hs[j].a == hs[i].a && hs[j].b == hs[i].b) ++j;
+    if (j - i > 2) { rc = ORC_EINVAL; break; }
+    ++ne; i = j;
+  }
+  if (rc != ORC_OK) { free(v); free(tg); free(hs); orc_destroy(m); return rc; }
+  m->n_edges = ne;
+  m->eL = (int64_t*)malloc(ne * sizeof(int64_t));
+  m->eR = (int64_t*)malloc(ne * sizeof(int64_t));
+  m->nx = (double*)malloc(ne * sizeof(double));
+  m->ny = (double*)malloc(ne * sizeof(double));
+  m->len = (double*)malloc(ne * sizeof(double));
+  m->cL = (double*)malloc(3 * ne * sizeof(double));
+  m->cR = (double*)malloc(3 * ne * sizeof(double));
+  m->qin = (double*)calloc(ne, sizeof(double));
+  if (!m->eL || !m->eR || !m->nx || !m->ny || !m->len || !m->cL || !m->cR || !m->qin) {
+    free(v); free(tg); free(hs); orc_destroy(m); return ORC_ENOMEM;
+  }
+  int64_t e = 0;
+  m->inflow_len = 0;
+  for (int64_t i = 0; i < 3 * N; ++e) {
+    int64_t j = i + 1;
+    while (j < 3 * N && hs[j].a == hs[i].a && hs[j].b == hs[i].b) ++j;
+    /* the lower cell index is the left cell; the normal is computed from the left
+     * cell's counter-clockwise traversal of the edge: outward = (dy, -dx) / l */
+    int64_t tl = hs[i].t; int kl = hs[i].k;
+    int64_t p0 = v[3 * tl + kl], p1 = v[3 * tl + (kl + 1) % 3];
+    double dx = xy[2 * p1] - xy[2 * p0], dy = xy[2 * p1 + 1] - xy[2 * p0 + 1];
+    double l = sqrt(dx * dx + dy * dy);
+    m->eL[e] = tl;
+    m->nx[e] = dy / l;
+    m->ny[e] = -dx / l;
+    m->len[e] = l;
+    m->cedge[3 * tl + kl] = e;
+    if (j - i == 2) {
+      int64_t tr = hs[i + 1].t; int kr = hs[i + 1].k;
+      int64_t q0 = v[3 * tr + kr], q1 = v[3 * tr + (kr + 1) % 3];
+      if (!(q0 == p1 && q1 == p0)) { rc = ORC_EINVAL; } /* both traverse the edge the same way */
+      m->eR[e] = tr;
+      m->cedge[3 * tr + kr] = e;
+    } else {
+      uint8_t tag = tg[3 * tl + kl];
+      if (tag > 2) rc = ORC_EINVAL;
+      m->eR[e] = -1 - (int64_t)tag;
+      if (tag == 2) m->inflow_len += l;
+    }
+    i = j;
+  }
+  free(v); free(tg); free(hs);
+  if (rc != ORC_OK) { orc_destroy(m); return rc; }
+  if (p->hydro_n > 0) {
+    m->ht = (double*)malloc(p->hydro_n * sizeof(double));
+    m->hq = (double*)malloc(p->hydro_n * sizeof(double));
+    if (!m->ht || !m->hq) { orc_destroy(m); return ORC_ENOMEM; }
+    memcpy(m->ht, p->hydro_t, p->hydro_n * sizeof(double));
+    memcpy(m->hq, p->hydro_q, p->hydro_n * sizeof(double));
+    m->p.hydro_t = m->ht; m->p.hydro_q = m->hq;
+  }
+  *out = m;
+  return ORC_OK;
+}
+
+/* ---------- point-wise pieces (exported for the pins) ---------- */
+
+/* Q(t): piecewise linear through (hydro_t, hydro_q), constant beyond the ends; 0 if empty */
+double orc_hydrograph(const orc_params* p, double t) {
+  if (p->hydro_n <= 0) return 0.0;
+  if (t <= p->hydro_t[0]) return p->hydro_q[0];
+  for (int64_t i = 1; i < p->hydro_n; ++i) {
+    if (t <= p->hydro_t[i]) {
+      double w = (t - p->hydro_t[i - 1]) / (p->hydro_t[i] - p->hydro_t[i - 1]);
+      return p->hydro_q[i - 1] + w * (p->hydro_q[i] - p->hydro_q[i - 1]);
+    }
+  }
+  return p->hydro_q[p->hydro_n - 1];
+}
+
+/*
+ * HLLC flux of the 1D shallow-water Riemann problem in the edge frame (normal
+ * velocity un, tangential velocity ut passively carried by the contact wave),
+ * Toro 2001 ch. 10 as named in the "Hydrodynamics" numerics subsection.
+ * Wave speeds: two-rarefaction estimates for wet/wet, dry-front speeds if one
+ * side has zero depth.  Writes (F_h, F_n, F_t).
+ */
+/* Wave-speed bounds (S_L, S_R) of the HLL family: star values from the
+ * two-rarefaction approximation for a wet/wet problem, exact dry-front speeds if
+ * one side is dry.  They must bracket the exact Riemann waves. */
+void orc_wave_speeds(double hL, double uL, double hR, double uR, double g, double* SL, double* SR) {
+  double cL = sqrt(g * hL), cR = sqrt(g * hR);
+  if (hL <= 0) {
+    *SL = uR - 2 * cR; *SR = uR + cR;
+  } else if (hR <= 0) {
+    *SL = uL - cL; *SR = uL + 2 * cL;
+  } else {
+    double us = 0.5 * (uL + uR) + cL - cR;
+    double cs = 0.5 * (cL + cR) + 0.25 * (uL - uR);
+    *SL = fmin(uL - cL, us - cs);
+    *SR = fmax(uR + cR, us + cs);
+  }
+}
+
+void orc_hllc(double hL, double uL, double vL, double hR, double uR, double vR, double g,
+              double* F) {
+  if (hL <= 0 && hR <= 0) { F[0] = 0; F[1] = 0; F[2] = 0; return; }
+  double SL, SR;
+  orc_wave_speeds(hL, uL, hR, uR, g, &SL, &SR);
+  /* physical fluxes of the left and right state; the pressure 1/2 g h^2 is the
+   * same expression as the correction the caller subtracts */
+  double pL = 0.5 * g * hL * hL, pR = 0.5 * g * hR * hR;
+  double FL0 = hL * uL, FL1 = hL * uL * uL + pL, FL2 = hL * uL * vL;
+  double FR0 = hR * uR, FR1 = hR * uR * uR + pR, FR2 = hR * uR * vR;
+  if (SL >= 0) { F[0] = FL0; F[1] = FL1; F[2] = FL2; return; }
+  if (SR <= 0) { F[0] = FR0; F[1] = FR1; F[2] = FR2; return; }
+  /* HLL state-flux: F_L - S_L (F_R - F_L - S_R (U_R - U_L)) / (S_R - S_L) */
+  double d = SR - SL;
+  double H0 = FL0 - SL * ((FR0 - FL0) - SR * (hR - hL)) / d;
+  double H1 = FL1 - SL * ((FR1 - FL1) - SR * (hR * uR - hL * uL)) / d;
+  /* contact speed decides which tangential velocity is advected */
+  double Ss = (SL * hR * (uR - SR) - SR * hL * (uL - SL)) / (hR * (uR - SR) - hL * (uL - SL));
+  F[0] = H0;
+  F[1] = H1;
+  F[2] = H0 * (Ss >= 0 ? vL : vR);
+}
+
+/*
+ * Friction split step (Eq. 2 with Manning c_f, Table 1): dq/dt = -k(q) q with
+ * k(q) = g n^2 |q| / h^(7/3), h frozen.  Two semi-implicit (linearly implicit)
+ * Euler stages combined as Heun's RK2: q1 = q0/(1+dt k(q0)), q2 = q1/(1+dt k(q1)),
+ * q = (q0 + q2)/2.  Skipped when h <= h_min or n = 0.
+ */
+void orc_friction(double h, double n, double g, double dt, double h_min, double* qx, double* qy) {
+  if (!(h > h_min) || n == 0) return;
+  double c = g * n * n / pow(h, 7.0 / 3.0);
+  double q0x = *qx, q0y = *qy;
+  double k0 = c * sqrt(q0x * q0x + q0y * q0y);
+  double q1x = q0x / (1 + dt * k0), q1y = q0y / (1 + dt * k0);
+  double k1 = c * sqrt(q1x * q1x + q1y * q1y);
+  double q2x = q1x / (1 + dt * k1), q2y = q1y / (1 + dt * k1);
+  *qx = 0.5 * (q0x + q2x);
+  *qy = 0.5 * (q0y + q2y);
+}
+
+/* cell velocity of the unmodified state: q/h where h > h_min, else 0 */
+static void cell_velocity(const orc_mesh* m, const double* H, const double* qx, const double* qy,
+                          int64_t i, double* u, double* w) {
+  double h = H[i] - m->z[i];
+  if (h > m->p.h_min) { *u = qx[i] / h; *w = qy[i] / h; }
+  else { *u = 0; *w = 0; }
+}
+
+/* inflow: unit discharge per inflow edge at time t, conveyance-weighted */
+static void inflow_discharge(orc_mesh* m, const double* H, double t) {
+  double Q = orc_hydrograph(&m->p, t);
+  double W = 0;
+  for (int64_t e = 0; e < m->n_edges; ++e) {
+    if (m->eR[e] != -3) continue;
+    double h = H[m->eL[e]] - m->z[m->eL[e]];
+    double w = h > m->p.h_min ? m->len[e] * pow(h, 5.0 / 3.0) : 0.0;
+    W += w;
+  }
+  for (int64_t e = 0; e < m->n_edges; ++e) {
+    if (m->eR[e] != -3) { m->qin[e] = 0; continue; }
+    double h = H[m->eL[e]] - m->z[m->eL[e]];
+    if (W > 0) {
+      double w = h > m->p.h_min ? m->len[e] * pow(h, 5.0 / 3.0) : 0.0;
+      m->qin[e] = Q * w / (m->len[e] * W);
+    } else {
+      m->qin[e] = m->inflow_len > 0 ? Q / m->inflow_len : 0.0;
+    }
+  }
+}
+
+/* depth at an inflow edge: the cell depth or the critical depth of q_e, the larger */
+static double inflow_depth(double hc, double q, double g) {
+  double hcr = cbrt(q * q / g);
+  return hc > hcr ? hc : hcr;
+}
+
+/* Eq. 21: dt = CFL * min_i min_j rho_ij / lambda_ij on wet cells (or, cfl_mode 1,
+ * CFL * min_i |Omega_i| / sum_j l_ij lambda_ij); inflow edges add their own
+ * boundary wave speed.  Returns +inf if nothing constrains dt.  Requires qin. */
+double orc_cfl(const orc_mesh* m, const double* H, const double* qx, const double* qy) {
+  const double g = m->p.g;
+  double best = INFINITY;
+  for (int64_t i = 0; i < m->n_cells; ++i) {
+    double h = H[i] - m->z[i];
+    int wet = h > m->p.h_min;
+    double u = 0, w = 0, c = 0;
+    if (wet) { u = qx[i] / h; w = qy[i] / h; c = sqrt(g * h); }
+    double sum = 0;
+    for (int k = 0; k < 3; ++k) {
+      int64_t e = m->cedge[3 * i + k];
+      double sgn = (m->eL[e] == i) ? 1.0 : -1.0;
+      double nx = sgn * m->nx[e], ny = sgn * m->ny[e];
+      double lam = wet ? fabs(u * nx + w * ny) + c : 0.0;
+      if (m->eR[e] == -3 && m->qin[e] > 0) {
+        double hb = inflow_depth(h > 0 ? h : 0.0, m->qin[e], g);
+        double lb = m->qin[e] / hb + sqrt(g * hb);
+        if (m->p.cfl_mode == 0) {
+          double rho = 4.0 * m->area[i] / (3.0 * m->len[e]);
+          if (rho / lb < best) best = rho / lb;
+        } else {
+          double r = m->area[i] / (m->len[e] * lb);
+          if (r < best) best = r;
+        }
+      }
+      if (lam > 0) {
+        double rho = 4.0 * m->area[i] / (3.0 * m->len[e]);
+        if (m->p.cfl_mode == 0 && rho / lam < best) best = rho / lam;
+      }
+      sum += m->len[e] * lam;
+    }
+    if (m->p.cfl_mode == 1 && sum > 0) {
+      double r = m->area[i] / sum;
+      if (r < best) best = r;
+    }
+  }
+  return best;
+}
+
+/*
+ * One explicit step from (t, H, qx, qy) to t + dt, in place.  t_end clips dt
+ * (pass +inf for none).  bvol accumulates the net volume that entered through
+ * the boundary (positive = inflow).  Returns dt (0 if t >= t_end).
+ */
+double orc_step(orc_mesh* m, double* H, double* qx, double* qy, double* t, double t_end,
+                double* bvol) {
+  const double g = m->p.g, hmin = m->p.h_min;
+  if (!(*t < t_end)) return 0.0;
+  /* 0. time step from U^n (Eq. 21) */
+  inflow_discharge(m, H, *t);
+  double mcfl = orc_cfl(m, H, qx, qy);
+  double dt = isinf(mcfl) ? m->p.dt_max : m->p.cfl * mcfl;
+  if (dt > m->p.dt_max) dt = m->p.dt_max;
+  int clipped = 0;
+  if (dt >= t_end - *t) { dt = t_end - *t; clipped = 1; }
+  /* 1.-2. edge fluxes */
+  double bflux = 0; /* sum over boundary edges of l * F_h (outward) */
+  for (int64_t e = 0; e < m->n_edges; ++e) {
+    int64_t L = m->eL[e], R = m->eR[e];
+    double nx = m->nx[e], ny = m->ny[e], l = m->len[e];
+    double uL, vL; cell_velocity(m, H, qx, qy, L, &uL, &vL);
+    double unL = uL * nx + vL * ny, utL = -uL * ny + vL * nx;
+    double F[3];
+    if (R >= 0) {
+      double zs = fmax(m->z[L], m->z[R]);
+      double hLs = fmax(0.0, H[L] - zs), hRs = fmax(0.0, H[R] - zs);
+      double uR, vR; cell_velocity(m, H, qx, qy, R, &uR, &vR);
+      double unR = uR * nx + vR * ny, utR = -uR * ny + vR * nx;
+      orc_hllc(hLs, unL, utL, hRs, unR, utR, g, F);
+      double pL = 0.5 * g * hLs * hLs, pR = 0.5 * g * hRs * hRs;
+      double GL = F[1] - pL, GR = F[1] - pR;
+      m->cL[3 * e] = l * F[0];
+      m->cL[3 * e + 1] = l * (GL * nx - F[2] * ny);
+      m->cL[3 * e + 2] = l * (GL * ny + F[2] * nx);
+      m->cR[3 * e] = -l * F[0];
+      m->cR[3 * e + 1] = -l * (GR * nx - F[2] * ny);
+      m->cR[3 * e + 2] = -l * (GR * ny + F[2] * nx);
+    } else {
+      double hs = fmax(0.0, H[L] - m->z[L]);
+      double p = 0.5 * g * hs * hs;
+      double Fh, Gn, Ft;
+      if (R == -1) { /* wall: mirrored normal velocity, impermeable */
+        orc_hllc(hs, unL, utL, hs, -unL, utL, g, F);
+        Fh = 0; Gn = F[1] - p; Ft = 0;
+      } else if (R == -2) { /* transmissive: the outside state equals the inside state */
+        orc_hllc(hs, unL, utL, hs, unL, utL, g, F);
+        Fh = F[0]; Gn = F[1] - p; Ft = F[2];
+      } else { /* inflow: imposed unit discharge q_e entering along -n */
+        double q = m->qin[e];
+        if (q > 0) {
+          double hb = inflow_depth(hs, q, g);
+          Fh = -q; Gn = q * q / hb + 0.5 * g * hb * hb - p; Ft = 0;
+        } else { Fh = 0; Gn = 0; Ft = 0; }
+      }
+      m->cL[3 * e] = l * Fh;
+      m->cL[3 * e + 1] = l * (Gn * nx - Ft * ny);
+      m->cL[3 * e + 2] = l * (Gn * ny + Ft * nx);
+      bflux += l * Fh;
+    }
+  }
+  /* 3.-5. cell update (Eq. 12), friction, dry clean-up */
+  for (int64_t i = 0; i < m->n_cells; ++i) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int k = 0; k < 3; ++k) {
+      int64_t e = m->cedge[3 * i + k];
+      const double* c = (m->eL[e] == i) ? &m->cL[3 * e] : &m->cR[3 * e];
+      s0 += c[0]; s1 += c[1]; s2 += c[2];
+    }
+    double r = dt / m->area[i];
+    double Hn = H[i] - r * s0;
+    double ux = qx[i] - r * s1;
+    double uy = qy[i] - r * s2;
+    double h = Hn - m->z[i];
+    orc_friction(h, m->man[i], g, dt, hmin, &ux, &uy);
+    if (!(h > hmin)) { ux = 0; uy = 0; }
+    H[i] = Hn; qx[i] = ux; qy[i] = uy;
+  }
+  *bvol += -dt * bflux;
+  *t = clipped ? t_end : *t + dt;
+  return dt;
+}
+
+/* run up to n_steps steps, stopping early at t_end; returns the number taken */
+int64_t orc_run(orc_mesh* m, double* H, double* qx, double* qy, double* t, double t_end,
+                int64_t n_steps, double* bvol) {
+  int64_t s = 0;
+  for (; s < n_steps; ++s) {
+    if (!(*t < t_end)) break;
+    orc_step(m, H, qx, qy, t, t_end, bvol);
+  }
+  return s;
+}
+
+/* V = sum_i |Omega_i| (H_i - z_i), fixed order */
+double orc_volume(const orc_mesh* m, const double* H) {
+  double v = 0;
+  for (int64_t i = 0; i < m->n_cells; ++i) v += m->area[i] * (H[i] - m->z[i]);
+  return v;
+}
+
+/* next dt that orc_step would take from this state (Eq. 21 with dt_max), no clipping */
+double orc_next_dt(orc_mesh* m, const double* H, const double* qx, const double* qy, double t) {
+  inflow_discharge(m, H, t);
+  double mcfl = orc_cfl(m, H, qx, qy);
+  double dt = isinf(mcfl) ? m->p.dt_max : m->p.cfl * mcfl;
+  return dt > m->p.dt_max ? m->p.dt_max : dt;
+}
+
+/* accessors for tests */
+int64_t orc_n_edges(const orc_mesh* m) { return m->n_edges; }
+void orc_cell_area(const orc_mesh* m, double* out) { memcpy(out, m->area, m->n_cells * sizeof(double)); }
+void orc_edges(const orc_mesh* m, int64_t* L, int64_t* R, double* nx, double* ny, double* len) {
+  memcpy(L, m->eL, m->n_edges * sizeof(int64_t));
+  memcpy(R, m->eR, m->n_edges * sizeof(int64_t));
+  memcpy(nx, m->nx, m->n_edges * sizeof(double));
+  memcpy(ny, m->ny, m->n_edges * sizeof(double));
+  memcpy(len, m->len, m->n_edges * sizeof(double));
+}

@@ -1,0 +1,54 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that the pins catch
+each one: a pin suite that passes a mutated oracle would not be pinning anything.
+
+Each mutant is a one-token change of oracle/bm_oracle.c compiled into a private
+library; the pin tests run against it in a subprocess and must fail.  The
+discharge-inflow boundary depth is not in the list: it is "parity unpinned"
+(only mass balance and agreement with the CUDA path check it).
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "bm_oracle.c")
+
+# (name, original text, mutated text); every original occurs exactly once
+MUTANTS = [
+    ("pressure_correction_sign", "double GL = F[1] - pL, GR = F[1] - pR;",
+     "double GL = F[1] + pL, GR = F[1] - pR;"),
+    ("modified_state_min_bed", "double zs = fmax(m->z[L], m->z[R]);", "double zs = fmin(m->z[L], m->z[R]);"),
+    ("contact_picks_wrong_side", "F[2] = H0 * (Ss >= 0 ? vL : vR);", "F[2] = H0 * (Ss >= 0 ? vR : vL);"),
+    ("wave_speed_sign", "double us = 0.5 * (uL + uR) + cL - cR;", "double us = 0.5 * (uL + uR) - cL + cR;"),
+    ("dry_front_speed", "*SL = uL - cL; *SR = uL + 2 * cL;", "*SL = uL - cL; *SR = uL + cL;"),
+    ("wall_not_mirrored", "orc_hllc(hs, unL, utL, hs, -unL, utL, g, F);",
+     "orc_hllc(hs, unL, utL, hs, unL, utL, g, F);"),
+    ("rho_factor", "double rho = 4.0 * m->area[i] / (3.0 * m->len[e]);\n        if (m->p.cfl_mode == 0 && rho",
+     "double rho = 2.0 * m->area[i] / (3.0 * m->len[e]);\n        if (m->p.cfl_mode == 0 && rho"),
+    ("friction_stage_state", "double k1 = c * sqrt(q1x * q1x + q1y * q1y);",
+     "double k1 = c * sqrt(q0x * q0x + q0y * q0y);"),
+    ("friction_exponent", "double c = g * n * n / pow(h, 7.0 / 3.0);", "double c = g * n * n / pow(h, 4.0 / 3.0);"),
+    ("normal_transposed", "m->nx[e] = dy / l;\n    m->ny[e] = -dx / l;", "m->nx[e] = -dy / l;\n    m->ny[e] = dx / l;"),
+    ("tangent_rotation", "double unL = uL * nx + vL * ny, utL = -uL * ny + vL * nx;",
+     "double unL = uL * nx + vL * ny, utL = uL * ny + vL * nx;"),
+    ("update_sign", "double Hn = H[i] - r * s0;", "double Hn = H[i] + r * s0;"),
+    ("hll_state_jump", "double H0 = FL0 - SL * ((FR0 - FL0) - SR * (hR - hL)) / d;",
+     "double H0 = FL0 - SL * ((FR0 - FL0) - SR * (hL - hR)) / d;"),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,orig,mut", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(name, orig, mut, tmp_path):
+    src = open(SRC).read()
+    assert src.count(orig) == 1, f"mutation site for {name} not unique"
+    msrc = tmp_path / "bm_oracle_mutant.c"
+    msrc.write_text(src.replace(orig, mut))
+    env = dict(os.environ, ORACLE_MUTANT_SRC=str(msrc), ORACLE_MUTANT_LIB=str(tmp_path / "libmut.so"),
+               PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
