@@ -1,0 +1,165 @@
+/*
+ * bm.h -- C ABI of the B300-native explicit finite-volume shallow-water step.
+ *
+ * The method is the hydrodynamic module of BASEMENT v3 (arXiv 2102.12862):
+ * unknowns U = (H, q_x, q_y) per triangle (Eq. 1, Eq. 10), the explicit update of
+ * Eq. 12 with an HLLC edge flux and the modified-state bed treatment (Section
+ * "Numerical solution", subsection "Hydrodynamics"), Manning friction (Eq. 2,
+ * Table 1) integrated after splitting, and the time step of Eq. 21.
+ *
+ * Conventions for every entry point:
+ *  - Returns a bm_status; BM_OK is 0.  On failure bm_last_error() returns a
+ *    thread-local message.  No C++ exception crosses the ABI.
+ *  - Handles are opaque.  Input arrays are host pointers owned by the caller; the
+ *    library copies them before returning.  Output arrays are caller-allocated
+ *    host buffers.  All per-cell arrays are in the caller's triangle order (the
+ *    library renumbers cells internally along a Hilbert curve).
+ *  - Device work is ordered on the state's CUDA stream (bm_state_set_stream).
+ *  - Handles are not thread-safe; use one handle from one thread at a time.
+ */
+#ifndef BM_H
+#define BM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BM_OK = 0,
+  BM_EINVAL = 1,      /* invalid argument or malformed mesh */
+  BM_ENOMEM = 2,      /* host or device allocation failed, or admission budget exceeded */
+  BM_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
+  BM_ENONFINITE = 4,  /* the step produced a NaN or infinity */
+  BM_ENEGDEPTH = 5,   /* a depth fell below -h_min */
+  BM_ETIMEOUT = 6,    /* a bounded device wait gave up */
+  BM_EAGAIN = 7,      /* result not ready yet (bm_poll) */
+  BM_EBUSY = 8        /* resource in use */
+} bm_status;
+
+enum { BM_FP64 = 0, BM_FP32_BULK = 1 };
+enum { BM_TAG_WALL = 0, BM_TAG_TRANSMISSIVE = 1, BM_TAG_INFLOW = 2 };
+
+typedef struct bm_mesh bm_mesh;
+typedef struct bm_state bm_state;
+typedef struct bm_server bm_server;
+
+/*
+ * Run parameters: the hydrodynamic module's parameter list (CFL, minimum water
+ * depth, upper limit of the time step) plus the discharge hydrograph of the
+ * standard inflow boundary.
+ *   cfl       Eq. 21 coefficient, in (0, 1]; default 0.9.
+ *   g         gravity [m/s^2]; default 9.81.
+ *   h_min     minimum water depth [m]: below it a cell is dry (velocity 0,
+ *             excluded from Eq. 21, q set to 0 after the step); default 1e-6.
+ *   dt_max    upper limit of the time step [s]; default 1.
+ *   precision BM_FP64 (every array and operation in FP64) or BM_FP32_BULK
+ *             (state, bed and geometry as FP32 offsets from an FP64 datum;
+ *             thresholds and mass accumulators in FP64).
+ *   cfl_mode  0: Eq. 21 as printed (rho_ij = 4|Omega_i|/(3 l_ij));
+ *             1: dt <= CFL |Omega_i| / sum_j l_ij lambda_ij (positivity bound).
+ *   datum     FP32_BULK only: FP64 reference elevation; NaN = min(z_bed).
+ *   hydro_t, hydro_q, hydro_n  Q(t) [m^3/s] of the inflow boundary, piecewise
+ *             linear in t, constant outside; copied; hydro_n = 0 means Q = 0.
+ *             hydro_t must be strictly increasing and hydro_q >= 0.
+ */
+typedef struct {
+  double cfl;
+  double g;
+  double h_min;
+  double dt_max;
+  int32_t precision;
+  int32_t cfl_mode;
+  double datum;
+  const double* hydro_t;
+  const double* hydro_q;
+  int64_t hydro_n;
+} bm_params;
+
+/* Fill *p with the defaults listed above. */
+void bm_params_default(bm_params* p);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char* bm_last_error(void);
+
+/*
+ * Build a finite-volume mesh (Section "Domain discretization": conforming
+ * triangulation, edge lengths l_ij, unit normals n_ij, cell areas |Omega_i|).
+ *   xy        2*n_nodes doubles, node coordinates (x0, y0, x1, y1, ...).
+ *   tri       3*n_tri node indices; clockwise triangles are reoriented.
+ *   z_bed     n_tri bed elevations (one per cell).
+ *   manning_n n_tri Manning coefficients n >= 0 (Table 1); 0 = frictionless.
+ *   edge_tag  3*n_tri tags; tag[3t+k] applies to the edge (tri[3t+k],
+ *             tri[3t+(k+1)%3]) when it is on the boundary: 0 wall, 1 transmissive
+ *             (zero gradient), 2 discharge inflow.  Ignored on interior edges.
+ * Errors: BM_EINVAL for n_tri < 1, indices out of range, area <= 0, an edge
+ * shared by more than two triangles or traversed twice in one direction, a tag
+ * outside {0,1,2} on a boundary edge, n < 0 or a non-finite input.
+ * *out receives the handle (NULL on failure); free with bm_mesh_destroy.
+ */
+bm_status bm_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
+                         const double* z_bed, const double* manning_n, const uint8_t* edge_tag,
+                         bm_mesh** out);
+
+/* Sizes of a mesh: cells, edges, boundary edges, inflow edges, tiles (NULL pointers skipped). */
+bm_status bm_mesh_info(const bm_mesh* m, int64_t* n_cells, int64_t* n_edges, int64_t* n_boundary,
+                       int64_t* n_inflow, int64_t* n_tiles);
+void bm_mesh_destroy(bm_mesh* m);
+
+/*
+ * Create a device-resident state on a mesh (Section "Initial conditions",
+ * region-defined: free-surface elevation H and discharge q per cell).
+ *   H, qx, qy  n_tri doubles each; qx/qy may be NULL for zeros.  H < z_bed is
+ *              rejected (a dry cell is H = z_bed).  The time starts at 0.
+ * The mesh must outlive the state.  Allocates device memory.
+ */
+bm_status bm_state_init(const bm_mesh* m, const bm_params* p, const double* H, const double* qx,
+                        const double* qy, bm_state** out);
+void bm_state_destroy(bm_state* s);
+
+/* Order all later device work of this state on `cuda_stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  Until this is called the state uses a private
+ * non-blocking stream.  Waits for work already queued on the previous stream. */
+bm_status bm_state_set_stream(bm_state* s, void* cuda_stream);
+
+/* Take n_steps explicit steps (dt from Eq. 21 each step, dt_max applied).  Blocks
+ * until done; returns BM_ENONFINITE / BM_ENEGDEPTH if the device flagged it. */
+bm_status bm_step(bm_state* s, int64_t n_steps);
+
+/* Enqueue n_steps steps on the state's stream and return at once (no status check). */
+bm_status bm_step_async(bm_state* s, int64_t n_steps);
+
+/* Wait for the state's stream and report the device status (as bm_step). */
+bm_status bm_sync(bm_state* s);
+
+/* Step until t == t_end exactly (the last dt is clipped to t_end - t). */
+bm_status bm_run_until(bm_state* s, double t_end);
+
+/* Replace the state and time (checkpoint resume); arrays as in bm_state_init. */
+bm_status bm_state_upload(bm_state* s, const double* H, const double* qx, const double* qy, double t);
+
+/* Copy the state to host arrays (caller order); any pointer may be NULL. */
+bm_status bm_state_download(bm_state* s, double* H, double* qx, double* qy, double* t);
+
+/*
+ * Scalars of the state: time, the dt the next step will take, steps taken,
+ * water volume V = sum |Omega_i| (H_i - z_i) (FP64, fixed summation order), and
+ * the net volume that entered through the boundary since init/upload.
+ */
+bm_status bm_state_stats(bm_state* s, double* t, double* dt_next, int64_t* steps, double* volume,
+                         double* boundary_volume);
+
+/*
+ * Diagnostic timing: take n_steps steps as plain kernel launches (no graph) with a
+ * CUDA event pair around every launch of the step kernel on the state's stream.
+ * *step_kernel_ms receives the summed duration of the step-kernel launches and
+ * *total_ms the time from the first to the last event; either may be NULL.  The
+ * state advances exactly as bm_step would.
+ */
+bm_status bm_step_timed(bm_state* s, int64_t n_steps, double* step_kernel_ms, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BM_H */

@@ -1,0 +1,85 @@
+// bm_internal.h -- internal data structures shared by the host mesh preparation,
+// the C ABI and the CUDA kernels of the shallow-water step.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bm.h"
+
+namespace bm {
+
+// Cells are renumbered along a Hilbert curve and grouped in tiles of kTile
+// consecutive cells; each tile owns the list of every edge incident to one of
+// its cells, so one CTA evaluates each of those edges once (edges shared with
+// another tile are evaluated by both; about 12 % of them on large meshes).
+constexpr int kTile = 256;
+constexpr int kMaxTileEdges = 3 * kTile;
+
+// Boundary codes stored in place of the right cell of an edge.
+constexpr int32_t kWall = -1;
+constexpr int32_t kTransmissive = -2;
+constexpr int32_t kInflow = -3;
+
+// Set the thread-local error message and return the status.
+bm_status fail(bm_status st, const std::string& msg);
+void clear_error();
+
+// Host-side mesh after preparation (new Hilbert numbering).
+struct HostMesh {
+  int64_t n_cells = 0, n_edges = 0, n_boundary = 0, n_inflow = 0;
+  int64_t n_tiles = 0;
+  // per cell, new numbering (padded to n_tiles * kTile with inert cells)
+  std::vector<int32_t> perm;        // new -> caller index (n_cells entries)
+  std::vector<double> z, man, inv_area, area;
+  std::vector<uint64_t> slots;      // 3 x 16 bit: (tile-local edge index << 1) | side (1 = right)
+  // per tile edge lists (concatenated; tile t owns [eoff[t], eoff[t+1]))
+  std::vector<int64_t> eoff;
+  std::vector<int32_t> eL, eR;      // left cell (new id), right cell (new id) or boundary code
+  std::vector<double> enx, eny, elen;
+  // inflow edges (one entry per inflow edge): cell (new id), length, normal
+  std::vector<int32_t> in_cell;
+  std::vector<double> in_len;
+  double inflow_len = 0;
+  double z_min = 0;
+};
+
+bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
+                       const double* z, const double* man, const uint8_t* tag, HostMesh* out);
+
+// Device-side control block of one state (one instance).
+struct Ctl {
+  double t;        // current time t^n
+  double dt;       // dt^n, the step the next launch takes
+  double t_end;    // run_until target (+inf for bm_step)
+  double bvol;     // net boundary volume since init (FP64)
+  double qscale;   // inflow: q_e = qscale * h_e^(5/3) when wsum > 0
+  double quni;     // inflow: q_e = quni on every inflow edge when wsum == 0
+  double Q;        // Q(t^n)
+  double pad0;
+  long long steps;
+  int parity;      // which state buffer holds U^n
+  int active;      // 0 once t reached t_end
+  int clipped;     // dt^n was clipped to t_end - t^n
+  int wpos;        // wsum > 0
+  int status;      // bit 0: non-finite value, bit 1: depth < -h_min
+  int pad1;
+};
+
+// Per-tile reduction slots written by the step kernel.
+struct TilePartial {
+  double rmax;   // max over the tile's cells of lambda/rho (Eq. 21) or sum l lambda / |Omega|
+  double bflux;  // sum over the tile's boundary edges of l * F_h (outward)
+};
+
+// Kernel parameters (plain values).
+struct Params {
+  double cfl, g, h_min, dt_max;
+  int cfl_mode;
+  int hydro_n;
+  const double* hydro_t;
+  const double* hydro_q;
+};
+
+}  // namespace bm

@@ -291,13 +291,16 @@ def ensemble_instance(k: int, base_seed: int = 5000, n_lo: float = 5e3, n_hi: fl
 
 
 def random_state(s: Scenario, seed: int, dry_frac: float = 0.2, vel: float = 2.0,
-                 depth=(0.01, 2.0)) -> Scenario:
-    """Random valid state on a scenario's mesh: random bed, a fraction of dry cells
-    (H = z), random depths and velocities elsewhere.  For one-step parity checks."""
+                 depth=(0.01, 2.0), keep_bed: bool = False) -> Scenario:
+    """Random valid state on a scenario's mesh: random bed (unless keep_bed), a
+    fraction of dry cells (H = z), random depths, velocities and Manning n
+    (unless keep_bed) elsewhere.  For short parity checks."""
     rng = np.random.default_rng(seed)
     n = s.n_cells
     out = s.copy()
-    out.z = rng.uniform(-1.0, 1.0, n)
+    zr = rng.uniform(-1.0, 1.0, n)
+    if not keep_bed:
+        out.z = zr
     h = rng.uniform(*depth, n)
     dry = rng.random(n) < dry_frac
     h[dry] = 0.0
@@ -306,7 +309,9 @@ def random_state(s: Scenario, seed: int, dry_frac: float = 0.2, vel: float = 2.0
     out.H = out.z + h
     out.qx = np.where(h > 0, h * rng.uniform(-vel, vel, n), 0.0)
     out.qy = np.where(h > 0, h * rng.uniform(-vel, vel, n), 0.0)
-    out.manning = rng.uniform(0.0, 0.06, n)
+    mr = rng.uniform(0.0, 0.06, n)
+    if not keep_bed:
+        out.manning = mr
     return out
 
 
