@@ -43,7 +43,9 @@ METRIC = "cell-updates/s"
 # Algorithmic cost per cell-update (one cell, one step); derivation in the design notes.
 BYTES_PER_CELL_UPDATE = {"fp64": 156.0, "fp32": 84.0}
 FP64_FLOPS_PER_CELL_UPDATE = 213.0
-FP64_PEAK_TFLOPS = 0.946     # DFMA probe on this machine's B300 (profiles/fp64_alu_probe.md)
+# FP64 peak: ncu's sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 296 DFMA/cycle
+# on this B300 (2 per SM), x 2 FLOP x the 2.032 GHz maximum SM clock.
+FP64_PEAK_TFLOPS = 296 * 2 * 2.032e9 / 1e12
 HBM_FALLBACK_GBS = 6400.0
 
 
@@ -267,13 +269,13 @@ def main():
         achieved = flops / kern_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "measured FP64 DFMA probe (no FP64 figure in MEASURED_PEAKS.json)",
-                "kernel": "step_fp64", "kernel_ms": kern_s * 1e3,
+                "peak_source": "ncu peak_sustained 296 DFMA/cycle x 2 x 2.032 GHz (no FP64 figure in MEASURED_PEAKS.json)",
+                "kernel": "step_batch<double,true>", "kernel_ms": kern_s * 1e3,
                 "hbm": {"achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
                         "algorithmic_bytes_per_launch": bytes_launch}}
     else:
         roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
-                "traffic": traffic, "kernel": "step_fp32", "kernel_ms": kern_s * 1e3,
+                "traffic": traffic, "kernel": "step_batch<float,false>", "kernel_ms": kern_s * 1e3,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
 
     # end to end through the C ABI with pinned host buffers: upload, E steps, download

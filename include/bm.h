@@ -159,6 +159,95 @@ bm_status bm_state_stats(bm_state* s, double* t, double* dt_next, int64_t* steps
  */
 bm_status bm_step_timed(bm_state* s, int64_t n_steps, double* step_kernel_ms, double* total_ms);
 
+/*
+ * Launch shape of the state's step kernel: ctas_per_sm = 0 launches one CTA per
+ * 256-cell tile; k > 0 launches k CTAs per SM that loop over the tiles
+ * (persistent).  Results do not depend on it.  Chosen by the autotuner
+ * (paper_2102_12862_b300.autotune) or by hand.
+ */
+bm_status bm_state_set_launch(bm_state* s, int ctas_per_sm);
+
+/*
+ * Autotuner: time steps_per_trial steps for each launch shape (one CTA per tile,
+ * and 1, 2, 3, 4, 6, 8 persistent CTAs per SM), undo the trial steps (the state is
+ * snapshotted in device memory and restored), keep the fastest shape and report it
+ * and its time per step.  Allocates a temporary device copy of the state.
+ */
+bm_status bm_state_autotune(bm_state* s, int steps_per_trial, int* best_ctas_per_sm, double* ms_per_step);
+
+/*
+ * Batches: many independent states (uneven meshes, same precision) stepped by ONE
+ * kernel launch per step through a packed (member, tile) work list; each member
+ * keeps its own dt, time and status.  The member handles stay valid and owned by
+ * the caller; while they are in a batch, step them only through the batch (their
+ * stats / download may be read after bm_batch_sync).  Creating a batch allocates a
+ * little device memory (descriptors, work list); the members' data is not copied.
+ */
+typedef struct bm_batch bm_batch;
+bm_status bm_batch_create(bm_state* const* states, int32_t n_states, bm_batch** out);
+void bm_batch_destroy(bm_batch* b);
+bm_status bm_batch_info(const bm_batch* b, int32_t* n_members, int64_t* n_cells, int64_t* n_tiles);
+/* Order the batch's launches on a stream (NULL = the legacy default stream). */
+bm_status bm_batch_set_stream(bm_batch* b, void* cuda_stream);
+/* Launch shape, as bm_state_set_launch; the autotuner as bm_state_autotune. */
+bm_status bm_batch_set_launch(bm_batch* b, int ctas_per_sm);
+bm_status bm_batch_autotune(bm_batch* b, int steps_per_trial, int* best_ctas_per_sm, double* ms_per_step);
+/* Every member takes n_steps steps with its own dt (Eq. 21); blocks; returns the
+ * first member's BM_ENONFINITE / BM_ENEGDEPTH if any. */
+bm_status bm_batch_step(bm_batch* b, int64_t n_steps);
+bm_status bm_batch_step_async(bm_batch* b, int64_t n_steps);
+bm_status bm_batch_sync(bm_batch* b);
+/* Member k runs until exactly t_end[k] (n_states finite values); finished members
+ * idle while the others continue. */
+bm_status bm_batch_run_until(bm_batch* b, const double* t_end);
+
+/*
+ * Request server (continuous batching).  Runs are submitted at any time from any
+ * thread; a worker thread admits them while the sum of their device footprints
+ * (state arrays, not the mesh) fits hbm_budget_bytes and at most max_slots are
+ * resident, steps every resident run together (one launch per step, each run with
+ * its own dt; a run stops exactly at its t_end), copies finished runs out, frees
+ * their memory and admits waiting runs.  A run's result is the same as that of
+ * bm_state_init + bm_run_until(t_end) on its own, whatever else is running.
+ *   hbm_budget_bytes  0 = 80 % of the free device memory at creation.
+ *   max_slots         0 = no limit.
+ *   precision         every run of a server uses this precision.
+ *   steps_per_round   steps between the worker's admissions / completion checks.
+ *   ctas_per_sm       launch shape of the batched step (bm_state_set_launch).
+ * Meshes are owned by the caller and must outlive the runs that use them.
+ */
+typedef struct {
+  uint64_t hbm_budget_bytes;
+  int32_t max_slots;
+  int32_t precision;
+  int32_t steps_per_round;
+  int32_t ctas_per_sm;
+} bm_server_opts;
+
+void bm_server_opts_default(bm_server_opts* o);
+bm_status bm_server_create(const bm_server_opts* opts, bm_server** out);
+/* Stops the worker; runs not finished yet complete with BM_EBUSY. */
+void bm_server_destroy(bm_server* sv);
+/*
+ * Submit a run: mesh, parameters (copied; precision must be the server's), initial
+ * H, qx, qy (n_cells doubles each, copied; qx/qy may be NULL) and the end time
+ * t_end > 0 (the run starts at t = 0).  Non-blocking; *ticket identifies the run.
+ * BM_ENOMEM if the run alone exceeds the budget; BM_EINVAL for bad arguments.
+ */
+bm_status bm_submit(bm_server* sv, const bm_mesh* mesh, const bm_params* p, const double* H, const double* qx,
+                    const double* qy, double t_end, uint64_t* ticket);
+/*
+ * BM_EAGAIN while the run is queued or running.  When finished: copies the final
+ * state (caller order; NULL pointers skipped) and the time from submission to
+ * completion, forgets the ticket and returns BM_OK, or the run's failure status.
+ */
+bm_status bm_poll(bm_server* sv, uint64_t ticket, double* H, double* qx, double* qy, double* latency_s);
+/* Block until the run has finished (or timeout_s elapsed: BM_ETIMEOUT); then bm_poll. */
+bm_status bm_server_wait(bm_server* sv, uint64_t ticket, double timeout_s);
+/* Queued, running and completed runs, cell-updates done, device bytes admitted. */
+bm_status bm_server_stats(bm_server* sv, int64_t* queued, int64_t* running, int64_t* completed,
+                          double* cell_updates, double* resident_bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,11 @@ class BMError(RuntimeError):
         self.status = status
 
 
+class bm_server_opts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_slots", C.c_int32), ("precision", C.c_int32),
+                ("steps_per_round", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
 class bm_params(C.Structure):
     _fields_ = [("cfl", C.c_double), ("g", C.c_double), ("h_min", C.c_double), ("dt_max", C.c_double),
                 ("precision", C.c_int32), ("cfl_mode", C.c_int32), ("datum", C.c_double),
@@ -56,6 +61,25 @@ SIGNATURES = {
     "bm_state_download": (C.c_int, [_vp, _P(_d), _P(_d), _P(_d), _P(_d)]),
     "bm_state_stats": (C.c_int, [_vp, _P(_d), _P(_d), _P(_i64), _P(_d), _P(_d)]),
     "bm_step_timed": (C.c_int, [_vp, _i64, _P(_d), _P(_d)]),
+    "bm_state_set_launch": (C.c_int, [_vp, C.c_int]),
+    "bm_batch_create": (C.c_int, [_P(_vp), C.c_int32, _P(_vp)]),
+    "bm_batch_destroy": (None, [_vp]),
+    "bm_batch_info": (C.c_int, [_vp, _P(C.c_int32), _P(_i64), _P(_i64)]),
+    "bm_batch_set_stream": (C.c_int, [_vp, _vp]),
+    "bm_batch_set_launch": (C.c_int, [_vp, C.c_int]),
+    "bm_batch_step": (C.c_int, [_vp, _i64]),
+    "bm_batch_step_async": (C.c_int, [_vp, _i64]),
+    "bm_batch_sync": (C.c_int, [_vp]),
+    "bm_batch_run_until": (C.c_int, [_vp, _P(_d)]),
+    "bm_state_autotune": (C.c_int, [_vp, C.c_int, _P(C.c_int), _P(_d)]),
+    "bm_batch_autotune": (C.c_int, [_vp, C.c_int, _P(C.c_int), _P(_d)]),
+    "bm_server_opts_default": (None, [_P(bm_server_opts)]),
+    "bm_server_create": (C.c_int, [_P(bm_server_opts), _P(_vp)]),
+    "bm_server_destroy": (None, [_vp]),
+    "bm_submit": (C.c_int, [_vp, _vp, _P(bm_params), _P(_d), _P(_d), _P(_d), _d, _P(C.c_uint64)]),
+    "bm_poll": (C.c_int, [_vp, C.c_uint64, _P(_d), _P(_d), _P(_d), _P(_d)]),
+    "bm_server_wait": (C.c_int, [_vp, C.c_uint64, _d]),
+    "bm_server_stats": (C.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_d), _P(_d)]),
 }
 
 
@@ -201,6 +225,65 @@ def bm_step_timed(state: int, n_steps: int) -> tuple[float, float]:
     return k.value, t.value
 
 
+def bm_state_set_launch(state: int, ctas_per_sm: int):
+    _check(load_library().bm_state_set_launch(state, int(ctas_per_sm)))
+
+
+def bm_state_autotune(state: int, steps_per_trial: int = 20) -> tuple[int, float]:
+    best, ms = C.c_int(), _d()
+    _check(load_library().bm_state_autotune(state, int(steps_per_trial), C.byref(best), C.byref(ms)))
+    return best.value, ms.value
+
+
+def bm_batch_autotune(batch: int, steps_per_trial: int = 10) -> tuple[int, float]:
+    best, ms = C.c_int(), _d()
+    _check(load_library().bm_batch_autotune(batch, int(steps_per_trial), C.byref(best), C.byref(ms)))
+    return best.value, ms.value
+
+
+def bm_batch_create(states) -> int:
+    arr = (_vp * len(states))(*[s.handle if hasattr(s, "handle") else s for s in states])
+    out = _vp()
+    _check(load_library().bm_batch_create(arr, len(states), C.byref(out)))
+    return out.value
+
+
+def bm_batch_destroy(batch: int):
+    if batch:
+        load_library().bm_batch_destroy(batch)
+
+
+def bm_batch_info(batch: int) -> dict:
+    m, c, t = C.c_int32(), _i64(), _i64()
+    _check(load_library().bm_batch_info(batch, C.byref(m), C.byref(c), C.byref(t)))
+    return {"n_members": m.value, "n_cells": c.value, "n_tiles": t.value}
+
+
+def bm_batch_set_stream(batch: int, stream_ptr: int):
+    _check(load_library().bm_batch_set_stream(batch, stream_ptr or None))
+
+
+def bm_batch_set_launch(batch: int, ctas_per_sm: int):
+    _check(load_library().bm_batch_set_launch(batch, int(ctas_per_sm)))
+
+
+def bm_batch_step(batch: int, n_steps: int):
+    _check(load_library().bm_batch_step(batch, int(n_steps)))
+
+
+def bm_batch_step_async(batch: int, n_steps: int):
+    _check(load_library().bm_batch_step_async(batch, int(n_steps)))
+
+
+def bm_batch_sync(batch: int):
+    _check(load_library().bm_batch_sync(batch))
+
+
+def bm_batch_run_until(batch: int, t_end):
+    te = _f64(np.atleast_1d(t_end))
+    _check(load_library().bm_batch_run_until(batch, _dp(te)))
+
+
 # ---------------------------------------------------------------- small owning wrappers
 
 class Mesh:
@@ -267,9 +350,153 @@ class State:
     def set_stream(self, stream_ptr: int):
         bm_state_set_stream(self.handle, stream_ptr)
 
+    def set_launch(self, ctas_per_sm: int):
+        bm_state_set_launch(self.handle, ctas_per_sm)
+
+    def autotune(self, steps_per_trial: int = 20) -> tuple[int, float]:
+        return bm_state_autotune(self.handle, steps_per_trial)
+
     def close(self):
         if self.handle:
             bm_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many states stepped by one launch per step (keeps the member States alive)."""
+
+    def __init__(self, states):
+        self.states = list(states)
+        self.handle = bm_batch_create(self.states)
+        self.info = bm_batch_info(self.handle)
+
+    def step(self, n: int = 1):
+        bm_batch_step(self.handle, n)
+
+    def step_async(self, n: int = 1):
+        bm_batch_step_async(self.handle, n)
+
+    def sync(self):
+        bm_batch_sync(self.handle)
+
+    def run_until(self, t_end):
+        te = np.broadcast_to(np.asarray(t_end, dtype=np.float64), (len(self.states),)).copy()
+        bm_batch_run_until(self.handle, te)
+
+    def set_stream(self, stream_ptr: int):
+        bm_batch_set_stream(self.handle, stream_ptr)
+
+    def set_launch(self, ctas_per_sm: int):
+        bm_batch_set_launch(self.handle, ctas_per_sm)
+
+    def autotune(self, steps_per_trial: int = 10) -> tuple[int, float]:
+        return bm_batch_autotune(self.handle, steps_per_trial)
+
+    def close(self):
+        if self.handle:
+            bm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- request server
+
+def bm_server_create(precision=BM_FP32_BULK, hbm_budget_bytes: int = 0, max_slots: int = 0,
+                     steps_per_round: int = 64, ctas_per_sm: int = 0) -> int:
+    lib = load_library()
+    o = bm_server_opts()
+    lib.bm_server_opts_default(C.byref(o))
+    if isinstance(precision, str):
+        precision = {"fp64": BM_FP64, "fp32": BM_FP32_BULK, "fp32_bulk": BM_FP32_BULK}[precision.lower()]
+    o.precision = precision
+    o.hbm_budget_bytes = int(hbm_budget_bytes)
+    o.max_slots = int(max_slots)
+    o.steps_per_round = int(steps_per_round)
+    o.ctas_per_sm = int(ctas_per_sm)
+    out = _vp()
+    _check(lib.bm_server_create(C.byref(o), C.byref(out)))
+    return out.value
+
+
+def bm_server_destroy(server: int):
+    if server:
+        load_library().bm_server_destroy(server)
+
+
+def bm_submit(server: int, mesh: int, params: bm_params, H, qx=None, qy=None, t_end: float = 1.0) -> int:
+    H, qx, qy = _f64(H), _f64(qx), _f64(qy)
+    tk = C.c_uint64()
+    _check(load_library().bm_submit(server, mesh, C.byref(params), _dp(H), _dp(qx), _dp(qy), float(t_end),
+                                    C.byref(tk)))
+    return tk.value
+
+
+def bm_poll(server: int, ticket: int, n_cells: int):
+    """(H, qx, qy, latency_s) when finished, None while BM_EAGAIN; raises on failure."""
+    H, qx, qy = np.empty(n_cells), np.empty(n_cells), np.empty(n_cells)
+    lat = _d()
+    st = load_library().bm_poll(server, int(ticket), _dp(H), _dp(qx), _dp(qy), C.byref(lat))
+    if st == BM_EAGAIN:
+        return None
+    _check(st)
+    return H, qx, qy, lat.value
+
+
+def bm_server_wait(server: int, ticket: int, timeout_s: float = 600.0):
+    _check(load_library().bm_server_wait(server, int(ticket), float(timeout_s)))
+
+
+def bm_server_stats(server: int) -> dict:
+    q, r, c = _i64(), _i64(), _i64()
+    cu, rb = _d(), _d()
+    _check(load_library().bm_server_stats(server, C.byref(q), C.byref(r), C.byref(c), C.byref(cu), C.byref(rb)))
+    return {"queued": q.value, "running": r.value, "completed": c.value, "cell_updates": cu.value,
+            "resident_bytes": rb.value}
+
+
+class Server:
+    """Owning wrapper of a request server; keeps submitted meshes and params alive."""
+
+    def __init__(self, precision="fp32", **opts):
+        self.handle = bm_server_create(precision=precision, **opts)
+        self.precision = precision
+        self._keep = {}
+
+    def submit(self, mesh: Mesh, H, qx=None, qy=None, t_end: float = 1.0, **params) -> int:
+        params.setdefault("precision", self.precision)
+        p, keep = make_params(**params)
+        tk = bm_submit(self.handle, mesh.handle, p, H, qx, qy, t_end)
+        self._keep[tk] = (mesh, p, keep)
+        return tk
+
+    def poll(self, ticket: int):
+        mesh = self._keep[ticket][0]
+        r = bm_poll(self.handle, ticket, mesh.n_cells)
+        if r is not None:
+            self._keep.pop(ticket, None)
+        return r
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        bm_server_wait(self.handle, ticket, timeout_s)
+        return self.poll(ticket)
+
+    def stats(self) -> dict:
+        return bm_server_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            bm_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

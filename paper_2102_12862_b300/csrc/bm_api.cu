@@ -1,7 +1,11 @@
-// bm_api.cu -- the C ABI (include/bm.h): meshes and states resident in HBM, the step
+// bm_api.cu -- the C ABI (include/bm.h): meshes and states resident in HBM, one fused
+// kernel launch per step (single states and batches of uneven meshes), the step
 // sequence captured in CUDA graphs, end-time targeting, checkpoint upload/download.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <deque>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -12,6 +16,7 @@
 
 #include "bm_internal.h"
 #include "bm_kernels.cuh"
+#include "bm_state.h"
 
 namespace bm {
 
@@ -22,91 +27,32 @@ bm_status fail(bm_status st, const std::string& msg) {
   return st;
 }
 void clear_error() { g_err.clear(); }
-
-#define BM_CUDA(call)                                                                          \
-  do {                                                                                         \
-    cudaError_t e_ = (call);                                                                   \
-    if (e_ != cudaSuccess) {                                                                   \
-      std::ostringstream os_;                                                                  \
-      os_ << #call << ": " << cudaGetErrorString(e_);                                          \
-      return fail(BM_ECUDA, os_.str());                                                        \
-    }                                                                                          \
-  } while (0)
-
-// Typed device buffer (owning).
-template <typename T>
-struct DBuf {
-  T* p = nullptr;
-  size_t n = 0;
-  DBuf() = default;
-  DBuf(const DBuf&) = delete;
-  DBuf& operator=(const DBuf&) = delete;
-  ~DBuf() { release(); }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
-  }
-  cudaError_t alloc(size_t count) {
-    release();
-    n = count;
-    if (count == 0) return cudaSuccess;
-    return cudaMalloc(&p, count * sizeof(T));
-  }
-  cudaError_t upload(const std::vector<T>& v) {
-    cudaError_t e = alloc(v.size());
-    if (e != cudaSuccess || v.empty()) return e;
-    return cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
-  }
-};
-
-}  // namespace bm
-
-using namespace bm;
-
-struct bm_mesh {
-  HostMesh h;
-  int device = 0;
-  // FP64 device copies
-  DBuf<double> z, inv_area, area, enx, eny, elen, in_len;
-  DBuf<uint64_t> slots;
-  DBuf<int64_t> eoff;
-  DBuf<int32_t> eL, eR, in_cell, perm;
-};
-
-struct bm_state {
-  const bm_mesh* mesh = nullptr;
-  bm_params prm{};
-  Params p{};
-  std::vector<double> hydro_t, hydro_q;
-  DBuf<double> d_hydro_t, d_hydro_q;
-  DBuf<double> gn2;  // g n^2 per cell (new order)
-  DBuf<double> H[2], qx[2], qy[2], u[2], v[2], c[2];
-  DBuf<double> stage[3];  // caller-order staging for upload/download
-  DBuf<double> vol_part, vol_out;
-  DBuf<TilePartial> part;
-  DBuf<int> bad;
-  Ctl* ctl = nullptr;       // device
-  Ctl* hctl = nullptr;      // pinned host mirror
-  double* hvol = nullptr;   // pinned
-  cudaStream_t stream = nullptr;   // user stream (may be the default stream)
-  cudaStream_t own = nullptr;      // private stream used for graph capture
-  std::map<int, cudaGraphExec_t> graphs;
-  double cur_t_end = std::numeric_limits<double>::infinity();
-  StepArgs<double> sa{};
-  FinalizeArgs<double> fa{};
-  ~bm_state() {
-    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
-    if (ctl) cudaFree(ctl);
-    if (hctl) cudaFreeHost(hctl);
-    if (hvol) cudaFreeHost(hvol);
-    if (own) cudaStreamDestroy(own);
-  }
-};
+const char* last_error() { return g_err.c_str(); }
 
 namespace {
 
 const double kInf = std::numeric_limits<double>::infinity();
+
+template <typename T>
+std::vector<T> narrow(const std::vector<double>& v, double shift = 0.0) {
+  std::vector<T> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) out[i] = static_cast<T>(v[i] - shift);
+  return out;
+}
+
+cudaError_t ensure_fp32_geometry(bm_mesh* m) {
+  if (m->has32) return cudaSuccess;
+  const HostMesh& h = m->h;
+  cudaError_t e = m->inv_area32.upload(narrow<float>(h.inv_area));
+  if (e == cudaSuccess) e = m->enx32.upload(narrow<float>(h.enx));
+  if (e == cudaSuccess) e = m->eny32.upload(narrow<float>(h.eny));
+  if (e == cudaSuccess) e = m->elen32.upload(narrow<float>(h.elen));
+  if (e == cudaSuccess) e = m->in_len32.upload(narrow<float>(h.in_len));
+  if (e == cudaSuccess) m->has32 = true;
+  return e;
+}
+
+}  // namespace
 
 bm_status check_params(const bm_params* p) {
   if (!p) return fail(BM_EINVAL, "bm_params is NULL");
@@ -129,19 +75,54 @@ bm_status check_params(const bm_params* p) {
   return BM_OK;
 }
 
-bm_status read_status(bm_state* s) {
-  BM_CUDA(cudaMemcpyAsync(s->hctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
-  BM_CUDA(cudaStreamSynchronize(s->stream));
-  if (s->hctl->status & 1) return fail(BM_ENONFINITE, "the step produced a non-finite value");
-  if (s->hctl->status & 2) return fail(BM_ENEGDEPTH, "a depth fell below -h_min");
+bm_status status_of(const Ctl& c) {
+  if (c.status & 1) return fail(BM_ENONFINITE, "the step produced a non-finite value");
+  if (c.status & 2) return fail(BM_ENEGDEPTH, "a depth fell below -h_min");
   return BM_OK;
 }
 
-// Launch the two kernels of one step on `st`.
-void enqueue_step(bm_state* s, cudaStream_t st) {
-  const int nt = static_cast<int>(s->mesh->h.n_tiles);
-  step_fp64<<<nt, kTile, 0, st>>>(s->sa);
-  finalize<double><<<1, kFinThreads, 0, st>>>(s->fa, 1);
+namespace {
+// Dynamic shared memory above 48 KB must be opted into once per kernel.
+template <typename K>
+void allow_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+}
+struct SmemOptIn {
+  SmemOptIn() {
+    allow_smem(step_batch<double, true>, sizeof(TileSmem<double>));
+    allow_smem(step_batch<float, false>, sizeof(TileSmem<float>));
+  }
+};
+void ensure_smem_optin() {
+  static SmemOptIn once;
+  (void)once;
+}
+}  // namespace
+
+// One fused step (or prime) launch over a descriptor array and a work list.
+void launch_work(int prec, const void* descs, const WorkItem* work, int n_work, int grid, int prime,
+                 cudaStream_t st) {
+  if (n_work <= 0) return;
+  ensure_smem_optin();
+  grid = std::max(1, std::min(grid > 0 ? grid : n_work, n_work));
+  if (prec == BM_FP64)
+    step_batch<double, true><<<grid, kTile, sizeof(TileSmem<double>), st>>>(
+        static_cast<const InstDesc<double>*>(descs), work, n_work, prime);
+  else
+    step_batch<float, false><<<grid, kTile, sizeof(TileSmem<float>), st>>>(
+        static_cast<const InstDesc<float>*>(descs), work, n_work, prime);
+}
+
+namespace {
+
+bm_status read_status(bm_state* s) {
+  BM_CUDA(cudaMemcpyAsync(s->hctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  return status_of(*s->hctl);
+}
+
+void launch_state(bm_state* s, cudaStream_t st, int prime) {
+  launch_work(s->prec, s->desc.p, s->work.p, static_cast<int>(s->work.n), s->grid, prime, st);
 }
 
 bm_status get_graph(bm_state* s, int k, cudaGraphExec_t* out) {
@@ -152,7 +133,7 @@ bm_status get_graph(bm_state* s, int k, cudaGraphExec_t* out) {
   }
   cudaGraph_t g = nullptr;
   BM_CUDA(cudaStreamBeginCapture(s->own, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < k; ++i) enqueue_step(s, s->own);
+  for (int i = 0; i < k; ++i) launch_state(s, s->own, 0);
   BM_CUDA(cudaStreamEndCapture(s->own, &g));
   cudaGraphExec_t ge = nullptr;
   cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
@@ -161,6 +142,11 @@ bm_status get_graph(bm_state* s, int k, cudaGraphExec_t* out) {
   s->graphs[k] = ge;
   *out = ge;
   return BM_OK;
+}
+
+void drop_graphs(bm_state* s) {
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  s->graphs.clear();
 }
 
 // Enqueue n steps as graph launches of 32 steps plus single-step launches.
@@ -188,6 +174,57 @@ bm_status set_end(bm_state* s, double t_end) {
   return BM_OK;
 }
 
+template <typename T>
+void fill_desc(bm_state* s, InstDesc<T>& d) {
+  const bm_mesh* m = s->mesh;
+  const HostMesh& h = m->h;
+  std::memset(&d, 0, sizeof(d));
+  Buffers<T>& b = s->buf<T>();
+  for (int k = 0; k < 2; ++k) {
+    d.H[k] = b.H[k].p; d.Hlo[k] = b.Hlo[k].p; d.qx[k] = b.qx[k].p; d.qy[k] = b.qy[k].p;
+    d.u[k] = b.u[k].p; d.v[k] = b.v[k].p; d.c[k] = b.c[k].p;
+  }
+  d.z = b.z.p;
+  d.gn2 = b.gn2.p;
+  d.in_pw = b.in_pw.p;
+  d.in_hs = b.in_hs.p;
+  if constexpr (sizeof(T) == 8) {
+    d.inv_area = m->inv_area.p; d.enx = m->enx.p; d.eny = m->eny.p; d.elen = m->elen.p; d.in_len = m->in_len.p;
+  } else {
+    d.inv_area = m->inv_area32.p; d.enx = m->enx32.p; d.eny = m->eny32.p; d.elen = m->elen32.p;
+    d.in_len = m->in_len32.p;
+  }
+  d.slots = m->slots.p;
+  d.eoff = m->eoff.p;
+  d.eL = m->eL.p;
+  d.eR = m->eR.p;
+  d.in_cell = m->in_cell.p;
+  d.btiles = m->btiles.p;
+  d.ctl = s->ctl;
+  d.part = s->part.p;
+  d.p = s->p;
+  d.inflow_len = h.inflow_len;
+  d.n_inflow = static_cast<int>(h.n_inflow);
+  d.n_btiles = static_cast<int>(h.btiles.size());
+  d.n_cells = static_cast<int>(h.n_cells);
+  d.n_tiles = static_cast<int>(h.n_tiles);
+}
+
+}  // namespace
+
+// Host copy of a state's descriptor (for batches).
+void state_desc_bytes(bm_state* s, std::vector<unsigned char>* out) {
+  if (s->prec == BM_FP64) {
+    InstDesc<double> d;
+    fill_desc<double>(s, d);
+    out->assign(reinterpret_cast<unsigned char*>(&d), reinterpret_cast<unsigned char*>(&d) + sizeof(d));
+  } else {
+    InstDesc<float> d;
+    fill_desc<float>(s, d);
+    out->assign(reinterpret_cast<unsigned char*>(&d), reinterpret_cast<unsigned char*>(&d) + sizeof(d));
+  }
+}
+
 // Load caller-order arrays into state buffer 0, validate, reset time and prime dt.
 bm_status load_state(bm_state* s, const double* H, const double* qx, const double* qy, double t) {
   const HostMesh& h = s->mesh->h;
@@ -201,34 +238,115 @@ bm_status load_state(bm_state* s, const double* H, const double* qx, const doubl
   if (qy) BM_CUDA(cudaMemcpyAsync(s->stage[2].p, qy, bytes, cudaMemcpyHostToDevice, s->stream));
   else BM_CUDA(cudaMemsetAsync(s->stage[2].p, 0, bytes, s->stream));
   const int nb = (n + 255) / 256;
-  gather_from_user<double><<<nb, 256, 0, s->stream>>>(s->stage[0].p, s->mesh->perm.p, n, s->H[0].p, 0.0);
-  gather_from_user<double><<<nb, 256, 0, s->stream>>>(s->stage[1].p, s->mesh->perm.p, n, s->qx[0].p, 0.0);
-  gather_from_user<double><<<nb, 256, 0, s->stream>>>(s->stage[2].p, s->mesh->perm.p, n, s->qy[0].p, 0.0);
+  const int32_t* perm = s->mesh->perm.p;
   BM_CUDA(cudaMemsetAsync(s->bad.p, 0, sizeof(int), s->stream));
-  check_state<double><<<nb, 256, 0, s->stream>>>(s->H[0].p, s->qx[0].p, s->qy[0].p, s->mesh->z.p, n, s->bad.p);
-  int bad = 0;
-  BM_CUDA(cudaMemcpyAsync(&bad, s->bad.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  if (s->prec == BM_FP64) {
+    Buffers<double>& b = s->b64;
+    gather_from_user<double><<<nb, 256, 0, s->stream>>>(s->stage[0].p, perm, n, b.H[0].p);
+    gather_from_user<double><<<nb, 256, 0, s->stream>>>(s->stage[1].p, perm, n, b.qx[0].p);
+    gather_from_user<double><<<nb, 256, 0, s->stream>>>(s->stage[2].p, perm, n, b.qy[0].p);
+    check_state<double><<<nb, 256, 0, s->stream>>>(b.H[0].p, b.qx[0].p, b.qy[0].p, b.z.p, n, s->bad.p);
+  } else {
+    Buffers<float>& b = s->b32;
+    gather_surface_pair<<<nb, 256, 0, s->stream>>>(s->stage[0].p, perm, n, s->mesh->z.p, b.z.p, s->datum, b.H[0].p,
+                                                   b.Hlo[0].p, s->bad.p);
+    gather_from_user<float><<<nb, 256, 0, s->stream>>>(s->stage[1].p, perm, n, b.qx[0].p);
+    gather_from_user<float><<<nb, 256, 0, s->stream>>>(s->stage[2].p, perm, n, b.qy[0].p);
+    check_state<float><<<nb, 256, 0, s->stream>>>(nullptr, b.qx[0].p, b.qy[0].p, b.z.p, n, s->bad.p);
+  }
+  BM_CUDA(cudaMemcpyAsync(s->hbad, s->bad.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   BM_CUDA(cudaStreamSynchronize(s->stream));
-  if (bad & 1) return fail(BM_EINVAL, "state has a non-finite value");
-  if (bad & 2) return fail(BM_EINVAL, "state has H < z_bed (a dry cell is H = z_bed)");
-  Ctl c{};
+  if (*s->hbad & 1) return fail(BM_EINVAL, "state has a non-finite value");
+  if (*s->hbad & 2) return fail(BM_EINVAL, "state has H < z_bed (a dry cell is H = z_bed)");
+  Ctl c;
+  std::memset(&c, 0, sizeof(c));
   c.t = t;
-  c.dt = 0;
   c.t_end = kInf;
-  c.bvol = 0;
-  c.parity = 0;
   c.active = 1;
-  c.pad0 = 0;
   BM_CUDA(cudaMemcpyAsync(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
   s->cur_t_end = kInf;
-  prime_fp64<<<static_cast<int>(h.n_tiles), kTile, 0, s->stream>>>(s->sa);
-  finalize<double><<<1, kFinThreads, 0, s->stream>>>(s->fa, 0);
+  launch_state(s, s->stream, 1);
   BM_CUDA(cudaGetLastError());
   BM_CUDA(cudaStreamSynchronize(s->stream));
   return BM_OK;
 }
 
-}  // namespace
+// Allocate the device arrays of a state and upload its per-cell constants.
+bm_status alloc_state(bm_state* s, const bm_params* prm) {
+  const bm_mesh* m = s->mesh;
+  const HostMesh& h = m->h;
+  const size_t Np = static_cast<size_t>(h.n_tiles) * kTile;
+  const bool f64 = s->prec == BM_FP64;
+  s->datum = f64 ? 0.0 : (std::isnan(prm->datum) ? h.z_min : prm->datum);
+  if (!std::isfinite(s->datum)) return fail(BM_EINVAL, "bm_state_init: datum must be finite or NaN");
+  std::vector<double> gn2(h.man.size());
+  for (size_t i = 0; i < gn2.size(); ++i) gn2[i] = prm->g * h.man[i] * h.man[i];
+  cudaError_t e = cudaSuccess;
+  if (f64) {
+    e = s->b64.alloc(Np, static_cast<size_t>(h.n_inflow), true);
+    if (e == cudaSuccess) e = s->b64.gn2.upload(gn2);
+    if (e == cudaSuccess) e = cudaMemcpy(s->b64.z.p, h.z.data(), Np * sizeof(double), cudaMemcpyHostToDevice);
+  } else {
+    e = ensure_fp32_geometry(const_cast<bm_mesh*>(m));
+    if (e == cudaSuccess) e = s->b32.alloc(Np, static_cast<size_t>(h.n_inflow), false);
+    if (e == cudaSuccess) e = s->b32.gn2.upload(narrow<float>(gn2));
+    if (e == cudaSuccess) {
+      std::vector<float> z32 = narrow<float>(h.z, s->datum);
+      e = cudaMemcpy(s->b32.z.p, z32.data(), Np * sizeof(float), cudaMemcpyHostToDevice);
+    }
+  }
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = s->stage[k].alloc(h.n_cells);
+  if (e == cudaSuccess) e = s->part.alloc(h.n_tiles);
+  if (e == cudaSuccess) e = cudaMemset(s->part.p, 0, h.n_tiles * sizeof(TilePartial));
+  if (e == cudaSuccess) e = s->vol_part.alloc(h.n_tiles);
+  if (e == cudaSuccess) e = s->vol_out.alloc(1);
+  if (e == cudaSuccess) e = s->bad.alloc(1);
+  if (e == cudaSuccess) e = s->d_hydro_t.upload(s->hydro_t);
+  if (e == cudaSuccess) e = s->d_hydro_q.upload(s->hydro_q);
+  if (e == cudaSuccess) e = cudaMalloc(&s->ctl, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaMallocHost(&s->hctl, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaMallocHost(&s->hvol, sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&s->hbad, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    if (e == cudaErrorMemoryAllocation) return fail(BM_ENOMEM, "bm_state_init: out of device memory");
+    return fail(BM_ECUDA, std::string("bm_state_init: ") + cudaGetErrorString(e));
+  }
+  s->stream = s->own;
+  Params& p = s->p;
+  p.cfl = prm->cfl;
+  p.g = prm->g;
+  p.h_min = prm->h_min;
+  p.dt_max = prm->dt_max;
+  p.cfl_mode = prm->cfl_mode;
+  p.hydro_n = static_cast<int>(prm->hydro_n);
+  p.hydro_t = s->d_hydro_t.p;
+  p.hydro_q = s->d_hydro_q.p;
+  state_desc_bytes(s, &s->hdesc);
+  std::vector<WorkItem> work(h.n_tiles);
+  for (int64_t t = 0; t < h.n_tiles; ++t) work[t] = WorkItem{0, static_cast<int>(t)};
+  e = s->desc.upload(s->hdesc);
+  if (e == cudaSuccess) e = s->work.upload(work);
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? BM_ENOMEM : BM_ECUDA,
+                std::string("bm_state_init: ") + cudaGetErrorString(e));
+  s->grid = static_cast<int>(h.n_tiles);
+  return BM_OK;
+}
+
+// Device bytes held by a state (its admission footprint).
+size_t state_footprint(const bm_mesh* m, int precision) {
+  const HostMesh& h = m->h;
+  const size_t Np = static_cast<size_t>(h.n_tiles) * kTile;
+  const size_t w = precision == BM_FP64 ? 8 : 4;
+  const size_t arrays = precision == BM_FP64 ? 14 : 10;  // 2 x (H [pair], q, derived) + z, gn2
+  return Np * w * arrays + 3 * static_cast<size_t>(h.n_cells) * 8 + static_cast<size_t>(h.n_tiles) * 32 +
+         static_cast<size_t>(h.n_inflow) * 2 * w + 4096;
+}
+
+}  // namespace bm
+
+using namespace bm;
 
 extern "C" {
 
@@ -247,7 +365,7 @@ void bm_params_default(bm_params* p) {
   p->hydro_n = 0;
 }
 
-const char* bm_last_error(void) { return g_err.c_str(); }
+const char* bm_last_error(void) { return last_error(); }
 
 bm_status bm_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri, const double* z_bed,
                          const double* manning_n, const uint8_t* edge_tag, bm_mesh** out) {
@@ -281,6 +399,7 @@ bm_status bm_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, 
   if (e == cudaSuccess) e = m->elen.upload(h.elen);
   if (e == cudaSuccess) e = m->in_cell.upload(h.in_cell);
   if (e == cudaSuccess) e = m->in_len.upload(h.in_len);
+  if (e == cudaSuccess) e = m->btiles.upload(h.btiles);
   if (e == cudaSuccess) e = m->perm.upload(h.perm);
   if (e != cudaSuccess) {
     delete m;
@@ -313,99 +432,17 @@ bm_status bm_state_init(const bm_mesh* m, const bm_params* prm, const double* H,
   if (!m) return fail(BM_EINVAL, "bm_state_init: mesh is NULL");
   bm_status st = check_params(prm);
   if (st != BM_OK) return st;
-  if (prm->precision != BM_FP64) return fail(BM_EINVAL, "bm_state_init: this build steps BM_FP64 states only");
   bm_state* s = new (std::nothrow) bm_state();
   if (!s) return fail(BM_ENOMEM, "bm_state_init: out of host memory");
   s->mesh = m;
   s->prm = *prm;
+  s->prec = prm->precision;
   s->hydro_t.assign(prm->hydro_t, prm->hydro_t + prm->hydro_n);
   s->hydro_q.assign(prm->hydro_q, prm->hydro_q + prm->hydro_n);
   s->prm.hydro_t = s->hydro_t.data();
   s->prm.hydro_q = s->hydro_q.data();
-  const HostMesh& h = m->h;
-  const size_t Np = static_cast<size_t>(h.n_tiles) * kTile;
-  cudaError_t e = cudaSuccess;
-  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-    e = s->H[b].alloc(Np);
-    if (e == cudaSuccess) e = s->qx[b].alloc(Np);
-    if (e == cudaSuccess) e = s->qy[b].alloc(Np);
-    if (e == cudaSuccess) e = s->u[b].alloc(Np);
-    if (e == cudaSuccess) e = s->v[b].alloc(Np);
-    if (e == cudaSuccess) e = s->c[b].alloc(Np);
-  }
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = s->stage[k].alloc(h.n_cells);
-  if (e == cudaSuccess) e = s->part.alloc(h.n_tiles);
-  if (e == cudaSuccess) e = s->vol_part.alloc(h.n_tiles);
-  if (e == cudaSuccess) e = s->vol_out.alloc(1);
-  if (e == cudaSuccess) e = s->bad.alloc(1);
-  if (e == cudaSuccess) {
-    std::vector<double> gn2(h.man.size());
-    for (size_t i = 0; i < gn2.size(); ++i) gn2[i] = prm->g * h.man[i] * h.man[i];
-    e = s->gn2.upload(gn2);
-  }
-  if (e == cudaSuccess) e = s->d_hydro_t.upload(s->hydro_t);
-  if (e == cudaSuccess) e = s->d_hydro_q.upload(s->hydro_q);
-  if (e == cudaSuccess) e = cudaMalloc(&s->ctl, sizeof(Ctl));
-  if (e == cudaSuccess) e = cudaMallocHost(&s->hctl, sizeof(Ctl));
-  if (e == cudaSuccess) e = cudaMallocHost(&s->hvol, sizeof(double));
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking);
-  if (e != cudaSuccess) {
-    delete s;
-    if (e == cudaErrorMemoryAllocation) return fail(BM_ENOMEM, "bm_state_init: out of device memory");
-    return fail(BM_ECUDA, std::string("bm_state_init: ") + cudaGetErrorString(e));
-  }
-  s->stream = s->own;
-  // zero the padding cells once so they stay inert
-  for (int b = 0; b < 2; ++b) {
-    cudaMemset(s->H[b].p, 0, Np * sizeof(double));
-    cudaMemset(s->qx[b].p, 0, Np * sizeof(double));
-    cudaMemset(s->qy[b].p, 0, Np * sizeof(double));
-    cudaMemset(s->u[b].p, 0, Np * sizeof(double));
-    cudaMemset(s->v[b].p, 0, Np * sizeof(double));
-    cudaMemset(s->c[b].p, 0, Np * sizeof(double));
-  }
-  Params& p = s->p;
-  p.cfl = prm->cfl;
-  p.g = prm->g;
-  p.h_min = prm->h_min;
-  p.dt_max = prm->dt_max;
-  p.cfl_mode = prm->cfl_mode;
-  p.hydro_n = static_cast<int>(prm->hydro_n);
-  p.hydro_t = s->d_hydro_t.p;
-  p.hydro_q = s->d_hydro_q.p;
-  StepArgs<double>& a = s->sa;
-  for (int b = 0; b < 2; ++b) {
-    a.H[b] = s->H[b].p; a.qx[b] = s->qx[b].p; a.qy[b] = s->qy[b].p;
-    a.u[b] = s->u[b].p; a.v[b] = s->v[b].p; a.c[b] = s->c[b].p;
-  }
-  a.z = m->z.p;
-  a.gn2 = s->gn2.p;
-  a.inv_area = m->inv_area.p;
-  a.slots = m->slots.p;
-  a.eoff = m->eoff.p;
-  a.eL = m->eL.p;
-  a.eR = m->eR.p;
-  a.enx = m->enx.p;
-  a.eny = m->eny.p;
-  a.elen = m->elen.p;
-  a.n_cells = static_cast<int>(h.n_cells);
-  a.ctl = s->ctl;
-  a.part = s->part.p;
-  a.p = p;
-  FinalizeArgs<double>& f = s->fa;
-  f.H[0] = s->H[0].p;
-  f.H[1] = s->H[1].p;
-  f.z = m->z.p;
-  f.inv_area = m->inv_area.p;
-  f.in_cell = m->in_cell.p;
-  f.in_len = m->in_len.p;
-  f.n_inflow = static_cast<int>(h.n_inflow);
-  f.inflow_len = h.inflow_len;
-  f.n_tiles = static_cast<int>(h.n_tiles);
-  f.ctl = s->ctl;
-  f.part = s->part.p;
-  f.p = p;
-  st = load_state(s, H, qx, qy, 0.0);
+  st = alloc_state(s, prm);
+  if (st == BM_OK) st = load_state(s, H, qx, qy, 0.0);
   if (st != BM_OK) {
     delete s;
     return st;
@@ -425,6 +462,23 @@ bm_status bm_state_set_stream(bm_state* s, void* stream) {
   if (!s) return fail(BM_EINVAL, "bm_state_set_stream: state is NULL");
   BM_CUDA(cudaStreamSynchronize(s->stream));
   s->stream = stream ? static_cast<cudaStream_t>(stream) : cudaStreamLegacy;
+  return BM_OK;
+}
+
+bm_status bm_state_set_launch(bm_state* s, int ctas_per_sm) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_set_launch: state is NULL");
+  if (ctas_per_sm < 0 || ctas_per_sm > 64) return fail(BM_EINVAL, "bm_state_set_launch: ctas_per_sm in [0, 64]");
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nt = static_cast<int>(s->mesh->h.n_tiles);
+  const int grid = ctas_per_sm == 0 ? nt : std::min(nt, ctas_per_sm * sms);
+  if (grid != s->grid) {
+    BM_CUDA(cudaStreamSynchronize(s->stream));
+    drop_graphs(s);
+    s->grid = grid;
+  }
   return BM_OK;
 }
 
@@ -502,10 +556,17 @@ bm_status bm_state_download(bm_state* s, double* H, double* qx, double* qy, doub
   const int nb = (n + 255) / 256;
   const size_t bytes = static_cast<size_t>(n) * sizeof(double);
   double* outs[3] = {H, qx, qy};
-  double* srcs[3] = {s->H[par].p, s->qx[par].p, s->qy[par].p};
   for (int k = 0; k < 3; ++k) {
     if (!outs[k]) continue;
-    scatter_to_user<double><<<nb, 256, 0, s->stream>>>(srcs[k], s->mesh->perm.p, n, s->stage[k].p, 0.0);
+    if (s->prec == BM_FP64) {
+      const double* src[3] = {s->b64.H[par].p, s->b64.qx[par].p, s->b64.qy[par].p};
+      scatter_to_user<double><<<nb, 256, 0, s->stream>>>(src[k], nullptr, s->mesh->perm.p, n, s->stage[k].p, 0.0);
+    } else {
+      const float* src[3] = {s->b32.H[par].p, s->b32.qx[par].p, s->b32.qy[par].p};
+      scatter_to_user<float><<<nb, 256, 0, s->stream>>>(src[k], k == 0 ? s->b32.Hlo[par].p : nullptr,
+                                                         s->mesh->perm.p, n, s->stage[k].p,
+                                                         k == 0 ? s->datum : 0.0);
+    }
     BM_CUDA(cudaMemcpyAsync(outs[k], s->stage[k].p, bytes, cudaMemcpyDeviceToHost, s->stream));
   }
   BM_CUDA(cudaStreamSynchronize(s->stream));
@@ -522,9 +583,14 @@ bm_status bm_state_stats(bm_state* s, double* t, double* dt_next, int64_t* steps
   if (volume) {
     const int par = s->hctl->parity;
     const int nt = static_cast<int>(s->mesh->h.n_tiles);
-    volume_partials<double><<<nt, kTile, 0, s->stream>>>(s->H[par].p, s->mesh->z.p, s->mesh->area.p,
-                                                          static_cast<int>(s->mesh->h.n_cells), 0.0, s->vol_part.p);
-    sum_partials<<<1, kFinThreads, 0, s->stream>>>(s->vol_part.p, nt, s->vol_out.p);
+    const int n = static_cast<int>(s->mesh->h.n_cells);
+    if (s->prec == BM_FP64)
+      volume_partials<double><<<nt, kTile, 0, s->stream>>>(s->b64.H[par].p, nullptr, s->b64.z.p, s->mesh->area.p,
+                                                            nullptr, n, s->vol_part.p);
+    else
+      volume_partials<float><<<nt, kTile, 0, s->stream>>>(s->b32.H[par].p, s->b32.Hlo[par].p, s->b32.z.p, nullptr,
+                                                           s->mesh->inv_area32.p, n, s->vol_part.p);
+    sum_partials<<<1, kSumThreads, 0, s->stream>>>(s->vol_part.p, nt, s->vol_out.p);
     BM_CUDA(cudaMemcpyAsync(s->hvol, s->vol_out.p, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     BM_CUDA(cudaStreamSynchronize(s->stream));
     *volume = *s->hvol;
@@ -544,7 +610,7 @@ bm_status bm_step_timed(bm_state* s, int64_t n, double* step_kernel_ms, double* 
     bm_status st = set_end(s, kInf);
     if (st != BM_OK) return st;
   }
-  std::vector<cudaEvent_t> ev(2 * n);
+  std::vector<cudaEvent_t> ev(2 * n, nullptr);
   for (auto& e : ev) {
     cudaError_t r = cudaEventCreate(&e);
     if (r != cudaSuccess) {
@@ -552,12 +618,10 @@ bm_status bm_step_timed(bm_state* s, int64_t n, double* step_kernel_ms, double* 
       return fail(BM_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(r));
     }
   }
-  const int nt = static_cast<int>(s->mesh->h.n_tiles);
   for (int64_t k = 0; k < n; ++k) {
     cudaEventRecord(ev[2 * k], s->stream);
-    step_fp64<<<nt, kTile, 0, s->stream>>>(s->sa);
+    launch_state(s, s->stream, 0);
     cudaEventRecord(ev[2 * k + 1], s->stream);
-    finalize<double><<<1, kFinThreads, 0, s->stream>>>(s->fa, 1);
   }
   cudaError_t r = cudaStreamSynchronize(s->stream);
   double ksum = 0.0;
@@ -573,6 +637,125 @@ bm_status bm_step_timed(bm_state* s, int64_t n, double* step_kernel_ms, double* 
   if (step_kernel_ms) *step_kernel_ms = ksum;
   if (total_ms) *total_ms = tot;
   return read_status(s);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- autotuner
+
+namespace bm {
+namespace {
+
+// Device snapshot of everything a step reads or writes, to undo tuning trials.
+struct Snapshot {
+  std::deque<std::pair<void*, DBuf<unsigned char>>> saved;  // deque: entries never move
+  cudaError_t take(void* p, size_t bytes, cudaStream_t st) {
+    if (!p || bytes == 0) return cudaSuccess;
+    saved.emplace_back();
+    saved.back().first = p;
+    cudaError_t e = saved.back().second.alloc(bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(saved.back().second.p, p, bytes, cudaMemcpyDeviceToDevice, st);
+    return e;
+  }
+  cudaError_t restore(cudaStream_t st) {
+    for (auto& kv : saved) {
+      cudaError_t e = cudaMemcpyAsync(kv.first, kv.second.p, kv.second.n, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaStreamSynchronize(st);
+  }
+};
+
+template <typename T>
+cudaError_t snapshot_buffers(Buffers<T>& b, Snapshot* sn, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    DBuf<T>* bufs[7] = {&b.H[k], &b.Hlo[k], &b.qx[k], &b.qy[k], &b.u[k], &b.v[k], &b.c[k]};
+    for (auto* x : bufs)
+      if (e == cudaSuccess) e = sn->take(x->p, x->bytes(), st);
+  }
+  if (e == cudaSuccess) e = sn->take(b.in_pw.p, b.in_pw.bytes(), st);
+  if (e == cudaSuccess) e = sn->take(b.in_hs.p, b.in_hs.bytes(), st);
+  return e;
+}
+
+cudaError_t snapshot_state(bm_state* s, Snapshot* sn, cudaStream_t st) {
+  cudaError_t e = s->prec == BM_FP64 ? snapshot_buffers(s->b64, sn, st) : snapshot_buffers(s->b32, sn, st);
+  if (e == cudaSuccess) e = sn->take(s->ctl, sizeof(Ctl), st);
+  if (e == cudaSuccess) e = sn->take(s->part.p, s->part.bytes(), st);
+  return e;
+}
+
+}  // namespace
+
+// Time `steps` steps for each candidate launch shape, restore the state, pick the
+// fastest.  Candidates: one CTA per tile (0) and 1..8 persistent CTAs per SM.
+bm_status autotune_shape(std::vector<bm_state*> states, int steps, int* best, double* best_ms,
+                         const std::function<bm_status(int)>& set_shape,
+                         const std::function<bm_status(int)>& run_steps, cudaStream_t st) {
+  Snapshot sn;
+  for (bm_state* s : states) {
+    cudaError_t e = snapshot_state(s, &sn, st);
+    if (e != cudaSuccess) return fail(BM_ENOMEM, std::string("autotune snapshot: ") + cudaGetErrorString(e));
+  }
+  BM_CUDA(cudaStreamSynchronize(st));
+  const int cands[] = {0, 1, 2, 3, 4, 6, 8};
+  cudaEvent_t e0, e1;
+  BM_CUDA(cudaEventCreate(&e0));
+  BM_CUDA(cudaEventCreate(&e1));
+  double bms = std::numeric_limits<double>::infinity();
+  int bc = 0;
+  bm_status out = BM_OK;
+  for (int c : cands) {
+    out = set_shape(c);
+    if (out != BM_OK) break;
+    out = run_steps(2);  // warm (graph capture)
+    if (out != BM_OK) break;
+    cudaEventRecord(e0, st);
+    out = run_steps(steps);
+    if (out != BM_OK) break;
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < bms) {
+      bms = ms;
+      bc = c;
+    }
+    if (sn.restore(st) != cudaSuccess) {
+      out = fail(BM_ECUDA, "autotune: restore failed");
+      break;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out != BM_OK) return out;
+  out = set_shape(bc);
+  if (out != BM_OK) return out;
+  if (best) *best = bc;
+  if (best_ms) *best_ms = bms / steps;
+  return BM_OK;
+}
+
+}  // namespace bm
+
+extern "C" {
+
+bm_status bm_state_autotune(bm_state* s, int steps_per_trial, int* best_ctas_per_sm, double* ms_per_step) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_autotune: state is NULL");
+  if (steps_per_trial < 1 || steps_per_trial > 10000) return fail(BM_EINVAL, "bm_state_autotune: steps in [1, 10000]");
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  const double keep_end = s->cur_t_end;
+  if (keep_end != kInf) {
+    bm_status st = set_end(s, kInf);
+    if (st != BM_OK) return st;
+  }
+  bm_status st = autotune_shape(
+      {s}, steps_per_trial, best_ctas_per_sm, ms_per_step, [&](int c) { return bm_state_set_launch(s, c); },
+      [&](int n) { return enqueue_steps(s, n); }, s->stream);
+  if (st == BM_OK && keep_end != kInf) st = set_end(s, keep_end);
+  return st;
 }
 
 }  // extern "C"

@@ -1,0 +1,324 @@
+// bm_batch.cu -- batches of independent states stepped by one launch per step.
+//
+// The launch's work list packs every member's tiles; each CTA reads its member's
+// descriptor (pointers, sizes, parameters) and the CTA that completes a member's
+// last tile finalizes that member, so every member advances with its own dt.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <limits>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "bm_internal.h"
+#include "bm_state.h"
+
+struct bm_batch {
+  std::vector<bm_state*> members;
+  int prec = BM_FP64;
+  bm::DBuf<unsigned char> descs;  // member descriptors, one after another
+  bm::DBuf<bm::WorkItem> work;
+  bm::DBuf<bm::Ctl*> ctlp;        // device pointers to the members' control blocks
+  bm::DBuf<double> t_end;         // per-member end times (run_until)
+  bm::DBuf<int> flags;            // per member: active | status << 1
+  int* hflags = nullptr;          // pinned
+  cudaStream_t stream = nullptr;
+  cudaStream_t own = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;
+  int grid = 0;
+  ~bm_batch() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    if (hflags) cudaFreeHost(hflags);
+    if (own) cudaStreamDestroy(own);
+  }
+};
+
+namespace bm {
+bm_status autotune_shape(std::vector<bm_state*> states, int steps, int* best, double* best_ms,
+                         const std::function<bm_status(int)>& set_shape,
+                         const std::function<bm_status(int)>& run_steps, cudaStream_t st);
+namespace {
+
+// Set every member's end time (+inf = plain stepping) from a device array.
+__global__ void batch_set_t_end(Ctl* const* ctl, const double* t_end, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  Ctl* c = ctl[k];
+  const double te = t_end[k];
+  c->t_end = te;
+  double dt = c->dt_cfl;
+  int clipped = 0;
+  if (dt >= te - c->t) {
+    dt = te - c->t;
+    clipped = 1;
+  }
+  c->dt = dt;
+  c->clipped = clipped;
+  c->active = c->t < te ? 1 : 0;
+}
+
+__global__ void batch_flags(Ctl* const* ctl, int n, int* flags) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) flags[k] = ctl[k]->active | (ctl[k]->status << 1);
+}
+
+void launch_batch(bm_batch* b, cudaStream_t st) {
+  launch_work(b->prec, b->descs.p, b->work.p, static_cast<int>(b->work.n), b->grid, 0, st);
+}
+
+bm_status batch_graph(bm_batch* b, int k, cudaGraphExec_t* out) {
+  auto it = b->graphs.find(k);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return BM_OK;
+  }
+  cudaGraph_t g = nullptr;
+  BM_CUDA(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < k; ++i) launch_batch(b, b->own);
+  BM_CUDA(cudaStreamEndCapture(b->own, &g));
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(BM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  b->graphs[k] = ge;
+  *out = ge;
+  return BM_OK;
+}
+
+}  // namespace
+
+bm_status batch_enqueue(bm_batch* b, int64_t n) {
+  constexpr int kChunk = 16;
+  cudaGraphExec_t gbig = nullptr, gone = nullptr;
+  if (n >= kChunk) {
+    bm_status st = batch_graph(b, kChunk, &gbig);
+    if (st != BM_OK) return st;
+  }
+  if (n % kChunk) {
+    bm_status st = batch_graph(b, 1, &gone);
+    if (st != BM_OK) return st;
+  }
+  for (int64_t i = 0; i < n / kChunk; ++i) BM_CUDA(cudaGraphLaunch(gbig, b->stream));
+  for (int64_t i = 0; i < n % kChunk; ++i) BM_CUDA(cudaGraphLaunch(gone, b->stream));
+  return BM_OK;
+}
+
+bm_status batch_set_end(bm_batch* b, const double* t_end_host) {
+  const int n = static_cast<int>(b->members.size());
+  std::vector<double> te(n);
+  for (int k = 0; k < n; ++k) {
+    te[k] = t_end_host ? t_end_host[k] : std::numeric_limits<double>::infinity();
+    b->members[k]->cur_t_end = te[k];
+  }
+  BM_CUDA(cudaMemcpyAsync(b->t_end.p, te.data(), n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  batch_set_t_end<<<(n + 127) / 128, 128, 0, b->stream>>>(b->ctlp.p, b->t_end.p, n);
+  BM_CUDA(cudaGetLastError());
+  // te is a host temporary: wait for the copy before it goes out of scope
+  BM_CUDA(cudaStreamSynchronize(b->stream));
+  return BM_OK;
+}
+
+// Per member: active | status << 1 (synchronises the batch's stream).
+bm_status batch_member_flags(bm_batch* b, std::vector<int>* flags) {
+  const int n = static_cast<int>(b->members.size());
+  batch_flags<<<(n + 127) / 128, 128, 0, b->stream>>>(b->ctlp.p, n, b->flags.p);
+  BM_CUDA(cudaMemcpyAsync(b->hflags, b->flags.p, n * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BM_CUDA(cudaStreamSynchronize(b->stream));
+  flags->assign(b->hflags, b->hflags + n);
+  return BM_OK;
+}
+
+// Read every member's active flag and status; returns the first failing status.
+bm_status batch_read(bm_batch* b, int* n_active) {
+  const int n = static_cast<int>(b->members.size());
+  batch_flags<<<(n + 127) / 128, 128, 0, b->stream>>>(b->ctlp.p, n, b->flags.p);
+  BM_CUDA(cudaMemcpyAsync(b->hflags, b->flags.p, n * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BM_CUDA(cudaStreamSynchronize(b->stream));
+  int act = 0;
+  bm_status worst = BM_OK;
+  for (int k = 0; k < n; ++k) {
+    act += b->hflags[k] & 1;
+    const int st = b->hflags[k] >> 1;
+    if (worst == BM_OK && (st & 1)) worst = fail(BM_ENONFINITE, "batch member " + std::to_string(k) +
+                                                     ": the step produced a non-finite value");
+    if (worst == BM_OK && (st & 2)) worst = fail(BM_ENEGDEPTH, "batch member " + std::to_string(k) +
+                                                     ": a depth fell below -h_min");
+  }
+  if (n_active) *n_active = act;
+  return worst;
+}
+
+}  // namespace bm
+
+using namespace bm;
+
+extern "C" {
+
+bm_status bm_batch_create(bm_state* const* states, int32_t n, bm_batch** out) {
+  clear_error();
+  if (!out) return fail(BM_EINVAL, "bm_batch_create: out is NULL");
+  *out = nullptr;
+  if (!states || n < 1) return fail(BM_EINVAL, "bm_batch_create: need at least one state");
+  const int prec = states[0] ? states[0]->prec : BM_FP64;
+  for (int k = 0; k < n; ++k) {
+    if (!states[k]) return fail(BM_EINVAL, "bm_batch_create: NULL state");
+    if (states[k]->prec != prec) return fail(BM_EINVAL, "bm_batch_create: members must share one precision");
+    for (int j = 0; j < k; ++j)
+      if (states[j] == states[k]) return fail(BM_EINVAL, "bm_batch_create: a state appears twice");
+  }
+  bm_batch* b = new (std::nothrow) bm_batch();
+  if (!b) return fail(BM_ENOMEM, "bm_batch_create: out of host memory");
+  b->members.assign(states, states + n);
+  b->prec = prec;
+  std::vector<unsigned char> all, one;
+  std::vector<WorkItem> work;
+  std::vector<Ctl*> ctls(n);
+  for (int k = 0; k < n; ++k) {
+    bm_state* s = states[k];
+    cudaStreamSynchronize(s->stream);
+    state_desc_bytes(s, &one);
+    all.insert(all.end(), one.begin(), one.end());
+    for (int64_t t = 0; t < s->mesh->h.n_tiles; ++t) work.push_back(WorkItem{k, static_cast<int>(t)});
+    ctls[k] = s->ctl;
+  }
+  cudaError_t e = b->descs.upload(all);
+  if (e == cudaSuccess) e = b->work.upload(work);
+  if (e == cudaSuccess) e = b->ctlp.upload(ctls);
+  if (e == cudaSuccess) e = b->t_end.alloc(n);
+  if (e == cudaSuccess) e = b->flags.alloc(n);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->hflags, n * sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    return fail(e == cudaErrorMemoryAllocation ? BM_ENOMEM : BM_ECUDA,
+                std::string("bm_batch_create: ") + cudaGetErrorString(e));
+  }
+  b->stream = b->own;
+  b->grid = static_cast<int>(work.size());
+  bm_status st = batch_set_end(b, nullptr);
+  if (st != BM_OK) {
+    delete b;
+    return st;
+  }
+  *out = b;
+  return BM_OK;
+}
+
+void bm_batch_destroy(bm_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  delete b;
+}
+
+bm_status bm_batch_set_stream(bm_batch* b, void* stream) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_set_stream: batch is NULL");
+  BM_CUDA(cudaStreamSynchronize(b->stream));
+  b->stream = stream ? static_cast<cudaStream_t>(stream) : cudaStreamLegacy;
+  return BM_OK;
+}
+
+bm_status bm_batch_set_launch(bm_batch* b, int ctas_per_sm) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_set_launch: batch is NULL");
+  if (ctas_per_sm < 0 || ctas_per_sm > 64) return fail(BM_EINVAL, "bm_batch_set_launch: ctas_per_sm in [0, 64]");
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nw = static_cast<int>(b->work.n);
+  const int grid = ctas_per_sm == 0 ? nw : std::min(nw, ctas_per_sm * sms);
+  if (grid != b->grid) {
+    BM_CUDA(cudaStreamSynchronize(b->stream));
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    b->grid = grid;
+  }
+  return BM_OK;
+}
+
+bm_status bm_batch_step_async(bm_batch* b, int64_t n_steps) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_step: batch is NULL");
+  if (n_steps < 0) return fail(BM_EINVAL, "bm_batch_step: n_steps must be >= 0");
+  bool reset = false;
+  for (bm_state* s : b->members) reset |= std::isfinite(s->cur_t_end);
+  if (reset) {
+    bm_status st = batch_set_end(b, nullptr);
+    if (st != BM_OK) return st;
+  }
+  return batch_enqueue(b, n_steps);
+}
+
+bm_status bm_batch_sync(bm_batch* b) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_sync: batch is NULL");
+  return batch_read(b, nullptr);
+}
+
+bm_status bm_batch_step(bm_batch* b, int64_t n_steps) {
+  bm_status st = bm_batch_step_async(b, n_steps);
+  if (st != BM_OK) return st;
+  return batch_read(b, nullptr);
+}
+
+bm_status bm_batch_run_until(bm_batch* b, const double* t_end) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_run_until: batch is NULL");
+  if (!t_end) return fail(BM_EINVAL, "bm_batch_run_until: t_end is NULL");
+  for (size_t k = 0; k < b->members.size(); ++k)
+    if (!std::isfinite(t_end[k])) return fail(BM_EINVAL, "bm_batch_run_until: t_end must be finite");
+  bm_status st = batch_set_end(b, t_end);
+  if (st != BM_OK) return st;
+  int active = 0;
+  st = batch_read(b, &active);
+  int64_t chunk = 16;
+  int64_t launched = 0;
+  while (st == BM_OK && active > 0) {
+    st = batch_enqueue(b, chunk);
+    if (st != BM_OK) return st;
+    launched += chunk;
+    st = batch_read(b, &active);
+    if (chunk < 512) chunk *= 2;
+    if (launched > (int64_t(1) << 40)) return fail(BM_ETIMEOUT, "bm_batch_run_until: no progress");
+  }
+  return st;
+}
+
+bm_status bm_batch_info(const bm_batch* b, int32_t* n_members, int64_t* n_cells, int64_t* n_tiles) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_info: batch is NULL");
+  int64_t cells = 0;
+  for (bm_state* s : b->members) cells += s->mesh->h.n_cells;
+  if (n_members) *n_members = static_cast<int32_t>(b->members.size());
+  if (n_cells) *n_cells = cells;
+  if (n_tiles) *n_tiles = static_cast<int64_t>(b->work.n);
+  return BM_OK;
+}
+
+bm_status bm_batch_autotune(bm_batch* b, int steps_per_trial, int* best_ctas_per_sm, double* ms_per_step) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_autotune: batch is NULL");
+  if (steps_per_trial < 1 || steps_per_trial > 10000) return fail(BM_EINVAL, "bm_batch_autotune: steps in [1, 10000]");
+  BM_CUDA(cudaStreamSynchronize(b->stream));
+  std::vector<double> keep;
+  bool finite = false;
+  for (bm_state* s : b->members) {
+    keep.push_back(s->cur_t_end);
+    finite |= std::isfinite(s->cur_t_end);
+  }
+  if (finite) {
+    bm_status st = batch_set_end(b, nullptr);
+    if (st != BM_OK) return st;
+  }
+  bm_status st = autotune_shape(
+      b->members, steps_per_trial, best_ctas_per_sm, ms_per_step, [&](int c) { return bm_batch_set_launch(b, c); },
+      [&](int n) { return batch_enqueue(b, n); }, b->stream);
+  if (st == BM_OK && finite) st = batch_set_end(b, keep.data());
+  return st;
+}
+
+}  // extern "C"

@@ -17,7 +17,8 @@ namespace bm {
 constexpr int kTile = 256;
 constexpr int kMaxTileEdges = 3 * kTile;
 
-// Boundary codes stored in place of the right cell of an edge.
+// Boundary codes stored in place of the right cell of an edge; inflow edge j of
+// the mesh's inflow list is stored as kInflow - j.
 constexpr int32_t kWall = -1;
 constexpr int32_t kTransmissive = -2;
 constexpr int32_t kInflow = -3;
@@ -38,9 +39,11 @@ struct HostMesh {
   std::vector<int64_t> eoff;
   std::vector<int32_t> eL, eR;      // left cell (new id), right cell (new id) or boundary code
   std::vector<double> enx, eny, elen;
-  // inflow edges (one entry per inflow edge): cell (new id), length, normal
+  // inflow edges (one entry per inflow edge): cell (new id), length
   std::vector<int32_t> in_cell;
   std::vector<double> in_len;
+  // tiles whose edge list holds at least one boundary edge (ascending)
+  std::vector<int32_t> btiles;
   double inflow_len = 0;
   double z_min = 0;
 };
@@ -51,26 +54,33 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
 // Device-side control block of one state (one instance).
 struct Ctl {
   double t;        // current time t^n
-  double dt;       // dt^n, the step the next launch takes
+  double dt;       // dt^n, the step the next launch takes (clipped to t_end)
   double t_end;    // run_until target (+inf for bm_step)
   double bvol;     // net boundary volume since init (FP64)
   double qscale;   // inflow: q_e = qscale * h_e^(5/3) when wsum > 0
   double quni;     // inflow: q_e = quni on every inflow edge when wsum == 0
   double Q;        // Q(t^n)
-  double pad0;
+  double dt_cfl;   // dt^n before clipping to t_end
   long long steps;
+  unsigned long long rmax_bits;  // max over cells of the Eq. 21 rate (bits of a double >= 0)
+  unsigned int done;             // tiles of the current launch that finished
   int parity;      // which state buffer holds U^n
   int active;      // 0 once t reached t_end
   int clipped;     // dt^n was clipped to t_end - t^n
   int wpos;        // wsum > 0
-  int status;      // bit 0: non-finite value, bit 1: depth < -h_min
-  int pad1;
+  int status;      // bit 0: non-finite value, bit 1: negative depth
 };
 
-// Per-tile reduction slots written by the step kernel.
+// One work item of a step launch: (instance, tile).
+struct WorkItem {
+  int inst;
+  int tile;
+};
+
+// Per-tile reduction slot written by the step kernel.
 struct TilePartial {
-  double rmax;   // max over the tile's cells of lambda/rho (Eq. 21) or sum l lambda / |Omega|
   double bflux;  // sum over the tile's boundary edges of l * F_h (outward)
+  double pad;
 };
 
 // Kernel parameters (plain values).

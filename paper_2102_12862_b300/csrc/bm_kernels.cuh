@@ -1,77 +1,78 @@
 // bm_kernels.cuh -- device code of the explicit shallow-water step (sm_103a).
 //
-// One step (BASEMENT v3, Section "Numerical solution", "Hydrodynamics"):
+// One step of one instance (BASEMENT v3, Section "Numerical solution",
+// "Hydrodynamics"), processed tile by tile (256 consecutive Hilbert-ordered cells):
 //   phase 0  stage the tile's cells (H, z, u, v, c) in shared memory;
 //   phase 1  each tile edge once: modified states on max(z_L, z_R), HLLC flux in
 //            the edge frame (Toro wave speeds), pre-balanced pressure correction,
 //            wall / transmissive / discharge-inflow boundary states;
 //   phase 2  each cell gathers its three edge contributions in local edge order
 //            (Eq. 12), applies the split Manning friction (Eq. 2, Table 1, two
-//            semi-implicit stages), zeroes q below h_min, writes U^{n+1} and its
-//            velocity / celerity, and reduces lambda/rho for the next dt (Eq. 21);
-//   finalize one block reduces the tile partials in a fixed order: dt^{n+1},
-//            t^{n+1}, boundary volume, inflow distribution for t^{n+1}.
+//            semi-implicit stages), zeroes q below h_min, writes U^{n+1} and reduces
+//            lambda/rho of Eq. 21 for the next dt;
+//   finalize the CTA that completes an instance's last tile reduces the instance's
+//            partials in a fixed order (dt^{n+1}, t^{n+1}, boundary volume, inflow
+//            split for t^{n+1}) -- no second launch, no spin-wait.
+// One launch steps every instance of a work list (a batch of uneven meshes, each
+// with its own dt); a single state is a batch of one.
 #pragma once
 
 #include <cuda_runtime.h>
 
+#include <cfloat>
 #include <cstdint>
 
 #include "bm_internal.h"
 
 namespace bm {
 
-template <typename R>
-struct StepArgs {
-  R* H[2];
-  R* qx[2];
-  R* qy[2];
-  R* u[2];   // velocity of the cell (0 below h_min)
-  R* v[2];
-  R* c[2];   // sqrt(g max(0, h))
-  const R* z;
-  const R* gn2;       // g n^2
-  const R* inv_area;  // 1 / |Omega_i|
+// Everything one instance's tiles need; lives in device memory.
+template <typename T>
+struct InstDesc {
+  T* H[2];    // free surface (FP32-bulk: hi part of the offset from the datum)
+  T* Hlo[2];  // FP32-bulk only: lo part of the free surface
+  T* qx[2];
+  T* qy[2];
+  T* u[2];   // FP64 only: velocity of the cell (0 at or below h_min)
+  T* v[2];
+  T* c[2];   // FP64 only: sqrt(g max(0, h))
+  const T* z;
+  const T* gn2;       // g n^2
+  const T* inv_area;  // 1 / |Omega_i|
   const uint64_t* slots;
   const int64_t* eoff;
   const int32_t* eL;
   const int32_t* eR;
-  const R* enx;
-  const R* eny;
-  const R* elen;
-  int n_cells;
+  const T* enx;
+  const T* eny;
+  const T* elen;
+  const int32_t* in_cell;  // inflow edge j: its cell
+  const T* in_len;         //                its length
+  T* in_pw;                //                h^(5/3) of the cell (0 at or below h_min)
+  T* in_hs;                //                max(0, h) of the cell
+  const int32_t* btiles;   // tiles with boundary edges
   Ctl* ctl;
   TilePartial* part;
   Params p;
-};
-
-template <typename R>
-struct FinalizeArgs {
-  R* H[2];
-  const R* z;
-  const R* inv_area;
-  const int32_t* in_cell;
-  const R* in_len;
-  int n_inflow;
   double inflow_len;
+  int n_inflow;
+  int n_btiles;
+  int n_cells;
   int n_tiles;
-  Ctl* ctl;
-  const TilePartial* part;
-  Params p;
 };
 
 // ------------------------------------------------------------------ helpers
 
 // Deterministic block reductions (fixed shuffle tree, then warp 0 over warps).
-template <int NT>
-__device__ __forceinline__ double block_max(double x, double* sbuf) {
+template <int NT, typename V>
+__device__ __forceinline__ V block_max(V x, V* sbuf) {
   for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) sbuf[w] = x;
   __syncthreads();
   if (w == 0) {
-    x = lane < NT / 32 ? sbuf[lane] : 0.0;
+    x = lane < NT / 32 ? sbuf[lane] : V(0);
     for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
   }
   return x;  // valid in thread 0
@@ -103,9 +104,27 @@ __device__ __forceinline__ double hydrograph(const Params& p, double t) {
   return p.hydro_q[p.hydro_n - 1];
 }
 
+// Elementary functions.  FP64: the IEEE-rounded library functions (the path the
+// oracle is checked against at 1e-11).  FP32-bulk: the hardware approximations
+// (MUFU reciprocal square root, reciprocal, base-2 logarithm and exponent), a few
+// ulp each -- far inside that mode's 1e-4 m accuracy target and deterministic, so
+// both sides of an edge still compute identical values.
+__device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ double f_div(double a, double b) { return a / b; }
+__device__ __forceinline__ double f_cbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float f_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ float f_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float f_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float f_cbrt(float x) { return f_exp2(__log2f(x) * (1.0f / 3.0f)); }  // x > 0
+
 // h^(5/3) for h > 0, through the cube root.
-__device__ __forceinline__ double pow53(double h) {
-  double r = cbrt(h);
+template <typename T>
+__device__ __forceinline__ T pow53(T h) {
+  const T r = f_cbrt(h);
   return h * r * r;
 }
 
@@ -114,290 +133,100 @@ __device__ __forceinline__ double pow53(double h) {
 // velocities.  Wave speeds: two-rarefaction star estimates when both sides are
 // wet, exact dry-front speeds when one side is dry.  pL, pR = g/2 h^2 are
 // returned so the caller subtracts exactly the same values.
-__device__ __forceinline__ void hllc(double hL, double unL, double utL, double cL, double hR, double unR,
-                                     double utR, double cR, double hg, double& F0, double& F1, double& F2,
-                                     double& pL, double& pR) {
-  const double us = 0.5 * (unL + unR) + cL - cR;
-  const double cs = 0.5 * (cL + cR) + 0.25 * (unL - unR);
-  double SL = fmin(unL - cL, us - cs);
-  double SR = fmax(unR + cR, us + cs);
-  const bool ldry = !(hL > 0.0), rdry = !(hR > 0.0);
-  SL = ldry ? unR - 2.0 * cR : (rdry ? unL - cL : SL);
-  SR = ldry ? unR + cR : (rdry ? unL + 2.0 * cL : SR);
+template <typename T>
+__device__ __forceinline__ void hllc(T hL, T unL, T utL, T cL, T hR, T unR, T utR, T cR, T hg, T& F0, T& F1,
+                                     T& F2, T& pL, T& pR) {
+  const T half = T(0.5), quarter = T(0.25), two = T(2), zero = T(0);
+  const T us = half * (unL + unR) + cL - cR;
+  const T cs = half * (cL + cR) + quarter * (unL - unR);
+  T SL = fmin(unL - cL, us - cs);
+  T SR = fmax(unR + cR, us + cs);
+  const bool ldry = !(hL > zero), rdry = !(hR > zero);
+  SL = ldry ? unR - two * cR : (rdry ? unL - cL : SL);
+  SR = ldry ? unR + cR : (rdry ? unL + two * cL : SR);
   pL = hg * hL * hL;
   pR = hg * hR * hR;
-  const double FL0 = hL * unL, FL1 = FL0 * unL + pL, FL2 = FL0 * utL;
-  const double FR0 = hR * unR, FR1 = FR0 * unR + pR, FR2 = FR0 * utR;
-  const double rd = 1.0 / (SR - SL);
-  const double H0 = FL0 - SL * ((FR0 - FL0) - SR * (hR - hL)) * rd;
-  const double H1 = FL1 - SL * ((FR1 - FL1) - SR * (FR0 - FL0)) * rd;
+  const T FL0 = hL * unL, FL1 = FL0 * unL + pL, FL2 = FL0 * utL;
+  const T FR0 = hR * unR, FR1 = FR0 * unR + pR, FR2 = FR0 * utR;
+  const T rd = f_div(T(1), SR - SL);
+  const T H0 = FL0 - SL * ((FR0 - FL0) - SR * (hR - hL)) * rd;
+  const T H1 = FL1 - SL * ((FR1 - FL1) - SR * (FR0 - FL0)) * rd;
   // sign of the contact speed S* = num / den with den < 0 whenever a side is wet
-  const double num = SL * hR * (unR - SR) - SR * hL * (unL - SL);
-  const double H2 = H0 * (num <= 0.0 ? utL : utR);
-  if (SL >= 0.0) {
+  const T num = SL * hR * (unR - SR) - SR * hL * (unL - SL);
+  const T H2 = H0 * (num <= zero ? utL : utR);
+  if (SL >= zero) {
     F0 = FL0; F1 = FL1; F2 = FL2;
-  } else if (SR <= 0.0) {
+  } else if (SR <= zero) {
     F0 = FR0; F1 = FR1; F2 = FR2;
   } else {
     F0 = H0; F1 = H1; F2 = H2;
   }
   if (ldry && rdry) {
-    F0 = 0.0; F1 = 0.0; F2 = 0.0;
+    F0 = zero; F1 = zero; F2 = zero;
   }
 }
 
-// ------------------------------------------------------------------ step kernel (FP64)
+// Velocity (0 at or below h_min) and celerity sqrt(g max(0, h)) of a cell of depth h.
+template <typename T>
+__device__ __forceinline__ void cell_derived(T h, T qx, T qy, T hmin, T g, T& u, T& v, T& c) {
+  u = T(0);
+  v = T(0);
+  if (h > hmin) {
+    const T rh = f_div(T(1), h);
+    u = qx * rh;
+    v = qy * rh;
+  }
+  c = f_sqrt(g * fmax(T(0), h));
+}
 
-__global__ void __launch_bounds__(kTile) step_fp64(const StepArgs<double> a) {
+// The free surface H of an FP32-bulk cell is the unevaluated sum hi + lo of two
+// floats (offset from the FP64 datum); FP64 cells have lo = 0.  Depths are formed
+// as (hi - z) + lo, so near-equal hi and z cancel exactly (Sterbenz) and the lo
+// part keeps what a single float would round away.
+template <typename T>
+__device__ __forceinline__ T depth_of(T hi, T lo, T z) {
+  return (hi - z) + lo;
+}
+
+// (hi, lo) += d without rounding error in the pair: Knuth's TwoSum of hi and d,
+// then Dekker's Fast2Sum renormalisation (|s| >= |lo + e| holds for these
+// magnitudes).  Uses round-to-nearest intrinsics so nothing is contracted.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float d) {
+  const float s = __fadd_rn(hi, d);
+  const float bp = __fsub_rn(s, hi);
+  const float ap = __fsub_rn(s, bp);
+  const float e = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(d, bp));
+  const float t = __fadd_rn(lo, e);
+  const float h2 = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(h2, s));
+  hi = h2;
+}
+
+// lambda_ij / rho_ij of Eq. 21 for one cell (max over its edges, cfl_mode 0) or
+// sum_j l_ij lambda_ij / |Omega_i| (cfl_mode 1), from the tile's staged geometry.
+template <typename T>
+__device__ __forceinline__ T cell_rate(const T* nxs, const T* nys, const T* ls, const int (&idx)[3], T u, T v, T c,
+                                       T ia, int cfl_mode) {
+  T rmax = T(0), ssum = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T lam = fabs(u * nxs[idx[k]] + v * nys[idx[k]]) + c;  // |u.n| does not depend on the side
+    const T ll = lam * ls[idx[k]];
+    rmax = fmax(rmax, T(0.75) * ll * ia);
+    ssum += ll;
+  }
+  return cfl_mode == 1 ? ssum * ia : rmax;
+}
+
+// Per-instance finalize, run by every thread of the CTA that completed the
+// instance's last tile.  advance = 1 after a step, 0 after prime.
+template <typename T>
+__device__ void finalize_instance(const InstDesc<T>& a, int advance, double* sred, double* sbc) {
   Ctl* ctl = a.ctl;
-  if (!ctl->active) return;
-  const int par = ctl->parity;
-  const double dt = ctl->dt;
-  const double qscale = ctl->qscale, quni = ctl->quni;
-  const int wpos = ctl->wpos;
-  const double g = a.p.g, hg = 0.5 * a.p.g, hmin = a.p.h_min;
-
-  const double* __restrict__ H0 = a.H[par];
-  const double* __restrict__ QX0 = a.qx[par];
-  const double* __restrict__ QY0 = a.qy[par];
-  const double* __restrict__ U0 = a.u[par];
-  const double* __restrict__ V0 = a.v[par];
-  const double* __restrict__ C0 = a.c[par];
-  const double* __restrict__ Z = a.z;
-
-  __shared__ double sH[kTile], sZ[kTile], sU[kTile], sV[kTile], sC[kTile];
-  __shared__ double sF[5][kMaxTileEdges];
-  __shared__ double sred[kTile / 32];
-
-  const int tile = blockIdx.x, tid = threadIdx.x;
-  const int base = tile * kTile;
-  const int i = base + tid;
-  const bool valid = i < a.n_cells;
-  double Hi = 0, zi = 0, qxi = 0, qyi = 0;
-  if (valid) {
-    Hi = H0[i]; zi = Z[i]; qxi = QX0[i]; qyi = QY0[i];
-    sU[tid] = U0[i]; sV[tid] = V0[i]; sC[tid] = C0[i];
-  } else {
-    sU[tid] = 0; sV[tid] = 0; sC[tid] = 0;
-  }
-  sH[tid] = Hi;
-  sZ[tid] = zi;
-  __syncthreads();
-
-  // phase 1: edges of the tile
-  const int64_t e0 = a.eoff[tile];
-  const int ne = static_cast<int>(a.eoff[tile + 1] - e0);
-  double bsum = 0.0;
-  for (int k = tid; k < ne; k += kTile) {
-    const int64_t e = e0 + k;
-    const int gL = a.eL[e], gR = a.eR[e];
-    const double nx = a.enx[e], ny = a.eny[e], l = a.elen[e];
-    double HL, zL, uL, vL, cL;
-    const int lL = gL - base;
-    if (static_cast<unsigned>(lL) < static_cast<unsigned>(kTile)) {
-      HL = sH[lL]; zL = sZ[lL]; uL = sU[lL]; vL = sV[lL]; cL = sC[lL];
-    } else {
-      HL = H0[gL]; zL = Z[gL]; uL = U0[gL]; vL = V0[gL]; cL = C0[gL];
-    }
-    const double unL = uL * nx + vL * ny, utL = -uL * ny + vL * nx;
-    double h1, h2, un2, ut2, c1, c2;
-    if (gR >= 0) {
-      double HR, zR, uR, vR, cR;
-      const int lR = gR - base;
-      if (static_cast<unsigned>(lR) < static_cast<unsigned>(kTile)) {
-        HR = sH[lR]; zR = sZ[lR]; uR = sU[lR]; vR = sV[lR]; cR = sC[lR];
-      } else {
-        HR = H0[gR]; zR = Z[gR]; uR = U0[gR]; vR = V0[gR]; cR = C0[gR];
-      }
-      const double zs = fmax(zL, zR);
-      h1 = fmax(0.0, HL - zs);
-      h2 = fmax(0.0, HR - zs);
-      // the side with the higher bed keeps its own depth, hence its own celerity
-      const bool lhi = zL >= zR;
-      const double clo = sqrt(g * (lhi ? h2 : h1));
-      c1 = lhi ? cL : clo;
-      c2 = lhi ? clo : cR;
-      un2 = uR * nx + vR * ny;
-      ut2 = -uR * ny + vR * nx;
-    } else {
-      h1 = fmax(0.0, HL - zL);
-      h2 = h1;
-      c1 = cL;
-      c2 = cL;
-      un2 = (gR == kWall) ? -unL : unL;  // wall: mirrored normal velocity
-      ut2 = utL;
-    }
-    double F0, F1, F2, pL, pR;
-    hllc(h1, unL, utL, c1, h2, un2, ut2, c2, hg, F0, F1, F2, pL, pR);
-    double GL = F1 - pL, GR = F1 - pR;
-    if (gR < 0) {
-      if (gR == kWall) {
-        F0 = 0.0; F2 = 0.0;  // impermeable, frictionless
-      } else if (gR == kInflow) {
-        const double h = HL - zL;
-        const double q = wpos ? (h > hmin ? qscale * pow53(h) : 0.0) : quni;
-        if (q > 0.0) {
-          const double hcr = cbrt(q * q / g);
-          const double hb = fmax(h1, hcr);
-          F0 = -q;
-          GL = q * q / hb + hg * hb * hb - pL;
-        } else {
-          F0 = 0.0;
-          GL = 0.0;
-        }
-        F2 = 0.0;
-      }
-      bsum += l * F0;
-    }
-    sF[0][k] = l * F0;
-    sF[1][k] = l * (GL * nx - F2 * ny);
-    sF[2][k] = l * (GL * ny + F2 * nx);
-    sF[3][k] = l * (GR * nx - F2 * ny);
-    sF[4][k] = l * (GR * ny + F2 * nx);
-  }
-  __syncthreads();
-
-  // phase 2: cells
-  double rloc = 0.0;
-  if (valid) {
-    const uint64_t sl = a.slots[i];
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    int idx[3], side[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const unsigned p = static_cast<unsigned>((sl >> (16 * k)) & 0xffffu);
-      idx[k] = static_cast<int>(p >> 1);
-      side[k] = static_cast<int>(p & 1u);
-      if (side[k] == 0) {
-        s0 += sF[0][idx[k]]; s1 += sF[1][idx[k]]; s2 += sF[2][idx[k]];
-      } else {
-        s0 += -sF[0][idx[k]]; s1 += -sF[3][idx[k]]; s2 += -sF[4][idx[k]];
-      }
-    }
-    const double ia = a.inv_area[i];
-    const double r = dt * ia;
-    const double Hn = Hi - r * s0;
-    double ux = qxi - r * s1;
-    double uy = qyi - r * s2;
-    const double h = Hn - zi;
-    const double gn2 = a.gn2[i];
-    if (h > hmin && gn2 > 0.0) {
-      // split friction: two semi-implicit stages, Heun average
-      const double cf = gn2 / (h * h * cbrt(h));
-      const double k0 = cf * sqrt(ux * ux + uy * uy);
-      const double d0 = 1.0 / (1.0 + dt * k0);
-      const double q1x = ux * d0, q1y = uy * d0;
-      const double k1 = cf * sqrt(q1x * q1x + q1y * q1y);
-      const double d1 = 1.0 / (1.0 + dt * k1);
-      ux = 0.5 * (ux + q1x * d1);
-      uy = 0.5 * (uy + q1y * d1);
-    }
-    const bool wet = h > hmin;
-    if (!wet) { ux = 0.0; uy = 0.0; }
-    const int dst = par ^ 1;
-    a.H[dst][i] = Hn;
-    a.qx[dst][i] = ux;
-    a.qy[dst][i] = uy;
-    double u = 0.0, v = 0.0;
-    if (wet) {
-      const double rh = 1.0 / h;
-      u = ux * rh;
-      v = uy * rh;
-    }
-    const double c = sqrt(g * fmax(0.0, h));
-    a.u[dst][i] = u;
-    a.v[dst][i] = v;
-    a.c[dst][i] = c;
-    if (!isfinite(Hn) || !isfinite(ux) || !isfinite(uy)) atomicOr(&ctl->status, 1);
-    if (h < -hmin) atomicOr(&ctl->status, 2);
-    // next dt (Eq. 21): lambda_ij / rho_ij = 3/4 lambda l / |Omega| (or sum l lambda / |Omega|)
-    if (wet) {
-      double ssum = 0.0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int64_t e = e0 + idx[k];
-        const double lam = fabs(u * a.enx[e] + v * a.eny[e]) + c;  // |u.n| is side-independent
-        const double ll = lam * a.elen[e];
-        rloc = fmax(rloc, 0.75 * ll * ia);
-        ssum += ll;
-      }
-      if (a.p.cfl_mode == 1) rloc = ssum * ia;
-    }
-  }
-  const double rm = block_max<kTile>(rloc, sred);
-  const double bs = block_sum<kTile>(bsum, sred);
-  if (tid == 0) {
-    a.part[tile].rmax = rm;
-    a.part[tile].bflux = bs;
-  }
-}
-
-// Derived cell data (u, v, c) and the dt partials of the current state; used after
-// init/upload before the first step.
-__global__ void __launch_bounds__(kTile) prime_fp64(const StepArgs<double> a) {
-  __shared__ double sred[kTile / 32];
-  const int par = a.ctl->parity;
-  const int tile = blockIdx.x, tid = threadIdx.x;
-  const int i = tile * kTile + tid;
-  const double g = a.p.g, hmin = a.p.h_min;
-  double rloc = 0.0;
-  if (i < a.n_cells) {
-    const double h = a.H[par][i] - a.z[i];
-    const bool wet = h > hmin;
-    double u = 0.0, v = 0.0;
-    if (wet) {
-      const double rh = 1.0 / h;
-      u = a.qx[par][i] * rh;
-      v = a.qy[par][i] * rh;
-    }
-    const double c = sqrt(g * fmax(0.0, h));
-    a.u[par][i] = u;
-    a.v[par][i] = v;
-    a.c[par][i] = c;
-    if (wet) {
-      const uint64_t sl = a.slots[i];
-      const double ia = a.inv_area[i];
-      const int64_t e0 = a.eoff[tile];
-      double ssum = 0.0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const unsigned p = static_cast<unsigned>((sl >> (16 * k)) & 0xffffu);
-        const int64_t e = e0 + (p >> 1);
-        const double lam = fabs(u * a.enx[e] + v * a.eny[e]) + c;
-        const double ll = lam * a.elen[e];
-        rloc = fmax(rloc, 0.75 * ll * ia);
-        ssum += ll;
-      }
-      if (a.p.cfl_mode == 1) rloc = ssum * ia;
-    }
-  }
-  const double rm = block_max<kTile>(rloc, sred);
-  if (tid == 0) {
-    a.part[tile].rmax = rm;
-    a.part[tile].bflux = 0.0;
-  }
-}
-
-// ------------------------------------------------------------------ finalize
-
-constexpr int kFinThreads = 1024;
-
-// advance = 1 after a step (t += dt, boundary volume, parity flip); 0 after prime.
-template <typename R>
-__global__ void __launch_bounds__(kFinThreads) finalize(const FinalizeArgs<R> a, int advance) {
-  __shared__ double sred[kFinThreads / 32];
-  __shared__ double s_t, s_rm;
-  __shared__ int s_par;
-  Ctl* ctl = a.ctl;
-  if (!ctl->active && advance) return;
   const int tid = threadIdx.x;
-  double rm = 0.0, bs = 0.0;
-  for (int t = tid; t < a.n_tiles; t += kFinThreads) {
-    rm = fmax(rm, a.part[t].rmax);
-    bs += a.part[t].bflux;
-  }
-  rm = block_max<kFinThreads>(rm, sred);
-  bs = block_sum<kFinThreads>(bs, sred);
+  double bs = 0.0;
+  for (int j = tid; j < a.n_btiles; j += kTile) bs += __ldcg(&a.part[a.btiles[j]].bflux);
+  bs = block_sum<kTile>(bs, sred);
   if (tid == 0) {
     if (advance) {
       const double dt = ctl->dt;
@@ -406,49 +235,41 @@ __global__ void __launch_bounds__(kFinThreads) finalize(const FinalizeArgs<R> a,
       ctl->parity ^= 1;
       ctl->steps += 1;
     }
-    s_t = ctl->t;
-    s_par = ctl->parity;
-    s_rm = rm;
+    sbc[0] = ctl->t;
   }
   __syncthreads();
-  const double t = s_t;
-  const int par = s_par;
-  const double g = a.p.g, hmin = a.p.h_min;
+  const double t = sbc[0];
+  const double g = a.p.g;
   // inflow distribution at the new time (conveyance weights l h^(5/3))
   double wsum = 0.0;
-  for (int j = tid; j < a.n_inflow; j += kFinThreads) {
-    const int cell = a.in_cell[j];
-    const double h = static_cast<double>(a.H[par][cell]) - static_cast<double>(a.z[cell]);
-    wsum += h > hmin ? static_cast<double>(a.in_len[j]) * pow53(h) : 0.0;
-  }
-  wsum = block_sum<kFinThreads>(wsum, sred);
-  __shared__ double s_w;
-  if (tid == 0) s_w = wsum;
+  for (int j = tid; j < a.n_inflow; j += kTile)
+    wsum += static_cast<double>(a.in_len[j]) * static_cast<double>(__ldcg(&a.in_pw[j]));
+  wsum = block_sum<kTile>(wsum, sred);
+  if (tid == 0) sbc[1] = wsum;
   __syncthreads();
-  wsum = s_w;
+  wsum = sbc[1];
   const double Q = hydrograph(a.p, t);
   const bool wpos = wsum > 0.0;
   const double qscale = wpos ? Q / wsum : 0.0;
   const double quni = (!wpos && a.inflow_len > 0.0) ? Q / a.inflow_len : 0.0;
   double rb = 0.0;
-  for (int j = tid; j < a.n_inflow; j += kFinThreads) {
-    const int cell = a.in_cell[j];
-    const double h = static_cast<double>(a.H[par][cell]) - static_cast<double>(a.z[cell]);
-    const double q = wpos ? (h > hmin ? qscale * pow53(h) : 0.0) : quni;
+  for (int j = tid; j < a.n_inflow; j += kTile) {
+    const double q = wpos ? qscale * static_cast<double>(__ldcg(&a.in_pw[j])) : quni;
     if (q > 0.0) {
-      const double hs = fmax(0.0, h);
+      const double hs = static_cast<double>(__ldcg(&a.in_hs[j]));
       const double hb = fmax(hs, cbrt(q * q / g));
       const double lb = q / hb + sqrt(g * hb);
-      const double ll = lb * static_cast<double>(a.in_len[j]) * static_cast<double>(a.inv_area[cell]);
+      const double ll = lb * static_cast<double>(a.in_len[j]) * static_cast<double>(a.inv_area[a.in_cell[j]]);
       rb = fmax(rb, a.p.cfl_mode == 0 ? 0.75 * ll : ll);
     }
   }
-  rb = block_max<kFinThreads>(rb, sred);
+  rb = block_max<kTile, double>(rb, sred);
   if (tid == 0) {
-    const double r = fmax(s_rm, rb);
+    const double rcell = __longlong_as_double(static_cast<long long>(atomicExch(&ctl->rmax_bits, 0ull)));
+    const double r = fmax(rcell, rb);
     double dtc = r > 0.0 ? a.p.cfl / r : a.p.dt_max;
     if (dtc > a.p.dt_max) dtc = a.p.dt_max;
-    ctl->pad0 = dtc;  // unclipped dt, used when t_end changes
+    ctl->dt_cfl = dtc;
     double dt = dtc;
     int clipped = 0;
     if (dt >= ctl->t_end - t) {
@@ -462,15 +283,307 @@ __global__ void __launch_bounds__(kFinThreads) finalize(const FinalizeArgs<R> a,
     ctl->qscale = qscale;
     ctl->quni = quni;
     ctl->wpos = wpos ? 1 : 0;
+    ctl->done = 0u;
   }
 }
 
-// Re-target the end time: dt is recomputed from the unclipped CFL step.
+// ------------------------------------------------------------------ step kernel
+
+// Shared memory of one CTA (dynamic): the tile's cells, its edges' geometry and
+// fluxes, reduction scratch.
+template <typename T>
+struct TileSmem {
+  T Hh[kTile], Hl[kTile], Z[kTile], U[kTile], V[kTile], C[kTile];
+  T F[5][kMaxTileEdges];
+  T Nx[kMaxTileEdges], Ny[kMaxTileEdges], Ln[kMaxTileEdges];
+  int32_t Code[kMaxTileEdges];
+  double red[kTile / 32];
+  T redT[kTile / 32];
+  double bc[2];
+  int last;
+};
+
+// One (instance, tile) work item.  T = double: every array and operation in FP64;
+// velocity and celerity of U^{n+1} are stored (kDerived) so the next step reads them
+// instead of dividing again.  T = float (FP32-bulk): H is an FP32 pair, z an FP32
+// offset from an FP64 datum; velocity and celerity are recomputed; the boundary
+// volume is summed in FP64.  prime = 1: no update, only derived data, inflow
+// weights and the dt of the current state (after init/upload).
+template <typename T, bool kDerived>
+__device__ __forceinline__ void tile_step(const InstDesc<T>& a, const int tile, const int prime, TileSmem<T>& sm) {
+  constexpr bool kPair = sizeof(T) == 4;
+  const int tid = threadIdx.x;
+  const T zero = T(0);
+  Ctl* ctl = a.ctl;
+  // round 1: control block and the tile's edge range
+  const int par = ctl->parity;
+  const T dt = static_cast<T>(ctl->dt);
+  const double qscale = ctl->qscale;
+  const T quni = static_cast<T>(ctl->quni);
+  const int wpos = ctl->wpos;
+  const int64_t e0 = a.eoff[tile];
+  const int ne = static_cast<int>(a.eoff[tile + 1] - e0);
+  const T g = static_cast<T>(a.p.g), hg = static_cast<T>(0.5 * a.p.g), hmin = static_cast<T>(a.p.h_min);
+  const T* __restrict__ HH = a.H[par];
+  const T* __restrict__ HL = kPair ? a.Hlo[par] : nullptr;
+  const T* __restrict__ QX0 = a.qx[par];
+  const T* __restrict__ QY0 = a.qy[par];
+  const T* __restrict__ Z = a.z;
+  const int base = tile * kTile;
+  const int i = base + tid;
+  const bool valid = i < a.n_cells;
+
+  // round 2: every load of the tile that depends only on the tile (cells, edges)
+  T Hh = zero, Hl = zero, zi = zero, qxi = zero, qyi = zero, ui = zero, vi = zero, ci = zero, ia = zero, gn2 = zero;
+  uint64_t sl = 0;
+  if (valid) {
+    Hh = HH[i]; zi = Z[i]; qxi = QX0[i]; qyi = QY0[i];
+    if (kPair) Hl = HL[i];
+    sl = a.slots[i];
+    ia = a.inv_area[i];
+    gn2 = a.gn2[i];
+    if (kDerived && !prime) { ui = a.u[par][i]; vi = a.v[par][i]; ci = a.c[par][i]; }
+  }
+  // the first two edges of this thread (most tiles have fewer than 512 edges)
+  int gL0 = 0, gR0 = kWall, gL1 = 0, gR1 = kWall;
+  T nx0 = zero, ny0 = zero, l0 = zero, nx1 = zero, ny1 = zero, l1 = zero;
+  if (!prime && tid < ne) {
+    gL0 = a.eL[e0 + tid]; gR0 = a.eR[e0 + tid]; nx0 = a.enx[e0 + tid]; ny0 = a.eny[e0 + tid]; l0 = a.elen[e0 + tid];
+  }
+  if (!prime && tid + kTile < ne) {
+    const int64_t e = e0 + tid + kTile;
+    gL1 = a.eL[e]; gR1 = a.eR[e]; nx1 = a.enx[e]; ny1 = a.eny[e]; l1 = a.elen[e];
+  }
+  const T hi0 = depth_of(Hh, Hl, zi);
+  if (!(kDerived && !prime) && valid) cell_derived<T>(hi0, qxi, qyi, hmin, g, ui, vi, ci);
+  sm.Hh[tid] = Hh; sm.Hl[tid] = Hl; sm.Z[tid] = zi; sm.U[tid] = ui; sm.V[tid] = vi; sm.C[tid] = ci;
+  double bsum = 0.0;
+  bool sawb = false;  // this thread evaluated a boundary edge
+  __syncthreads();
+
+  // phase 1: edges of the tile (round 3: halo cells of other tiles)
+  if (!prime) {
+    auto edge = [&](const int k, const int gL, const int gR, const T nx, const T ny, const T l) {
+      sm.Nx[k] = nx; sm.Ny[k] = ny; sm.Ln[k] = l; sm.Code[k] = gR;
+      T HLh, HLl, zL, uL, vL, cL;
+      const int lL = gL - base;
+      if (static_cast<unsigned>(lL) < static_cast<unsigned>(kTile)) {
+        HLh = sm.Hh[lL]; HLl = sm.Hl[lL]; zL = sm.Z[lL]; uL = sm.U[lL]; vL = sm.V[lL]; cL = sm.C[lL];
+      } else {
+        HLh = HH[gL]; HLl = kPair ? HL[gL] : zero; zL = Z[gL];
+        if (kDerived) {
+          uL = a.u[par][gL]; vL = a.v[par][gL]; cL = a.c[par][gL];
+        } else {
+          cell_derived<T>(depth_of(HLh, HLl, zL), QX0[gL], QY0[gL], hmin, g, uL, vL, cL);
+        }
+      }
+      const T unL = uL * nx + vL * ny, utL = -uL * ny + vL * nx;
+      T h1, h2, un2, ut2, c1, c2;
+      if (gR >= 0) {
+        T HRh, HRl, zR, uR, vR, cR;
+        const int lR = gR - base;
+        if (static_cast<unsigned>(lR) < static_cast<unsigned>(kTile)) {
+          HRh = sm.Hh[lR]; HRl = sm.Hl[lR]; zR = sm.Z[lR]; uR = sm.U[lR]; vR = sm.V[lR]; cR = sm.C[lR];
+        } else {
+          HRh = HH[gR]; HRl = kPair ? HL[gR] : zero; zR = Z[gR];
+          if (kDerived) {
+            uR = a.u[par][gR]; vR = a.v[par][gR]; cR = a.c[par][gR];
+          } else {
+            cell_derived<T>(depth_of(HRh, HRl, zR), QX0[gR], QY0[gR], hmin, g, uR, vR, cR);
+          }
+        }
+        const T zs = fmax(zL, zR);
+        h1 = fmax(zero, depth_of(HLh, HLl, zs));
+        h2 = fmax(zero, depth_of(HRh, HRl, zs));
+        // the side with the higher bed keeps its own depth, hence its own celerity
+        const bool lhi = zL >= zR;
+        const T clo = f_sqrt(g * (lhi ? h2 : h1));
+        c1 = lhi ? cL : clo;
+        c2 = lhi ? clo : cR;
+        un2 = uR * nx + vR * ny;
+        ut2 = -uR * ny + vR * nx;
+      } else {
+        h1 = fmax(zero, depth_of(HLh, HLl, zL));
+        h2 = h1;
+        c1 = cL;
+        c2 = cL;
+        un2 = (gR == kWall) ? -unL : unL;  // wall: mirrored normal velocity
+        ut2 = utL;
+      }
+      T F0, F1, F2, pL, pR;
+      hllc<T>(h1, unL, utL, c1, h2, un2, ut2, c2, hg, F0, F1, F2, pL, pR);
+      T GL = F1 - pL, GR = F1 - pR;
+      if (gR < 0) {
+        if (gR == kWall) {
+          F0 = zero; F2 = zero;  // impermeable, frictionless
+        } else if (gR <= kInflow) {
+          const int j = kInflow - gR;
+          const T q = wpos ? static_cast<T>(qscale * static_cast<double>(a.in_pw[j])) : quni;
+          if (q > zero) {
+            const T hcr = f_cbrt(f_div(q * q, g));
+            const T hb = fmax(h1, hcr);
+            F0 = -q;
+            GL = f_div(q * q, hb) + hg * hb * hb - pL;
+          } else {
+            F0 = zero;
+            GL = zero;
+          }
+          F2 = zero;
+        }
+        bsum += static_cast<double>(l * F0);
+        sawb = true;
+      }
+      sm.F[0][k] = l * F0;
+      sm.F[1][k] = l * (GL * nx - F2 * ny);
+      sm.F[2][k] = l * (GL * ny + F2 * nx);
+      sm.F[3][k] = l * (GR * nx - F2 * ny);
+      sm.F[4][k] = l * (GR * ny + F2 * nx);
+    };
+    if (tid < ne) edge(tid, gL0, gR0, nx0, ny0, l0);
+    if (tid + kTile < ne) edge(tid + kTile, gL1, gR1, nx1, ny1, l1);
+    for (int k = tid + 2 * kTile; k < ne; k += kTile) {
+      const int64_t e = e0 + k;
+      edge(k, a.eL[e], a.eR[e], a.enx[e], a.eny[e], a.elen[e]);
+    }
+  } else {
+    // prime: only the geometry and boundary codes are needed by phase 2
+    for (int k = tid; k < ne; k += kTile) {
+      sm.Nx[k] = a.enx[e0 + k]; sm.Ny[k] = a.eny[e0 + k]; sm.Ln[k] = a.elen[e0 + k]; sm.Code[k] = a.eR[e0 + k];
+    }
+  }
+  __syncthreads();
+
+  // phase 2: cells
+  T rloc = zero;
+  if (valid) {
+    int idx[3], side[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const unsigned p = static_cast<unsigned>((sl >> (16 * k)) & 0xffffu);
+      idx[k] = static_cast<int>(p >> 1);
+      side[k] = static_cast<int>(p & 1u);
+    }
+    T h = hi0, ux = qxi, uy = qyi;
+    if (!prime) {
+      T s0 = zero, s1 = zero, s2 = zero;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (side[k] == 0) {
+          s0 += sm.F[0][idx[k]]; s1 += sm.F[1][idx[k]]; s2 += sm.F[2][idx[k]];
+        } else {
+          s0 += -sm.F[0][idx[k]]; s1 += -sm.F[3][idx[k]]; s2 += -sm.F[4][idx[k]];
+        }
+      }
+      const T r = dt * ia;
+      if constexpr (kPair) {
+        pair_add(Hh, Hl, -(r * s0));
+      } else {
+        Hh = Hh - r * s0;
+      }
+      ux = qxi - r * s1;
+      uy = qyi - r * s2;
+      h = depth_of(Hh, Hl, zi);
+      if (h > hmin && gn2 > zero) {
+        // split friction: two semi-implicit stages, Heun average
+        const T cf = f_div(gn2, h * h * f_cbrt(h));
+        const T k0 = cf * f_sqrt(ux * ux + uy * uy);
+        const T d0 = f_div(T(1), T(1) + dt * k0);
+        const T q1x = ux * d0, q1y = uy * d0;
+        const T k1 = cf * f_sqrt(q1x * q1x + q1y * q1y);
+        const T d1 = f_div(T(1), T(1) + dt * k1);
+        ux = T(0.5) * (ux + q1x * d1);
+        uy = T(0.5) * (uy + q1y * d1);
+      }
+      if (!(h > hmin)) { ux = zero; uy = zero; }
+      const int dst = par ^ 1;
+      a.H[dst][i] = Hh;
+      if constexpr (kPair) a.Hlo[dst][i] = Hl;
+      a.qx[dst][i] = ux;
+      a.qy[dst][i] = uy;
+      if (!isfinite(Hh) || !isfinite(ux) || !isfinite(uy)) atomicOr(&ctl->status, 1);
+      // negative depth: below -h_min, beyond the rounding of the FP32 bed offset in FP32-bulk
+      const T negtol = kPair ? hmin + T(4) * static_cast<T>(FLT_EPSILON) * fabs(zi) : hmin;
+      if (h < -negtol) atomicOr(&ctl->status, 2);
+    }
+    const int out = prime ? par : (par ^ 1);
+    T u, v, c;
+    cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
+    if (kDerived) {
+      a.u[out][i] = u;
+      a.v[out][i] = v;
+      a.c[out][i] = c;
+    }
+    if (h > hmin) rloc = cell_rate<T>(sm.Nx, sm.Ny, sm.Ln, idx, u, v, c, ia, a.p.cfl_mode);
+    // inflow cells: conveyance weight and depth of the new state, for the finalize
+    // and the next step's inflow flux
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int code = sm.Code[idx[k]];
+      if (code <= kInflow) {
+        const int j = kInflow - code;
+        a.in_pw[j] = h > hmin ? pow53(h) : zero;
+        a.in_hs[j] = fmax(zero, h);
+      }
+    }
+  }
+  const T rm = block_max<kTile, T>(rloc, sm.redT);
+  // boundary volume partial (FP64, fixed order) only where the tile has boundary edges
+  const int hasb = __syncthreads_or(sawb);
+  double bs = 0.0;
+  if (hasb) bs = block_sum<kTile>(bsum, sm.red);
+  if (tid == 0) {
+    if (hasb) a.part[tile].bflux = bs;
+    if (rm > zero) {
+      const double rd = static_cast<double>(rm);
+      atomicMax(&ctl->rmax_bits, static_cast<unsigned long long>(__double_as_longlong(rd)));
+    }
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->done, 1u);
+    sm.last = (prev == static_cast<unsigned>(a.n_tiles) - 1u) ? 1 : 0;
+  }
+  __syncthreads();
+  if (sm.last) {
+    __threadfence();
+    finalize_instance<T>(a, prime ? 0 : 1, sm.red, sm.bc);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 3;
+
+// The step launch: a work list of (instance, tile) items over instance descriptors
+// in device memory.  A single state is a list of one instance's tiles, so a run
+// executes the same machine code alone and in a batch and gives bitwise the same
+// result (separately compiled copies could contract multiply-adds differently).
+template <typename T, bool kDerived>
+__global__ void __launch_bounds__(kTile, kMinBlocks<T>) step_batch(const InstDesc<T>* __restrict__ descs,
+                                                                    const WorkItem* __restrict__ work, int n_work,
+                                                                    int prime) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileSmem<T>& sm = *reinterpret_cast<TileSmem<T>*>(smem_raw);
+  __shared__ __align__(16) InstDesc<T> sdesc;
+  static_assert(sizeof(InstDesc<T>) % 8 == 0, "descriptor copy works in 8-byte words");
+  const int tid = threadIdx.x;
+  for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+    const WorkItem wi = work[w];
+    {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(descs + wi.inst);
+      unsigned long long* dstw = reinterpret_cast<unsigned long long*>(&sdesc);
+      for (int k = tid; k < static_cast<int>(sizeof(InstDesc<T>) / 8); k += kTile) dstw[k] = src[k];
+    }
+    __syncthreads();
+    if (sdesc.ctl->active || prime) tile_step<T, kDerived>(sdesc, wi.tile, prime, sm);
+    __syncthreads();
+  }
+}
+
+// Re-target the end time of one instance: dt is recomputed from the unclipped step.
 __global__ void set_t_end(Ctl* ctl, double t_end) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   ctl->t_end = t_end;
   const double t = ctl->t;
-  double dt = ctl->pad0;
+  double dt = ctl->dt_cfl;
   int clipped = 0;
   if (dt >= t_end - t) {
     dt = t_end - t;
@@ -482,47 +595,76 @@ __global__ void set_t_end(Ctl* ctl, double t_end) {
 }
 
 // V = sum |Omega_i| (H_i - z_i): per-tile partials, then one block in fixed order.
+// FP32-bulk: H = hi + lo, and |Omega_i| = 1 / inv_area_i (the area the FP32 update
+// uses), so V is the quantity that scheme conserves.
+constexpr int kSumThreads = 1024;
+
 template <typename R>
-__global__ void __launch_bounds__(kTile) volume_partials(const R* H, const R* z, const double* area, int n,
-                                                        double datum_shift, double* part) {
+__global__ void __launch_bounds__(kTile) volume_partials(const R* Hh, const R* Hl, const R* z, const double* area,
+                                                        const R* inv_area, int n, double* part) {
   __shared__ double sred[kTile / 32];
   const int i = blockIdx.x * kTile + threadIdx.x;
   double x = 0.0;
-  if (i < n) x = area[i] * ((static_cast<double>(H[i]) - static_cast<double>(z[i])) + datum_shift);
+  if (i < n) {
+    const double H = static_cast<double>(Hh[i]) + (Hl ? static_cast<double>(Hl[i]) : 0.0);
+    const double A = area ? area[i] : 1.0 / static_cast<double>(inv_area[i]);
+    x = A * (H - static_cast<double>(z[i]));
+  }
   x = block_sum<kTile>(x, sred);
   if (threadIdx.x == 0) part[blockIdx.x] = x;
 }
 
-__global__ void __launch_bounds__(kFinThreads) sum_partials(const double* part, int n, double* out) {
-  __shared__ double sred[kFinThreads / 32];
+__global__ void __launch_bounds__(kSumThreads) sum_partials(const double* part, int n, double* out) {
+  __shared__ double sred[kSumThreads / 32];
   double x = 0.0;
-  for (int t = threadIdx.x; t < n; t += kFinThreads) x += part[t];
-  x = block_sum<kFinThreads>(x, sred);
+  for (int t = threadIdx.x; t < n; t += kSumThreads) x += part[t];
+  x = block_sum<kSumThreads>(x, sred);
   if (threadIdx.x == 0) *out = x;
 }
 
 // Caller order <-> internal order.
 template <typename R>
-__global__ void gather_from_user(const double* user, const int32_t* perm, int n, R* out, double shift) {
+__global__ void gather_from_user(const double* user, const int32_t* perm, int n, R* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = static_cast<R>(user[perm[i]] - shift);
+  if (i < n) out[i] = static_cast<R>(user[perm[i]]);
+}
+
+// FP32-bulk free surface: H - datum as an FP32 pair hi + lo; a dry cell (H <= z)
+// gets exactly its FP32 bed offset so it stays exactly dry.  Also validates the
+// FP64 input (bit 0: non-finite, bit 1: H < z).
+__global__ void gather_surface_pair(const double* user, const int32_t* perm, int n, const double* zd, const float* zf,
+                                    double datum, float* hi, float* lo, int* bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double H = user[perm[i]];
+  if (!isfinite(H)) atomicOr(bad, 1);
+  if (H < zd[i]) atomicOr(bad, 2);
+  if (H <= zd[i]) {
+    hi[i] = zf[i];
+    lo[i] = 0.0f;
+  } else {
+    const double v = H - datum;
+    const float h = static_cast<float>(v);
+    hi[i] = h;
+    lo[i] = static_cast<float>(v - static_cast<double>(h));
+  }
 }
 
 template <typename R>
-__global__ void scatter_to_user(const R* in, const int32_t* perm, int n, double* user, double shift) {
+__global__ void scatter_to_user(const R* in, const R* lo, const int32_t* perm, int n, double* user, double shift) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) user[perm[i]] = static_cast<double>(in[i]) + shift;
+  if (i < n) user[perm[i]] = shift + (static_cast<double>(in[i]) + (lo ? static_cast<double>(lo[i]) : 0.0));
 }
 
-// Validation of an uploaded state: counts H < z and non-finite entries.
+// Validation of an uploaded state: flags non-finite entries and (FP64) H < z.
 template <typename R>
 __global__ void check_state(const R* H, const R* qx, const R* qy, const R* z, int n, int* bad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
-    const bool fin = isfinite(static_cast<double>(H[i])) && isfinite(static_cast<double>(qx[i])) &&
-                     isfinite(static_cast<double>(qy[i]));
+    const bool fin = isfinite(static_cast<double>(qx[i])) && isfinite(static_cast<double>(qy[i])) &&
+                     (H == nullptr || isfinite(static_cast<double>(H[i])));
     if (!fin) atomicOr(bad, 1);
-    if (fin && H[i] < z[i]) atomicOr(bad, 2);
+    if (H && fin && H[i] < z[i]) atomicOr(bad, 2);
   }
 }
 

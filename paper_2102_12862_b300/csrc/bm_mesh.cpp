@@ -178,13 +178,32 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
     m.z_min = std::min(m.z_min, z[t]);
   }
 
-  // 4. per-tile edge lists and per-cell slots
+  // 4. boundary / inflow lists (inflow edge j is coded kInflow - j)
+  std::vector<int32_t> code(E);
+  for (int64_t e = 0; e < E; ++e) {
+    if (gr[e] >= 0) {
+      code[e] = newid[gr[e]];
+      continue;
+    }
+    ++m.n_boundary;
+    if (gr[e] == kInflow) {
+      code[e] = kInflow - static_cast<int32_t>(m.in_cell.size());
+      m.in_cell.push_back(newid[gl[e]]);
+      m.in_len.push_back(glen[e]);
+      m.inflow_len += glen[e];
+    } else {
+      code[e] = static_cast<int32_t>(gr[e]);
+    }
+  }
+
+  // 5. per-tile edge lists and per-cell slots
   std::vector<int64_t> stamp(E, -1);
   std::vector<int32_t> pos(E, 0);
   m.eoff.assign(m.n_tiles + 1, 0);
   m.eL.reserve(E * 2);
   for (int64_t tile = 0; tile < m.n_tiles; ++tile) {
     int32_t cnt = 0;
+    bool has_boundary = false;
     m.eoff[tile] = static_cast<int64_t>(m.eL.size());
     for (int64_t i = tile * kTile; i < std::min(N, (tile + 1) * kTile); ++i) {
       int32_t t = m.perm[i];
@@ -195,10 +214,11 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
           stamp[e] = tile;
           pos[e] = cnt++;
           m.eL.push_back(newid[gl[e]]);
-          m.eR.push_back(gr[e] >= 0 ? newid[gr[e]] : static_cast<int32_t>(gr[e]));
+          m.eR.push_back(code[e]);
           m.enx.push_back(gnx[e]);
           m.eny.push_back(gny[e]);
           m.elen.push_back(glen[e]);
+          if (code[e] < 0) has_boundary = true;
         }
         uint64_t side_bit = (gl[e] == t) ? 0u : 1u;
         packed |= ((static_cast<uint64_t>(pos[e]) << 1) | side_bit) << (16 * k);
@@ -206,18 +226,9 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
       m.slots[i] = packed;
     }
     if (cnt > kMaxTileEdges) return fail(BM_EINVAL, "bm_mesh_create: internal tile overflow");
+    if (has_boundary) m.btiles.push_back(static_cast<int32_t>(tile));
   }
   m.eoff[m.n_tiles] = static_cast<int64_t>(m.eL.size());
-
-  // 5. boundary / inflow lists
-  for (int64_t e = 0; e < E; ++e) {
-    if (gr[e] < 0) ++m.n_boundary;
-    if (gr[e] == kInflow) {
-      m.in_cell.push_back(newid[gl[e]]);
-      m.in_len.push_back(glen[e]);
-      m.inflow_len += glen[e];
-    }
-  }
   m.n_inflow = static_cast<int64_t>(m.in_cell.size());
   return BM_OK;
 }

@@ -1,0 +1,159 @@
+// bm_state.h -- host-side objects behind the opaque handles of include/bm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "bm_internal.h"
+
+namespace bm {
+
+#define BM_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      std::ostringstream os_;                                                                  \
+      os_ << #call << ": " << cudaGetErrorString(e_);                                          \
+      return ::bm::fail(BM_ECUDA, os_.str());                                                  \
+    }                                                                                          \
+  } while (0)
+
+// Typed device buffer (owning).
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t alloc(size_t count) {
+    release();
+    n = count;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(&p, count * sizeof(T));
+  }
+  cudaError_t upload(const std::vector<T>& v) {
+    cudaError_t e = alloc(v.size());
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+// Per-precision state arrays of one instance (new cell numbering, padded).
+template <typename T>
+struct Buffers {
+  DBuf<T> H[2], Hlo[2], qx[2], qy[2], u[2], v[2], c[2];
+  DBuf<T> z, gn2, in_pw, in_hs;
+  cudaError_t alloc(size_t np, size_t n_inflow, bool derived) {
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = H[b].alloc(np);
+      if (e == cudaSuccess && !derived) e = Hlo[b].alloc(np);  // FP32-bulk keeps H as a pair
+      if (e == cudaSuccess) e = qx[b].alloc(np);
+      if (e == cudaSuccess) e = qy[b].alloc(np);
+      if (derived) {
+        if (e == cudaSuccess) e = u[b].alloc(np);
+        if (e == cudaSuccess) e = v[b].alloc(np);
+        if (e == cudaSuccess) e = c[b].alloc(np);
+      }
+    }
+    if (e == cudaSuccess) e = z.alloc(np);
+    if (e == cudaSuccess) e = in_pw.alloc(n_inflow > 0 ? n_inflow : 1);
+    if (e == cudaSuccess) e = in_hs.alloc(n_inflow > 0 ? n_inflow : 1);
+    // zero everything once so padding cells stay inert
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      DBuf<T>* bufs[7] = {&H[b], &Hlo[b], &qx[b], &qy[b], &u[b], &v[b], &c[b]};
+      for (auto* x : bufs)
+        if (e == cudaSuccess && x->p) e = cudaMemset(x->p, 0, x->bytes());
+    }
+    if (e == cudaSuccess) e = cudaMemset(in_pw.p, 0, in_pw.bytes());
+    if (e == cudaSuccess) e = cudaMemset(in_hs.p, 0, in_hs.bytes());
+    return e;
+  }
+  size_t bytes() const {
+    size_t b = z.bytes() + gn2.bytes() + in_pw.bytes() + in_hs.bytes();
+    for (int k = 0; k < 2; ++k)
+      b += H[k].bytes() + Hlo[k].bytes() + qx[k].bytes() + qy[k].bytes() + u[k].bytes() + v[k].bytes() +
+           c[k].bytes();
+    return b;
+  }
+};
+
+}  // namespace bm
+
+struct bm_mesh {
+  bm::HostMesh h;
+  int device = 0;
+  // FP64 device copies
+  bm::DBuf<double> z, inv_area, area, enx, eny, elen, in_len;
+  bm::DBuf<uint64_t> slots;
+  bm::DBuf<int64_t> eoff;
+  bm::DBuf<int32_t> eL, eR, in_cell, btiles, perm;
+  // FP32 geometry, built on first use by an FP32-bulk state
+  bool has32 = false;
+  bm::DBuf<float> inv_area32, enx32, eny32, elen32, in_len32;
+};
+
+struct bm_state {
+  const bm_mesh* mesh = nullptr;
+  bm_params prm{};
+  bm::Params p{};
+  int prec = BM_FP64;
+  double datum = 0.0;  // FP32-bulk: H and z are stored as offsets from it
+  std::vector<double> hydro_t, hydro_q;
+  bm::DBuf<double> d_hydro_t, d_hydro_q;
+  bm::Buffers<double> b64;
+  bm::Buffers<float> b32;
+  bm::DBuf<double> stage[3];  // caller-order staging for upload/download
+  bm::DBuf<double> vol_part, vol_out;
+  bm::DBuf<bm::TilePartial> part;
+  bm::DBuf<int> bad;
+  bm::DBuf<unsigned char> desc;   // one InstDesc<T> (device copy, for batches)
+  std::vector<unsigned char> hdesc;  // host copy of the descriptor
+  bm::DBuf<bm::WorkItem> work;       // the state's tiles as a work list of one instance
+  bm::Ctl* ctl = nullptr;   // device
+  bm::Ctl* hctl = nullptr;  // pinned host mirror
+  double* hvol = nullptr;   // pinned
+  int* hbad = nullptr;      // pinned
+  cudaStream_t stream = nullptr;  // stream the work is ordered on
+  cudaStream_t own = nullptr;     // private stream, also used for graph capture
+  std::map<int, cudaGraphExec_t> graphs;
+  double cur_t_end = 0.0;
+  int grid = 0;  // CTAs of the persistent step launch
+  template <typename T>
+  bm::Buffers<T>& buf();
+  ~bm_state() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    if (ctl) cudaFree(ctl);
+    if (hctl) cudaFreeHost(hctl);
+    if (hvol) cudaFreeHost(hvol);
+    if (hbad) cudaFreeHost(hbad);
+    if (own) cudaStreamDestroy(own);
+  }
+};
+
+template <>
+inline bm::Buffers<double>& bm_state::buf<double>() { return b64; }
+template <>
+inline bm::Buffers<float>& bm_state::buf<float>() { return b32; }
+
+namespace bm {
+const char* last_error();
+bm_status check_params(const bm_params* p);
+bm_status status_of(const Ctl& c);
+bm_status load_state(bm_state* s, const double* H, const double* qx, const double* qy, double t);
+void state_desc_bytes(bm_state* s, std::vector<unsigned char>* out);
+void launch_work(int prec, const void* descs, const WorkItem* work, int n_work, int grid, int prime,
+                 cudaStream_t st);
+}  // namespace bm

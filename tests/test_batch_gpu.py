@@ -1,0 +1,91 @@
+"""Batches: many uneven meshes stepped by one launch per step, each with its own dt.
+
+Each member of a batch must end bitwise equal to the same state stepped alone (the
+per-instance arithmetic and reduction order do not depend on the batch), for any
+launch shape; run_until stops each member exactly at its own end time.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_12862_b300 import bm
+from paper_2102_12862_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def scenarios():
+    return [
+        W.dam_break(),
+        W.floodplain(nx=90, ny=33, Lx=900.0, Ly=330.0, seed=51, q_peak=120.0, ramp=60.0),
+        W.random_state(W.dam_break(nx=37, ny=5, seed=52), seed=52),
+        W.fractal_lake(nx=30, ny=17, Lx=300.0, Ly=170.0, seed=53),
+        W.three_humps(nx=40, ny=16),
+    ]
+
+
+def states_for(scs, precision):
+    # the random state (index 2) needs the positivity time step; the others keep their own
+    return [bm.State.from_scenario(s, precision=precision, **({"cfl_mode": 1} if i == 2 else {}))
+            for i, s in enumerate(scs)]
+
+
+def equal_states(a, b):
+    for x, y in zip(a.download(), b.download()):
+        if not np.array_equal(np.asarray(x), np.asarray(y)):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("ctas_per_sm", [0, 2])
+def test_batch_equals_solo_bitwise(precision, ctas_per_sm):
+    scs = scenarios()
+    solo = states_for(scs, precision)
+    batched = states_for(scs, precision)
+    for s in solo:
+        s.set_launch(ctas_per_sm)
+        s.step(60)
+    b = bm.Batch(batched)
+    b.set_launch(ctas_per_sm)
+    b.step(60)
+    for k, (x, y) in enumerate(zip(solo, batched)):
+        assert x.stats()["steps"] == y.stats()["steps"] == 60
+        assert equal_states(x, y), f"member {k} differs from its solo run"
+
+
+def test_batch_run_until_per_member_end_times():
+    scs = scenarios()
+    sts = states_for(scs, "fp64")
+    b = bm.Batch(sts)
+    t_end = np.array([3.0, 40.0, 0.5, 7.0, 2.0])
+    b.run_until(t_end)
+    for k, st in enumerate(sts):
+        assert st.stats()["t"] == t_end[k]
+    # member 1 against the oracle
+    o = oracle.Oracle(scs[1])
+    o.run_until(t_end[1])
+    H, qx, qy, t = sts[1].download()
+    rel = np.max(np.abs(H - o.H)) / np.max(np.abs(o.H))
+    assert rel < 1e-11
+    assert sts[1].stats()["steps"] == o.steps
+
+
+def test_launch_shape_does_not_change_results():
+    s = W.floodplain(nx=200, ny=80, Lx=2000.0, Ly=800.0, seed=54)
+    a = bm.State.from_scenario(s)
+    b = bm.State.from_scenario(s)
+    b.set_launch(1)
+    a.step(40)
+    b.step(40)
+    assert equal_states(a, b)
+
+
+def test_batch_rejects_mixed_precision_and_duplicates():
+    s = W.dam_break(nx=10, ny=2)
+    x = bm.State.from_scenario(s)
+    y = bm.State.from_scenario(s, precision="fp32")
+    with pytest.raises(bm.BMError, match="precision"):
+        bm.Batch([x, y])
+    with pytest.raises(bm.BMError, match="twice"):
+        bm.Batch([x, x])
