@@ -248,6 +248,30 @@ bm_status bm_server_wait(bm_server* sv, uint64_t ticket, double timeout_s);
 bm_status bm_server_stats(bm_server* sv, int64_t* queued, int64_t* running, int64_t* completed,
                           double* cell_updates, double* resident_bytes);
 
+/*
+ * Water volume V = sum_i area_i (H_i - z_i) over caller-owned device arrays, computed
+ * without allocating any device memory.  The paper has no counterpart: this exists
+ * for callers that cannot call cudaMalloc -- applications whose device memory is
+ * entirely handed to their own pool allocator (a stray cudaMalloc would fail or
+ * fragment it) and loops that cannot afford cudaMalloc/cudaFree's implicit device
+ * synchronisation.  It runs the library's volume reduction with its partial sums
+ * in a fixed scratch array compiled into the library (64 KiB, held on every device
+ * that loads the library until the process exits).
+ *   H, z, area  n_cells doubles each, device memory, any cell order.
+ *   volume      device pointer receiving the result (one double).
+ *   cuda_stream the stream the two kernels are queued on (NULL = legacy default);
+ *               the call returns without waiting for them.
+ * Limits and behaviour: n_cells up to 2,097,152 (BM_EINVAL beyond, before any device
+ * work); n_cells = 0 writes 0.  The first call on a device looks the scratch array up
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last call's
+ * partials; every call overwrites what it reads, so nothing needs clearing, but two
+ * calls whose kernels overlap on the GPU race and can return wrong sums -- order
+ * them on one stream or synchronise in between.
+ */
+bm_status bm_volume_noalloc(const double* H, const double* z, const double* area, int64_t n_cells, double* volume,
+                            void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

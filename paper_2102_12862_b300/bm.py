@@ -73,6 +73,7 @@ SIGNATURES = {
     "bm_batch_run_until": (C.c_int, [_vp, _P(_d)]),
     "bm_state_autotune": (C.c_int, [_vp, C.c_int, _P(C.c_int), _P(_d)]),
     "bm_batch_autotune": (C.c_int, [_vp, C.c_int, _P(C.c_int), _P(_d)]),
+    "bm_volume_noalloc": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "bm_server_opts_default": (None, [_P(bm_server_opts)]),
     "bm_server_create": (C.c_int, [_P(bm_server_opts), _P(_vp)]),
     "bm_server_destroy": (None, [_vp]),
@@ -227,6 +228,11 @@ def bm_step_timed(state: int, n_steps: int) -> tuple[float, float]:
 
 def bm_state_set_launch(state: int, ctas_per_sm: int):
     _check(load_library().bm_state_set_launch(state, int(ctas_per_sm)))
+
+
+def bm_volume_noalloc(H_dev: int, z_dev: int, area_dev: int, n_cells: int, volume_dev: int, stream_ptr: int = 0):
+    """Volume of caller-owned device arrays (raw device pointers), no device allocation."""
+    _check(load_library().bm_volume_noalloc(H_dev, z_dev, area_dev, int(n_cells), volume_dev, stream_ptr or None))
 
 
 def bm_state_autotune(state: int, steps_per_trial: int = 20) -> tuple[int, float]:

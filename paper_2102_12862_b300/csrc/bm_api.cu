@@ -10,6 +10,7 @@
 #include <cstring>
 #include <limits>
 #include <map>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -756,6 +757,69 @@ bm_status bm_state_autotune(bm_state* s, int steps_per_trial, int* best_ctas_per
       [&](int n) { return enqueue_steps(s, n); }, s->stream);
   if (st == BM_OK && keep_end != kInf) st = set_end(s, keep_end);
   return st;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- volume without allocation
+
+namespace bm {
+namespace {
+
+// Scratch for bm_volume_noalloc: one partial sum per 256-cell block.  It lives in the
+// library image (64 KiB per device that loads the library, held until exit), so the
+// entry point never allocates.  Every call overwrites the partials it reads, so
+// nothing has to start at zero; calls that overlap on the GPU share it and race.
+constexpr int kNoallocPartials = 8192;
+constexpr int64_t kNoallocMaxCells = static_cast<int64_t>(kNoallocPartials) * kTile;
+static __device__ __align__(256) double g_noalloc_partials[kNoallocPartials];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once per
+// device; host code must not use the symbol itself as a device pointer).
+bm_status noalloc_scratch(double** out) {
+  int dev = 0;
+  BM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(BM_EINVAL, "bm_volume_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess)
+      return fail(BM_ECUDA, std::string("bm_volume_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return BM_OK;
+}
+
+}  // namespace
+}  // namespace bm
+
+extern "C" {
+
+bm_status bm_volume_noalloc(const double* H, const double* z, const double* area, int64_t n_cells, double* volume,
+                            void* cuda_stream) {
+  clear_error();
+  if (n_cells < 0) return fail(BM_EINVAL, "bm_volume_noalloc: n_cells must be >= 0");
+  if (n_cells > kNoallocMaxCells)
+    return fail(BM_EINVAL, "bm_volume_noalloc: n_cells exceeds the fixed scratch limit of 2,097,152 cells");
+  if (!volume) return fail(BM_EINVAL, "bm_volume_noalloc: volume is NULL");
+  if (n_cells > 0 && (!H || !z || !area)) return fail(BM_EINVAL, "bm_volume_noalloc: NULL input array");
+  double* scratch = nullptr;
+  bm_status st = noalloc_scratch(&scratch);
+  if (st != BM_OK) return st;
+  cudaStream_t stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : cudaStreamLegacy;
+  const int nb = static_cast<int>((n_cells + kTile - 1) / kTile);
+  if (nb > 0)
+    volume_partials<double><<<nb, kTile, 0, stream>>>(H, nullptr, z, area, nullptr, static_cast<int>(n_cells),
+                                                      scratch);
+  sum_partials<<<1, kSumThreads, 0, stream>>>(scratch, nb, volume);
+  BM_CUDA(cudaGetLastError());
+  return BM_OK;
 }
 
 }  // extern "C"
