@@ -2,25 +2,30 @@
 """Throughput of the explicit shallow-water step (cell-updates/s) on one B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision fp64|fp32]
 
 Workload: the single-floodplain configuration -- 5 km x 2 km, 1600 x 625 jittered
 quads = 2,000,000 triangles, seeded sinusoid + noise bed 400 m above datum,
 64-patch Manning map, a 2 m deep meandering main channel (the rest dry), inflow
 hydrograph 0 -> 500 m^3/s over 600 s on the upstream side, transmissive outlet,
-walls.  Synthetic inputs from paper_2102_12862_b300.workloads (seed 2).
+walls, positivity time step.  Synthetic inputs from paper_2102_12862_b300.workloads
+(seed 2).
 
 A step is one pass of the whole hot path over all cells (edge fluxes, update,
-friction, dt reduction, time advance).  W untimed warm-up steps run from t = 0,
-then K steps are timed with CUDA events on the stream the kernels run on.  The
-working set (about 0.5 GB in FP64) is larger than the 126 MB L2, so no flush is
-needed between steps.  Under torchrun every rank steps its own replica of the
-workload (the path has no exchange between independent runs: replicas only,
-weak scaling); value = all ranks' cell-updates / the slowest rank's time.
+friction, dt reduction, time advance: one kernel launch).  The line's `value` is
+the plain FP64 step; `fp32_bulk` repeats every measurement for the FP32-bulk
+precision mode on the same workload.  Each: W untimed warm-up steps from t = 0,
+then K steps timed with CUDA events on the stream the kernels run on.  The working
+set (0.3-0.5 GB) is larger than the 126 MB L2, so no flush is needed.  Under
+torchrun every rank steps its own replica (no exchange between independent runs:
+replicas only, weak scaling); value = all ranks' cell-updates / the slowest rank's
+time.
 
---impl reference times the FP64 CPU oracle (the serial edge-loop program the
-CUDA path is checked against) on the host cores, one oracle step of the same
-workload per step.
+Accuracy: the end-to-end leg (upload, E steps from t = 0, download through the C
+ABI with pinned host buffers) is compared with the FP64 CPU oracle run for the same
+E steps, which is also the timed CPU baseline.
+
+--impl reference times that oracle alone (serial C on the host cores) on the same
+workload and metric.
 """
 from __future__ import annotations
 
@@ -47,19 +52,28 @@ FP64_FLOPS_PER_CELL_UPDATE = 213.0
 # on this B300 (2 per SM), x 2 FLOP x the 2.032 GHz maximum SM clock.
 FP64_PEAK_TFLOPS = 296 * 2 * 2.032e9 / 1e12
 HBM_FALLBACK_GBS = 6400.0
+KERNEL_NAME = {"fp64": "step_batch<double,true>", "fp32": "step_batch<float,false>"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--e2e-steps", type=int, default=50, help="steps per end-to-end call")
     ap.add_argument("--e2e-iters", type=int, default=3)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle (and the accuracy check)")
+    ap.add_argument("--precisions", default="fp64,fp32")
+    ap.add_argument("--workload", choices=["floodplain", "ensemble", "serve"], default="floodplain",
+                    help="floodplain: the default line; ensemble: batched uneven meshes; serve: request loop")
+    ap.add_argument("--instances", type=int, default=256, help="ensemble members")
+    ap.add_argument("--requests", type=int, default=200, help="serving trace length")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving arrivals per second (Poisson)")
+    ap.add_argument("--time-scale", type=float, default=0.1,
+                    help="serving: requested simulated durations U[600, 7200] s are scaled by this")
+    ap.add_argument("--mesh-pool", type=int, default=16, help="serving: distinct meshes reused by requests")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp32", help="ensemble / serve precision")
     return ap.parse_args()
 
 
@@ -73,7 +87,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("bm_kernels.cuh", "bm_api.cu", "bm_internal.h"):
+    for f in ("bm_kernels.cuh", "bm_internal.h"):
         with open(os.path.join(ROOT, "paper_2102_12862_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -152,22 +166,37 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_baseline_sample(seconds: float, rank: int):
-    """Time the FP64 oracle, as it stands, on the floodplain workload from t = 0."""
-    import oracle
-    from paper_2102_12862_b300 import workloads as W
-    s = W.floodplain()
-    o = oracle.Oracle(s)
-    t0 = time.perf_counter()
-    o.step(1)
-    one = time.perf_counter() - t0
-    n = max(1, min(200, int(seconds / max(one, 1e-6))))
-    t0 = time.perf_counter()
-    o.step(n)
-    dt = time.perf_counter() - t0
-    return {"value": s.n_cells * n / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"serial FP64 oracle (gcc -O2 -ffp-contract=off), {n} steps of the 2,000,000-cell "
-                      f"floodplain from t = 0 after 1 untimed step, {dt:.1f} s wall"}
+def replica_aggregate(dist, n_cells_local: float, steps: int, ms_local: float, device=None) -> tuple[float, float]:
+    """Replicas only: each rank stepped its own copy of the workload.  Returns the
+    slowest rank's time and the whole-job rate (all ranks' cell-updates / that time)."""
+    if dist is None:
+        return ms_local, n_cells_local * steps / (ms_local / 1e3)
+    import torch
+    t = torch.tensor([ms_local, n_cells_local], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    tot = t.clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms_max = float(mx[0].item())
+    return ms_max, float(tot[1].item()) * steps / (ms_max / 1e3)
+
+
+def errors_vs_oracle(s, H, qx, qy, o) -> dict:
+    """L1 / L-inf of depth and velocity, relative mass defect of the GPU state vs the oracle."""
+    area = o.area()
+    h, ho = H - s.z, o.H - s.z
+    wet = (ho > 1e-3) & (h > 1e-3)
+    du = np.abs(qx[wet] / h[wet] - o.qx[wet] / ho[wet]) if wet.any() else np.zeros(1)
+    dv = np.abs(qy[wet] / h[wet] - o.qy[wet] / ho[wet]) if wet.any() else np.zeros(1)
+    vo = float(np.sum(area * ho))
+    return {"l1_h_m": float(np.sum(area * np.abs(h - ho)) / area.sum()),
+            "linf_h_m": float(np.max(np.abs(h - ho))),
+            "rel_linf_h": float(np.max(np.abs(h - ho)) / max(np.max(np.abs(ho)), 1e-300)),
+            "rel_linf_hu": float(np.max(np.abs(qx - o.qx)) / max(np.max(np.abs(o.qx)), 1e-300)),
+            "rel_linf_hv": float(np.max(np.abs(qy - o.qy)) / max(np.max(np.abs(o.qy)), 1e-300)),
+            "l1_vel_ms": float(np.mean(np.hypot(du, dv))),
+            "linf_vel_ms": float(max(du.max(), dv.max())),
+            "rel_mass_vs_oracle": abs(float(np.sum(area * h)) - vo) / max(abs(vo), 1e-300)}
 
 
 def run_reference(args, ws, rank):
@@ -190,30 +219,18 @@ def run_reference(args, ws, rank):
             "requested_steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / k,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "floodplain 2,000,000 triangles, FP64, oracle from t = 0", "cells": s.n_cells},
+            "config": {"workload": "floodplain 2,000,000 triangles, FP64 oracle, steps from t = 0",
+                       "cells": s.n_cells},
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{k} oracle steps of the full workload from t = 0 (bounded to about 2 min)"},
+                             "sample": f"{k} oracle steps of the full workload after {args.warmup} warm-up steps "
+                                       f"(bounded to about 2 min)"},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def main():
-    args = parse()
-    ws, rank, local = dist_env()
-    if args.impl == "reference":
-        return run_reference(args, ws, rank)
-
-    import torch
-    from paper_2102_12862_b300 import bm
-    from paper_2102_12862_b300 import workloads as W
-
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
-
+def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
+    """Timed steps, per-kernel timing, roofline and the end-to-end leg of one precision."""
     def barrier():
         if dist is not None:
             dist.barrier()
@@ -225,15 +242,14 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    s = W.floodplain()
-    mesh = bm.Mesh.from_scenario(s)
-    st = bm.State.from_scenario(s, mesh=mesh, precision=args.precision)
+    n = s.n_cells
+    st = bm.State.from_scenario(s, mesh=mesh, precision=prec)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     st.set_stream(stream.cuda_stream)
     st.step(args.warmup)
-    wet_before = None
-
+    H0, _, _, _ = st.download()
+    wet0 = float(np.mean(H0 - s.z > 1e-6))
     clocks = ClockSampler(torch.cuda.current_device())
     barrier()
     torch.cuda.synchronize()
@@ -248,34 +264,33 @@ def main():
     barrier()
     clk = clocks.stop()
     st.sync()
-    ms = e0.elapsed_time(e1)
-    ms_max = allmax(ms)
-    n = s.n_cells
-    value = n * args.steps * ws / (ms_max / 1e3)
+    ms_max, value = replica_aggregate(dist, n, args.steps, e0.elapsed_time(e1), device="cuda")
     stats = st.stats()
+    H1, _, _, _ = st.download()
+    wet1 = float(np.mean(H1 - s.z > 1e-6))
 
     # dominant kernel: average duration of the step kernel, events around each launch
     nk = min(args.steps, 200)
-    k_ms, tot_ms = st.step_timed(nk)
+    k_ms, _ = st.step_timed(nk)
     kern_s = k_ms / nk / 1e3
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
-    prec = args.precision
     bytes_launch = BYTES_PER_CELL_UPDATE[prec] * n
-    traffic = ncu_traffic(prec)
     hbm_gbs = bytes_launch / kern_s / 1e9
+    traffic = ncu_traffic(prec)
     if prec == "fp64":
-        flops = FP64_FLOPS_PER_CELL_UPDATE * n
-        achieved = flops / kern_s / 1e12
+        achieved = FP64_FLOPS_PER_CELL_UPDATE * n / kern_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "ncu peak_sustained 296 DFMA/cycle x 2 x 2.032 GHz (no FP64 figure in MEASURED_PEAKS.json)",
-                "kernel": "step_batch<double,true>", "kernel_ms": kern_s * 1e3,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": KERNEL_NAME[prec],
+                "kernel_ms": kern_s * 1e3,
+                "peak_source": "ncu peak_sustained 296 DFMA/cycle x 2 x 2.032 GHz (no FP64 figure in "
+                               "MEASURED_PEAKS.json)",
                 "hbm": {"achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
                         "algorithmic_bytes_per_launch": bytes_launch}}
     else:
         roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
-                "traffic": traffic, "kernel": "step_batch<float,false>", "kernel_ms": kern_s * 1e3,
+                "traffic": traffic, "kernel": KERNEL_NAME[prec], "kernel_ms": kern_s * 1e3,
+                "algorithmic_bytes_per_launch": bytes_launch,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
 
     # end to end through the C ABI with pinned host buffers: upload, E steps, download
@@ -297,24 +312,169 @@ def main():
     e2e = {"value": n * E * ws / e2e_t, "unit": METRIC, "h2d_bytes_per_step": 3 * 8 * n / E,
            "d2h_bytes_per_step": 3 * 8 * n / E,
            "call": f"bm_state_upload + bm_step({E}) + bm_state_download, pinned host arrays"}
+    final = (Ho.copy(), qxo.copy(), qyo.copy())
+    out = {"value": value, "ms_per_step": ms_max / args.steps, "roofline": roof, "e2e": e2e, "clocks": clk,
+           "gpu_launches": args.steps, "sim_time_s": stats["t"], "wet_fraction": [wet0, wet1]}
+    st.close()
+    return out, final
 
-    cpu = None
+
+def run_ensemble(args, ws, rank, torch, bm, W):
+    """Batched ensemble: args.instances floodplain-recipe meshes, log-uniform sizes in
+    [5k, 500k] triangles (member k seeded 5000 + k), stepped together by one launch
+    per step, each with its own dt."""
+    scs = [W.ensemble_instance(k) for k in range(args.instances)]
+    meshes = [bm.Mesh.from_scenario(s) for s in scs]
+    sts = [bm.State.from_scenario(s, mesh=m, precision=args.precision) for s, m in zip(scs, meshes)]
+    b = bm.Batch(sts)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    b.set_stream(stream.cuda_stream)
+    best, _ = b.autotune(5)
+    b.step(args.warmup)
+    cells = sum(s.n_cells for s in scs)
+    clocks = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step_async(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    b.sync()
+    ms = e0.elapsed_time(e1)
+    value = cells * args.steps / (ms / 1e3)
+    # every member to 600 s of simulated time (per-member dt), timed as one job
+    t0 = time.perf_counter()
+    b.run_until(600.0)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    upd = sum(st.stats(volume=False)["steps"] * sc.n_cells for st, sc in zip(sts, scs)) - cells * (args.steps + args.warmup)
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": f"batched ensemble, {args.instances} floodplain-recipe meshes, log-uniform "
+                                   f"5k-500k triangles, one launch per step, per-member dt",
+                       "members": args.instances, "cells": cells, "precision": args.precision,
+                       "ctas_per_sm": best, "l2": "working set > L2, no flush"},
+            "run_until_600s": {"wall_s": wall, "cell_updates_per_s": upd / wall},
+            "gpu_launches": args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args, ws, rank, torch, bm, W):
+    """Request loop: Poisson arrivals at args.rate per second of flood scenarios on a
+    pool of meshes (sizes log-uniform in [10k, 2M] triangles), each run for a
+    duration drawn from U[600, 7200] s x time_scale; bounded trace of args.requests
+    arrivals, then drained.  Reports p50 / p99 time-to-result and the throughput."""
+    rng = np.random.default_rng(6)
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(2e6), args.mesh_pool)).astype(int)
+    pool = [W.ensemble_instance(1000 + k, size_override=int(n)) for k, n in enumerate(sizes)]
+    meshes = [bm.Mesh.from_scenario(s) for s in pool]
+    sv = bm.Server(precision=args.precision, steps_per_round=32)
+    gaps = rng.exponential(1.0 / args.rate, args.requests)
+    picks = rng.integers(0, args.mesh_pool, args.requests)
+    t_ends = rng.uniform(600.0, 7200.0, args.requests) * args.time_scale
+    tickets = []
+    t_start = time.perf_counter()
+    next_t = t_start
+    for k in range(args.requests):
+        next_t += gaps[k]
+        while time.perf_counter() < next_t:
+            time.sleep(min(0.001, max(0.0, next_t - time.perf_counter())))
+        sc = pool[picks[k]]
+        tickets.append(sv.submit(meshes[picks[k]], sc.H, sc.qx, sc.qy, t_end=float(t_ends[k]), **sc.params))
+    lat = []
+    for tk in tickets:
+        r = sv.wait(tk, 3600.0)
+        lat.append(r[3])
+    wall = time.perf_counter() - t_start
+    st = sv.stats()
+    sv.close()
+    line = {"metric": "p50/p99 time-to-result", "value": float(np.percentile(lat, 50)), "unit": "s",
+            "p99_s": float(np.percentile(lat, 99)), "n_gpus": ws, "steps": None, "warmup": 0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": f"serving: {args.requests} Poisson arrivals at {args.rate}/s, {args.mesh_pool}-mesh "
+                                   f"pool log-uniform 10k-2M triangles, durations U[600, 7200] s x {args.time_scale}",
+                       "precision": args.precision},
+            "throughput": {"value": st["cell_updates"] / wall, "unit": METRIC, "wall_s": wall,
+                           "completed": st["completed"]},
+            "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    if args.workload != "floodplain":
+        import torch
+        from paper_2102_12862_b300 import bm
+        from paper_2102_12862_b300 import workloads as W
+        torch.cuda.set_device(local)
+        fn = run_ensemble if args.workload == "ensemble" else run_serve
+        return fn(args, ws, rank, torch, bm, W) if rank == 0 or ws == 1 else 0
+
+    import torch
+    from paper_2102_12862_b300 import bm
+    from paper_2102_12862_b300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+
+    s = W.floodplain()
+    mesh = bm.Mesh.from_scenario(s)
+    precs = [p for p in args.precisions.split(",") if p]
+    res, finals = {}, {}
+    for p in precs:
+        res[p], finals[p] = measure(args, p, s, mesh, torch, bm, dist, ws, rank)
+
+    cpu, acc = None, {}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(args.cpu_seconds, rank)
+        import oracle
+        o = oracle.Oracle(s)
+        t0 = time.perf_counter()
+        o.step(args.e2e_steps)
+        dt = time.perf_counter() - t0
+        cpu = {"value": s.n_cells * args.e2e_steps / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": f"serial FP64 oracle (gcc -O2 -ffp-contract=off), the first {args.e2e_steps} steps of "
+                         f"the 2,000,000-cell floodplain from t = 0, {dt:.1f} s wall"}
+        for p in precs:
+            acc[p] = errors_vs_oracle(s, *finals[p], o)
+            acc[p]["steps"] = args.e2e_steps
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64",
+        main_p = precs[0]
+        r = res[main_p]
+        line = {"metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_p == "fp64" else "f32+f64",
                 "data": "synthetic",
-                "config": {"workload": f"floodplain 2,000,000 triangles, {prec.upper()}, steps from t = 0 "
-                                       f"after {args.warmup} warm-up steps", "cells": n,
-                           "edges": mesh.info["n_edges"], "precision": prec,
+                "config": {"workload": f"floodplain 2,000,000 triangles, {main_p.upper()}, K steps from t = 0 after "
+                                       f"{args.warmup} warm-up steps", "cells": s.n_cells,
+                           "edges": mesh.info["n_edges"], "precision": main_p,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                           "l2": "working set > 126 MB L2, no flush",
-                           "sim_time_s": stats["t"], "e2e_steps_per_call": E},
-                "roofline": roof, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk,
-                "cpu_baseline": cpu}
+                           "l2": "working set > 126 MB L2, no flush", "sim_time_s": r["sim_time_s"],
+                           "wet_fraction_first_last": r["wet_fraction"], "e2e_steps_per_call": args.e2e_steps},
+                "roofline": r["roofline"], "e2e": r["e2e"], "gpu_launches": r["gpu_launches"],
+                "clocks": r["clocks"], "cpu_baseline": cpu, "accuracy_vs_oracle": acc.get(main_p)}
+        for p in precs[1:]:
+            q = res[p]
+            key = "fp32_bulk" if p == "fp32" else p
+            line[key] = {"value": q["value"], "unit": METRIC, "ms_per_step": q["ms_per_step"],
+                         "dtype": "f32+f64" if p == "fp32" else "f64", "roofline": q["roofline"], "e2e": q["e2e"],
+                         "clocks": q["clocks"], "gpu_launches": q["gpu_launches"], "sim_time_s": q["sim_time_s"],
+                         "wet_fraction_first_last": q["wet_fraction"], "accuracy_vs_oracle": acc.get(p)}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -323,6 +323,10 @@ bm_status alloc_state(bm_state* s, const bm_params* prm) {
   p.hydro_n = static_cast<int>(prm->hydro_n);
   p.hydro_t = s->d_hydro_t.p;
   p.hydro_q = s->d_hydro_q.p;
+  p.g_f = static_cast<float>(prm->g);
+  p.hg_f = static_cast<float>(0.5 * prm->g);
+  p.hmin_f = static_cast<float>(prm->h_min);
+  p.pad_f = 0.0f;
   state_desc_bytes(s, &s->hdesc);
   std::vector<WorkItem> work(h.n_tiles);
   for (int64_t t = 0; t < h.n_tiles; ++t) work[t] = WorkItem{0, static_cast<int>(t)};

@@ -57,6 +57,7 @@ __global__ void batch_set_t_end(Ctl* const* ctl, const double* t_end, int n) {
     clipped = 1;
   }
   c->dt = dt;
+  c->dt_f = static_cast<float>(dt);
   c->clipped = clipped;
   c->active = c->t < te ? 1 : 0;
 }

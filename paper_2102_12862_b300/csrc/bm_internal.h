@@ -69,6 +69,8 @@ struct Ctl {
   int clipped;     // dt^n was clipped to t_end - t^n
   int wpos;        // wsum > 0
   int status;      // bit 0: non-finite value, bit 1: negative depth
+  float dt_f;      // dt and quni rounded once for FP32-bulk steps
+  float quni_f;
 };
 
 // One work item of a step launch: (instance, tile).
@@ -90,6 +92,7 @@ struct Params {
   int hydro_n;
   const double* hydro_t;
   const double* hydro_q;
+  float g_f, hg_f, hmin_f, pad_f;  // g, g/2, h_min rounded once for FP32-bulk steps
 };
 
 }  // namespace bm

@@ -277,17 +277,29 @@ __device__ void finalize_instance(const InstDesc<T>& a, int advance, double* sre
       clipped = 1;
     }
     ctl->dt = dt;
+    ctl->dt_f = static_cast<float>(dt);
     ctl->clipped = clipped;
     ctl->active = t < ctl->t_end ? 1 : 0;
     ctl->Q = Q;
     ctl->qscale = qscale;
     ctl->quni = quni;
+    ctl->quni_f = static_cast<float>(quni);
     ctl->wpos = wpos ? 1 : 0;
     ctl->done = 0u;
   }
 }
 
 // ------------------------------------------------------------------ step kernel
+
+// Step constants in the working precision (read, not converted, per thread).
+__device__ __forceinline__ void step_consts(const Ctl* c, const Params& p, double& dt, double& quni, double& g,
+                                            double& hg, double& hmin) {
+  dt = c->dt; quni = c->quni; g = p.g; hg = 0.5 * p.g; hmin = p.h_min;
+}
+__device__ __forceinline__ void step_consts(const Ctl* c, const Params& p, float& dt, float& quni, float& g,
+                                            float& hg, float& hmin) {
+  dt = c->dt_f; quni = c->quni_f; g = p.g_f; hg = p.hg_f; hmin = p.hmin_f;
+}
 
 // Shared memory of one CTA (dynamic): the tile's cells, its edges' geometry and
 // fluxes, reduction scratch.
@@ -298,9 +310,9 @@ struct TileSmem {
   T Nx[kMaxTileEdges], Ny[kMaxTileEdges], Ln[kMaxTileEdges];
   int32_t Code[kMaxTileEdges];
   double red[kTile / 32];
-  T redT[kTile / 32];
   double bc[2];
-  int last;
+  unsigned long long rbits;  // max Eq. 21 rate of the tile (bits of a value >= 0)
+  int anyb;                  // the tile has boundary edges
 };
 
 // One (instance, tile) work item.  T = double: every array and operation in FP64;
@@ -317,13 +329,12 @@ __device__ __forceinline__ void tile_step(const InstDesc<T>& a, const int tile, 
   Ctl* ctl = a.ctl;
   // round 1: control block and the tile's edge range
   const int par = ctl->parity;
-  const T dt = static_cast<T>(ctl->dt);
+  T dt, quni, g, hg, hmin;
+  step_consts(ctl, a.p, dt, quni, g, hg, hmin);
   const double qscale = ctl->qscale;
-  const T quni = static_cast<T>(ctl->quni);
   const int wpos = ctl->wpos;
   const int64_t e0 = a.eoff[tile];
   const int ne = static_cast<int>(a.eoff[tile + 1] - e0);
-  const T g = static_cast<T>(a.p.g), hg = static_cast<T>(0.5 * a.p.g), hmin = static_cast<T>(a.p.h_min);
   const T* __restrict__ HH = a.H[par];
   const T* __restrict__ HL = kPair ? a.Hlo[par] : nullptr;
   const T* __restrict__ QX0 = a.qx[par];
@@ -365,71 +376,90 @@ __device__ __forceinline__ void tile_step(const InstDesc<T>& a, const int tile, 
   if (!prime) {
     auto edge = [&](const int k, const int gL, const int gR, const T nx, const T ny, const T l) {
       sm.Nx[k] = nx; sm.Ny[k] = ny; sm.Ln[k] = l; sm.Code[k] = gR;
-      T HLh, HLl, zL, uL, vL, cL;
+      // surfaces and beds of both sides (the right side mirrors the left at a boundary)
       const int lL = gL - base;
-      if (static_cast<unsigned>(lL) < static_cast<unsigned>(kTile)) {
-        HLh = sm.Hh[lL]; HLl = sm.Hl[lL]; zL = sm.Z[lL]; uL = sm.U[lL]; vL = sm.V[lL]; cL = sm.C[lL];
+      const bool inL = static_cast<unsigned>(lL) < static_cast<unsigned>(kTile);
+      T HLh, HLl, zL;
+      if (inL) {
+        HLh = sm.Hh[lL]; HLl = sm.Hl[lL]; zL = sm.Z[lL];
       } else {
         HLh = HH[gL]; HLl = kPair ? HL[gL] : zero; zL = Z[gL];
-        if (kDerived) {
+      }
+      const int lR = gR - base;
+      const bool inR = gR >= 0 && static_cast<unsigned>(lR) < static_cast<unsigned>(kTile);
+      T HRh = HLh, HRl = HLl, zR = zL;
+      if (gR >= 0) {
+        if (inR) {
+          HRh = sm.Hh[lR]; HRl = sm.Hl[lR]; zR = sm.Z[lR];
+        } else {
+          HRh = HH[gR]; HRl = kPair ? HL[gR] : zero; zR = Z[gR];
+        }
+      }
+      // modified states (hydrostatic reconstruction on the higher bed)
+      const T zs = fmax(zL, zR);
+      const T h1 = fmax(zero, depth_of(HLh, HLl, zs));
+      const T h2 = fmax(zero, depth_of(HRh, HRl, zs));
+      T F0 = zero, F2 = zero, GL = zero, GR = zero;
+      // with both modified depths zero every contribution is exactly zero: skip the
+      // flux (warps whose edges are all dry do no flux arithmetic); inflow edges
+      // always impose their discharge
+      if (h1 > zero || h2 > zero || gR <= kInflow) {
+        T uL, vL, cL;
+        if (inL) {
+          uL = sm.U[lL]; vL = sm.V[lL]; cL = sm.C[lL];
+        } else if (kDerived) {
           uL = a.u[par][gL]; vL = a.v[par][gL]; cL = a.c[par][gL];
         } else {
           cell_derived<T>(depth_of(HLh, HLl, zL), QX0[gL], QY0[gL], hmin, g, uL, vL, cL);
         }
-      }
-      const T unL = uL * nx + vL * ny, utL = -uL * ny + vL * nx;
-      T h1, h2, un2, ut2, c1, c2;
-      if (gR >= 0) {
-        T HRh, HRl, zR, uR, vR, cR;
-        const int lR = gR - base;
-        if (static_cast<unsigned>(lR) < static_cast<unsigned>(kTile)) {
-          HRh = sm.Hh[lR]; HRl = sm.Hl[lR]; zR = sm.Z[lR]; uR = sm.U[lR]; vR = sm.V[lR]; cR = sm.C[lR];
-        } else {
-          HRh = HH[gR]; HRl = kPair ? HL[gR] : zero; zR = Z[gR];
-          if (kDerived) {
+        const T unL = uL * nx + vL * ny, utL = -uL * ny + vL * nx;
+        T un2, ut2, c1, c2;
+        if (gR >= 0) {
+          T uR, vR, cR;
+          if (inR) {
+            uR = sm.U[lR]; vR = sm.V[lR]; cR = sm.C[lR];
+          } else if (kDerived) {
             uR = a.u[par][gR]; vR = a.v[par][gR]; cR = a.c[par][gR];
           } else {
             cell_derived<T>(depth_of(HRh, HRl, zR), QX0[gR], QY0[gR], hmin, g, uR, vR, cR);
           }
+          // the side with the higher bed keeps its own depth, hence its own celerity
+          const bool lhi = zL >= zR;
+          const T clo = f_sqrt(g * (lhi ? h2 : h1));
+          c1 = lhi ? cL : clo;
+          c2 = lhi ? clo : cR;
+          un2 = uR * nx + vR * ny;
+          ut2 = -uR * ny + vR * nx;
+        } else {
+          c1 = cL;
+          c2 = cL;
+          un2 = (gR == kWall) ? -unL : unL;  // wall: mirrored normal velocity
+          ut2 = utL;
         }
-        const T zs = fmax(zL, zR);
-        h1 = fmax(zero, depth_of(HLh, HLl, zs));
-        h2 = fmax(zero, depth_of(HRh, HRl, zs));
-        // the side with the higher bed keeps its own depth, hence its own celerity
-        const bool lhi = zL >= zR;
-        const T clo = f_sqrt(g * (lhi ? h2 : h1));
-        c1 = lhi ? cL : clo;
-        c2 = lhi ? clo : cR;
-        un2 = uR * nx + vR * ny;
-        ut2 = -uR * ny + vR * nx;
-      } else {
-        h1 = fmax(zero, depth_of(HLh, HLl, zL));
-        h2 = h1;
-        c1 = cL;
-        c2 = cL;
-        un2 = (gR == kWall) ? -unL : unL;  // wall: mirrored normal velocity
-        ut2 = utL;
-      }
-      T F0, F1, F2, pL, pR;
-      hllc<T>(h1, unL, utL, c1, h2, un2, ut2, c2, hg, F0, F1, F2, pL, pR);
-      T GL = F1 - pL, GR = F1 - pR;
-      if (gR < 0) {
-        if (gR == kWall) {
-          F0 = zero; F2 = zero;  // impermeable, frictionless
-        } else if (gR <= kInflow) {
-          const int j = kInflow - gR;
-          const T q = wpos ? static_cast<T>(qscale * static_cast<double>(a.in_pw[j])) : quni;
-          if (q > zero) {
-            const T hcr = f_cbrt(f_div(q * q, g));
-            const T hb = fmax(h1, hcr);
-            F0 = -q;
-            GL = f_div(q * q, hb) + hg * hb * hb - pL;
-          } else {
-            F0 = zero;
-            GL = zero;
+        T F1, pL, pR;
+        hllc<T>(h1, unL, utL, c1, h2, un2, ut2, c2, hg, F0, F1, F2, pL, pR);
+        GL = F1 - pL;
+        GR = F1 - pR;
+        if (gR < 0) {
+          if (gR == kWall) {
+            F0 = zero; F2 = zero;  // impermeable, frictionless
+          } else if (gR <= kInflow) {
+            const int j = kInflow - gR;
+            const T q = wpos ? static_cast<T>(qscale * static_cast<double>(a.in_pw[j])) : quni;
+            if (q > zero) {
+              const T hcr = f_cbrt(f_div(q * q, g));
+              const T hb = fmax(h1, hcr);
+              F0 = -q;
+              GL = f_div(q * q, hb) + hg * hb * hb - pL;
+            } else {
+              F0 = zero;
+              GL = zero;
+            }
+            F2 = zero;
           }
-          F2 = zero;
         }
+      }
+      if (gR < 0) {
         bsum += static_cast<double>(l * F0);
         sawb = true;
       }
@@ -526,27 +556,37 @@ __device__ __forceinline__ void tile_step(const InstDesc<T>& a, const int tile, 
       }
     }
   }
-  const T rm = block_max<kTile, T>(rloc, sm.redT);
-  // boundary volume partial (FP64, fixed order) only where the tile has boundary edges
-  const int hasb = __syncthreads_or(sawb);
-  double bs = 0.0;
-  if (hasb) bs = block_sum<kTile>(bsum, sm.red);
-  if (tid == 0) {
-    if (hasb) a.part[tile].bflux = bs;
-    if (rm > zero) {
-      const double rd = static_cast<double>(rm);
-      atomicMax(&ctl->rmax_bits, static_cast<unsigned long long>(__double_as_longlong(rd)));
-    }
-    __threadfence();
-    const unsigned prev = atomicAdd(&ctl->done, 1u);
-    sm.last = (prev == static_cast<unsigned>(a.n_tiles) - 1u) ? 1 : 0;
+  // end of the tile: rate max (warp shuffle, then one shared atomic per warp) and
+  // whether any thread saw a boundary edge
+  T rw = rloc;
+  for (int o = 16; o > 0; o >>= 1) rw = fmax(rw, __shfl_xor_sync(0xffffffffu, rw, o));
+  const bool wb = __any_sync(0xffffffffu, sawb);
+  if ((tid & 31) == 0) {
+    if (rw > zero) atomicMax(&sm.rbits, static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(rw))));
+    if (wb) sm.anyb = 1;
   }
   __syncthreads();
-  if (sm.last) {
+  const int hasb = sm.anyb;
+  const unsigned long long rbits = sm.rbits;
+  // boundary volume partial (FP64, fixed order) only where the tile has boundary edges
+  double bs = 0.0;
+  if (hasb) bs = block_sum<kTile>(bsum, sm.red);
+  int is_last = 0;
+  if (tid == 0) {
+    if (hasb) a.part[tile].bflux = bs;
+    if (rbits) atomicMax(&ctl->rmax_bits, rbits);
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->done, 1u);
+    is_last = (prev == static_cast<unsigned>(a.n_tiles) - 1u) ? 1 : 0;
+  }
+  if (__syncthreads_or(is_last)) {
     __threadfence();
     finalize_instance<T>(a, prime ? 0 : 1, sm.red, sm.bc);
   }
-  __syncthreads();
+  if (tid == 0) {  // every thread read them before the barrier above
+    sm.rbits = 0ull;
+    sm.anyb = 0;
+  }
 }
 
 template <typename T>
@@ -565,16 +605,22 @@ __global__ void __launch_bounds__(kTile, kMinBlocks<T>) step_batch(const InstDes
   __shared__ __align__(16) InstDesc<T> sdesc;
   static_assert(sizeof(InstDesc<T>) % 8 == 0, "descriptor copy works in 8-byte words");
   const int tid = threadIdx.x;
+  if (tid == 0) {
+    sm.rbits = 0ull;
+    sm.anyb = 0;
+  }
+  int staged = -1;  // instance whose descriptor is in shared memory
   for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
     const WorkItem wi = work[w];
-    {
+    if (wi.inst != staged) {  // consecutive items usually belong to one instance
+      __syncthreads();        // nobody still reads the previous descriptor
       const unsigned long long* src = reinterpret_cast<const unsigned long long*>(descs + wi.inst);
       unsigned long long* dstw = reinterpret_cast<unsigned long long*>(&sdesc);
       for (int k = tid; k < static_cast<int>(sizeof(InstDesc<T>) / 8); k += kTile) dstw[k] = src[k];
+      staged = wi.inst;
+      __syncthreads();
     }
-    __syncthreads();
     if (sdesc.ctl->active || prime) tile_step<T, kDerived>(sdesc, wi.tile, prime, sm);
-    __syncthreads();
   }
 }
 
@@ -590,6 +636,7 @@ __global__ void set_t_end(Ctl* ctl, double t_end) {
     clipped = 1;
   }
   ctl->dt = dt;
+  ctl->dt_f = static_cast<float>(dt);
   ctl->clipped = clipped;
   ctl->active = t < t_end ? 1 : 0;
 }

@@ -186,7 +186,7 @@ def _patch_map(rng, x, y, Lx, Ly, n_patches, lo, hi, chunk=1 << 18):
 
 def floodplain(nx: int = 1600, ny: int = 625, Lx: float = 5000.0, Ly: float = 2000.0, seed: int = 2,
                datum: float = 400.0, q_peak: float = 500.0, ramp: float = 600.0,
-               n_range=(0.025, 0.06), jitter: float = 0.1) -> Scenario:
+               n_range=(0.025, 0.06), jitter: float = 0.1, outlet: int = WALL) -> Scenario:
     """Floodplain fed by a discharge hydrograph (default 1600 x 625 quads = 2,000,000
     triangles on 5 km x 2 km, seed 2).
 
@@ -195,14 +195,17 @@ def floodplain(nx: int = 1600, ny: int = 625, Lx: float = 5000.0, Ly: float = 20
     uniform in n_range.  A meandering main channel (cells within 40 m of
     y = Ly/2 + 300 sin(2 pi x / 2500 + phi)) is carved 3 m below the local bed and
     holds 2 m of water; everything else starts dry.  Inflow on the whole x = 0
-    side, Q ramping 0 -> q_peak over ``ramp`` s then constant; x = Lx transmissive;
-    y sides walls.  Time step: the positivity bound (cfl_mode 1), because with
+    side, Q ramping 0 -> q_peak over ``ramp`` s then constant; the other sides are
+    walls (``outlet`` sets the x = Lx side: a transmissive, zero-gradient outlet lets
+    water in wherever the flow next to it turns inward, and on this terrain that
+    inflow runs away after about 20 simulated minutes, so the default is a wall and the
+    basin fills).  Time step: the positivity bound (cfl_mode 1), because with
     Eq. 21 as printed (cfl_mode 0) the depth goes negative near the inflow on this
     recipe (the oracle reaches -10 m on a 160 x 64 version).
     """
     rng = np.random.default_rng(seed)
     xy, tri, tag = rect_mesh(nx, ny, Lx, Ly, jitter=jitter, seed=seed,
-                             side_tags=(INFLOW, TRANSMISSIVE, WALL, WALL))
+                             side_tags=(INFLOW, outlet, WALL, WALL))
     c = _centroids(xy, tri)
     x, y = c[:, 0], c[:, 1]
     z = datum + 1e-3 * (Lx - x) + _sinusoid_bed(rng, x, y) + rng.normal(0.0, 0.05, size=len(x))

@@ -168,7 +168,7 @@ def test_lake_at_rest_bitwise_fp64():
 
 def test_lake_at_rest_open_boundaries():
     """Transmissive and (zero-discharge) inflow boundaries also keep still water still."""
-    s = W.floodplain(nx=30, ny=12, Lx=300.0, Ly=120.0, seed=12, q_peak=0.0)
+    s = W.floodplain(nx=30, ny=12, Lx=300.0, Ly=120.0, seed=12, q_peak=0.0, outlet=W.TRANSMISSIVE)
     level = np.median(s.z) + 0.5
     s.H = np.maximum(s.z, level)
     o = oracle.Oracle(s)
@@ -209,7 +209,7 @@ def test_mass_closed_domain():
 
 def test_mass_open_domain_balance():
     """Open domain with inflow and outflow: V_n - V_0 equals the boundary volume."""
-    s = W.floodplain(nx=40, ny=16, Lx=500.0, Ly=200.0, seed=13, q_peak=50.0, ramp=60.0)
+    s = W.floodplain(nx=40, ny=16, Lx=500.0, Ly=200.0, seed=13, q_peak=50.0, ramp=60.0, outlet=W.TRANSMISSIVE)
     o = oracle.Oracle(s)
     v0 = o.volume()
     o.run_until(200.0)

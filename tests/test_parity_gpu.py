@@ -67,7 +67,8 @@ def test_random_states_wet_dry_friction(seed, nx, ny):
 
 def test_floodplain_inflow_transmissive_small():
     """Small floodplain: inflow hydrograph, transmissive outlet, walls, wet/dry fronts."""
-    s = W.floodplain(nx=120, ny=50, Lx=1200.0, Ly=500.0, seed=22, q_peak=200.0, ramp=100.0)
+    s = W.floodplain(nx=120, ny=50, Lx=1200.0, Ly=500.0, seed=22, q_peak=200.0, ramp=100.0,
+                     outlet=W.TRANSMISSIVE)
     st, o = both(s)
     st.run_until(150.0)
     o.run_until(150.0)
