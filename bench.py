@@ -45,14 +45,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s"
-# Algorithmic cost per cell-update (one cell, one step); derivation in the design notes.
-BYTES_PER_CELL_UPDATE = {"fp64": 156.0, "fp32": 84.0}
-FP64_FLOPS_PER_CELL_UPDATE = 213.0
-# FP64 peak: ncu's sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 296 DFMA/cycle
-# on this B300 (2 per SM), x 2 FLOP x the 2.032 GHz maximum SM clock.
-FP64_PEAK_TFLOPS = 296 * 2 * 2.032e9 / 1e12
+# Algorithmic DRAM bytes of one step: every byte the step must move once.  Per cell:
+# the state read and written (FP64: H, qx, qy, u, v, c; FP32-bulk: H hi/lo, qx, qy),
+# z, g n^2, 1/|Omega| and the 4-byte slot word; per mesh edge (each read once): the
+# 4-byte code word and nx, ny, l.
+BYTES_PER_CELL = {"fp64": 2 * 48 + 3 * 8 + 4, "fp32": 2 * 16 + 3 * 4 + 4}
+BYTES_PER_EDGE = {"fp64": 4 + 3 * 8, "fp32": 4 + 3 * 4}
 HBM_FALLBACK_GBS = 6400.0
-KERNEL_NAME = {"fp64": "step_batch<double,true>", "fp32": "step_batch<float,false>"}
+KERNEL_NAME = {"fp64": "step_pipe<double>", "fp32": "step_pipe<float>"}
 
 
 def parse():
@@ -275,23 +275,13 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
     kern_s = k_ms / nk / 1e3
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
-    bytes_launch = BYTES_PER_CELL_UPDATE[prec] * n
+    bytes_launch = BYTES_PER_CELL[prec] * n + BYTES_PER_EDGE[prec] * mesh.info["n_edges"]
     hbm_gbs = bytes_launch / kern_s / 1e9
     traffic = ncu_traffic(prec)
-    if prec == "fp64":
-        achieved = FP64_FLOPS_PER_CELL_UPDATE * n / kern_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": KERNEL_NAME[prec],
-                "kernel_ms": kern_s * 1e3,
-                "peak_source": "ncu peak_sustained 296 DFMA/cycle x 2 x 2.032 GHz (no FP64 figure in "
-                               "MEASURED_PEAKS.json)",
-                "hbm": {"achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
-                        "algorithmic_bytes_per_launch": bytes_launch}}
-    else:
-        roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
-                "traffic": traffic, "kernel": KERNEL_NAME[prec], "kernel_ms": kern_s * 1e3,
-                "algorithmic_bytes_per_launch": bytes_launch,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
+    roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
+            "traffic": traffic, "kernel": KERNEL_NAME[prec], "kernel_ms": kern_s * 1e3,
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
 
     # end to end through the C ABI with pinned host buffers: upload, E steps, download
     E = args.e2e_steps

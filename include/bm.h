@@ -97,6 +97,8 @@ const char* bm_last_error(void);
  * shared by more than two triangles or traversed twice in one direction, a tag
  * outside {0,1,2} on a boundary edge, n < 0 or a non-finite input.
  * *out receives the handle (NULL on failure); free with bm_mesh_destroy.
+ * Host work only: the mesh is copied to the device by the first state created on
+ * it (and stays on that device), so this call needs no GPU.
  */
 bm_status bm_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
                          const double* z_bed, const double* manning_n, const uint8_t* edge_tag,
@@ -105,6 +107,17 @@ bm_status bm_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, 
 /* Sizes of a mesh: cells, edges, boundary edges, inflow edges, tiles (NULL pointers skipped). */
 bm_status bm_mesh_info(const bm_mesh* m, int64_t* n_cells, int64_t* n_edges, int64_t* n_boundary,
                        int64_t* n_inflow, int64_t* n_tiles);
+
+/*
+ * Tile layout of a mesh for a precision (BM_FP64 or BM_FP32_BULK): the step reads
+ * each tile of 256 Hilbert-ordered cells as one record (inverse areas, edge slots,
+ * edge codes and geometry, halo list).  Builds and checks the records on the host
+ * (no GPU needed; cached in the mesh) and reports the largest edge list and halo of a
+ * tile and the records' total size in bytes (NULL pointers skipped).
+ * Errors: BM_EINVAL for a bad precision or an inconsistent layout, BM_ENOMEM.
+ */
+bm_status bm_mesh_layout(const bm_mesh* m, int32_t precision, int64_t* max_tile_edges, int64_t* max_tile_halo,
+                         int64_t* record_bytes);
 void bm_mesh_destroy(bm_mesh* m);
 
 /*
@@ -124,7 +137,8 @@ void bm_state_destroy(bm_state* s);
 bm_status bm_state_set_stream(bm_state* s, void* cuda_stream);
 
 /* Take n_steps explicit steps (dt from Eq. 21 each step, dt_max applied).  Blocks
- * until done; returns BM_ENONFINITE / BM_ENEGDEPTH if the device flagged it. */
+ * until done; returns BM_ENONFINITE / BM_ENEGDEPTH if the device flagged it, or
+ * BM_ETIMEOUT if a step's data copies did not arrive within about a second. */
 bm_status bm_step(bm_state* s, int64_t n_steps);
 
 /* Enqueue n_steps steps on the state's stream and return at once (no status check). */
@@ -160,16 +174,16 @@ bm_status bm_state_stats(bm_state* s, double* t, double* dt_next, int64_t* steps
 bm_status bm_step_timed(bm_state* s, int64_t n_steps, double* step_kernel_ms, double* total_ms);
 
 /*
- * Launch shape of the state's step kernel: ctas_per_sm = 0 launches one CTA per
- * 256-cell tile; k > 0 launches k CTAs per SM that loop over the tiles
- * (persistent).  Results do not depend on it.  Chosen by the autotuner
- * (paper_2102_12862_b300.autotune) or by hand.
+ * Launch shape of the state's step kernel, whose CTAs stay resident and loop over
+ * the 256-cell tiles: ctas_per_sm = 0 launches as many CTAs per SM as fit (the
+ * default), k > 0 launches k per SM.  Results do not depend on it.  Chosen by the
+ * autotuner or by hand.
  */
 bm_status bm_state_set_launch(bm_state* s, int ctas_per_sm);
 
 /*
- * Autotuner: time steps_per_trial steps for each launch shape (one CTA per tile,
- * and 1, 2, 3, 4, 6, 8 persistent CTAs per SM), undo the trial steps (the state is
+ * Autotuner: time steps_per_trial steps for each launch shape (as many CTAs per SM
+ * as fit, and 1, 2, 3, 4 CTAs per SM), undo the trial steps (the state is
  * snapshotted in device memory and restored), keep the fastest shape and report it
  * and its time per step.  Allocates a temporary device copy of the state.
  */

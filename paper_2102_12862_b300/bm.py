@@ -50,6 +50,7 @@ SIGNATURES = {
     "bm_mesh_create": (C.c_int, [_P(_d), _i64, _P(C.c_int32), _i64, _P(_d), _P(_d), _P(C.c_uint8), _P(_vp)]),
     "bm_mesh_info": (C.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64), _P(_i64)]),
     "bm_mesh_destroy": (None, [_vp]),
+    "bm_mesh_layout": (C.c_int, [_vp, C.c_int32, _P(_i64), _P(_i64), _P(_i64)]),
     "bm_state_init": (C.c_int, [_vp, _P(bm_params), _P(_d), _P(_d), _P(_d), _P(_vp)]),
     "bm_state_destroy": (None, [_vp]),
     "bm_state_set_stream": (C.c_int, [_vp, _vp]),
@@ -83,6 +84,12 @@ SIGNATURES = {
     "bm_server_stats": (C.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_d), _P(_d)]),
 }
 
+
+
+def _precision(prec) -> int:
+    if isinstance(prec, str):
+        return {"fp64": BM_FP64, "fp32": BM_FP32_BULK, "fp32_bulk": BM_FP32_BULK}[prec.lower()]
+    return int(prec)
 
 def load_library(path: str = LIB_PATH):
     """Load libbm.so (built by paper_2102_12862_b300.build); raises if it is missing."""
@@ -123,10 +130,7 @@ def make_params(**kw) -> tuple[bm_params, tuple]:
     lib.bm_params_default(C.byref(p))
     ht = _f64(kw.pop("hydro_t", np.zeros(0)))
     hq = _f64(kw.pop("hydro_q", np.zeros(0)))
-    prec = kw.pop("precision", BM_FP64)
-    if isinstance(prec, str):
-        prec = {"fp64": BM_FP64, "fp32": BM_FP32_BULK, "fp32_bulk": BM_FP32_BULK}[prec.lower()]
-    p.precision = prec
+    p.precision = _precision(kw.pop("precision", BM_FP64))
     for k, v in kw.items():
         if k == "datum" and v is None:
             v = math.nan
@@ -156,6 +160,12 @@ def bm_mesh_info(mesh: int) -> dict:
     v = [_i64() for _ in range(5)]
     _check(load_library().bm_mesh_info(mesh, *[C.byref(x) for x in v]))
     return dict(zip(["n_cells", "n_edges", "n_boundary", "n_inflow", "n_tiles"], [x.value for x in v]))
+
+
+def bm_mesh_layout(mesh: int, precision) -> dict:
+    v = [_i64() for _ in range(3)]
+    _check(load_library().bm_mesh_layout(mesh, _precision(precision), *[C.byref(x) for x in v]))
+    return dict(zip(["max_tile_edges", "max_tile_halo", "record_bytes"], [x.value for x in v]))
 
 
 def bm_mesh_destroy(mesh: int):
@@ -302,6 +312,9 @@ class Mesh:
     def from_scenario(cls, s) -> "Mesh":
         return cls(s.xy, s.tri, s.z, s.manning, s.edge_tag)
 
+    def layout(self, precision="fp64") -> dict:
+        return bm_mesh_layout(self.handle, precision)
+
     def close(self):
         if self.handle:
             bm_mesh_destroy(self.handle)
@@ -424,7 +437,7 @@ def bm_server_create(precision=BM_FP32_BULK, hbm_budget_bytes: int = 0, max_slot
     o = bm_server_opts()
     lib.bm_server_opts_default(C.byref(o))
     if isinstance(precision, str):
-        precision = {"fp64": BM_FP64, "fp32": BM_FP32_BULK, "fp32_bulk": BM_FP32_BULK}[precision.lower()]
+        precision = _precision(precision)
     o.precision = precision
     o.hbm_budget_bytes = int(hbm_budget_bytes)
     o.max_slots = int(max_slots)

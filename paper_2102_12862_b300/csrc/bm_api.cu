@@ -17,6 +17,7 @@
 
 #include "bm_internal.h"
 #include "bm_kernels.cuh"
+#include "bm_step.cuh"
 #include "bm_state.h"
 
 namespace bm {
@@ -39,18 +40,6 @@ std::vector<T> narrow(const std::vector<double>& v, double shift = 0.0) {
   std::vector<T> out(v.size());
   for (size_t i = 0; i < v.size(); ++i) out[i] = static_cast<T>(v[i] - shift);
   return out;
-}
-
-cudaError_t ensure_fp32_geometry(bm_mesh* m) {
-  if (m->has32) return cudaSuccess;
-  const HostMesh& h = m->h;
-  cudaError_t e = m->inv_area32.upload(narrow<float>(h.inv_area));
-  if (e == cudaSuccess) e = m->enx32.upload(narrow<float>(h.enx));
-  if (e == cudaSuccess) e = m->eny32.upload(narrow<float>(h.eny));
-  if (e == cudaSuccess) e = m->elen32.upload(narrow<float>(h.elen));
-  if (e == cudaSuccess) e = m->in_len32.upload(narrow<float>(h.in_len));
-  if (e == cudaSuccess) m->has32 = true;
-  return e;
 }
 
 }  // namespace
@@ -79,39 +68,144 @@ bm_status check_params(const bm_params* p) {
 bm_status status_of(const Ctl& c) {
   if (c.status & 1) return fail(BM_ENONFINITE, "the step produced a non-finite value");
   if (c.status & 2) return fail(BM_ENEGDEPTH, "a depth fell below -h_min");
+  if (c.status & 4) return fail(BM_ETIMEOUT, "a step's data copies did not arrive in time");
   return BM_OK;
 }
 
 namespace {
-// Dynamic shared memory above 48 KB must be opted into once per kernel.
-template <typename K>
-void allow_smem(K kernel, size_t bytes) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+// Largest dynamic shared memory of a step CTA: the device's per-block opt-in limit
+// less the kernel's static shared memory (set once per kernel; above 48 KB it must
+// be opted into).
+template <typename T>
+int step_smem_limit() {
+  static int lim = [] {
+    int dev = 0, optin = 48 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, step_pipe<T>);
+    const int l = optin - static_cast<int>(fa.sharedSizeBytes);
+    if (cudaFuncSetAttribute(step_pipe<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, l) != cudaSuccess ||
+        cudaFuncSetAttribute(step_pipe<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) {
+      (void)cudaGetLastError();  // leave no sticky error behind; launches check the size
+      return 48 * 1024 - static_cast<int>(fa.sharedSizeBytes);
+    }
+    return l;
+  }();
+  return lim;
 }
-struct SmemOptIn {
-  SmemOptIn() {
-    allow_smem(step_batch<double, true>, sizeof(TileSmem<double>));
-    allow_smem(step_batch<float, false>, sizeof(TileSmem<float>));
-  }
-};
-void ensure_smem_optin() {
-  static SmemOptIn once;
-  (void)once;
+int sm_count() {
+  static int n = [] {
+    int dev = 0, v = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v;
+  }();
+  return n;
+}
+bm_status dev_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? BM_ENOMEM : BM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 }  // namespace
 
-// One fused step (or prime) launch over a descriptor array and a work list.
-void launch_work(int prec, const void* descs, const WorkItem* work, int n_work, int grid, int prime,
-                 cudaStream_t st) {
-  if (n_work <= 0) return;
-  ensure_smem_optin();
-  grid = std::max(1, std::min(grid > 0 ? grid : n_work, n_work));
+bm_status mesh_on_device(bm_mesh* m, int prec) {
+  std::lock_guard<std::mutex> lk(m->mu);
+  int dev = 0;
+  BM_CUDA(cudaGetDevice(&dev));
+  const HostMesh& h = m->h;
+  cudaError_t e = cudaSuccess;
+  if (!m->on_device) {
+    e = m->z.upload(h.z);
+    if (e == cudaSuccess) e = m->inv_area.upload(h.inv_area);
+    if (e == cudaSuccess) e = m->area.upload(h.area);
+    if (e == cudaSuccess) e = m->in_cell.upload(h.in_cell);
+    if (e == cudaSuccess) e = m->in_len.upload(h.in_len);
+    if (e == cudaSuccess) e = m->btiles.upload(h.btiles);
+    if (e == cudaSuccess) e = m->perm.upload(h.perm);
+    if (e != cudaSuccess) return dev_fail(e, "mesh upload");
+    m->device = dev;
+    m->on_device = true;
+  } else if (dev != m->device) {
+    return fail(BM_EINVAL, "the mesh is resident on another device");
+  }
+  const int r = prec == BM_FP64 ? 0 : 1;
+  if (r == 1 && !m->has32) {
+    e = m->inv_area32.upload(narrow<float>(h.inv_area));
+    if (e == cudaSuccess) e = m->in_len32.upload(narrow<float>(h.in_len));
+    if (e != cudaSuccess) return dev_fail(e, "mesh upload");
+    m->has32 = true;
+  }
+  if (!m->rec_built[r]) {
+    bm_status st = build_tile_records(h, r == 0 ? 8 : 4, &m->rec[r]);
+    if (st != BM_OK) return st;
+    m->rec_built[r] = true;
+  }
+  if (!m->rec_dev[r].p) {
+    e = m->rec_dev[r].upload(m->rec[r].data);
+    if (e != cudaSuccess) return dev_fail(e, "tile record upload");
+  }
+  return BM_OK;
+}
+
+bm_status build_step_list(const std::vector<bm_state*>& members, const std::vector<const void*>& descs,
+                          StepList* out) {
+  const int prec = members.at(0)->prec;
+  const int r = prec == BM_FP64 ? 0 : 1;
+  std::vector<PipeItem> items;
+  uint32_t ne4 = 4, nh4 = 4;
+  for (size_t k = 0; k < members.size(); ++k) {
+    const bm_mesh* m = members[k]->mesh;
+    const TileRecords& R = m->rec[r];
+    if (!m->rec_built[r] || !m->rec_dev[r].p) return fail(BM_EINVAL, "internal: tile records missing");
+    for (int64_t t = 0; t < m->h.n_tiles; ++t) {
+      PipeItem it{};
+      it.rec = m->rec_dev[r].p + R.off[t];
+      it.desc = descs[k];
+      it.ctl = members[k]->ctl;
+      it.rec_bytes = R.bytes[t];
+      it.tile = static_cast<int32_t>(t);
+      it.ne_nh = R.ne_nh[t];
+      it.inst = static_cast<int32_t>(k);
+      it.flags = R.flags[t];
+      items.push_back(it);
+    }
+    ne4 = std::max(ne4, R.ne4_max);
+    nh4 = std::max(nh4, R.nh4_max);
+  }
+  cudaError_t e = out->items.upload(items);
+  if (e != cudaSuccess) return dev_fail(e, "work list upload");
+  out->n = static_cast<int>(items.size());
+  out->ne4 = ne4;
+  out->nh4 = nh4;
+  out->smem = prec == BM_FP64 ? StepLayout<double>(ne4, nh4).total : StepLayout<float>(ne4, nh4).total;
+  const int lim = prec == BM_FP64 ? step_smem_limit<double>() : step_smem_limit<float>();
+  if (out->smem > static_cast<size_t>(lim)) return fail(BM_EINVAL, "tile layout exceeds the device's shared memory");
+  int occ = 0;
   if (prec == BM_FP64)
-    step_batch<double, true><<<grid, kTile, sizeof(TileSmem<double>), st>>>(
-        static_cast<const InstDesc<double>*>(descs), work, n_work, prime);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_pipe<double>, kStepThreads, out->smem);
   else
-    step_batch<float, false><<<grid, kTile, sizeof(TileSmem<float>), st>>>(
-        static_cast<const InstDesc<float>*>(descs), work, n_work, prime);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_pipe<float>, kStepThreads, out->smem);
+  if (e != cudaSuccess) return dev_fail(e, "occupancy query");
+  out->occupancy = std::max(1, occ);
+  return BM_OK;
+}
+
+int step_grid(const StepList& l, int ctas_per_sm) {
+  const int per = ctas_per_sm > 0 ? ctas_per_sm : l.occupancy;
+  const long long g = static_cast<long long>(per) * sm_count();
+  return static_cast<int>(std::max(1LL, std::min<long long>(g, l.n)));
+}
+
+// One fused step (or prime) launch over a work list.
+void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st) {
+  if (l.n <= 0) return;
+  grid = std::max(1, std::min(grid, l.n));
+  if (prec == BM_FP64)
+    step_pipe<double><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, static_cast<int>(l.ne4), static_cast<int>(l.nh4),
+                                                    prime);
+  else
+    step_pipe<float><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, static_cast<int>(l.ne4), static_cast<int>(l.nh4),
+                                                   prime);
 }
 
 namespace {
@@ -123,7 +217,7 @@ bm_status read_status(bm_state* s) {
 }
 
 void launch_state(bm_state* s, cudaStream_t st, int prime) {
-  launch_work(s->prec, s->desc.p, s->work.p, static_cast<int>(s->work.n), s->grid, prime, st);
+  launch_work(s->prec, s->list, s->grid, prime, st);
 }
 
 bm_status get_graph(bm_state* s, int k, cudaGraphExec_t* out) {
@@ -190,15 +284,12 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
   d.in_pw = b.in_pw.p;
   d.in_hs = b.in_hs.p;
   if constexpr (sizeof(T) == 8) {
-    d.inv_area = m->inv_area.p; d.enx = m->enx.p; d.eny = m->eny.p; d.elen = m->elen.p; d.in_len = m->in_len.p;
+    d.inv_area = m->inv_area.p;
+    d.in_len = m->in_len.p;
   } else {
-    d.inv_area = m->inv_area32.p; d.enx = m->enx32.p; d.eny = m->eny32.p; d.elen = m->elen32.p;
+    d.inv_area = m->inv_area32.p;
     d.in_len = m->in_len32.p;
   }
-  d.slots = m->slots.p;
-  d.eoff = m->eoff.p;
-  d.eL = m->eL.p;
-  d.eR = m->eR.p;
   d.in_cell = m->in_cell.p;
   d.btiles = m->btiles.p;
   d.ctl = s->ctl;
@@ -282,14 +373,15 @@ bm_status alloc_state(bm_state* s, const bm_params* prm) {
   if (!std::isfinite(s->datum)) return fail(BM_EINVAL, "bm_state_init: datum must be finite or NaN");
   std::vector<double> gn2(h.man.size());
   for (size_t i = 0; i < gn2.size(); ++i) gn2[i] = prm->g * h.man[i] * h.man[i];
+  bm_status mst = mesh_on_device(const_cast<bm_mesh*>(m), s->prec);
+  if (mst != BM_OK) return mst;
   cudaError_t e = cudaSuccess;
   if (f64) {
     e = s->b64.alloc(Np, static_cast<size_t>(h.n_inflow), true);
     if (e == cudaSuccess) e = s->b64.gn2.upload(gn2);
     if (e == cudaSuccess) e = cudaMemcpy(s->b64.z.p, h.z.data(), Np * sizeof(double), cudaMemcpyHostToDevice);
   } else {
-    e = ensure_fp32_geometry(const_cast<bm_mesh*>(m));
-    if (e == cudaSuccess) e = s->b32.alloc(Np, static_cast<size_t>(h.n_inflow), false);
+    e = s->b32.alloc(Np, static_cast<size_t>(h.n_inflow), false);
     if (e == cudaSuccess) e = s->b32.gn2.upload(narrow<float>(gn2));
     if (e == cudaSuccess) {
       std::vector<float> z32 = narrow<float>(h.z, s->datum);
@@ -328,14 +420,11 @@ bm_status alloc_state(bm_state* s, const bm_params* prm) {
   p.hmin_f = static_cast<float>(prm->h_min);
   p.pad_f = 0.0f;
   state_desc_bytes(s, &s->hdesc);
-  std::vector<WorkItem> work(h.n_tiles);
-  for (int64_t t = 0; t < h.n_tiles; ++t) work[t] = WorkItem{0, static_cast<int>(t)};
   e = s->desc.upload(s->hdesc);
-  if (e == cudaSuccess) e = s->work.upload(work);
-  if (e != cudaSuccess)
-    return fail(e == cudaErrorMemoryAllocation ? BM_ENOMEM : BM_ECUDA,
-                std::string("bm_state_init: ") + cudaGetErrorString(e));
-  s->grid = static_cast<int>(h.n_tiles);
+  if (e != cudaSuccess) return dev_fail(e, "bm_state_init");
+  bm_status lst = build_step_list({s}, {static_cast<const void*>(s->desc.p)}, &s->list);
+  if (lst != BM_OK) return lst;
+  s->grid = step_grid(s->list, 0);
   return BM_OK;
 }
 
@@ -345,7 +434,8 @@ size_t state_footprint(const bm_mesh* m, int precision) {
   const size_t Np = static_cast<size_t>(h.n_tiles) * kTile;
   const size_t w = precision == BM_FP64 ? 8 : 4;
   const size_t arrays = precision == BM_FP64 ? 14 : 10;  // 2 x (H [pair], q, derived) + z, gn2
-  return Np * w * arrays + 3 * static_cast<size_t>(h.n_cells) * 8 + static_cast<size_t>(h.n_tiles) * 32 +
+  // + caller-order staging, per tile: boundary partial, volume partial, work item
+  return Np * w * arrays + 3 * static_cast<size_t>(h.n_cells) * 8 + static_cast<size_t>(h.n_tiles) * 72 +
          static_cast<size_t>(h.n_inflow) * 2 * w + 4096;
 }
 
@@ -389,28 +479,6 @@ bm_status bm_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, 
     delete m;
     return st;
   }
-  cudaGetDevice(&m->device);
-  cudaError_t e = cudaSuccess;
-  const HostMesh& h = m->h;
-  if (e == cudaSuccess) e = m->z.upload(h.z);
-  if (e == cudaSuccess) e = m->inv_area.upload(h.inv_area);
-  if (e == cudaSuccess) e = m->area.upload(h.area);
-  if (e == cudaSuccess) e = m->slots.upload(h.slots);
-  if (e == cudaSuccess) e = m->eoff.upload(h.eoff);
-  if (e == cudaSuccess) e = m->eL.upload(h.eL);
-  if (e == cudaSuccess) e = m->eR.upload(h.eR);
-  if (e == cudaSuccess) e = m->enx.upload(h.enx);
-  if (e == cudaSuccess) e = m->eny.upload(h.eny);
-  if (e == cudaSuccess) e = m->elen.upload(h.elen);
-  if (e == cudaSuccess) e = m->in_cell.upload(h.in_cell);
-  if (e == cudaSuccess) e = m->in_len.upload(h.in_len);
-  if (e == cudaSuccess) e = m->btiles.upload(h.btiles);
-  if (e == cudaSuccess) e = m->perm.upload(h.perm);
-  if (e != cudaSuccess) {
-    delete m;
-    if (e == cudaErrorMemoryAllocation) return fail(BM_ENOMEM, "bm_mesh_create: out of device memory");
-    return fail(BM_ECUDA, std::string("bm_mesh_create: ") + cudaGetErrorString(e));
-  }
   *out = m;
   return BM_OK;
 }
@@ -428,6 +496,32 @@ bm_status bm_mesh_info(const bm_mesh* m, int64_t* n_cells, int64_t* n_edges, int
 }
 
 void bm_mesh_destroy(bm_mesh* m) { delete m; }
+
+bm_status bm_mesh_layout(const bm_mesh* cm, int32_t precision, int64_t* max_tile_edges, int64_t* max_tile_halo,
+                         int64_t* record_bytes) {
+  clear_error();
+  if (!cm) return fail(BM_EINVAL, "bm_mesh_layout: mesh is NULL");
+  if (precision != BM_FP64 && precision != BM_FP32_BULK)
+    return fail(BM_EINVAL, "bm_mesh_layout: precision must be BM_FP64 or BM_FP32_BULK");
+  bm_mesh* m = const_cast<bm_mesh*>(cm);
+  std::lock_guard<std::mutex> lk(m->mu);
+  const int r = precision == BM_FP64 ? 0 : 1;
+  if (!m->rec_built[r]) {
+    bm_status st = build_tile_records(m->h, r == 0 ? 8 : 4, &m->rec[r]);
+    if (st != BM_OK) return st;
+    m->rec_built[r] = true;
+  }
+  const TileRecords& R = m->rec[r];
+  uint32_t ne = 0, nh = 0;
+  for (uint32_t v : R.ne_nh) {
+    ne = std::max(ne, v & 0xffffu);
+    nh = std::max(nh, v >> 16);
+  }
+  if (max_tile_edges) *max_tile_edges = ne;
+  if (max_tile_halo) *max_tile_halo = nh;
+  if (record_bytes) *record_bytes = static_cast<int64_t>(R.data.size());
+  return BM_OK;
+}
 
 bm_status bm_state_init(const bm_mesh* m, const bm_params* prm, const double* H, const double* qx, const double* qy,
                         bm_state** out) {
@@ -474,11 +568,8 @@ bm_status bm_state_set_launch(bm_state* s, int ctas_per_sm) {
   clear_error();
   if (!s) return fail(BM_EINVAL, "bm_state_set_launch: state is NULL");
   if (ctas_per_sm < 0 || ctas_per_sm > 64) return fail(BM_EINVAL, "bm_state_set_launch: ctas_per_sm in [0, 64]");
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int nt = static_cast<int>(s->mesh->h.n_tiles);
-  const int grid = ctas_per_sm == 0 ? nt : std::min(nt, ctas_per_sm * sms);
+  const int grid = step_grid(s->list, ctas_per_sm);
+  s->ctas_per_sm = ctas_per_sm;
   if (grid != s->grid) {
     BM_CUDA(cudaStreamSynchronize(s->stream));
     drop_graphs(s);
@@ -694,7 +785,7 @@ cudaError_t snapshot_state(bm_state* s, Snapshot* sn, cudaStream_t st) {
 }  // namespace
 
 // Time `steps` steps for each candidate launch shape, restore the state, pick the
-// fastest.  Candidates: one CTA per tile (0) and 1..8 persistent CTAs per SM.
+// fastest.  Candidates: as many persistent CTAs per SM as fit (0), and 1..4.
 bm_status autotune_shape(std::vector<bm_state*> states, int steps, int* best, double* best_ms,
                          const std::function<bm_status(int)>& set_shape,
                          const std::function<bm_status(int)>& run_steps, cudaStream_t st) {
@@ -704,7 +795,7 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int* best, do
     if (e != cudaSuccess) return fail(BM_ENOMEM, std::string("autotune snapshot: ") + cudaGetErrorString(e));
   }
   BM_CUDA(cudaStreamSynchronize(st));
-  const int cands[] = {0, 1, 2, 3, 4, 6, 8};
+  const int cands[] = {0, 1, 2, 3, 4};
   cudaEvent_t e0, e1;
   BM_CUDA(cudaEventCreate(&e0));
   BM_CUDA(cudaEventCreate(&e1));

@@ -21,7 +21,7 @@ struct bm_batch {
   std::vector<bm_state*> members;
   int prec = BM_FP64;
   bm::DBuf<unsigned char> descs;  // member descriptors, one after another
-  bm::DBuf<bm::WorkItem> work;
+  bm::StepList list;
   bm::DBuf<bm::Ctl*> ctlp;        // device pointers to the members' control blocks
   bm::DBuf<double> t_end;         // per-member end times (run_until)
   bm::DBuf<int> flags;            // per member: active | status << 1
@@ -68,7 +68,7 @@ __global__ void batch_flags(Ctl* const* ctl, int n, int* flags) {
 }
 
 void launch_batch(bm_batch* b, cudaStream_t st) {
-  launch_work(b->prec, b->descs.p, b->work.p, static_cast<int>(b->work.n), b->grid, 0, st);
+  launch_work(b->prec, b->list, b->grid, 0, st);
 }
 
 bm_status batch_graph(bm_batch* b, int k, cudaGraphExec_t* out) {
@@ -148,6 +148,8 @@ bm_status batch_read(bm_batch* b, int* n_active) {
                                                      ": the step produced a non-finite value");
     if (worst == BM_OK && (st & 2)) worst = fail(BM_ENEGDEPTH, "batch member " + std::to_string(k) +
                                                      ": a depth fell below -h_min");
+    if (worst == BM_OK && (st & 4)) worst = fail(BM_ETIMEOUT, "batch member " + std::to_string(k) +
+                                                     ": a step's data copies did not arrive in time");
   }
   if (n_active) *n_active = act;
   return worst;
@@ -176,18 +178,25 @@ bm_status bm_batch_create(bm_state* const* states, int32_t n, bm_batch** out) {
   b->members.assign(states, states + n);
   b->prec = prec;
   std::vector<unsigned char> all, one;
-  std::vector<WorkItem> work;
   std::vector<Ctl*> ctls(n);
   for (int k = 0; k < n; ++k) {
     bm_state* s = states[k];
     cudaStreamSynchronize(s->stream);
     state_desc_bytes(s, &one);
     all.insert(all.end(), one.begin(), one.end());
-    for (int64_t t = 0; t < s->mesh->h.n_tiles; ++t) work.push_back(WorkItem{k, static_cast<int>(t)});
     ctls[k] = s->ctl;
   }
+  const size_t dsz = one.size();  // a multiple of 16: members' descriptors stay aligned
   cudaError_t e = b->descs.upload(all);
-  if (e == cudaSuccess) e = b->work.upload(work);
+  if (e == cudaSuccess) {
+    std::vector<const void*> dptr(n);
+    for (int k = 0; k < n; ++k) dptr[k] = b->descs.p + k * dsz;
+    bm_status lst = build_step_list(b->members, dptr, &b->list);
+    if (lst != BM_OK) {
+      delete b;
+      return lst;
+    }
+  }
   if (e == cudaSuccess) e = b->ctlp.upload(ctls);
   if (e == cudaSuccess) e = b->t_end.alloc(n);
   if (e == cudaSuccess) e = b->flags.alloc(n);
@@ -199,7 +208,7 @@ bm_status bm_batch_create(bm_state* const* states, int32_t n, bm_batch** out) {
                 std::string("bm_batch_create: ") + cudaGetErrorString(e));
   }
   b->stream = b->own;
-  b->grid = static_cast<int>(work.size());
+  b->grid = step_grid(b->list, 0);
   bm_status st = batch_set_end(b, nullptr);
   if (st != BM_OK) {
     delete b;
@@ -227,11 +236,7 @@ bm_status bm_batch_set_launch(bm_batch* b, int ctas_per_sm) {
   clear_error();
   if (!b) return fail(BM_EINVAL, "bm_batch_set_launch: batch is NULL");
   if (ctas_per_sm < 0 || ctas_per_sm > 64) return fail(BM_EINVAL, "bm_batch_set_launch: ctas_per_sm in [0, 64]");
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int nw = static_cast<int>(b->work.n);
-  const int grid = ctas_per_sm == 0 ? nw : std::min(nw, ctas_per_sm * sms);
+  const int grid = step_grid(b->list, ctas_per_sm);
   if (grid != b->grid) {
     BM_CUDA(cudaStreamSynchronize(b->stream));
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
@@ -296,7 +301,7 @@ bm_status bm_batch_info(const bm_batch* b, int32_t* n_members, int64_t* n_cells,
   for (bm_state* s : b->members) cells += s->mesh->h.n_cells;
   if (n_members) *n_members = static_cast<int32_t>(b->members.size());
   if (n_cells) *n_cells = cells;
-  if (n_tiles) *n_tiles = static_cast<int64_t>(b->work.n);
+  if (n_tiles) *n_tiles = static_cast<int64_t>(b->list.n);
   return BM_OK;
 }
 

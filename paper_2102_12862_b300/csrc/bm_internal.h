@@ -51,6 +51,54 @@ struct HostMesh {
 bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
                        const double* z, const double* man, const uint8_t* tag, HostMesh* out);
 
+#if defined(__CUDACC__)
+#define BM_HD __host__ __device__ __forceinline__
+#else
+#define BM_HD inline
+#endif
+
+BM_HD uint32_t round4(uint32_t x) { return (x + 3u) & ~3u; }
+BM_HD uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+// Tile record: everything static one tile's step reads, as one contiguous block so a
+// single bulk copy brings it into shared memory.  With ne4 / nh4 = the tile's edge /
+// halo counts rounded up to a multiple of 4 and S = sizeof(T):
+//   inv_area[kTile] T | slot[kTile] u32 | lr[ne4] u32 | nx[ne4] T | ny[ne4] T |
+//   len[ne4] T | hidx[nh4] i32
+// slot: the cell's three tile-local edge indices, 10 bits each (the side follows from
+// lr: the cell is the edge's left cell iff the left index is the cell's).
+// lr: left local index in bits 0..9, right local index or boundary code (signed) in
+// bits 10..31.  Local index j < kTile is cell tile*kTile + j, j >= kTile is halo cell
+// hidx[j - kTile] (another tile's cell, instance numbering).  Every segment is a
+// multiple of 16 bytes, so records concatenate 16-byte aligned.
+constexpr int kLocBits = 10;
+constexpr int kMaxLocal = 1 << kLocBits;           // tile cells + halo cells
+constexpr int32_t kMinCode = -(1 << 21);           // most negative code in lr
+template <int S>
+struct RecLayout {
+  static BM_HD uint32_t ia() { return 0; }
+  static BM_HD uint32_t slot() { return kTile * S; }
+  static BM_HD uint32_t lr() { return kTile * S + kTile * 4; }
+  static BM_HD uint32_t nx(uint32_t ne4) { return lr() + ne4 * 4; }
+  static BM_HD uint32_t ny(uint32_t ne4) { return nx(ne4) + ne4 * S; }
+  static BM_HD uint32_t len(uint32_t ne4) { return ny(ne4) + ne4 * S; }
+  static BM_HD uint32_t hidx(uint32_t ne4) { return len(ne4) + ne4 * S; }
+  static BM_HD uint32_t bytes(uint32_t ne4, uint32_t nh4) { return hidx(ne4) + nh4 * 4; }
+};
+
+// Tile records of one mesh in one precision (host side).
+struct TileRecords {
+  std::vector<unsigned char> data;   // concatenated records
+  std::vector<uint64_t> off;         // byte offset of tile t's record
+  std::vector<uint32_t> bytes;       // its size (multiple of 16)
+  std::vector<uint32_t> ne_nh;       // edges | halo cells << 16
+  std::vector<uint8_t> flags;        // bit 0: boundary edges, bit 1: inflow edges
+  uint32_t ne4_max = 0, nh4_max = 0;
+};
+
+// Build (and check) the tile records of a prepared mesh; S = 8 (FP64) or 4 (FP32).
+bm_status build_tile_records(const HostMesh& m, int S, TileRecords* out);
+
 // Device-side control block of one state (one instance).
 struct Ctl {
   double t;        // current time t^n
@@ -73,11 +121,22 @@ struct Ctl {
   float quni_f;
 };
 
-// One work item of a step launch: (instance, tile).
-struct WorkItem {
-  int inst;
-  int tile;
+static_assert(sizeof(Ctl) % 16 == 0, "Ctl is bulk-copied: its size must be a multiple of 16");
+
+// One work item of a step launch: a tile of an instance, with the addresses its bulk
+// copies read (items of one instance are consecutive; 48 bytes, 16-byte aligned).
+struct PipeItem {
+  const unsigned char* rec;  // the tile's record
+  const void* desc;          // the instance's descriptor (InstDesc<T>)
+  Ctl* ctl;                  // the instance's control block
+  uint32_t rec_bytes;        // record size (multiple of 16)
+  int32_t tile;
+  uint32_t ne_nh;            // edges | halo cells << 16
+  int32_t inst;              // instance index within the launch
+  uint32_t flags;            // bit 0: the tile has boundary edges, bit 1: inflow edges
+  uint32_t pad;
 };
+static_assert(sizeof(PipeItem) == 48, "PipeItem layout");
 
 // Per-tile reduction slot written by the step kernel.
 struct TilePartial {

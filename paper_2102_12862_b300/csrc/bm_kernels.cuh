@@ -1,20 +1,8 @@
-// bm_kernels.cuh -- device code of the explicit shallow-water step (sm_103a).
-//
-// One step of one instance (BASEMENT v3, Section "Numerical solution",
-// "Hydrodynamics"), processed tile by tile (256 consecutive Hilbert-ordered cells):
-//   phase 0  stage the tile's cells (H, z, u, v, c) in shared memory;
-//   phase 1  each tile edge once: modified states on max(z_L, z_R), HLLC flux in
-//            the edge frame (Toro wave speeds), pre-balanced pressure correction,
-//            wall / transmissive / discharge-inflow boundary states;
-//   phase 2  each cell gathers its three edge contributions in local edge order
-//            (Eq. 12), applies the split Manning friction (Eq. 2, Table 1, two
-//            semi-implicit stages), zeroes q below h_min, writes U^{n+1} and reduces
-//            lambda/rho of Eq. 21 for the next dt;
-//   finalize the CTA that completes an instance's last tile reduces the instance's
-//            partials in a fixed order (dt^{n+1}, t^{n+1}, boundary volume, inflow
-//            split for t^{n+1}) -- no second launch, no spin-wait.
-// One launch steps every instance of a work list (a batch of uneven meshes, each
-// with its own dt); a single state is a batch of one.
+// bm_kernels.cuh -- device helpers of the explicit shallow-water step (sm_103a): the
+// instance descriptor, deterministic block reductions, the HLLC flux, cell-derived
+// quantities, the per-instance finalize (dt of Eq. 21, time, boundary volume, inflow
+// split), and the small kernels around the step (end-time targeting, volume, user-order
+// gather/scatter, state checks).  The step kernel itself is in bm_step.cuh.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,9 +14,10 @@
 
 namespace bm {
 
-// Everything one instance's tiles need; lives in device memory.
+// Everything one instance's tiles need besides their tile records; lives in device
+// memory and is bulk-copied into shared memory with each tile (size a multiple of 16).
 template <typename T>
-struct InstDesc {
+struct alignas(16) InstDesc {
   T* H[2];    // free surface (FP32-bulk: hi part of the offset from the datum)
   T* Hlo[2];  // FP32-bulk only: lo part of the free surface
   T* qx[2];
@@ -39,13 +28,6 @@ struct InstDesc {
   const T* z;
   const T* gn2;       // g n^2
   const T* inv_area;  // 1 / |Omega_i|
-  const uint64_t* slots;
-  const int64_t* eoff;
-  const int32_t* eL;
-  const int32_t* eR;
-  const T* enx;
-  const T* eny;
-  const T* elen;
   const int32_t* in_cell;  // inflow edge j: its cell
   const T* in_len;         //                its length
   T* in_pw;                //                h^(5/3) of the cell (0 at or below h_min)
@@ -63,14 +45,44 @@ struct InstDesc {
 
 // ------------------------------------------------------------------ helpers
 
-// Deterministic block reductions (fixed shuffle tree, then warp 0 over warps).
+// Barrier over the first NT threads of the block (named barrier 1): the step kernel's
+// compute warps synchronise without its copy warp.
+template <int NT>
+__device__ __forceinline__ void nbar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+template <int NT>
+__device__ __forceinline__ bool nbar_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(v)), "n"(NT)
+      : "memory");
+  return r != 0;
+}
+template <int NT>
+__device__ __forceinline__ bool nbar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(v)), "n"(NT)
+      : "memory");
+  return r != 0;
+}
+
+// Deterministic block reductions over the first NT threads (fixed shuffle tree, then
+// warp 0 over warps).
 template <int NT, typename V>
 __device__ __forceinline__ V block_max(V x, V* sbuf) {
   for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
+  nbar<NT>();
   if (lane == 0) sbuf[w] = x;
-  __syncthreads();
+  nbar<NT>();
   if (w == 0) {
     x = lane < NT / 32 ? sbuf[lane] : V(0);
     for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
@@ -82,9 +94,9 @@ template <int NT>
 __device__ __forceinline__ double block_sum(double x, double* sbuf) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
+  nbar<NT>();
   if (lane == 0) sbuf[w] = x;
-  __syncthreads();
+  nbar<NT>();
   if (w == 0) {
     x = lane < NT / 32 ? sbuf[lane] : 0.0;
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -218,8 +230,8 @@ __device__ __forceinline__ T cell_rate(const T* nxs, const T* nys, const T* ls, 
   return cfl_mode == 1 ? ssum * ia : rmax;
 }
 
-// Per-instance finalize, run by every thread of the CTA that completed the
-// instance's last tile.  advance = 1 after a step, 0 after prime.
+// Per-instance finalize, run by the kTile compute threads of the CTA that completed
+// the instance's last tile.  advance = 1 after a step, 0 after prime.
 template <typename T>
 __device__ void finalize_instance(const InstDesc<T>& a, int advance, double* sred, double* sbc) {
   Ctl* ctl = a.ctl;
@@ -237,7 +249,7 @@ __device__ void finalize_instance(const InstDesc<T>& a, int advance, double* sre
     }
     sbc[0] = ctl->t;
   }
-  __syncthreads();
+  nbar<kTile>();
   const double t = sbc[0];
   const double g = a.p.g;
   // inflow distribution at the new time (conveyance weights l h^(5/3))
@@ -246,7 +258,7 @@ __device__ void finalize_instance(const InstDesc<T>& a, int advance, double* sre
     wsum += static_cast<double>(a.in_len[j]) * static_cast<double>(__ldcg(&a.in_pw[j]));
   wsum = block_sum<kTile>(wsum, sred);
   if (tid == 0) sbc[1] = wsum;
-  __syncthreads();
+  nbar<kTile>();
   wsum = sbc[1];
   const double Q = hydrograph(a.p, t);
   const bool wpos = wsum > 0.0;
@@ -299,329 +311,6 @@ __device__ __forceinline__ void step_consts(const Ctl* c, const Params& p, doubl
 __device__ __forceinline__ void step_consts(const Ctl* c, const Params& p, float& dt, float& quni, float& g,
                                             float& hg, float& hmin) {
   dt = c->dt_f; quni = c->quni_f; g = p.g_f; hg = p.hg_f; hmin = p.hmin_f;
-}
-
-// Shared memory of one CTA (dynamic): the tile's cells, its edges' geometry and
-// fluxes, reduction scratch.
-template <typename T>
-struct TileSmem {
-  T Hh[kTile], Hl[kTile], Z[kTile], U[kTile], V[kTile], C[kTile];
-  T F[5][kMaxTileEdges];
-  T Nx[kMaxTileEdges], Ny[kMaxTileEdges], Ln[kMaxTileEdges];
-  int32_t Code[kMaxTileEdges];
-  double red[kTile / 32];
-  double bc[2];
-  unsigned long long rbits;  // max Eq. 21 rate of the tile (bits of a value >= 0)
-  int anyb;                  // the tile has boundary edges
-};
-
-// One (instance, tile) work item.  T = double: every array and operation in FP64;
-// velocity and celerity of U^{n+1} are stored (kDerived) so the next step reads them
-// instead of dividing again.  T = float (FP32-bulk): H is an FP32 pair, z an FP32
-// offset from an FP64 datum; velocity and celerity are recomputed; the boundary
-// volume is summed in FP64.  prime = 1: no update, only derived data, inflow
-// weights and the dt of the current state (after init/upload).
-template <typename T, bool kDerived>
-__device__ __forceinline__ void tile_step(const InstDesc<T>& a, const int tile, const int prime, TileSmem<T>& sm) {
-  constexpr bool kPair = sizeof(T) == 4;
-  const int tid = threadIdx.x;
-  const T zero = T(0);
-  Ctl* ctl = a.ctl;
-  // round 1: control block and the tile's edge range
-  const int par = ctl->parity;
-  T dt, quni, g, hg, hmin;
-  step_consts(ctl, a.p, dt, quni, g, hg, hmin);
-  const double qscale = ctl->qscale;
-  const int wpos = ctl->wpos;
-  const int64_t e0 = a.eoff[tile];
-  const int ne = static_cast<int>(a.eoff[tile + 1] - e0);
-  const T* __restrict__ HH = a.H[par];
-  const T* __restrict__ HL = kPair ? a.Hlo[par] : nullptr;
-  const T* __restrict__ QX0 = a.qx[par];
-  const T* __restrict__ QY0 = a.qy[par];
-  const T* __restrict__ Z = a.z;
-  const int base = tile * kTile;
-  const int i = base + tid;
-  const bool valid = i < a.n_cells;
-
-  // round 2: every load of the tile that depends only on the tile (cells, edges)
-  T Hh = zero, Hl = zero, zi = zero, qxi = zero, qyi = zero, ui = zero, vi = zero, ci = zero, ia = zero, gn2 = zero;
-  uint64_t sl = 0;
-  if (valid) {
-    Hh = HH[i]; zi = Z[i]; qxi = QX0[i]; qyi = QY0[i];
-    if (kPair) Hl = HL[i];
-    sl = a.slots[i];
-    ia = a.inv_area[i];
-    gn2 = a.gn2[i];
-    if (kDerived && !prime) { ui = a.u[par][i]; vi = a.v[par][i]; ci = a.c[par][i]; }
-  }
-  // the first two edges of this thread (most tiles have fewer than 512 edges)
-  int gL0 = 0, gR0 = kWall, gL1 = 0, gR1 = kWall;
-  T nx0 = zero, ny0 = zero, l0 = zero, nx1 = zero, ny1 = zero, l1 = zero;
-  if (!prime && tid < ne) {
-    gL0 = a.eL[e0 + tid]; gR0 = a.eR[e0 + tid]; nx0 = a.enx[e0 + tid]; ny0 = a.eny[e0 + tid]; l0 = a.elen[e0 + tid];
-  }
-  if (!prime && tid + kTile < ne) {
-    const int64_t e = e0 + tid + kTile;
-    gL1 = a.eL[e]; gR1 = a.eR[e]; nx1 = a.enx[e]; ny1 = a.eny[e]; l1 = a.elen[e];
-  }
-  const T hi0 = depth_of(Hh, Hl, zi);
-  if (!(kDerived && !prime) && valid) cell_derived<T>(hi0, qxi, qyi, hmin, g, ui, vi, ci);
-  sm.Hh[tid] = Hh; sm.Hl[tid] = Hl; sm.Z[tid] = zi; sm.U[tid] = ui; sm.V[tid] = vi; sm.C[tid] = ci;
-  double bsum = 0.0;
-  bool sawb = false;  // this thread evaluated a boundary edge
-  __syncthreads();
-
-  // phase 1: edges of the tile (round 3: halo cells of other tiles)
-  if (!prime) {
-    auto edge = [&](const int k, const int gL, const int gR, const T nx, const T ny, const T l) {
-      sm.Nx[k] = nx; sm.Ny[k] = ny; sm.Ln[k] = l; sm.Code[k] = gR;
-      // surfaces and beds of both sides (the right side mirrors the left at a boundary)
-      const int lL = gL - base;
-      const bool inL = static_cast<unsigned>(lL) < static_cast<unsigned>(kTile);
-      T HLh, HLl, zL;
-      if (inL) {
-        HLh = sm.Hh[lL]; HLl = sm.Hl[lL]; zL = sm.Z[lL];
-      } else {
-        HLh = HH[gL]; HLl = kPair ? HL[gL] : zero; zL = Z[gL];
-      }
-      const int lR = gR - base;
-      const bool inR = gR >= 0 && static_cast<unsigned>(lR) < static_cast<unsigned>(kTile);
-      T HRh = HLh, HRl = HLl, zR = zL;
-      if (gR >= 0) {
-        if (inR) {
-          HRh = sm.Hh[lR]; HRl = sm.Hl[lR]; zR = sm.Z[lR];
-        } else {
-          HRh = HH[gR]; HRl = kPair ? HL[gR] : zero; zR = Z[gR];
-        }
-      }
-      // modified states (hydrostatic reconstruction on the higher bed)
-      const T zs = fmax(zL, zR);
-      const T h1 = fmax(zero, depth_of(HLh, HLl, zs));
-      const T h2 = fmax(zero, depth_of(HRh, HRl, zs));
-      T F0 = zero, F2 = zero, GL = zero, GR = zero;
-      // with both modified depths zero every contribution is exactly zero: skip the
-      // flux (warps whose edges are all dry do no flux arithmetic); inflow edges
-      // always impose their discharge
-      if (h1 > zero || h2 > zero || gR <= kInflow) {
-        T uL, vL, cL;
-        if (inL) {
-          uL = sm.U[lL]; vL = sm.V[lL]; cL = sm.C[lL];
-        } else if (kDerived) {
-          uL = a.u[par][gL]; vL = a.v[par][gL]; cL = a.c[par][gL];
-        } else {
-          cell_derived<T>(depth_of(HLh, HLl, zL), QX0[gL], QY0[gL], hmin, g, uL, vL, cL);
-        }
-        const T unL = uL * nx + vL * ny, utL = -uL * ny + vL * nx;
-        T un2, ut2, c1, c2;
-        if (gR >= 0) {
-          T uR, vR, cR;
-          if (inR) {
-            uR = sm.U[lR]; vR = sm.V[lR]; cR = sm.C[lR];
-          } else if (kDerived) {
-            uR = a.u[par][gR]; vR = a.v[par][gR]; cR = a.c[par][gR];
-          } else {
-            cell_derived<T>(depth_of(HRh, HRl, zR), QX0[gR], QY0[gR], hmin, g, uR, vR, cR);
-          }
-          // the side with the higher bed keeps its own depth, hence its own celerity
-          const bool lhi = zL >= zR;
-          const T clo = f_sqrt(g * (lhi ? h2 : h1));
-          c1 = lhi ? cL : clo;
-          c2 = lhi ? clo : cR;
-          un2 = uR * nx + vR * ny;
-          ut2 = -uR * ny + vR * nx;
-        } else {
-          c1 = cL;
-          c2 = cL;
-          un2 = (gR == kWall) ? -unL : unL;  // wall: mirrored normal velocity
-          ut2 = utL;
-        }
-        T F1, pL, pR;
-        hllc<T>(h1, unL, utL, c1, h2, un2, ut2, c2, hg, F0, F1, F2, pL, pR);
-        GL = F1 - pL;
-        GR = F1 - pR;
-        if (gR < 0) {
-          if (gR == kWall) {
-            F0 = zero; F2 = zero;  // impermeable, frictionless
-          } else if (gR <= kInflow) {
-            const int j = kInflow - gR;
-            const T q = wpos ? static_cast<T>(qscale * static_cast<double>(a.in_pw[j])) : quni;
-            if (q > zero) {
-              const T hcr = f_cbrt(f_div(q * q, g));
-              const T hb = fmax(h1, hcr);
-              F0 = -q;
-              GL = f_div(q * q, hb) + hg * hb * hb - pL;
-            } else {
-              F0 = zero;
-              GL = zero;
-            }
-            F2 = zero;
-          }
-        }
-      }
-      if (gR < 0) {
-        bsum += static_cast<double>(l * F0);
-        sawb = true;
-      }
-      sm.F[0][k] = l * F0;
-      sm.F[1][k] = l * (GL * nx - F2 * ny);
-      sm.F[2][k] = l * (GL * ny + F2 * nx);
-      sm.F[3][k] = l * (GR * nx - F2 * ny);
-      sm.F[4][k] = l * (GR * ny + F2 * nx);
-    };
-    if (tid < ne) edge(tid, gL0, gR0, nx0, ny0, l0);
-    if (tid + kTile < ne) edge(tid + kTile, gL1, gR1, nx1, ny1, l1);
-    for (int k = tid + 2 * kTile; k < ne; k += kTile) {
-      const int64_t e = e0 + k;
-      edge(k, a.eL[e], a.eR[e], a.enx[e], a.eny[e], a.elen[e]);
-    }
-  } else {
-    // prime: only the geometry and boundary codes are needed by phase 2
-    for (int k = tid; k < ne; k += kTile) {
-      sm.Nx[k] = a.enx[e0 + k]; sm.Ny[k] = a.eny[e0 + k]; sm.Ln[k] = a.elen[e0 + k]; sm.Code[k] = a.eR[e0 + k];
-    }
-  }
-  __syncthreads();
-
-  // phase 2: cells
-  T rloc = zero;
-  if (valid) {
-    int idx[3], side[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const unsigned p = static_cast<unsigned>((sl >> (16 * k)) & 0xffffu);
-      idx[k] = static_cast<int>(p >> 1);
-      side[k] = static_cast<int>(p & 1u);
-    }
-    T h = hi0, ux = qxi, uy = qyi;
-    if (!prime) {
-      T s0 = zero, s1 = zero, s2 = zero;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        if (side[k] == 0) {
-          s0 += sm.F[0][idx[k]]; s1 += sm.F[1][idx[k]]; s2 += sm.F[2][idx[k]];
-        } else {
-          s0 += -sm.F[0][idx[k]]; s1 += -sm.F[3][idx[k]]; s2 += -sm.F[4][idx[k]];
-        }
-      }
-      const T r = dt * ia;
-      if constexpr (kPair) {
-        pair_add(Hh, Hl, -(r * s0));
-      } else {
-        Hh = Hh - r * s0;
-      }
-      ux = qxi - r * s1;
-      uy = qyi - r * s2;
-      h = depth_of(Hh, Hl, zi);
-      if (h > hmin && gn2 > zero) {
-        // split friction: two semi-implicit stages, Heun average
-        const T cf = f_div(gn2, h * h * f_cbrt(h));
-        const T k0 = cf * f_sqrt(ux * ux + uy * uy);
-        const T d0 = f_div(T(1), T(1) + dt * k0);
-        const T q1x = ux * d0, q1y = uy * d0;
-        const T k1 = cf * f_sqrt(q1x * q1x + q1y * q1y);
-        const T d1 = f_div(T(1), T(1) + dt * k1);
-        ux = T(0.5) * (ux + q1x * d1);
-        uy = T(0.5) * (uy + q1y * d1);
-      }
-      if (!(h > hmin)) { ux = zero; uy = zero; }
-      const int dst = par ^ 1;
-      a.H[dst][i] = Hh;
-      if constexpr (kPair) a.Hlo[dst][i] = Hl;
-      a.qx[dst][i] = ux;
-      a.qy[dst][i] = uy;
-      if (!isfinite(Hh) || !isfinite(ux) || !isfinite(uy)) atomicOr(&ctl->status, 1);
-      // negative depth: below -h_min, beyond the rounding of the FP32 bed offset in FP32-bulk
-      const T negtol = kPair ? hmin + T(4) * static_cast<T>(FLT_EPSILON) * fabs(zi) : hmin;
-      if (h < -negtol) atomicOr(&ctl->status, 2);
-    }
-    const int out = prime ? par : (par ^ 1);
-    T u, v, c;
-    cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
-    if (kDerived) {
-      a.u[out][i] = u;
-      a.v[out][i] = v;
-      a.c[out][i] = c;
-    }
-    if (h > hmin) rloc = cell_rate<T>(sm.Nx, sm.Ny, sm.Ln, idx, u, v, c, ia, a.p.cfl_mode);
-    // inflow cells: conveyance weight and depth of the new state, for the finalize
-    // and the next step's inflow flux
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int code = sm.Code[idx[k]];
-      if (code <= kInflow) {
-        const int j = kInflow - code;
-        a.in_pw[j] = h > hmin ? pow53(h) : zero;
-        a.in_hs[j] = fmax(zero, h);
-      }
-    }
-  }
-  // end of the tile: rate max (warp shuffle, then one shared atomic per warp) and
-  // whether any thread saw a boundary edge
-  T rw = rloc;
-  for (int o = 16; o > 0; o >>= 1) rw = fmax(rw, __shfl_xor_sync(0xffffffffu, rw, o));
-  const bool wb = __any_sync(0xffffffffu, sawb);
-  if ((tid & 31) == 0) {
-    if (rw > zero) atomicMax(&sm.rbits, static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(rw))));
-    if (wb) sm.anyb = 1;
-  }
-  __syncthreads();
-  const int hasb = sm.anyb;
-  const unsigned long long rbits = sm.rbits;
-  // boundary volume partial (FP64, fixed order) only where the tile has boundary edges
-  double bs = 0.0;
-  if (hasb) bs = block_sum<kTile>(bsum, sm.red);
-  int is_last = 0;
-  if (tid == 0) {
-    if (hasb) a.part[tile].bflux = bs;
-    if (rbits) atomicMax(&ctl->rmax_bits, rbits);
-    __threadfence();
-    const unsigned prev = atomicAdd(&ctl->done, 1u);
-    is_last = (prev == static_cast<unsigned>(a.n_tiles) - 1u) ? 1 : 0;
-  }
-  if (__syncthreads_or(is_last)) {
-    __threadfence();
-    finalize_instance<T>(a, prime ? 0 : 1, sm.red, sm.bc);
-  }
-  if (tid == 0) {  // every thread read them before the barrier above
-    sm.rbits = 0ull;
-    sm.anyb = 0;
-  }
-}
-
-template <typename T>
-constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 3;
-
-// The step launch: a work list of (instance, tile) items over instance descriptors
-// in device memory.  A single state is a list of one instance's tiles, so a run
-// executes the same machine code alone and in a batch and gives bitwise the same
-// result (separately compiled copies could contract multiply-adds differently).
-template <typename T, bool kDerived>
-__global__ void __launch_bounds__(kTile, kMinBlocks<T>) step_batch(const InstDesc<T>* __restrict__ descs,
-                                                                    const WorkItem* __restrict__ work, int n_work,
-                                                                    int prime) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem<T>& sm = *reinterpret_cast<TileSmem<T>*>(smem_raw);
-  __shared__ __align__(16) InstDesc<T> sdesc;
-  static_assert(sizeof(InstDesc<T>) % 8 == 0, "descriptor copy works in 8-byte words");
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    sm.rbits = 0ull;
-    sm.anyb = 0;
-  }
-  int staged = -1;  // instance whose descriptor is in shared memory
-  for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
-    const WorkItem wi = work[w];
-    if (wi.inst != staged) {  // consecutive items usually belong to one instance
-      __syncthreads();        // nobody still reads the previous descriptor
-      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(descs + wi.inst);
-      unsigned long long* dstw = reinterpret_cast<unsigned long long*>(&sdesc);
-      for (int k = tid; k < static_cast<int>(sizeof(InstDesc<T>) / 8); k += kTile) dstw[k] = src[k];
-      staged = wi.inst;
-      __syncthreads();
-    }
-    if (sdesc.ctl->active || prime) tile_step<T, kDerived>(sdesc, wi.tile, prime, sm);
-  }
 }
 
 // Re-target the end time of one instance: dt is recomputed from the unclipped step.

@@ -234,3 +234,103 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
 }
 
 }  // namespace bm
+
+namespace bm {
+
+namespace {
+template <typename T>
+void put(std::vector<unsigned char>& d, size_t at, T v) {
+  std::memcpy(d.data() + at, &v, sizeof(T));
+}
+
+template <typename T>
+bm_status build_records_t(const HostMesh& m, TileRecords* out) {
+  constexpr int S = sizeof(T);
+  using RL = RecLayout<S>;
+  TileRecords& r = *out;
+  r = TileRecords();
+  const int64_t N = m.n_cells;
+  r.off.resize(m.n_tiles);
+  r.bytes.resize(m.n_tiles);
+  r.ne_nh.resize(m.n_tiles);
+  r.flags.assign(m.n_tiles, 0);
+  std::vector<int32_t> halo;
+  for (int64_t tile = 0; tile < m.n_tiles; ++tile) {
+    const int64_t base = tile * kTile;
+    const int64_t e0 = m.eoff[tile], e1 = m.eoff[tile + 1];
+    const uint32_t ne = static_cast<uint32_t>(e1 - e0);
+    if (ne > static_cast<uint32_t>(kMaxTileEdges)) return fail(BM_EINVAL, "tile records: too many tile edges");
+    auto in_tile = [&](int64_t g) { return g >= base && g < base + kTile; };
+    halo.clear();
+    for (int64_t e = e0; e < e1; ++e) {
+      if (!in_tile(m.eL[e])) halo.push_back(m.eL[e]);
+      if (m.eR[e] >= 0 && !in_tile(m.eR[e])) halo.push_back(m.eR[e]);
+    }
+    std::sort(halo.begin(), halo.end());
+    halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+    const uint32_t nh = static_cast<uint32_t>(halo.size());
+    if (kTile + nh > static_cast<uint32_t>(kMaxLocal)) return fail(BM_EINVAL, "tile records: halo too large");
+    auto local = [&](int64_t g) -> uint32_t {
+      if (in_tile(g)) return static_cast<uint32_t>(g - base);
+      return kTile + static_cast<uint32_t>(std::lower_bound(halo.begin(), halo.end(), g) - halo.begin());
+    };
+    const uint32_t ne4 = round4(ne), nh4 = round4(nh);
+    const uint32_t bytes = RL::bytes(ne4, nh4);
+    const size_t at = r.data.size();
+    r.data.resize(at + bytes, 0);
+    r.off[tile] = at;
+    r.bytes[tile] = bytes;
+    r.ne_nh[tile] = ne | (nh << 16);
+    r.ne4_max = std::max(r.ne4_max, ne4);
+    r.nh4_max = std::max(r.nh4_max, nh4);
+    std::vector<uint32_t> lr(ne);
+    for (uint32_t k = 0; k < ne; ++k) {
+      const int64_t e = e0 + k;
+      const int32_t gR = m.eR[e];
+      int32_t R;
+      if (gR >= 0) {
+        R = static_cast<int32_t>(local(gR));
+      } else {
+        if (gR < kMinCode) return fail(BM_EINVAL, "tile records: too many inflow edges");
+        R = gR;
+        r.flags[tile] |= gR <= kInflow ? 3 : 1;
+      }
+      lr[k] = local(m.eL[e]) | (static_cast<uint32_t>(R) << kLocBits);
+      put<uint32_t>(r.data, at + RL::lr() + 4 * k, lr[k]);
+      put<T>(r.data, at + RL::nx(ne4) + S * k, static_cast<T>(m.enx[e]));
+      put<T>(r.data, at + RL::ny(ne4) + S * k, static_cast<T>(m.eny[e]));
+      put<T>(r.data, at + RL::len(ne4) + S * k, static_cast<T>(m.elen[e]));
+    }
+    for (uint32_t h = 0; h < nh; ++h) put<int32_t>(r.data, at + RL::hidx(ne4) + 4 * h, halo[h]);
+    for (int j = 0; j < kTile; ++j) {
+      const int64_t i = base + j;
+      put<T>(r.data, at + RL::ia() + S * j, static_cast<T>(m.inv_area[i]));
+      if (i >= N) continue;
+      uint32_t slot = 0;
+      for (int k = 0; k < 3; ++k) {
+        const uint32_t p = static_cast<uint32_t>((m.slots[i] >> (16 * k)) & 0xffffu);
+        const uint32_t pos = p >> 1, side = p & 1u;
+        if (pos >= ne) return fail(BM_EINVAL, "tile records: slot outside the tile's edge list");
+        // the side must follow from the edge's left index
+        const bool left = (lr[pos] & (kMaxLocal - 1)) == static_cast<uint32_t>(j);
+        if (left != (side == 0)) return fail(BM_EINVAL, "tile records: inconsistent edge side");
+        slot |= pos << (kLocBits * k);
+      }
+      put<uint32_t>(r.data, at + RL::slot() + 4 * j, slot);
+    }
+  }
+  return BM_OK;
+}
+}  // namespace
+
+bm_status build_tile_records(const HostMesh& m, int S, TileRecords* out) {
+  try {
+    if (S == 8) return build_records_t<double>(m, out);
+    if (S == 4) return build_records_t<float>(m, out);
+  } catch (const std::bad_alloc&) {
+    return fail(BM_ENOMEM, "tile records: out of host memory");
+  }
+  return fail(BM_EINVAL, "tile records: element size must be 4 or 8");
+}
+
+}  // namespace bm

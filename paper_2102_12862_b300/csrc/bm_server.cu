@@ -204,8 +204,11 @@ void worker_loop(bm_server* sv) {
       }
       const int f = flags[k];
       if (f >> 1) {
-        finish(sv, run[k], (f >> 1) & 1 ? BM_ENONFINITE : BM_ENEGDEPTH,
-               (f >> 1) & 1 ? "the step produced a non-finite value" : "a depth fell below -h_min");
+        const int code = f >> 1;
+        finish(sv, run[k], (code & 1) ? BM_ENONFINITE : (code & 2) ? BM_ENEGDEPTH : BM_ETIMEOUT,
+               (code & 1)   ? "the step produced a non-finite value"
+               : (code & 2) ? "a depth fell below -h_min"
+                            : "a step's data copies did not arrive in time");
         changed_now = true;
       } else if (!(f & 1)) {
         finish(sv, run[k], BM_OK, "");

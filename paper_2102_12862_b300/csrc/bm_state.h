@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -94,16 +95,30 @@ struct Buffers {
 
 struct bm_mesh {
   bm::HostMesh h;
-  int device = 0;
-  // FP64 device copies
-  bm::DBuf<double> z, inv_area, area, enx, eny, elen, in_len;
-  bm::DBuf<uint64_t> slots;
-  bm::DBuf<int64_t> eoff;
-  bm::DBuf<int32_t> eL, eR, in_cell, btiles, perm;
-  // FP32 geometry, built on first use by an FP32-bulk state
-  bool has32 = false;
-  bm::DBuf<float> inv_area32, enx32, eny32, elen32, in_len32;
+  // Device data is created on first use by a state (bm_mesh_create needs no GPU).
+  std::mutex mu;
+  int device = -1;
+  bool on_device = false;
+  bm::DBuf<double> z, inv_area, area, in_len;
+  bm::DBuf<int32_t> in_cell, btiles, perm;
+  bool has32 = false;  // FP32 copies for FP32-bulk states
+  bm::DBuf<float> inv_area32, in_len32;
+  // tile records, host and device, per precision (0: FP64, 1: FP32)
+  bm::TileRecords rec[2];
+  bool rec_built[2] = {false, false};
+  bm::DBuf<unsigned char> rec_dev[2];
 };
+
+namespace bm {
+// The work list of a step launch and the shared-memory layout it needs.
+struct StepList {
+  DBuf<PipeItem> items;
+  int n = 0;
+  uint32_t ne4 = 4, nh4 = 4;
+  size_t smem = 0;
+  int occupancy = 1;  // resident CTAs per SM at this shared-memory size
+};
+}  // namespace bm
 
 struct bm_state {
   const bm_mesh* mesh = nullptr;
@@ -119,9 +134,9 @@ struct bm_state {
   bm::DBuf<double> vol_part, vol_out;
   bm::DBuf<bm::TilePartial> part;
   bm::DBuf<int> bad;
-  bm::DBuf<unsigned char> desc;   // one InstDesc<T> (device copy, for batches)
+  bm::DBuf<unsigned char> desc;   // one InstDesc<T> (device copy)
   std::vector<unsigned char> hdesc;  // host copy of the descriptor
-  bm::DBuf<bm::WorkItem> work;       // the state's tiles as a work list of one instance
+  bm::StepList list;                 // the state's tiles as a work list of one instance
   bm::Ctl* ctl = nullptr;   // device
   bm::Ctl* hctl = nullptr;  // pinned host mirror
   double* hvol = nullptr;   // pinned
@@ -130,7 +145,8 @@ struct bm_state {
   cudaStream_t own = nullptr;     // private stream, also used for graph capture
   std::map<int, cudaGraphExec_t> graphs;
   double cur_t_end = 0.0;
-  int grid = 0;  // CTAs of the persistent step launch
+  int grid = 0;         // CTAs of the persistent step launch
+  int ctas_per_sm = 0;  // launch shape (0: as many as fit)
   template <typename T>
   bm::Buffers<T>& buf();
   ~bm_state() {
@@ -154,6 +170,13 @@ bm_status check_params(const bm_params* p);
 bm_status status_of(const Ctl& c);
 bm_status load_state(bm_state* s, const double* H, const double* qx, const double* qy, double t);
 void state_desc_bytes(bm_state* s, std::vector<unsigned char>* out);
-void launch_work(int prec, const void* descs, const WorkItem* work, int n_work, int grid, int prime,
-                 cudaStream_t st);
+// Device data of a mesh for a precision (uploads on first use; thread-safe).
+bm_status mesh_on_device(bm_mesh* m, int prec);
+// Work list over the tiles of several states; descs[k] = device address of member k's
+// descriptor.
+bm_status build_step_list(const std::vector<bm_state*>& members, const std::vector<const void*>& descs,
+                          StepList* out);
+// Grid of a step launch for a launch shape (ctas_per_sm = 0: all that fit).
+int step_grid(const StepList& l, int ctas_per_sm);
+void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st);
 }  // namespace bm

@@ -86,3 +86,26 @@ def test_params_validation_without_gpu():
     p, keep = bm.make_params(cfl=1.5)
     st = lib.bm_state_init(None, C.byref(p), None, None, None, C.byref(C.c_void_p()))
     assert st == bm.BM_EINVAL
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.dam_break(),
+    lambda: W.floodplain(nx=120, ny=50, Lx=1200.0, Ly=500.0, seed=5),
+    lambda: W.dam_break(nx=1000, ny=1, seed=6),  # a strip: tiles are long and thin
+])
+def test_mesh_layout_on_the_host(make):
+    """Meshes are built and tiled without a GPU; the tile records respect the step
+    kernel's limits (768 edges and halo cells per tile, 16-byte records)."""
+    s = make()
+    m = bm.Mesh.from_scenario(s)
+    info = m.info
+    assert info["n_cells"] == len(s.tri) and info["n_tiles"] == -(-len(s.tri) // 256)
+    lay64, lay32 = m.layout("fp64"), m.layout("fp32")
+    for lay, S in ((lay64, 8), (lay32, 4)):
+        assert 0 < lay["max_tile_edges"] <= 768 and 0 <= lay["max_tile_halo"] <= 768
+        assert lay["record_bytes"] % 16 == 0
+        # every tile stores its 256 cells (1/area, slot) and each mesh edge at least once
+        assert lay["record_bytes"] >= info["n_tiles"] * 256 * (S + 4) + info["n_edges"] * (4 + 3 * S)
+    assert lay64["max_tile_edges"] == lay32["max_tile_edges"] and lay64["max_tile_halo"] == lay32["max_tile_halo"]
+    with pytest.raises(bm.BMError, match="precision"):
+        bm.bm_mesh_layout(m.handle, 7)
