@@ -120,6 +120,11 @@ bm_status mesh_on_device(bm_mesh* m, int prec) {
     if (e == cudaSuccess) e = m->area.upload(h.area);
     if (e == cudaSuccess) e = m->in_cell.upload(h.in_cell);
     if (e == cudaSuccess) e = m->in_len.upload(h.in_len);
+    if (e == cudaSuccess) {
+      std::vector<double> lia(h.in_len.size());
+      for (size_t j = 0; j < lia.size(); ++j) lia[j] = h.in_len[j] * h.inv_area[h.in_cell[j]];
+      e = m->in_lia.upload(lia);
+    }
     if (e == cudaSuccess) e = m->btiles.upload(h.btiles);
     if (e == cudaSuccess) e = m->perm.upload(h.perm);
     if (e != cudaSuccess) return dev_fail(e, "mesh upload");
@@ -157,7 +162,21 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
     const bm_mesh* m = members[k]->mesh;
     const TileRecords& R = m->rec[r];
     if (!m->rec_built[r] || !m->rec_dev[r].p) return fail(BM_EINVAL, "internal: tile records missing");
-    for (int64_t t = 0; t < m->h.n_tiles; ++t) {
+    // boundary ranks in tile order; items in the order inflow tiles, other boundary
+    // tiles, interior tiles, so the per-instance inflow and boundary work (done by the
+    // CTA that completes the last such tile) happens early in the launch
+    std::vector<uint32_t> brank_of(m->h.n_tiles, 0);
+    for (int64_t t = 0, b = 0; t < m->h.n_tiles; ++t)
+      if (R.flags[t] & 1u) brank_of[t] = static_cast<uint32_t>(b++);
+    std::vector<int64_t> order;
+    order.reserve(m->h.n_tiles);
+    for (int pass = 0; pass < 3; ++pass)
+      for (int64_t t = 0; t < m->h.n_tiles; ++t) {
+        const uint8_t f = R.flags[t];
+        const int cls = (f & 2u) ? 0 : ((f & 1u) ? 1 : 2);
+        if (cls == pass) order.push_back(t);
+      }
+    for (int64_t t : order) {
       PipeItem it{};
       it.rec = m->rec_dev[r].p + R.off[t];
       it.desc = descs[k];
@@ -167,12 +186,15 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
       it.ne_nh = R.ne_nh[t];
       it.inst = static_cast<int32_t>(k);
       it.flags = R.flags[t];
+      it.bidx = brank_of[t];
       items.push_back(it);
     }
     ne4 = std::max(ne4, R.ne4_max);
     nh4 = std::max(nh4, R.nh4_max);
   }
   cudaError_t e = out->items.upload(items);
+  if (e == cudaSuccess) e = out->sched.alloc(2);
+  if (e == cudaSuccess) e = cudaMemset(out->sched.p, 0, 2 * sizeof(int));
   if (e != cudaSuccess) return dev_fail(e, "work list upload");
   out->n = static_cast<int>(items.size());
   out->ne4 = ne4;
@@ -201,11 +223,11 @@ void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t 
   if (l.n <= 0) return;
   grid = std::max(1, std::min(grid, l.n));
   if (prec == BM_FP64)
-    step_pipe<double><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, static_cast<int>(l.ne4), static_cast<int>(l.nh4),
-                                                    prime);
+    step_pipe<double><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, l.sched.p, static_cast<int>(l.ne4),
+                                                           static_cast<int>(l.nh4), prime);
   else
-    step_pipe<float><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, static_cast<int>(l.ne4), static_cast<int>(l.nh4),
-                                                   prime);
+    step_pipe<float><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, l.sched.p, static_cast<int>(l.ne4),
+                                                          static_cast<int>(l.nh4), prime);
 }
 
 namespace {
@@ -291,6 +313,7 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
     d.in_len = m->in_len32.p;
   }
   d.in_cell = m->in_cell.p;
+  d.in_lia = m->in_lia.p;
   d.btiles = m->btiles.p;
   d.ctl = s->ctl;
   d.part = s->part.p;
@@ -298,6 +321,12 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
   d.inflow_len = h.inflow_len;
   d.n_inflow = static_cast<int>(h.n_inflow);
   d.n_btiles = static_cast<int>(h.btiles.size());
+  {
+    const TileRecords& R = m->rec[sizeof(T) == 8 ? 0 : 1];
+    int nit = 0;
+    for (uint8_t f : R.flags) nit += (f & 2u) ? 1 : 0;
+    d.n_in_tiles = nit;
+  }
   d.n_cells = static_cast<int>(h.n_cells);
   d.n_tiles = static_cast<int>(h.n_tiles);
 }

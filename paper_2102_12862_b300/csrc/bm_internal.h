@@ -119,6 +119,9 @@ struct Ctl {
   int status;      // bit 0: non-finite value, bit 1: negative depth
   float dt_f;      // dt and quni rounded once for FP32-bulk steps
   float quni_f;
+  double rb;            // max inflow-edge rate of Eq. 21 at t^{n+1} (written mid-launch)
+  unsigned int in_done; // inflow tiles of the current launch that finished
+  unsigned int b_done;  // boundary tiles of the current launch that finished
 };
 
 static_assert(sizeof(Ctl) % 16 == 0, "Ctl is bulk-copied: its size must be a multiple of 16");
@@ -134,7 +137,7 @@ struct PipeItem {
   uint32_t ne_nh;            // edges | halo cells << 16
   int32_t inst;              // instance index within the launch
   uint32_t flags;            // bit 0: the tile has boundary edges, bit 1: inflow edges
-  uint32_t pad;
+  uint32_t bidx;             // boundary tiles: rank among the instance's boundary tiles
 };
 static_assert(sizeof(PipeItem) == 48, "PipeItem layout");
 

@@ -28,17 +28,19 @@ struct alignas(16) InstDesc {
   const T* z;
   const T* gn2;       // g n^2
   const T* inv_area;  // 1 / |Omega_i|
-  const int32_t* in_cell;  // inflow edge j: its cell
+  const int32_t* in_cell;
+  const double* in_lia;    // inflow edge j: l_j / |Omega| of its cell  // inflow edge j: its cell
   const T* in_len;         //                its length
   T* in_pw;                //                h^(5/3) of the cell (0 at or below h_min)
   T* in_hs;                //                max(0, h) of the cell
-  const int32_t* btiles;   // tiles with boundary edges
+  const int32_t* btiles;   // tiles with boundary edges (tile b's partial at part[b's rank])
   Ctl* ctl;
   TilePartial* part;
   Params p;
   double inflow_len;
   int n_inflow;
   int n_btiles;
+  int n_in_tiles;          // tiles with inflow edges
   int n_cells;
   int n_tiles;
 };
@@ -104,26 +106,45 @@ __device__ __forceinline__ double block_sum(double x, double* sbuf) {
   return x;  // valid in thread 0
 }
 
-__device__ __forceinline__ double hydrograph(const Params& p, double t) {
-  if (p.hydro_n <= 0) return 0.0;
-  if (t <= p.hydro_t[0]) return p.hydro_q[0];
-  for (int i = 1; i < p.hydro_n; ++i) {
-    if (t <= p.hydro_t[i]) {
-      double w = (t - p.hydro_t[i - 1]) / (p.hydro_t[i] - p.hydro_t[i - 1]);
-      return p.hydro_q[i - 1] + w * (p.hydro_q[i] - p.hydro_q[i - 1]);
-    }
+// Maximum of non-negative doubles over the first NT threads, returned to every
+// thread.  Non-negative doubles order like their bit patterns, so the reduction runs
+// on 64-bit integers (integer pipes, not the FP64 pipe; the result is exact).
+template <int NT>
+__device__ __forceinline__ double block_max_nonneg_all(double x, unsigned long long* sbuf) {
+  unsigned long long v = static_cast<unsigned long long>(__double_as_longlong(x));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
   }
-  return p.hydro_q[p.hydro_n - 1];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  nbar<NT>();
+  if (lane == 0) sbuf[w] = v;
+  nbar<NT>();
+  if (w == 0) {
+    v = lane < NT / 32 ? sbuf[lane] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+      v = u > v ? u : v;
+    }
+    if (lane == 0) sbuf[NT / 32] = v;
+  }
+  nbar<NT>();
+  return __longlong_as_double(static_cast<long long>(sbuf[NT / 32]));
 }
 
-// Elementary functions.  FP64: the IEEE-rounded library functions (the path the
-// oracle is checked against at 1e-11).  FP32-bulk: the hardware approximations
-// (MUFU reciprocal square root, reciprocal, base-2 logarithm and exponent), a few
-// ulp each -- far inside that mode's 1e-4 m accuracy target and deterministic, so
-// both sides of an edge still compute identical values.
+// Sum over one warp in a fixed order (lane-strided partial sums, then a shuffle tree).
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Elementary functions.  FP64: the IEEE-rounded library square root and division;
+// cube roots through f_rcbrt below.  FP32-bulk: the hardware approximations (MUFU
+// reciprocal square root, reciprocal, base-2 logarithm and exponent), a few ulp each --
+// far inside that mode's 1e-4 m accuracy target and deterministic, so both sides of an
+// edge still compute identical values.
 __device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ double f_div(double a, double b) { return a / b; }
-__device__ __forceinline__ double f_cbrt(double x) { return cbrt(x); }
 __device__ __forceinline__ float f_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 __device__ __forceinline__ float f_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ float f_exp2(float x) {
@@ -131,13 +152,32 @@ __device__ __forceinline__ float f_exp2(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float f_cbrt(float x) { return f_exp2(__log2f(x) * (1.0f / 3.0f)); }  // x > 0
 
-// h^(5/3) for h > 0, through the cube root.
+// x^(-1/3) for x > 0.  FP32-bulk: 2^(-log2(x)/3) from the hardware approximations.
+// FP64: that single-precision estimate refined by two Newton-Raphson steps on
+// f(r) = r^-3 - x, r <- r (4 - x r^3) / 3, which converge quadratically (about 21
+// correct bits -> 41 -> the full double) without a division or a library cube root;
+// outside [1e-30, 1e30] (beyond the estimate's range) it falls back to 1 / cbrt(x).
+__device__ __forceinline__ float f_rcbrt(float x) { return f_exp2(__log2f(x) * (-1.0f / 3.0f)); }
+__device__ __forceinline__ double f_rcbrt(double x) {
+  if (!(x >= 1e-30 && x <= 1e30)) return 1.0 / cbrt(x);
+  double r = static_cast<double>(f_rcbrt(static_cast<float>(x)));
+  constexpr double kThird = 1.0 / 3.0;
+  r = r * fma(-x, r * r * r, 4.0) * kThird;
+  r = r * fma(-x, r * r * r, 4.0) * kThird;
+  return r;
+}
+// Cube root of x > 0: x r^2 with r = x^(-1/3).
+__device__ __forceinline__ float f_cbrt(float x) { return f_exp2(__log2f(x) * (1.0f / 3.0f)); }
+__device__ __forceinline__ double f_cbrt(double x) {
+  const double r = f_rcbrt(x);
+  return x * r * r;
+}
+
+// h^(5/3) for h > 0: h^2 h^(-1/3).
 template <typename T>
 __device__ __forceinline__ T pow53(T h) {
-  const T r = f_cbrt(h);
-  return h * r * r;
+  return h * h * f_rcbrt(h);
 }
 
 // HLLC flux in the edge frame for the modified depths hL, hR (>= 0) with their
@@ -230,75 +270,191 @@ __device__ __forceinline__ T cell_rate(const T* nxs, const T* nys, const T* ls, 
   return cfl_mode == 1 ? ssum * ia : rmax;
 }
 
-// Per-instance finalize, run by the kTile compute threads of the CTA that completed
-// the instance's last tile.  advance = 1 after a step, 0 after prime.
+// The per-instance work at the end of a step is split three ways so that little of
+// it remains on the launch's critical path (B300 executes FP64 at 2 lanes per SM and
+// cycle, so FP64 chains and reductions in one CTA are slow; sums are finished in warp
+// 0 in a fixed order, maxima run on integer bit patterns).  Each runs in the kTile
+// compute threads of one CTA; cs is the control block as it was when the launch began
+// (t, dt, t_end, clipped, parity, bvol do not change during a launch).  The time the
+// step reaches: t^{n+1} after a step (advance = 1), t^n after prime (advance = 0).
+__device__ __forceinline__ double new_time(const Ctl& cs, int advance) {
+  return advance ? (cs.clipped ? cs.t_end : cs.t + cs.dt) : cs.t;
+}
+
+// Boundary volume: run by the CTA that completes the instance's last boundary tile.
 template <typename T>
-__device__ void finalize_instance(const InstDesc<T>& a, int advance, double* sred, double* sbc) {
-  Ctl* ctl = a.ctl;
+__device__ __noinline__ void finalize_boundary(const InstDesc<T>& a, const Ctl& cs, double* scratch) {
   const int tid = threadIdx.x;
   double bs = 0.0;
-  for (int j = tid; j < a.n_btiles; j += kTile) bs += __ldcg(&a.part[a.btiles[j]].bflux);
-  bs = block_sum<kTile>(bs, sred);
-  if (tid == 0) {
-    if (advance) {
-      const double dt = ctl->dt;
-      ctl->bvol += -dt * bs;
-      ctl->t = ctl->clipped ? ctl->t_end : ctl->t + dt;
-      ctl->parity ^= 1;
-      ctl->steps += 1;
+  for (int j = tid; j < a.n_btiles; j += kTile) bs += __ldcg(&a.part[j].bflux);
+  scratch[tid] = bs;
+  nbar<kTile>();
+  if (tid < 32) {
+    bs = 0.0;
+    for (int k = tid; k < kTile; k += 32) bs += scratch[k];
+    bs = warp_sum(bs);
+    if (tid == 0) {
+      a.ctl->bvol = cs.bvol - cs.dt * bs;
+      a.ctl->b_done = 0u;
     }
-    sbc[0] = ctl->t;
   }
   nbar<kTile>();
-  const double t = sbc[0];
+}
+
+// Inflow at the new time: Q(t), the conveyance-weighted split of Q (sum of l h^(5/3))
+// and the largest inflow-edge rate lambda_b l / |Omega| of Eq. 21.  Run by the CTA that
+// completes the instance's last inflow tile (only inflow tiles read the split, and
+// they are all done).  sred: 9 doubles, sbc: 3, scratch: kTile.
+template <typename T>
+__device__ __noinline__ void finalize_inflow(const InstDesc<T>& a, const Ctl& cs, int advance, double* sred,
+                                             double* sbc, double* scratch) {
+  Ctl* ctl = a.ctl;
+  const int tid = threadIdx.x;
   const double g = a.p.g;
-  // inflow distribution at the new time (conveyance weights l h^(5/3))
-  double wsum = 0.0;
-  for (int j = tid; j < a.n_inflow; j += kTile)
-    wsum += static_cast<double>(a.in_len[j]) * static_cast<double>(__ldcg(&a.in_pw[j]));
-  wsum = block_sum<kTile>(wsum, sred);
-  if (tid == 0) sbc[1] = wsum;
+  const double t = new_time(cs, advance);
+  unsigned long long* ured = reinterpret_cast<unsigned long long*>(sred);
+  // all global loads first, four elements per thread and array at a time
+  constexpr int U = 4;
+  const int ni = a.n_inflow;
+  double pwv[U], lv[U];
+  float hsv[U], liav[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int j = tid + u * kTile;
+    const bool in = j < ni;
+    pwv[u] = in ? static_cast<double>(__ldcg(&a.in_pw[j])) : 0.0;
+    lv[u] = in ? static_cast<double>(a.in_len[j]) : 0.0;
+    hsv[u] = in ? static_cast<float>(__ldcg(&a.in_hs[j])) : 0.0f;
+    liav[u] = in ? static_cast<float>(a.in_lia[j]) : 0.0f;
+  }
+  // Q(t): the thread of the hydrograph segment that contains t evaluates it
+  const int nq = a.p.hydro_n;
+  if (nq <= 0 && tid == 0) sbc[0] = 0.0;
+  for (int i = tid; i <= nq && nq > 0; i += kTile) {
+    const double* ht = a.p.hydro_t;
+    const double* hq = a.p.hydro_q;
+    if (i == 0) {
+      if (t <= ht[0]) sbc[0] = hq[0];
+    } else if (i == nq) {
+      if (t > ht[nq - 1]) sbc[0] = hq[nq - 1];
+    } else if (t > ht[i - 1] && t <= ht[i]) {
+      const double wgt = (t - ht[i - 1]) / (ht[i] - ht[i - 1]);
+      sbc[0] = hq[i - 1] + wgt * (hq[i] - hq[i - 1]);
+    }
+  }
+  {
+    double wsum = 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) wsum += lv[u] * pwv[u];
+    for (int j = tid + U * kTile; j < ni; j += kTile)
+      wsum += static_cast<double>(a.in_len[j]) * static_cast<double>(__ldcg(&a.in_pw[j]));
+    scratch[tid] = wsum;
+    nbar<kTile>();
+    if (tid < 32) {
+      wsum = 0.0;
+      for (int k = tid; k < kTile; k += 32) wsum += scratch[k];
+      wsum = warp_sum(wsum);
+      if (tid == 0) sbc[1] = wsum;
+    }
+  }
   nbar<kTile>();
-  wsum = sbc[1];
-  const double Q = hydrograph(a.p, t);
+  const double Q = sbc[0], wsum = sbc[1];
   const bool wpos = wsum > 0.0;
   const double qscale = wpos ? Q / wsum : 0.0;
   const double quni = (!wpos && a.inflow_len > 0.0) ? Q / a.inflow_len : 0.0;
-  double rb = 0.0;
-  for (int j = tid; j < a.n_inflow; j += kTile) {
-    const double q = wpos ? qscale * static_cast<double>(__ldcg(&a.in_pw[j])) : quni;
-    if (q > 0.0) {
-      const double hs = static_cast<double>(__ldcg(&a.in_hs[j]));
-      const double hb = fmax(hs, cbrt(q * q / g));
-      const double lb = q / hb + sqrt(g * hb);
-      const double ll = lb * static_cast<double>(a.in_len[j]) * static_cast<double>(a.inv_area[a.in_cell[j]]);
-      rb = fmax(rb, a.p.cfl_mode == 0 ? 0.75 * ll : ll);
-    }
+  // a single-precision screen of every inflow edge (relative error well below 1e-5),
+  // then exact FP64 only for the edges that can reach the maximum, which is therefore
+  // the exact FP64 maximum
+  const float gf = static_cast<float>(g), qscf = static_cast<float>(qscale), qunf = static_cast<float>(quni);
+  const float facf = a.p.cfl_mode == 0 ? 0.75f : 1.0f;
+  const double fac = a.p.cfl_mode == 0 ? 0.75 : 1.0;
+  auto screen = [&](float pw, float hs, float lia) {
+    const float q = wpos ? qscf * pw : qunf;
+    const float hbf = fmaxf(hs, f_cbrt(fmaxf(q, 1e-30f) * q / gf));
+    return q > 0.0f ? (q / hbf + sqrtf(gf * hbf)) * lia * facf : 0.0f;
+  };
+  auto exact = [&](double pw, double hs, double lia) {
+    const double q = wpos ? qscale * pw : quni;
+    if (!(q > 0.0)) return 0.0;
+    const double hb = fmax(hs, f_cbrt(q * q / g));
+    return (q / hb + sqrt(g * hb)) * lia * fac;
+  };
+  float scr[U];
+  float rbf = 0.0f;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    scr[u] = tid + u * kTile < ni ? screen(static_cast<float>(pwv[u]), hsv[u], liav[u]) : 0.0f;
+    rbf = fmaxf(rbf, scr[u]);
   }
-  rb = block_max<kTile, double>(rb, sred);
+  for (int j = tid + U * kTile; j < ni; j += kTile)
+    rbf = fmaxf(rbf, screen(static_cast<float>(__ldcg(&a.in_pw[j])), static_cast<float>(__ldcg(&a.in_hs[j])),
+                            static_cast<float>(a.in_lia[j])));
+  const double thr = block_max_nonneg_all<kTile>(static_cast<double>(rbf), ured) * (1.0 - 1e-4);
+  double rb = 0.0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int j = tid + u * kTile;
+    if (j < ni && static_cast<double>(scr[u]) >= thr)
+      rb = fmax(rb, exact(pwv[u], static_cast<double>(__ldcg(&a.in_hs[j])), a.in_lia[j]));
+  }
+  for (int j = tid + U * kTile; j < ni; j += kTile) {
+    const float sj = screen(static_cast<float>(__ldcg(&a.in_pw[j])), static_cast<float>(__ldcg(&a.in_hs[j])),
+                            static_cast<float>(a.in_lia[j]));
+    if (static_cast<double>(sj) >= thr)
+      rb = fmax(rb, exact(static_cast<double>(__ldcg(&a.in_pw[j])), static_cast<double>(__ldcg(&a.in_hs[j])),
+                          a.in_lia[j]));
+  }
+  rb = block_max_nonneg_all<kTile>(rb, ured);
   if (tid == 0) {
-    const double rcell = __longlong_as_double(static_cast<long long>(atomicExch(&ctl->rmax_bits, 0ull)));
-    const double r = fmax(rcell, rb);
-    double dtc = r > 0.0 ? a.p.cfl / r : a.p.dt_max;
-    if (dtc > a.p.dt_max) dtc = a.p.dt_max;
-    ctl->dt_cfl = dtc;
-    double dt = dtc;
-    int clipped = 0;
-    if (dt >= ctl->t_end - t) {
-      dt = ctl->t_end - t;
-      clipped = 1;
-    }
-    ctl->dt = dt;
-    ctl->dt_f = static_cast<float>(dt);
-    ctl->clipped = clipped;
-    ctl->active = t < ctl->t_end ? 1 : 0;
+    ctl->rb = rb;
     ctl->Q = Q;
     ctl->qscale = qscale;
     ctl->quni = quni;
     ctl->quni_f = static_cast<float>(quni);
     ctl->wpos = wpos ? 1 : 0;
-    ctl->done = 0u;
+    ctl->in_done = 0u;
   }
+  nbar<kTile>();
+}
+
+// The step itself: run (thread 0 only) by the CTA that completes the instance's last
+// tile, after the inflow and boundary parts (their CTAs counted their tiles after
+// them).  dt^{n+1} from the maximum cell rate and inflow rate (Eq. 21), then time,
+// parity and step count.
+template <typename T>
+__device__ __forceinline__ void finalize_step(const InstDesc<T>& a, const Ctl& cs, int advance) {
+  Ctl* ctl = a.ctl;
+  const double t = new_time(cs, advance);
+  const double rcell = __longlong_as_double(static_cast<long long>(__ldcg(&ctl->rmax_bits)));
+  const double rb = a.n_in_tiles > 0 ? __ldcg(&ctl->rb) : 0.0;
+  if (advance) {
+    ctl->t = t;
+    ctl->parity = cs.parity ^ 1;
+    ctl->steps = cs.steps + 1;
+  }
+  if (a.n_in_tiles == 0) {
+    ctl->Q = 0.0;
+    ctl->qscale = 0.0;
+    ctl->quni = 0.0;
+    ctl->quni_f = 0.0f;
+    ctl->wpos = 0;
+  }
+  ctl->rmax_bits = 0ull;
+  const double r = fmax(rcell, rb);
+  double dtc = r > 0.0 ? a.p.cfl / r : a.p.dt_max;
+  if (dtc > a.p.dt_max) dtc = a.p.dt_max;
+  ctl->dt_cfl = dtc;
+  double dt = dtc;
+  int clipped = 0;
+  if (dt >= cs.t_end - t) {
+    dt = cs.t_end - t;
+    clipped = 1;
+  }
+  ctl->dt = dt;
+  ctl->dt_f = static_cast<float>(dt);
+  ctl->clipped = clipped;
+  ctl->active = t < cs.t_end ? 1 : 0;
+  ctl->done = 0u;
 }
 
 // ------------------------------------------------------------------ step kernel

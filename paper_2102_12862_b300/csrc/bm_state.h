@@ -99,7 +99,7 @@ struct bm_mesh {
   std::mutex mu;
   int device = -1;
   bool on_device = false;
-  bm::DBuf<double> z, inv_area, area, in_len;
+  bm::DBuf<double> z, inv_area, area, in_len, in_lia;
   bm::DBuf<int32_t> in_cell, btiles, perm;
   bool has32 = false;  // FP32 copies for FP32-bulk states
   bm::DBuf<float> inv_area32, in_len32;
@@ -113,6 +113,7 @@ namespace bm {
 // The work list of a step launch and the shared-memory layout it needs.
 struct StepList {
   DBuf<PipeItem> items;
+  DBuf<int> sched;  // the kernel's tile counters (zero between launches)
   int n = 0;
   uint32_t ne4 = 4, nh4 = 4;
   size_t smem = 0;

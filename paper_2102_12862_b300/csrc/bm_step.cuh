@@ -1,19 +1,23 @@
 // bm_step.cuh -- the fused step kernel (sm_103a): persistent CTAs of eight compute
 // warps and one copy warp, a shared-memory pipeline fed by bulk asynchronous copies.
 //
-// Each CTA walks the launch's work items (tiles of 256 Hilbert-ordered cells of some
-// instance) with a stride of gridDim.x.  Its copy warp streams every tile's data into
-// shared memory ahead of the compute warps, in two groups completed on mbarriers:
+// CTAs take work items (tiles of 256 Hilbert-ordered cells of some instance) from a
+// launch-wide counter, so a CTA that meets expensive wet tiles simply takes fewer
+// (each tile's arithmetic and every reduction are order-independent or in a fixed
+// order, so the result does not depend on which CTA took which tile).  Its copy warp streams every tile's data
+// into a shared-memory slot ahead of the compute warps, in two groups completed on
+// mbarriers:
 //   group A  bulk copies (cp.async.bulk) of the tile record (inverse areas, slots,
-//            edge codes and geometry, halo list), the instance descriptor and a
-//            snapshot of the instance's control block;
-//   group B  issued once A has landed (its addresses come from A): bulk copies of the
-//            tile's slices of the state arrays (surface, discharge, bed, g n^2, FP64:
-//            velocity and celerity) and cp.async gathers of the halo cells' values
-//            (other tiles' cells, in ascending index order).
-// Three A slots and two B slots; the compute warps release a tile's slots when they
-// are done with it (empty barriers) and the copy warp refills them, so copying never
-// stalls the arithmetic.  The compute warps read shared memory only (BASEMENT v3,
+//            edge codes and geometry, halo list), the instance descriptor, a snapshot
+//            of its control block and the tile's slices of the state arrays (surface,
+//            discharge, bed, g n^2, FP64: velocity and celerity) -- addresses the copy
+//            warp knows without waiting (instance pointers cached per instance);
+//   group H  once A has landed (the halo list is in the record): cp.async gathers of
+//            the halo cells' values (other tiles' cells, in ascending index order).
+// Three slots in FP32-bulk, two in FP64 (shared memory).  The compute warps release a
+// slot when they are done with its tile; the copy warp polls for released slots and
+// landed records and issues whichever group can go, so copies run a few tiles ahead
+// of the arithmetic.  The compute warps read shared memory only (BASEMENT v3,
 // Section "Numerical solution"):
 //   phase D  wet/dry flag of every local cell (FP32-bulk: also its velocity/celerity);
 //            a tile whose cells and halo are dry, at rest and without inflow is quiet;
@@ -28,8 +32,8 @@
 //   flush    when the CTA leaves an instance: max rate and tile count to the
 //            instance's control block; the CTA that completes an instance finalizes it
 //            (next dt, time, boundary volume, inflow split) -- no second launch.
-// Every mbarrier wait is bounded (about a second): on timeout the CTA flags the
-// instance (status bit 2), its copy warp drains what it issued, and all warps return.
+// Every wait is bounded (about a second): on timeout the CTA flags the instance
+// (status bit 2), its copy warp drains what it issued, and all warps return.
 #pragma once
 
 #include "bm_kernels.cuh"
@@ -64,6 +68,18 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
       : "r"(saddr(b)), "r"(parity), "r"(100000u)
+      : "memory");
+  return ok != 0;
+}
+// Non-blocking test for completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
       : "memory");
   return ok != 0;
 }
@@ -113,23 +129,23 @@ struct StageInfo {
   int tile, ne, nh, inst;
   uint32_t flags;
   int next_inst;  // instance of the CTA's next tile (-1: none)
-  int pad[2];
+  int bidx;       // rank among the instance's tiles with boundary edges
+  int pad;
 };
-
-constexpr int kASlots = 3, kBSlots = 2;
 
 template <typename T>
 struct StepLayout {
   static constexpr bool k64 = sizeof(T) == 8;
   static constexpr int S = sizeof(T);
+  static constexpr int kSlots = k64 ? 2 : 3;
   static constexpr int kNA = k64 ? 7 : 5;  // staged per-cell arrays
   // array order: FP64 H qx qy z u v c; FP32-bulk H Hlo qx qy z
   static constexpr int kH = 0, kHl = 1, kQx = k64 ? 1 : 2, kQy = k64 ? 2 : 3, kZ = k64 ? 3 : 4, kU = 4, kV = 5, kC = 6;
   static constexpr uint32_t kDesc = (sizeof(InstDesc<T>) + 15) & ~15u;
+  static constexpr uint32_t kSlice = kTile * S;
   uint32_t ne4, nh4, nloc;
-  uint32_t desc, ctl, info, aslot;  // within an A slot (record at 0), A slot size
-  uint32_t gn2, bslot, b0;          // within a B slot (arrays at 0), B slot size, first B slot
-  uint32_t F, uvc, dry, skip, red, total;  // from the start of shared memory
+  uint32_t desc, ctl, info, arr, gn2, slot;  // within a slot (record at 0), slot size
+  uint32_t F, uvc, dry, skip, red, total;    // from the start of shared memory
   BM_HD StepLayout(uint32_t ne4_, uint32_t nh4_) {
     ne4 = ne4_;
     nh4 = nh4_;
@@ -137,25 +153,61 @@ struct StepLayout {
     desc = align16(RecLayout<S>::bytes(ne4, nh4));
     ctl = desc + kDesc;
     info = ctl + static_cast<uint32_t>(sizeof(Ctl));
-    aslot = (info + static_cast<uint32_t>(sizeof(StageInfo)) + 127u) & ~127u;
-    gn2 = kNA * nloc * S;
-    bslot = (gn2 + kTile * S + 127u) & ~127u;
-    b0 = kASlots * aslot;
-    F = b0 + kBSlots * bslot;
-    uvc = F + 5 * ne4 * S;
+    arr = info + static_cast<uint32_t>(sizeof(StageInfo));
+    gn2 = arr + kNA * nloc * S;
+    slot = (gn2 + kSlice + 127u) & ~127u;
+    F = kSlots * slot;
+    // the flux arrays; also the finalize's 2 kTile partial sums (free at the end of a tile)
+    uvc = F + (5 * ne4 * S > 2 * kTile * 8 ? 5 * ne4 * S : 2 * kTile * 8);
     dry = uvc + (k64 ? 0u : 3 * nloc * S);
     skip = dry + align16(nloc);
     red = skip + align16(ne4);
-    total = red + 10 * 8;
+    total = red + (4 + 24) * 8;  // finalize broadcast slots and reduction buffer
   }
 };
 
 // ------------------------------------------------------------------ the copy warp
 
-// Group A of a tile into an A slot (all lanes of the copy warp).
+// Lane l's source of a group-A state slice for an instance: lane 3 + j copies array j
+// (order of StepLayout), lane 3 + kNA copies g n^2; read from the instance's
+// descriptor in global memory at the parity of its control block.
+template <typename T>
+__device__ __forceinline__ const T* slice_src(const PipeItem& it, int lane) {
+  using SL = StepLayout<T>;
+  const InstDesc<T>* d = static_cast<const InstDesc<T>*>(it.desc);
+  const int par = it.ctl->parity;
+  const int j = lane - 3;
+  if constexpr (SL::k64) {
+    switch (j) {
+      case 0: return d->H[par];
+      case 1: return d->qx[par];
+      case 2: return d->qy[par];
+      case 3: return d->z;
+      case 4: return d->u[par];
+      case 5: return d->v[par];
+      case 6: return d->c[par];
+      case 7: return d->gn2;
+      default: return nullptr;
+    }
+  } else {
+    switch (j) {
+      case 0: return d->H[par];
+      case 1: return d->Hlo[par];
+      case 2: return d->qx[par];
+      case 3: return d->qy[par];
+      case 4: return d->z;
+      case 5: return d->gn2;
+      default: return nullptr;
+    }
+  }
+}
+
+// Group A of a tile into a slot (all lanes of the copy warp; src = this lane's slice
+// source for the tile's instance).
 template <typename T>
 __device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* sa, const PipeItem& it, int next_inst,
-                                        uint64_t* mb, int lane) {
+                                        const T* src, uint64_t* mb, int lane) {
+  using SL = StepLayout<T>;
   if (lane == 0) {
     StageInfo* inf = reinterpret_cast<StageInfo*>(sa + L.info);
     inf->tile = it.tile;
@@ -164,24 +216,28 @@ __device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* s
     inf->inst = it.inst;
     inf->flags = it.flags;
     inf->next_inst = next_inst;
+    inf->bidx = static_cast<int>(it.bidx);
     // the arrival (release) orders the stores above before the phase completes
-    mbar_expect_tx(mb, it.rec_bytes + StepLayout<T>::kDesc + static_cast<uint32_t>(sizeof(Ctl)));
+    mbar_expect_tx(mb, it.rec_bytes + SL::kDesc + static_cast<uint32_t>(sizeof(Ctl)) + (SL::kNA + 1) * SL::kSlice);
   }
   __syncwarp();
-  if (lane == 0)
+  if (lane == 0) {
     bulk_g2s(sa, it.rec, it.rec_bytes, mb);
-  else if (lane == 1)
-    bulk_g2s(sa + L.desc, it.desc, StepLayout<T>::kDesc, mb);
-  else if (lane == 2)
+  } else if (lane == 1) {
+    bulk_g2s(sa + L.desc, it.desc, SL::kDesc, mb);
+  } else if (lane == 2) {
     bulk_g2s(sa + L.ctl, it.ctl, static_cast<uint32_t>(sizeof(Ctl)), mb);
+  } else if (lane <= 3 + SL::kNA) {
+    const int j = lane - 3;
+    unsigned char* dst = j < SL::kNA ? sa + L.arr + j * L.nloc * SL::S : sa + L.gn2;
+    bulk_g2s(dst, src + static_cast<size_t>(it.tile) * kTile, SL::kSlice, mb);
+  }
 }
 
-// Group B of a tile into a B slot, from its landed A slot (all lanes of the copy warp):
-// state slices by bulk copy (lane j < kNA: array j, lane kNA: g n^2), halo values by
-// cp.async, each lane arriving on mb when its gathers have landed.
+// Group H of a tile from its landed slot (all lanes of the copy warp): the halo
+// cells' values by cp.async, each lane arriving on mb when its gathers have landed.
 template <typename T>
-__device__ __forceinline__ void issue_b(const StepLayout<T>& L, const unsigned char* sa, unsigned char* sbb,
-                                        uint64_t* mb, int lane) {
+__device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* sa, uint64_t* mb, int lane) {
   using SL = StepLayout<T>;
   const StageInfo& inf = *reinterpret_cast<const StageInfo*>(sa + L.info);
   const InstDesc<T>& a = *reinterpret_cast<const InstDesc<T>*>(sa + L.desc);
@@ -193,19 +249,7 @@ __device__ __forceinline__ void issue_b(const StepLayout<T>& L, const unsigned c
   } else {
     src[0] = a.H[par]; src[1] = a.Hlo[par]; src[2] = a.qx[par]; src[3] = a.qy[par]; src[4] = a.z;
   }
-  T* arr = reinterpret_cast<T*>(sbb);
-  constexpr uint32_t kSlice = kTile * sizeof(T);
-  if (lane == 0) mbar_expect_tx(mb, (SL::kNA + 1) * kSlice);
-  __syncwarp();
-  const T* sj = a.gn2;
-  unsigned char* dj = sbb + L.gn2;
-#pragma unroll
-  for (int j = 0; j < SL::kNA; ++j)
-    if (lane == j) {
-      sj = src[j];
-      dj = reinterpret_cast<unsigned char*>(arr + j * L.nloc);
-    }
-  if (lane <= SL::kNA) bulk_g2s(dj, sj + static_cast<size_t>(inf.tile) * kTile, kSlice, mb);
+  T* arr = reinterpret_cast<T*>(sa + L.arr);
   const int32_t* hidx = reinterpret_cast<const int32_t*>(sa + RecLayout<SL::S>::hidx(round4(inf.ne)));
   for (int h = lane; h < inf.nh; h += 32) {
     const int gi = hidx[h];
@@ -221,37 +265,33 @@ template <typename T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 3;
 
 // One step (prime = 0) or prime pass (prime = 1: no update; derived data, inflow
-// weights and the dt of the current state) over a work list.  ne4max / nh4max: the
-// largest record of the list (they fix the shared-memory layout).  A single state is
+// weights and the dt of the current state) over a work list.  sched: two counters,
+// zero at launch (next item, CTAs done); the last CTA to finish taking items zeroes
+// them for the next launch.  ne4max / nh4max: the largest record of the list (they
+// fix the shared-memory layout).  A single state is
 // a list of one instance's tiles, so a run executes the same machine code alone and in
 // a batch and gives bitwise the same result.
 template <typename T>
 __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const PipeItem* __restrict__ items,
-                                                                         int n_items, int ne4max, int nh4max,
-                                                                         int prime) {
+                                                                         int n_items, int* __restrict__ sched,
+                                                                         int ne4max, int nh4max, int prime) {
   using SL = StepLayout<T>;
   using RL = RecLayout<SL::S>;
   constexpr bool kPair = !SL::k64;
+  constexpr int S = SL::kSlots;
   extern __shared__ __align__(128) unsigned char smem[];
-  // full / empty barriers of the A slots and the B slots
-  __shared__ __align__(8) uint64_t mb_fa[kASlots], mb_ea[kASlots], mb_fb[kBSlots], mb_eb[kBSlots];
+  // per slot: group A landed, group H landed, slot released by the compute warps
+  __shared__ __align__(8) uint64_t mb_a[S], mb_h[S], mb_e[S];
   __shared__ int s_abort;
   const SL L(static_cast<uint32_t>(ne4max), static_cast<uint32_t>(nh4max));
   const int tid = threadIdx.x;
-  const int G = gridDim.x;
-  if (static_cast<int>(blockIdx.x) >= n_items) return;
-  auto aslot = [&](int k) { return smem + (k % kASlots) * L.aslot; };
-  auto bslot = [&](int k) { return smem + L.b0 + (k & 1) * L.bslot; };
-  const int n_mine = (n_items - static_cast<int>(blockIdx.x) + G - 1) / G;  // this CTA's tiles
+  auto slot = [&](int k) { return smem + (k % S) * L.slot; };
 
   if (tid == 0) {
-    for (int s = 0; s < kASlots; ++s) {
-      mbar_init(&mb_fa[s], 1);
-      mbar_init(&mb_ea[s], kTile / 32);
-    }
-    for (int s = 0; s < kBSlots; ++s) {
-      mbar_init(&mb_fb[s], 1 + 32);
-      mbar_init(&mb_eb[s], kTile / 32);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&mb_a[s], 1);
+      mbar_init(&mb_h[s], 32);
+      mbar_init(&mb_e[s], kTile / 32);
     }
     mbar_init_fence();
     s_abort = 0;
@@ -262,44 +302,92 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     // ---------------------------------------------------------------- copy warp
     const int lane = tid - kTile;
     volatile int* abort_flag = &s_abort;
-    // work items are read one tile ahead of their use, so no copy waits on that read
-    auto item = [&](int j) -> PipeItem { return j < n_mine ? items[blockIdx.x + j * G] : PipeItem{}; };
-    int a_next = 0;  // next tile whose group A is issued
+    // the next work item from the launch's counter (tile < 0: none left)
+    auto grab = [&]() -> PipeItem {
+      int t = 0;
+      if (lane == 0) t = atomicAdd(&sched[0], 1);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      PipeItem it{};
+      it.tile = -1;
+      if (t < n_items) it = items[t];
+      return it;
+    };
+    int a_next = 0, h_next = 0;  // next tile (in this CTA's order) whose group A / H is issued
+    bool ended = false;          // the end marker has been issued
+    // the next two items with this lane's slice sources, taken one tile ahead so the
+    // counter and descriptor reads overlap the previous tile
+    PipeItem pa = grab(), pb{};
+    pb.tile = -1;
+    if (pa.tile >= 0) pb = grab();
+    const T* src = pa.tile >= 0 ? slice_src<T>(pa, lane) : nullptr;
+    const T* src_b = (pb.tile >= 0 && pb.inst != pa.inst) ? slice_src<T>(pb, lane) : src;
+    long long idle0 = clock64();
     bool ok = true;
-    PipeItem it0 = item(0), it1 = item(1), it2 = item(2);
-    issue_a<T>(L, aslot(0), it0, n_mine > 1 ? it1.inst : -1, &mb_fa[0], lane);
-    a_next = 1;
-    if (n_mine > 1) {
-      issue_a<T>(L, aslot(1), it1, n_mine > 2 ? it2.inst : -1, &mb_fa[1], lane);
-      a_next = 2;
-    }
-    PipeItem ia = it2, ib = item(3);  // tiles k+2 and k+3 at iteration k
-    for (int k = 0; k < n_mine && ok; ++k) {
-      // B(k): its A landed and tile k-2 released its B slot
-      if (k >= 2) ok = mbar_wait(&mb_eb[k & 1], ((k - 2) >> 1) & 1);
-      ok = ok && mbar_wait(&mb_fa[k % kASlots], (k / kASlots) & 1);
-      ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
-      if (!ok) break;
-      issue_b<T>(L, aslot(k), bslot(k), &mb_fb[k & 1], lane);
-      // A(k+2): tile k-1 released its A slot
-      if (k + 2 < n_mine) {
-        if (k >= 1) ok = mbar_wait(&mb_ea[(k + 2) % kASlots], ((k - 1) / kASlots) & 1);
-        ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
-        if (!ok) break;
-        issue_a<T>(L, aslot(k + 2), ia, k + 3 < n_mine ? ib.inst : -1, &mb_fa[(k + 2) % kASlots], lane);
-        a_next = k + 3;
-        ia = ib;
-        ib = item(k + 4);
+    while (!ended || h_next < a_next) {
+      bool progress = false;
+      // group H of the oldest tile whose group A has landed
+      if (h_next < a_next) {
+        bool landed = false;
+        if (lane == 0) landed = mbar_test(&mb_a[h_next % S], (h_next / S) & 1);
+        if (__shfl_sync(0xffffffffu, landed, 0)) {
+          if (reinterpret_cast<const StageInfo*>(slot(h_next) + L.info)->tile >= 0)
+            issue_h<T>(L, slot(h_next), &mb_h[h_next % S], lane);
+          else
+            cp_async_arrive(&mb_h[h_next % S]);  // end marker: nothing to gather
+          ++h_next;
+          progress = true;
+        }
+      }
+      // group A of the next tile (or the end marker) once its slot is free
+      if (!ended) {
+        bool free_slot = a_next < S;
+        if (!free_slot && lane == 0) free_slot = mbar_test(&mb_e[a_next % S], ((a_next - S) / S) & 1);
+        if (__shfl_sync(0xffffffffu, free_slot, 0)) {
+          if (pa.tile >= 0) {
+            issue_a<T>(L, slot(a_next), pa, pb.tile >= 0 ? pb.inst : -1, src, &mb_a[a_next % S], lane);
+            pa = pb;
+            src = src_b;
+            if (pa.tile >= 0) {
+              pb = grab();
+              if (pb.tile >= 0 && pb.inst != pa.inst) src_b = slice_src<T>(pb, lane);
+            }
+          } else {
+            if (lane == 0) {
+              reinterpret_cast<StageInfo*>(slot(a_next) + L.info)->tile = -1;
+              mbar_expect_tx(&mb_a[a_next % S], 0);
+            }
+            ended = true;
+          }
+          ++a_next;
+          progress = true;
+        }
+      }
+      if (progress) {
+        idle0 = clock64();
+      } else {
+        if (*abort_flag || clock64() - idle0 > kWaitCycles) {
+          ok = false;
+          break;
+        }
+        __nanosleep(100);
       }
     }
     cp_async_wait_all();
-    if (!ok) {
-      if (lane == 0) {
+    if (lane == 0) {
+      if (!ok) {
         *abort_flag = 1;
-        atomicOr(&items[blockIdx.x].ctl->status, 4);
+        atomicOr(&items[0].ctl->status, 4);
       }
-      // let the bulk copies of the last groups issued land before the CTA exits
-      for (int j = a_next - 1; j >= 0 && j >= a_next - kASlots; --j) (void)mbar_wait(&mb_fa[j % kASlots], (j / kASlots) & 1);
+      // every CTA takes exactly one item past the end (or gives up); the last to do so
+      // zeroes the counters for the next launch
+      if (atomicAdd(&sched[1], 1) == static_cast<int>(gridDim.x) - 1) {
+        atomicExch(&sched[0], 0);
+        atomicExch(&sched[1], 0);
+      }
+    }
+    if (!ok) {
+      // let the bulk copies of the groups issued land before the CTA exits
+      for (int j = a_next - 1; j >= 0 && j >= a_next - S; --j) (void)mbar_wait(&mb_a[j % S], (j / S) & 1);
     }
     return;
   }
@@ -313,20 +401,19 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
   volatile int* abort_flag = &s_abort;
   double rrun = 0.0;  // this CTA's max Eq. 21 rate over the current instance's tiles
   unsigned cnt = 0;   // tiles of the current instance this CTA completed
-  int w = blockIdx.x;
-  for (int k = 0; k < n_mine; ++k) {
-    unsigned char* sb = aslot(k);
-    unsigned char* bs_ = bslot(k);
+  for (int k = 0;; ++k) {
+    unsigned char* sb = slot(k);
     {
-      const bool ok = mbar_wait(&mb_fa[k % kASlots], (k / kASlots) & 1) && mbar_wait(&mb_fb[k & 1], (k >> 1) & 1);
+      const bool ok = mbar_wait(&mb_a[k % S], (k / S) & 1) && mbar_wait(&mb_h[k % S], (k / S) & 1);
       if (nbar_or<kTile>(!ok || *abort_flag)) {
         if (tid == 0) {
           *abort_flag = 1;
-          atomicOr(&items[w].ctl->status, 4);
+          atomicOr(&items[0].ctl->status, 4);
         }
         return;
       }
     }
+    if (reinterpret_cast<const StageInfo*>(sb + L.info)->tile < 0) break;  // no more tiles
 
     const StageInfo& inf = *reinterpret_cast<const StageInfo*>(sb + L.info);
     const InstDesc<T>& a = *reinterpret_cast<const InstDesc<T>*>(sb + L.desc);
@@ -339,13 +426,13 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     const T* sNx = reinterpret_cast<const T*>(sb + RL::nx(ne4));
     const T* sNy = reinterpret_cast<const T*>(sb + RL::ny(ne4));
     const T* sLn = reinterpret_cast<const T*>(sb + RL::len(ne4));
-    const T* arr = reinterpret_cast<const T*>(bs_);
+    const T* arr = reinterpret_cast<const T*>(sb + L.arr);
     const T* sH = arr + SL::kH * L.nloc;
     const T* sHl = arr + SL::kHl * L.nloc;  // FP32-bulk only
     const T* sQx = arr + SL::kQx * L.nloc;
     const T* sQy = arr + SL::kQy * L.nloc;
     const T* sZ = arr + SL::kZ * L.nloc;
-    const T* sGn2 = reinterpret_cast<const T*>(bs_ + L.gn2);
+    const T* sGn2 = reinterpret_cast<const T*>(sb + L.gn2);
     T* U;
     T* V;
     T* C;
@@ -530,7 +617,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           h = depth_of(Hh, Hl, zi);
           if (h > hmin && gn2 > zero) {
             // split friction: two semi-implicit stages, Heun average
-            const T cf = f_div(gn2, h * h * f_cbrt(h));
+            const T r3 = f_rcbrt(h), r6 = r3 * r3 * r3 * r3 * r3 * r3;  // h^(-1/3), h^(-2)
+            const T cf = gn2 * (r6 * r3);                                 // g n^2 / h^(7/3)
             const T k0 = cf * f_sqrt(ux * ux + uy * uy);
             const T d0 = f_div(T(1), T(1) + dt * k0);
             const T q1x = ux * d0, q1y = uy * d0;
@@ -573,18 +661,43 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       }
     }
 
-    // end of the tile: boundary flux partial (fixed order), then, when the CTA leaves
-    // the instance, its rate max and tile count; the last CTA finalizes the instance
+    // end of the tile: boundary flux partial (fixed order) and inflow weights -- the
+    // CTA that completes the instance's last boundary / inflow tile sums the boundary
+    // volume / evaluates the inflow at t^{n+1} -- then, when the CTA leaves the
+    // instance, its rate max and tile count; the CTA that completes the last tile
+    // advances the instance
     if (run) {
       ++cnt;
+      double* scratch = reinterpret_cast<double*>(smem + L.F);  // the fluxes are consumed
       if (!prime && (inf.flags & 1u)) {
         const double bs = quiet ? 0.0 : block_sum<kTile>(bsum, red);
-        if (tid == 0) a.part[tile].bflux = bs;
+        int last_b = 0;
+        if (tid == 0) {
+          a.part[inf.bidx].bflux = bs;
+          __threadfence();
+          last_b = atomicAdd(&a.ctl->b_done, 1u) + 1u == static_cast<unsigned>(a.n_btiles) ? 1 : 0;
+        }
+        if (nbar_or<kTile>(last_b)) {
+          __threadfence();
+          finalize_boundary<T>(a, cs, scratch);
+        }
+      }
+      if (inf.flags & 2u) {
+        nbar<kTile>();  // every thread's inflow weights are stored
+        int last_in = 0;
+        if (tid == 0) {
+          __threadfence();
+          last_in = atomicAdd(&a.ctl->in_done, 1u) + 1u == static_cast<unsigned>(a.n_in_tiles) ? 1 : 0;
+        }
+        if (nbar_or<kTile>(last_in)) {
+          __threadfence();
+          finalize_inflow<T>(a, cs, prime ? 0 : 1, red + 4, red, scratch);
+        }
       }
     }
     const bool leave = inf.next_inst != inf.inst;
     if (leave && cnt > 0) {
-      const double r = block_max<kTile, double>(rrun, red);
+      const double r = block_max_nonneg_all<kTile>(rrun, reinterpret_cast<unsigned long long*>(red));
       int is_last = 0;
       if (tid == 0) {
         if (r > 0.0) atomicMax(&a.ctl->rmax_bits, static_cast<unsigned long long>(__double_as_longlong(r)));
@@ -592,21 +705,16 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         const unsigned prev = atomicAdd(&a.ctl->done, cnt);
         is_last = (prev + cnt == static_cast<unsigned>(a.n_tiles)) ? 1 : 0;
       }
-      if (nbar_or<kTile>(is_last)) {
+      if (tid == 0 && is_last) {
         __threadfence();
-        finalize_instance<T>(a, prime ? 0 : 1, red, red + 8);
+        finalize_step<T>(a, cs, prime ? 0 : 1);
       }
       rrun = 0.0;
       cnt = 0;
     }
-    // release the tile's slots to the copy warp (each warp once it is done with them)
+    // release the tile's slot to the copy warp (each warp once it is done with it)
     __syncwarp();
-    if ((tid & 31) == 0) {
-      mbar_arrive(&mb_ea[k % kASlots]);
-      mbar_arrive(&mb_eb[k & 1]);
-    }
-    w += G;
-
+    if ((tid & 31) == 0) mbar_arrive(&mb_e[k % S]);
   }
 }
 
