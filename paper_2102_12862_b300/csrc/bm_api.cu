@@ -193,8 +193,11 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
     nh4 = std::max(nh4, R.nh4_max);
   }
   cudaError_t e = out->items.upload(items);
-  if (e == cudaSuccess) e = out->sched.alloc(2);
-  if (e == cudaSuccess) e = cudaMemset(out->sched.p, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = out->sched.alloc(6);
+  if (e == cudaSuccess) e = cudaMemset(out->sched.p, 0, 6 * sizeof(int));
+  if (e == cudaSuccess) e = out->early.alloc(2 * items.size());
+  if (e == cudaSuccess) e = out->mark.alloc(items.size());
+  if (e == cudaSuccess) e = cudaMemset(out->mark.p, 0xff, items.size() * sizeof(int));  // stamp -1: none
   if (e != cudaSuccess) return dev_fail(e, "work list upload");
   out->n = static_cast<int>(items.size());
   out->ne4 = ne4;
@@ -223,11 +226,11 @@ void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t 
   if (l.n <= 0) return;
   grid = std::max(1, std::min(grid, l.n));
   if (prec == BM_FP64)
-    step_pipe<double><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, l.sched.p, static_cast<int>(l.ne4),
-                                                           static_cast<int>(l.nh4), prime);
+    step_pipe<double><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, l.sched.p, l.early.p, l.mark.p,
+                                                           static_cast<int>(l.ne4), static_cast<int>(l.nh4), prime);
   else
-    step_pipe<float><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, l.sched.p, static_cast<int>(l.ne4),
-                                                          static_cast<int>(l.nh4), prime);
+    step_pipe<float><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, l.sched.p, l.early.p, l.mark.p,
+                                                          static_cast<int>(l.ne4), static_cast<int>(l.nh4), prime);
 }
 
 namespace {

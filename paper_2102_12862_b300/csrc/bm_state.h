@@ -113,7 +113,9 @@ namespace bm {
 // The work list of a step launch and the shared-memory layout it needs.
 struct StepList {
   DBuf<PipeItem> items;
-  DBuf<int> sched;  // the kernel's tile counters (zero between launches)
+  DBuf<int> sched;  // the kernel's scheduling counters (see step_pipe)
+  DBuf<int> early;  // 2 x n: items a launch takes first (written by the previous launch)
+  DBuf<int> mark;   // n: launch stamp of the early list an item is on
   int n = 0;
   uint32_t ne4 = 4, nh4 = 4;
   size_t smem = 0;

@@ -2,9 +2,14 @@
 // warps and one copy warp, a shared-memory pipeline fed by bulk asynchronous copies.
 //
 // CTAs take work items (tiles of 256 Hilbert-ordered cells of some instance) from a
-// launch-wide counter, so a CTA that meets expensive wet tiles simply takes fewer
-// (each tile's arithmetic and every reduction are order-independent or in a fixed
-// order, so the result does not depend on which CTA took which tile).  Its copy warp streams every tile's data
+// launch-wide counter, so a CTA that meets expensive wet tiles simply takes fewer;
+// in FP64, where a wet tile costs many times a dry one (B300's FP64 rate), the tiles
+// the previous launch found wet, or that have boundary or inflow edges, are taken
+// first so the expensive tiles do not come last; the others (all tiles in FP32-bulk,
+// which is bound by memory traffic and profits from spatial order) follow in the work
+// list's order (each tile's arithmetic and every reduction are order-independent or
+// in a fixed order, so the result does not depend on which CTA took which tile, or
+// when).  Its copy warp streams every tile's data
 // into a shared-memory slot ahead of the compute warps, in two groups completed on
 // mbarriers:
 //   group A  bulk copies (cp.async.bulk) of the tile record (inverse areas, slots,
@@ -130,7 +135,7 @@ struct StageInfo {
   uint32_t flags;
   int next_inst;  // instance of the CTA's next tile (-1: none)
   int bidx;       // rank among the instance's tiles with boundary edges
-  int pad;
+  int item;       // index of the work item
 };
 
 template <typename T>
@@ -205,8 +210,8 @@ __device__ __forceinline__ const T* slice_src(const PipeItem& it, int lane) {
 // Group A of a tile into a slot (all lanes of the copy warp; src = this lane's slice
 // source for the tile's instance).
 template <typename T>
-__device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* sa, const PipeItem& it, int next_inst,
-                                        const T* src, uint64_t* mb, int lane) {
+__device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* sa, const PipeItem& it, int item,
+                                        int next_inst, const T* src, uint64_t* mb, int lane) {
   using SL = StepLayout<T>;
   if (lane == 0) {
     StageInfo* inf = reinterpret_cast<StageInfo*>(sa + L.info);
@@ -217,6 +222,7 @@ __device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* s
     inf->flags = it.flags;
     inf->next_inst = next_inst;
     inf->bidx = static_cast<int>(it.bidx);
+    inf->item = item;
     // the arrival (release) orders the stores above before the phase completes
     mbar_expect_tx(mb, it.rec_bytes + SL::kDesc + static_cast<uint32_t>(sizeof(Ctl)) + (SL::kNA + 1) * SL::kSlice);
   }
@@ -265,15 +271,21 @@ template <typename T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 3;
 
 // One step (prime = 0) or prime pass (prime = 1: no update; derived data, inflow
-// weights and the dt of the current state) over a work list.  sched: two counters,
-// zero at launch (next item, CTAs done); the last CTA to finish taking items zeroes
-// them for the next launch.  ne4max / nh4max: the largest record of the list (they
-// fix the shared-memory layout).  A single state is
+// weights and the dt of the current state) over a work list.  sched: [0] next ticket,
+// [1] CTAs done taking items (both zero at launch; the last CTA to finish taking zeroes
+// them), [2] launch stamp s, [3] early items listed for launch s + 1, [4] early items
+// listed for this launch (E), [5] items finished.  Ticket t < E takes early[s & 1][t];
+// t < E + n_items takes item t - E unless mark[t - E] == s (it was early).  Finished
+// early items are listed in early[(s + 1) & 1] and marked s + 1; the last item to
+// finish moves [3] to [4], zeroes [3] and [5] and increments s.  early: 2 x n_items,
+// mark: n_items.  ne4max / nh4max: the largest record of the list (they fix the
+// shared-memory layout).  A single state is
 // a list of one instance's tiles, so a run executes the same machine code alone and in
 // a batch and gives bitwise the same result.
 template <typename T>
 __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const PipeItem* __restrict__ items,
                                                                          int n_items, int* __restrict__ sched,
+                                                                         int* __restrict__ early, int* __restrict__ mark,
                                                                          int ne4max, int nh4max, int prime) {
   using SL = StepLayout<T>;
   using RL = RecLayout<SL::S>;
@@ -303,22 +315,47 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     const int lane = tid - kTile;
     volatile int* abort_flag = &s_abort;
     // the next work item from the launch's counter (tile < 0: none left)
-    auto grab = [&]() -> PipeItem {
-      int t = 0;
-      if (lane == 0) t = atomicAdd(&sched[0], 1);
-      t = __shfl_sync(0xffffffffu, t, 0);
+    int stamp = 0, n_early = 0;
+    if (SL::k64 && lane == 0) {
+      stamp = *reinterpret_cast<volatile int*>(&sched[2]);
+      n_early = *reinterpret_cast<volatile int*>(&sched[4]);
+    }
+    stamp = __shfl_sync(0xffffffffu, stamp, 0);
+    n_early = min(__shfl_sync(0xffffffffu, n_early, 0), n_items);
+    const int* ord = early + static_cast<size_t>(stamp & 1) * n_items;
+    int idx_a = -1, idx_b = -1;  // work-item indices of pa, pb
+    auto grab = [&](int& idx) -> PipeItem {
       PipeItem it{};
       it.tile = -1;
-      if (t < n_items) it = items[t];
-      return it;
+      idx = -1;
+      for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&sched[0], 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t < n_early) {
+          idx = ord[t];
+        } else if (t < n_early + n_items) {
+          idx = t - n_early;
+          // taken in the early pass: listed with stamp s, or already finished there and
+          // re-listed with s + 1 (an item only finishes after it was taken)
+          if (n_early > 0) {
+            const int m = __ldcg(&mark[idx]);
+            if (m == stamp || m == stamp + 1) continue;
+          }
+        } else {
+          return it;
+        }
+        it = items[idx];
+        return it;
+      }
     };
     int a_next = 0, h_next = 0;  // next tile (in this CTA's order) whose group A / H is issued
     bool ended = false;          // the end marker has been issued
     // the next two items with this lane's slice sources, taken one tile ahead so the
     // counter and descriptor reads overlap the previous tile
-    PipeItem pa = grab(), pb{};
+    PipeItem pa = grab(idx_a), pb{};
     pb.tile = -1;
-    if (pa.tile >= 0) pb = grab();
+    if (pa.tile >= 0) pb = grab(idx_b);
     const T* src = pa.tile >= 0 ? slice_src<T>(pa, lane) : nullptr;
     const T* src_b = (pb.tile >= 0 && pb.inst != pa.inst) ? slice_src<T>(pb, lane) : src;
     long long idle0 = clock64();
@@ -344,11 +381,12 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         if (!free_slot && lane == 0) free_slot = mbar_test(&mb_e[a_next % S], ((a_next - S) / S) & 1);
         if (__shfl_sync(0xffffffffu, free_slot, 0)) {
           if (pa.tile >= 0) {
-            issue_a<T>(L, slot(a_next), pa, pb.tile >= 0 ? pb.inst : -1, src, &mb_a[a_next % S], lane);
+            issue_a<T>(L, slot(a_next), pa, idx_a, pb.tile >= 0 ? pb.inst : -1, src, &mb_a[a_next % S], lane);
             pa = pb;
+            idx_a = idx_b;
             src = src_b;
             if (pa.tile >= 0) {
-              pb = grab();
+              pb = grab(idx_b);
               if (pb.tile >= 0 && pb.inst != pa.inst) src_b = slice_src<T>(pb, lane);
             }
           } else {
@@ -399,6 +437,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
   double* red = reinterpret_cast<double*>(smem + L.red);
   const T zero = T(0);
   volatile int* abort_flag = &s_abort;
+  const int stamp = *reinterpret_cast<volatile int*>(&sched[2]);  // read before any item can finish
+  int* next_early = early + static_cast<size_t>((stamp + 1) & 1) * n_items;
   double rrun = 0.0;  // this CTA's max Eq. 21 rate over the current instance's tiles
   unsigned cnt = 0;   // tiles of the current instance this CTA completed
   for (int k = 0;; ++k) {
@@ -711,6 +751,23 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       }
       rrun = 0.0;
       cnt = 0;
+    }
+    // FP64: wet, boundary and inflow tiles are taken early in the next launch; the last
+    // item to finish rolls the lists over
+    if (SL::k64 && tid == 0) {
+      if (!quiet || (inf.flags & 3u)) {
+        const int pos = atomicAdd(&sched[3], 1);
+        if (pos < n_items) {
+          next_early[pos] = inf.item;
+          mark[inf.item] = stamp + 1;
+        }
+      }
+      __threadfence();
+      if (atomicAdd(&sched[5], 1) == n_items - 1) {
+        atomicExch(&sched[4], min(atomicExch(&sched[3], 0), n_items));
+        atomicExch(&sched[5], 0);
+        atomicExch(&sched[2], stamp + 1);
+      }
     }
     // release the tile's slot to the copy warp (each warp once it is done with it)
     __syncwarp();
