@@ -87,7 +87,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("bm_kernels.cuh", "bm_internal.h"):
+    for f in ("bm_kernels.cuh", "bm_step.cuh", "bm_internal.h"):
         with open(os.path.join(ROOT, "paper_2102_12862_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
