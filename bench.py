@@ -46,10 +46,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s"
 # Algorithmic DRAM bytes of one step: every byte the step must move once.  Per cell:
-# the state read and written (FP64: H, qx, qy, u, v, c; FP32-bulk: H hi/lo, qx, qy),
-# z, g n^2, 1/|Omega| and the 4-byte slot word; per mesh edge (each read once): the
-# 4-byte code word and nx, ny, l.
-BYTES_PER_CELL = {"fp64": 2 * 48 + 3 * 8 + 4, "fp32": 2 * 16 + 3 * 4 + 4}
+# the state read and written (FP64: H, qx, qy; FP32-bulk: H hi/lo, qx, qy), z, g n^2,
+# 1/|Omega| and the 4-byte slot word; per mesh edge (each read once): the 4-byte code
+# word and nx, ny, l.
+BYTES_PER_CELL = {"fp64": 2 * 24 + 3 * 8 + 4, "fp32": 2 * 16 + 3 * 4 + 4}
 BYTES_PER_EDGE = {"fp64": 4 + 3 * 8, "fp32": 4 + 3 * 4}
 HBM_FALLBACK_GBS = 6400.0
 KERNEL_NAME = {"fp64": "step_pipe<double>", "fp32": "step_pipe<float>"}

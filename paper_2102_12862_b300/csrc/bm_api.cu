@@ -302,7 +302,6 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
   Buffers<T>& b = s->buf<T>();
   for (int k = 0; k < 2; ++k) {
     d.H[k] = b.H[k].p; d.Hlo[k] = b.Hlo[k].p; d.qx[k] = b.qx[k].p; d.qy[k] = b.qy[k].p;
-    d.u[k] = b.u[k].p; d.v[k] = b.v[k].p; d.c[k] = b.c[k].p;
   }
   d.z = b.z.p;
   d.gn2 = b.gn2.p;
@@ -364,6 +363,9 @@ bm_status load_state(bm_state* s, const double* H, const double* qx, const doubl
   const int nb = (n + 255) / 256;
   const int32_t* perm = s->mesh->perm.p;
   BM_CUDA(cudaMemsetAsync(s->bad.p, 0, sizeof(int), s->stream));
+  // a fresh scheduling state (a launch that gave up may have left it inconsistent)
+  BM_CUDA(cudaMemsetAsync(s->list.sched.p, 0, s->list.sched.bytes(), s->stream));
+  BM_CUDA(cudaMemsetAsync(s->list.mark.p, 0xff, s->list.mark.bytes(), s->stream));
   if (s->prec == BM_FP64) {
     Buffers<double>& b = s->b64;
     gather_from_user<double><<<nb, 256, 0, s->stream>>>(s->stage[0].p, perm, n, b.H[0].p);
@@ -409,11 +411,11 @@ bm_status alloc_state(bm_state* s, const bm_params* prm) {
   if (mst != BM_OK) return mst;
   cudaError_t e = cudaSuccess;
   if (f64) {
-    e = s->b64.alloc(Np, static_cast<size_t>(h.n_inflow), true);
+    e = s->b64.alloc(Np, static_cast<size_t>(h.n_inflow), false);
     if (e == cudaSuccess) e = s->b64.gn2.upload(gn2);
     if (e == cudaSuccess) e = cudaMemcpy(s->b64.z.p, h.z.data(), Np * sizeof(double), cudaMemcpyHostToDevice);
   } else {
-    e = s->b32.alloc(Np, static_cast<size_t>(h.n_inflow), false);
+    e = s->b32.alloc(Np, static_cast<size_t>(h.n_inflow), true);
     if (e == cudaSuccess) e = s->b32.gn2.upload(narrow<float>(gn2));
     if (e == cudaSuccess) {
       std::vector<float> z32 = narrow<float>(h.z, s->datum);
@@ -465,7 +467,7 @@ size_t state_footprint(const bm_mesh* m, int precision) {
   const HostMesh& h = m->h;
   const size_t Np = static_cast<size_t>(h.n_tiles) * kTile;
   const size_t w = precision == BM_FP64 ? 8 : 4;
-  const size_t arrays = precision == BM_FP64 ? 14 : 10;  // 2 x (H [pair], q, derived) + z, gn2
+  const size_t arrays = precision == BM_FP64 ? 8 : 10;  // 2 x (H [pair], q) + z, gn2
   // + caller-order staging, per tile: boundary partial, volume partial, work item
   return Np * w * arrays + 3 * static_cast<size_t>(h.n_cells) * 8 + static_cast<size_t>(h.n_tiles) * 72 +
          static_cast<size_t>(h.n_inflow) * 2 * w + 4096;
@@ -798,7 +800,7 @@ template <typename T>
 cudaError_t snapshot_buffers(Buffers<T>& b, Snapshot* sn, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-    DBuf<T>* bufs[7] = {&b.H[k], &b.Hlo[k], &b.qx[k], &b.qy[k], &b.u[k], &b.v[k], &b.c[k]};
+    DBuf<T>* bufs[4] = {&b.H[k], &b.Hlo[k], &b.qx[k], &b.qy[k]};
     for (auto* x : bufs)
       if (e == cudaSuccess) e = sn->take(x->p, x->bytes(), st);
   }

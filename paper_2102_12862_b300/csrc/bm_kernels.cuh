@@ -22,9 +22,6 @@ struct alignas(16) InstDesc {
   T* Hlo[2];  // FP32-bulk only: lo part of the free surface
   T* qx[2];
   T* qy[2];
-  T* u[2];   // FP64 only: velocity of the cell (0 at or below h_min)
-  T* v[2];
-  T* c[2];   // FP64 only: sqrt(g max(0, h))
   const T* z;
   const T* gn2;       // g n^2
   const T* inv_area;  // 1 / |Omega_i|

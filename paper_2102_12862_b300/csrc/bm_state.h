@@ -54,27 +54,22 @@ struct DBuf {
 // Per-precision state arrays of one instance (new cell numbering, padded).
 template <typename T>
 struct Buffers {
-  DBuf<T> H[2], Hlo[2], qx[2], qy[2], u[2], v[2], c[2];
+  DBuf<T> H[2], Hlo[2], qx[2], qy[2];
   DBuf<T> z, gn2, in_pw, in_hs;
-  cudaError_t alloc(size_t np, size_t n_inflow, bool derived) {
+  cudaError_t alloc(size_t np, size_t n_inflow, bool pair) {
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
       e = H[b].alloc(np);
-      if (e == cudaSuccess && !derived) e = Hlo[b].alloc(np);  // FP32-bulk keeps H as a pair
+      if (e == cudaSuccess && pair) e = Hlo[b].alloc(np);  // FP32-bulk keeps H as a pair
       if (e == cudaSuccess) e = qx[b].alloc(np);
       if (e == cudaSuccess) e = qy[b].alloc(np);
-      if (derived) {
-        if (e == cudaSuccess) e = u[b].alloc(np);
-        if (e == cudaSuccess) e = v[b].alloc(np);
-        if (e == cudaSuccess) e = c[b].alloc(np);
-      }
     }
     if (e == cudaSuccess) e = z.alloc(np);
     if (e == cudaSuccess) e = in_pw.alloc(n_inflow > 0 ? n_inflow : 1);
     if (e == cudaSuccess) e = in_hs.alloc(n_inflow > 0 ? n_inflow : 1);
     // zero everything once so padding cells stay inert
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-      DBuf<T>* bufs[7] = {&H[b], &Hlo[b], &qx[b], &qy[b], &u[b], &v[b], &c[b]};
+      DBuf<T>* bufs[4] = {&H[b], &Hlo[b], &qx[b], &qy[b]};
       for (auto* x : bufs)
         if (e == cudaSuccess && x->p) e = cudaMemset(x->p, 0, x->bytes());
     }
@@ -85,8 +80,7 @@ struct Buffers {
   size_t bytes() const {
     size_t b = z.bytes() + gn2.bytes() + in_pw.bytes() + in_hs.bytes();
     for (int k = 0; k < 2; ++k)
-      b += H[k].bytes() + Hlo[k].bytes() + qx[k].bytes() + qy[k].bytes() + u[k].bytes() + v[k].bytes() +
-           c[k].bytes();
+      b += H[k].bytes() + Hlo[k].bytes() + qx[k].bytes() + qy[k].bytes();
     return b;
   }
 };

@@ -15,16 +15,17 @@
 //   group A  bulk copies (cp.async.bulk) of the tile record (inverse areas, slots,
 //            edge codes and geometry, halo list), the instance descriptor, a snapshot
 //            of its control block and the tile's slices of the state arrays (surface,
-//            discharge, bed, g n^2, FP64: velocity and celerity) -- addresses the copy
-//            warp knows without waiting (instance pointers cached per instance);
-//   group H  once A has landed (the halo list is in the record): cp.async gathers of
-//            the halo cells' values (other tiles' cells, in ascending index order).
-// Three slots in FP32-bulk, two in FP64 (shared memory).  The compute warps release a
-// slot when they are done with its tile; the copy warp polls for released slots and
-// landed records and issues whichever group can go, so copies run a few tiles ahead
-// of the arithmetic.  The compute warps read shared memory only (BASEMENT v3,
+//            discharge, bed, g n^2) -- addresses the copy warp knows without waiting
+//            (instance pointers cached per instance);
+//   group H  issued right after A: cp.async gathers of the halo cells' values (other
+//            tiles' cells, in ascending index order), the halo list read from the
+//            record in global memory one tile ahead, so H does not wait for A.
+// Three slots per CTA.  The compute warps release a slot when they are done with its
+// tile; the copy warp polls for released slots and refills them, so copies run a few
+// tiles ahead of the arithmetic.  The compute warps read shared memory only (BASEMENT v3,
 // Section "Numerical solution"):
-//   phase D  wet/dry flag of every local cell (FP32-bulk: also its velocity/celerity);
+//   phase D  wet/dry flag, velocity and celerity of every local cell (dry: zero, without
+//            arithmetic);
 //            a tile whose cells and halo are dry, at rest and without inflow is quiet;
 //   phase F  each tile edge once: modified states on max(z_L, z_R), HLLC flux in the
 //            edge frame, pre-balanced pressure, wall / transmissive / inflow states;
@@ -142,10 +143,10 @@ template <typename T>
 struct StepLayout {
   static constexpr bool k64 = sizeof(T) == 8;
   static constexpr int S = sizeof(T);
-  static constexpr int kSlots = k64 ? 2 : 3;
-  static constexpr int kNA = k64 ? 7 : 5;  // staged per-cell arrays
-  // array order: FP64 H qx qy z u v c; FP32-bulk H Hlo qx qy z
-  static constexpr int kH = 0, kHl = 1, kQx = k64 ? 1 : 2, kQy = k64 ? 2 : 3, kZ = k64 ? 3 : 4, kU = 4, kV = 5, kC = 6;
+  static constexpr int kSlots = 3;
+  static constexpr int kNA = k64 ? 4 : 5;  // staged per-cell arrays
+  // array order: FP64 H qx qy z; FP32-bulk H Hlo qx qy z
+  static constexpr int kH = 0, kHl = 1, kQx = k64 ? 1 : 2, kQy = k64 ? 2 : 3, kZ = k64 ? 3 : 4;
   static constexpr uint32_t kDesc = (sizeof(InstDesc<T>) + 15) & ~15u;
   static constexpr uint32_t kSlice = kTile * S;
   uint32_t ne4, nh4, nloc;
@@ -164,7 +165,7 @@ struct StepLayout {
     F = kSlots * slot;
     // the flux arrays; also the finalize's 2 kTile partial sums (free at the end of a tile)
     uvc = F + (5 * ne4 * S > 2 * kTile * 8 ? 5 * ne4 * S : 2 * kTile * 8);
-    dry = uvc + (k64 ? 0u : 3 * nloc * S);
+    dry = uvc + 3 * nloc * S;
     skip = dry + align16(nloc);
     red = skip + align16(ne4);
     total = red + (4 + 24) * 8;  // finalize broadcast slots and reduction buffer
@@ -188,10 +189,7 @@ __device__ __forceinline__ const T* slice_src(const PipeItem& it, int lane) {
       case 1: return d->qx[par];
       case 2: return d->qy[par];
       case 3: return d->z;
-      case 4: return d->u[par];
-      case 5: return d->v[par];
-      case 6: return d->c[par];
-      case 7: return d->gn2;
+      case 4: return d->gn2;
       default: return nullptr;
     }
   } else {
@@ -240,27 +238,51 @@ __device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* s
   }
 }
 
-// Group H of a tile from its landed slot (all lanes of the copy warp): the halo
-// cells' values by cp.async, each lane arriving on mb when its gathers have landed.
+// The first kHaloPre halo indices of a tile, read from its record in global memory
+// (lane l holds entries l, l + 32, l + 64), ahead of the tile's issue.
+constexpr int kHaloPre = 3;
 template <typename T>
-__device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* sa, uint64_t* mb, int lane) {
-  using SL = StepLayout<T>;
-  const StageInfo& inf = *reinterpret_cast<const StageInfo*>(sa + L.info);
-  const InstDesc<T>& a = *reinterpret_cast<const InstDesc<T>*>(sa + L.desc);
-  const int par = reinterpret_cast<const Ctl*>(sa + L.ctl)->parity;
-  const T* src[SL::kNA];
-  if constexpr (SL::k64) {
-    src[0] = a.H[par]; src[1] = a.qx[par]; src[2] = a.qy[par]; src[3] = a.z;
-    src[4] = a.u[par]; src[5] = a.v[par]; src[6] = a.c[par];
-  } else {
-    src[0] = a.H[par]; src[1] = a.Hlo[par]; src[2] = a.qx[par]; src[3] = a.qy[par]; src[4] = a.z;
-  }
-  T* arr = reinterpret_cast<T*>(sa + L.arr);
-  const int32_t* hidx = reinterpret_cast<const int32_t*>(sa + RecLayout<SL::S>::hidx(round4(inf.ne)));
-  for (int h = lane; h < inf.nh; h += 32) {
-    const int gi = hidx[h];
+__device__ __forceinline__ void load_halo(const PipeItem& it, int lane, int (&hv)[kHaloPre]) {
+  const int nh = it.tile >= 0 ? static_cast<int>(it.ne_nh >> 16) : 0;
+  const int32_t* hg =
+      reinterpret_cast<const int32_t*>(it.rec + RecLayout<sizeof(T)>::hidx(round4(it.ne_nh & 0xffffu)));
 #pragma unroll
-    for (int j = 0; j < SL::kNA; ++j) cp_async<sizeof(T)>(arr + j * L.nloc + kTile + h, src[j] + gi);
+  for (int u = 0; u < kHaloPre; ++u) {
+    const int h = lane + 32 * u;
+    hv[u] = h < nh ? __ldg(hg + h) : 0;
+  }
+}
+
+// Group H of a tile (all lanes of the copy warp): the halo cells' values by cp.async,
+// each lane arriving on mb when its gathers have landed.  src: this lane's slice
+// source (lane 3 + j holds array j); hv: the prefetched halo indices.
+template <typename T>
+__device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* sa, const PipeItem& it, const T* src,
+                                        const int (&hv)[kHaloPre], uint64_t* mb, int lane) {
+  using SL = StepLayout<T>;
+  const int nh = static_cast<int>(it.ne_nh >> 16);
+  const T* sp[SL::kNA];
+#pragma unroll
+  for (int j = 0; j < SL::kNA; ++j)
+    sp[j] = reinterpret_cast<const T*>(
+        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(src), 3 + j));
+  T* arr = reinterpret_cast<T*>(sa + L.arr);
+#pragma unroll
+  for (int u = 0; u < kHaloPre; ++u) {
+    const int h = lane + 32 * u;
+    if (h < nh) {
+#pragma unroll
+      for (int j = 0; j < SL::kNA; ++j) cp_async<sizeof(T)>(arr + j * L.nloc + kTile + h, sp[j] + hv[u]);
+    }
+  }
+  if (nh > 32 * kHaloPre) {  // large halos (unusual meshes): the rest of the indices now
+    const int32_t* hg =
+        reinterpret_cast<const int32_t*>(it.rec + RecLayout<SL::S>::hidx(round4(it.ne_nh & 0xffffu)));
+    for (int h = 32 * kHaloPre + lane; h < nh; h += 32) {
+      const int gi = __ldg(hg + h);
+#pragma unroll
+      for (int j = 0; j < SL::kNA; ++j) cp_async<sizeof(T)>(arr + j * L.nloc + kTile + h, sp[j] + gi);
+    }
   }
   cp_async_arrive(mb);
 }
@@ -314,7 +336,10 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     // ---------------------------------------------------------------- copy warp
     const int lane = tid - kTile;
     volatile int* abort_flag = &s_abort;
-    // the next work item from the launch's counter (tile < 0: none left)
+    // Work items come from the launch's counter through a three-stage pipeline, so the
+    // copy warp never waits on a value in the iteration that asked for it: a ticket
+    // (atomic) -> the item read -> promotion to "next to issue" (instance pointers and
+    // halo indices read) -> issue.  FP64 tickets map through the early list first.
     int stamp = 0, n_early = 0;
     if (SL::k64 && lane == 0) {
       stamp = *reinterpret_cast<volatile int*>(&sched[2]);
@@ -323,82 +348,87 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     stamp = __shfl_sync(0xffffffffu, stamp, 0);
     n_early = min(__shfl_sync(0xffffffffu, n_early, 0), n_items);
     const int* ord = early + static_cast<size_t>(stamp & 1) * n_items;
-    int idx_a = -1, idx_b = -1;  // work-item indices of pa, pb
-    auto grab = [&](int& idx) -> PipeItem {
+    const int n_tickets = n_early + n_items;
+    // ticket -> work item (-1: taken in the early pass; -2: past the end).  An item
+    // listed with stamp s, or finished in the early pass and re-listed with s + 1, was
+    // taken early (an item only finishes after it was taken).
+    auto item_of = [&](int t) -> int {
+      if (t < n_early) return ord[t];
+      if (t >= n_tickets) return -2;
+      const int idx = t - n_early;
+      if (n_early > 0) {
+        const int m = __ldcg(&mark[idx]);
+        if (m == stamp || m == stamp + 1) return -1;
+      }
+      return idx;
+    };
+    auto fetch = [&](int idx) -> PipeItem {
       PipeItem it{};
       it.tile = -1;
-      idx = -1;
-      for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(&sched[0], 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t < n_early) {
-          idx = ord[t];
-        } else if (t < n_early + n_items) {
-          idx = t - n_early;
-          // taken in the early pass: listed with stamp s, or already finished there and
-          // re-listed with s + 1 (an item only finishes after it was taken)
-          if (n_early > 0) {
-            const int m = __ldcg(&mark[idx]);
-            if (m == stamp || m == stamp + 1) continue;
-          }
-        } else {
-          return it;
-        }
-        it = items[idx];
-        return it;
-      }
+      if (idx >= 0) it = items[idx];
+      return it;
     };
-    int a_next = 0, h_next = 0;  // next tile (in this CTA's order) whose group A / H is issued
-    bool ended = false;          // the end marker has been issued
-    // the next two items with this lane's slice sources, taken one tile ahead so the
-    // counter and descriptor reads overlap the previous tile
-    PipeItem pa = grab(idx_a), pb{};
-    pb.tile = -1;
-    if (pa.tile >= 0) pb = grab(idx_b);
+    auto take = [&]() -> int {  // the next ticket, synchronously (start-up and skips)
+      int t = 0;
+      if (lane == 0) t = atomicAdd(&sched[0], 1);
+      return __shfl_sync(0xffffffffu, t, 0);
+    };
+    auto next_idx = [&](int t) -> int {  // a ticket's item, taking more tickets past skips
+      int idx = item_of(t);
+      while (idx == -1) idx = item_of(take());
+      return idx;
+    };
+    // start-up: item a (next to issue), item b (read), ticket c (requested)
+    int idx_a = next_idx(take());
+    PipeItem pa = fetch(idx_a);
+    int idx_b = pa.tile >= 0 ? next_idx(take()) : -2;
+    PipeItem pb = fetch(idx_b);
+    int tc = 0;  // lane 0: the pending ticket
+    bool tc_live = pb.tile >= 0;
+    if (tc_live && lane == 0) tc = atomicAdd(&sched[0], 1);
     const T* src = pa.tile >= 0 ? slice_src<T>(pa, lane) : nullptr;
-    const T* src_b = (pb.tile >= 0 && pb.inst != pa.inst) ? slice_src<T>(pb, lane) : src;
+    int hv_a[kHaloPre];
+    load_halo<T>(pa, lane, hv_a);
+    int a_next = 0;      // next tile (in this CTA's order) whose groups are issued
+    bool ended = false;  // the end marker has been issued
     long long idle0 = clock64();
     bool ok = true;
-    while (!ended || h_next < a_next) {
+    while (!ended) {
       bool progress = false;
-      // group H of the oldest tile whose group A has landed
-      if (h_next < a_next) {
-        bool landed = false;
-        if (lane == 0) landed = mbar_test(&mb_a[h_next % S], (h_next / S) & 1);
-        if (__shfl_sync(0xffffffffu, landed, 0)) {
-          if (reinterpret_cast<const StageInfo*>(slot(h_next) + L.info)->tile >= 0)
-            issue_h<T>(L, slot(h_next), &mb_h[h_next % S], lane);
-          else
-            cp_async_arrive(&mb_h[h_next % S]);  // end marker: nothing to gather
-          ++h_next;
-          progress = true;
-        }
-      }
-      // group A of the next tile (or the end marker) once its slot is free
-      if (!ended) {
-        bool free_slot = a_next < S;
-        if (!free_slot && lane == 0) free_slot = mbar_test(&mb_e[a_next % S], ((a_next - S) / S) & 1);
-        if (__shfl_sync(0xffffffffu, free_slot, 0)) {
-          if (pa.tile >= 0) {
-            issue_a<T>(L, slot(a_next), pa, idx_a, pb.tile >= 0 ? pb.inst : -1, src, &mb_a[a_next % S], lane);
-            pa = pb;
-            idx_a = idx_b;
-            src = src_b;
-            if (pa.tile >= 0) {
-              pb = grab(idx_b);
-              if (pb.tile >= 0 && pb.inst != pa.inst) src_b = slice_src<T>(pb, lane);
-            }
+      // groups A and H of the next tile (or the end marker) once its slot is free
+      bool free_slot = a_next < S;
+      if (!free_slot && lane == 0) free_slot = mbar_test(&mb_e[a_next % S], ((a_next - S) / S) & 1);
+      if (__shfl_sync(0xffffffffu, free_slot, 0)) {
+        if (pa.tile >= 0) {
+          issue_a<T>(L, slot(a_next), pa, idx_a, pb.tile >= 0 ? pb.inst : -1, src, &mb_a[a_next % S], lane);
+          issue_h<T>(L, slot(a_next), pa, src, hv_a, &mb_h[a_next % S], lane);
+          // promote b (read one iteration ago); read its instance pointers and halo
+          // indices (used at the next issue)
+          if (pb.tile >= 0 && pb.inst != pa.inst) src = slice_src<T>(pb, lane);
+          pa = pb;
+          idx_a = idx_b;
+          load_halo<T>(pa, lane, hv_a);
+          // the pending ticket becomes the next read; request a new ticket
+          if (pa.tile >= 0 && tc_live) {
+            idx_b = next_idx(__shfl_sync(0xffffffffu, tc, 0));
+            pb = fetch(idx_b);
+            tc_live = pb.tile >= 0;
+            if (tc_live && lane == 0) tc = atomicAdd(&sched[0], 1);
           } else {
-            if (lane == 0) {
-              reinterpret_cast<StageInfo*>(slot(a_next) + L.info)->tile = -1;
-              mbar_expect_tx(&mb_a[a_next % S], 0);
-            }
-            ended = true;
+            pb.tile = -1;
+            idx_b = -2;
+            tc_live = false;
           }
-          ++a_next;
-          progress = true;
+        } else {
+          if (lane == 0) {
+            reinterpret_cast<StageInfo*>(slot(a_next) + L.info)->tile = -1;
+            mbar_expect_tx(&mb_a[a_next % S], 0);
+          }
+          cp_async_arrive(&mb_h[a_next % S]);  // end marker: nothing to gather
+          ended = true;
         }
+        ++a_next;
+        progress = true;
       }
       if (progress) {
         idle0 = clock64();
@@ -441,6 +471,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
   int* next_early = early + static_cast<size_t>((stamp + 1) & 1) * n_items;
   double rrun = 0.0;  // this CTA's max Eq. 21 rate over the current instance's tiles
   unsigned cnt = 0;   // tiles of the current instance this CTA completed
+  int n_done = 0;     // FP64: tiles this CTA completed in the launch
   for (int k = 0;; ++k) {
     unsigned char* sb = slot(k);
     {
@@ -473,18 +504,9 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     const T* sQy = arr + SL::kQy * L.nloc;
     const T* sZ = arr + SL::kZ * L.nloc;
     const T* sGn2 = reinterpret_cast<const T*>(sb + L.gn2);
-    T* U;
-    T* V;
-    T* C;
-    if constexpr (SL::k64) {
-      U = const_cast<T*>(arr + SL::kU * L.nloc);
-      V = const_cast<T*>(arr + SL::kV * L.nloc);
-      C = const_cast<T*>(arr + SL::kC * L.nloc);
-    } else {
-      U = reinterpret_cast<T*>(smem + L.uvc);
-      V = U + L.nloc;
-      C = V + L.nloc;
-    }
+    T* U = reinterpret_cast<T*>(smem + L.uvc);
+    T* V = U + L.nloc;
+    T* C = V + L.nloc;
     const bool run = prime || cs.active;
     T dt, quni, g, hg, hmin;
     step_consts(&cs, a.p, dt, quni, g, hg, hmin);
@@ -492,7 +514,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     const int wpos = cs.wpos;
     const int par = cs.parity;
 
-    // phase D: wet/dry flags (FP32-bulk: velocity and celerity) of tile and halo cells.
+    // phase D: wet/dry flags, velocity and celerity of tile and halo cells.
     // A tile whose cells and halo cells are all dry, whose cells are at rest and which
     // has no inflow edge is quiet: every flux is zero and U^{n+1} = U^n.
     bool tq = true;
@@ -502,13 +524,11 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         const bool dj = cell_dry(Hj, Hlj, zj);
         dry[j] = dj ? 1 : 0;
         tq = tq && dj && (j >= kTile || (is_zero(sQx[j]) && is_zero(sQy[j])));
-        if constexpr (kPair) {
-          T u = zero, v = zero, c = zero;  // dry: at rest, zero celerity
-          if (!dj) cell_derived<T>(depth_of(Hj, Hlj, zj), sQx[j], sQy[j], hmin, g, u, v, c);
-          U[j] = u;
-          V[j] = v;
-          C[j] = c;
-        }
+        T u = zero, v = zero, c = zero;  // dry: at rest, zero celerity
+        if (!dj) cell_derived<T>(depth_of(Hj, Hlj, zj), sQx[j], sQy[j], hmin, g, u, v, c);
+        U[j] = u;
+        V[j] = v;
+        C[j] = c;
       }
     }
     const bool quiet = nbar_and<kTile>(tq) && !prime && !(inf.flags & 2u);
@@ -616,11 +636,6 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         if constexpr (kPair) a.Hlo[dst][i] = Hl;
         a.qx[dst][i] = zero;
         a.qy[dst][i] = zero;
-        if constexpr (SL::k64) {
-          a.u[dst][i] = zero;
-          a.v[dst][i] = zero;
-          a.c[dst][i] = zero;
-        }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int code = static_cast<int32_t>(sLR[idx[q]]) >> kLocBits;
@@ -680,14 +695,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           const T negtol = kPair ? hmin + T(4) * static_cast<T>(FLT_EPSILON) * fabs(zi) : hmin;
           if (h < -negtol) atomicOr(&a.ctl->status, 2);
         }
-        const int out = prime ? par : dst;
         T u, v, c;
         cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
-        if constexpr (SL::k64) {
-          a.u[out][i] = u;
-          a.v[out][i] = v;
-          a.c[out][i] = c;
-        }
         if (h > hmin) rrun = fmax(rrun, static_cast<double>(cell_rate<T>(sNx, sNy, sLn, idx, u, v, c, ia, a.p.cfl_mode)));
         // inflow cells: conveyance weight and depth of the new state
 #pragma unroll
@@ -752,9 +761,10 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       rrun = 0.0;
       cnt = 0;
     }
-    // FP64: wet, boundary and inflow tiles are taken early in the next launch; the last
-    // item to finish rolls the lists over
+    // FP64: wet, boundary and inflow tiles are taken early in the next launch (only the
+    // next launch reads the list, so no fence)
     if (SL::k64 && tid == 0) {
+      ++n_done;
       if (!quiet || (inf.flags & 3u)) {
         const int pos = atomicAdd(&sched[3], 1);
         if (pos < n_items) {
@@ -762,16 +772,21 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           mark[inf.item] = stamp + 1;
         }
       }
-      __threadfence();
-      if (atomicAdd(&sched[5], 1) == n_items - 1) {
-        atomicExch(&sched[4], min(atomicExch(&sched[3], 0), n_items));
-        atomicExch(&sched[5], 0);
-        atomicExch(&sched[2], stamp + 1);
-      }
     }
     // release the tile's slot to the copy warp (each warp once it is done with it)
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(&mb_e[k % S]);
+  }
+  // FP64: the CTA whose tiles complete the launch rolls the early lists over (the
+  // fence orders this CTA's list entries before its count)
+  if (SL::k64 && tid == 0 && n_done > 0) {
+    __threadfence();
+    if (atomicAdd(&sched[5], n_done) + n_done == n_items) {
+      __threadfence();
+      atomicExch(&sched[4], min(atomicExch(&sched[3], 0), n_items));
+      atomicExch(&sched[5], 0);
+      atomicExch(&sched[2], stamp + 1);
+    }
   }
 }
 
