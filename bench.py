@@ -65,7 +65,10 @@ def parse():
     ap.add_argument("--e2e-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle (and the accuracy check)")
     ap.add_argument("--precisions", default="fp64,fp32")
-    ap.add_argument("--workload", choices=["floodplain", "ensemble", "serve"], default="floodplain",
+    ap.add_argument("--lake-steps", type=int, default=500,
+                    help="steps of the mostly wet lake-at-rest line (0: skip it)")
+    ap.add_argument("--stress-steps", type=int, default=100000, help="stress: lake-at-rest steps")
+    ap.add_argument("--workload", choices=["floodplain", "ensemble", "serve", "stress"], default="floodplain",
                     help="floodplain: the default line; ensemble: batched uneven meshes; serve: request loop")
     ap.add_argument("--instances", type=int, default=256, help="ensemble members")
     ap.add_argument("--requests", type=int, default=200, help="serving trace length")
@@ -309,6 +312,103 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
     return out, final
 
 
+def measure_lake(args, torch, bm, W):
+    """The same step on a mostly wet mesh, as context for the floodplain numbers: the
+    1,000,000-triangle lake at rest on 5 m fractal relief (partially dry islands).  Its
+    wet tiles run the full flux and friction arithmetic every step.  Also reports the
+    largest velocity and the relative volume change after the timed steps (the lake
+    must stay at rest)."""
+    s = W.fractal_lake()
+    mesh = bm.Mesh.from_scenario(s)
+    out = {"workload": "lake at rest, 1,000,000 triangles, z = 400 m + fractal relief (5 m), surface 403 m",
+           "cells": s.n_cells, "wet_fraction": float(np.mean(s.H - s.z > 1e-6)), "steps": args.lake_steps}
+    for prec in [p for p in args.precisions.split(",") if p]:
+        st = bm.State.from_scenario(s, mesh=mesh, precision=prec)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        st.set_stream(stream.cuda_stream)
+        st.step(args.warmup)
+        v0 = st.stats()["volume"]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.step_async(args.lake_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st.sync()
+        ms = e0.elapsed_time(e1)
+        H, qx, qy, _ = st.download()
+        h = H - s.z
+        wet = h > 1e-3
+        speed = float(np.max(np.hypot(qx[wet], qy[wet]) / h[wet])) if wet.any() else 0.0
+        v1 = st.stats()["volume"]
+        out["fp32_bulk" if prec == "fp32" else prec] = {
+            "value": s.n_cells * args.lake_steps / (ms / 1e3), "unit": METRIC, "ms_per_step": ms / args.lake_steps,
+            "max_speed_ms": speed, "rel_volume_change": abs(v1 - v0) / abs(v0)}
+        st.close()
+    return out
+
+
+def tri_areas(s):
+    a, b, c = s.xy[s.tri[:, 0]], s.xy[s.tri[:, 1]], s.xy[s.tri[:, 2]]
+    return 0.5 * np.abs((b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (c[:, 0] - a[:, 0]) * (b[:, 1] - a[:, 1]))
+
+
+def run_stress(args, ws, rank, torch, bm, W):
+    """Precision stress: (1) the 1,000,000-triangle lake at rest on fractal relief
+    (surface 403 m over a 400 m datum, partially dry) for args.stress_steps FP32-bulk
+    steps -- largest velocity, surface drift and relative mass defect; (2) Thacker's
+    planar sloshing in a paraboloid on 250k cells for one period, FP64 and FP32-bulk --
+    errors against the closed form, between the two precisions, and mass defects."""
+    out = {"metric": "precision stress", "n_gpus": ws, "data": "synthetic"}
+    s = W.fractal_lake()
+    area = tri_areas(s)
+    st = bm.State.from_scenario(s, precision="fp32")
+    v0 = st.stats()["volume"]
+    t0 = time.perf_counter()
+    st.step(args.stress_steps)
+    wall = time.perf_counter() - t0
+    H, qx, qy, _ = st.download()
+    h = H - s.z
+    wet = h > 1e-3
+    v1 = st.stats()["volume"]
+    out["lake_fp32"] = {"workload": "lake at rest, 1,000,000 triangles, z = 400 m + fractal relief (5 m), "
+                                    "surface 403 m", "steps": args.stress_steps, "wall_s": wall,
+                        "max_speed_ms": float(np.max(np.hypot(qx[wet], qy[wet]) / h[wet])),
+                        "max_surface_drift_m": float(np.max(np.abs(H - s.H))),
+                        "rel_mass_defect": abs(v1 - v0) / abs(v0)}
+    st.close()
+    s = W.thacker()
+    area = tri_areas(s)
+    c = s.xy[s.tri].mean(axis=1)
+    om = np.sqrt(2 * 9.81 * 10.0) / 3000.0
+    T = 2 * np.pi / om
+    he, ue, ve = W.thacker_exact(c[:, 0], c[:, 1], T)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        st = bm.State.from_scenario(s, precision=prec)
+        v0 = st.stats()["volume"]
+        st.run_until(T)
+        H, qx, qy, _ = st.download()
+        v1 = st.stats()["volume"]
+        res[prec] = (H - s.z, qx, qy)
+        h = H - s.z
+        out[f"thacker_{prec}"] = {"cells": s.n_cells, "t_s": T, "steps": st.stats(volume=False)["steps"],
+                                  "l1_depth_vs_exact_m": float(np.sum(area * np.abs(h - he)) / area.sum()),
+                                  "rel_mass_defect": abs(v1 - v0) / abs(v0)}
+        st.close()
+    (h64, qx64, qy64), (h32, qx32, qy32) = res["fp64"], res["fp32"]
+    wet = (h64 > 1e-3) & (h32 > 1e-3)
+    out["thacker_fp32_vs_fp64"] = {
+        "l1_depth_m": float(np.sum(area * np.abs(h32 - h64)) / area.sum()),
+        "linf_depth_m": float(np.max(np.abs(h32 - h64))),
+        "l1_speed_ms": float(np.mean(np.hypot(qx32[wet] / h32[wet] - qx64[wet] / h64[wet],
+                                              qy32[wet] / h32[wet] - qy64[wet] / h64[wet])))}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ensemble(args, ws, rank, torch, bm, W):
     """Batched ensemble: args.instances floodplain-recipe meshes, log-uniform sizes in
     [5k, 500k] triangles (member k seeded 5000 + k), stepped together by one launch
@@ -409,7 +509,7 @@ def main():
         from paper_2102_12862_b300 import bm
         from paper_2102_12862_b300 import workloads as W
         torch.cuda.set_device(local)
-        fn = run_ensemble if args.workload == "ensemble" else run_serve
+        fn = {"ensemble": run_ensemble, "serve": run_serve, "stress": run_stress}[args.workload]
         return fn(args, ws, rank, torch, bm, W) if rank == 0 or ws == 1 else 0
 
     import torch
@@ -428,6 +528,8 @@ def main():
     res, finals = {}, {}
     for p in precs:
         res[p], finals[p] = measure(args, p, s, mesh, torch, bm, dist, ws, rank)
+
+    lake = measure_lake(args, torch, bm, W) if (rank == 0 and args.lake_steps > 0) else None
 
     cpu, acc = None, {}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -465,6 +567,8 @@ def main():
                          "dtype": "f32+f64" if p == "fp32" else "f64", "roofline": q["roofline"], "e2e": q["e2e"],
                          "clocks": q["clocks"], "gpu_launches": q["gpu_launches"], "sim_time_s": q["sim_time_s"],
                          "wet_fraction_first_last": q["wet_fraction"], "accuracy_vs_oracle": acc.get(p)}
+        if lake is not None:
+            line["wet_lake"] = lake
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
