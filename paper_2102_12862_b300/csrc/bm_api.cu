@@ -222,15 +222,29 @@ int step_grid(const StepList& l, int ctas_per_sm) {
 }
 
 // One fused step (or prime) launch over a work list.
+// Launched as a programmatic dependent of the previous kernel in the stream: its CTAs
+// may start while that kernel's last CTAs finish and wait (griddepcontrol.wait) before
+// touching anything the previous kernel writes.
 void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st) {
   if (l.n <= 0) return;
   grid = std::max(1, std::min(grid, l.n));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(kStepThreads);
+  cfg.dynamicSmemBytes = l.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int ne4 = static_cast<int>(l.ne4), nh4 = static_cast<int>(l.nh4);
   if (prec == BM_FP64)
-    step_pipe<double><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, l.sched.p, l.early.p, l.mark.p,
-                                                           static_cast<int>(l.ne4), static_cast<int>(l.nh4), prime);
+    (void)cudaLaunchKernelEx(&cfg, step_pipe<double>, static_cast<const PipeItem*>(l.items.p), l.n, l.sched.p,
+                             l.early.p, l.mark.p, ne4, nh4, prime);
   else
-    step_pipe<float><<<grid, kStepThreads, l.smem, st>>>(l.items.p, l.n, l.sched.p, l.early.p, l.mark.p,
-                                                          static_cast<int>(l.ne4), static_cast<int>(l.nh4), prime);
+    (void)cudaLaunchKernelEx(&cfg, step_pipe<float>, static_cast<const PipeItem*>(l.items.p), l.n, l.sched.p,
+                             l.early.p, l.mark.p, ne4, nh4, prime);
 }
 
 namespace {

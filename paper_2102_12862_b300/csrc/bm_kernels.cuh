@@ -25,8 +25,8 @@ struct alignas(16) InstDesc {
   const T* z;
   const T* gn2;       // g n^2
   const T* inv_area;  // 1 / |Omega_i|
-  const int32_t* in_cell;
-  const double* in_lia;    // inflow edge j: l_j / |Omega| of its cell  // inflow edge j: its cell
+  const int32_t* in_cell;  // inflow edge j: its cell
+  const double* in_lia;    //                l_j / |Omega| of its cell
   const T* in_len;         //                its length
   T* in_pw;                //                h^(5/3) of the cell (0 at or below h_min)
   T* in_hs;                //                max(0, h) of the cell

@@ -115,6 +115,11 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(b)) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Programmatic dependent launch: wait until the previous kernel in the stream has
+// completed and its memory is visible (returns at once without such a dependency);
+// allow the next kernel to begin launching.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Order-preserving integer key of a double (for x, y not NaN: key(x) <= key(y)
 // implies x <= y), so wet/dry tests of FP64 cells need no FP64 instruction.
@@ -176,33 +181,32 @@ struct StepLayout {
 
 // Lane l's source of a group-A state slice for an instance: lane 3 + j copies array j
 // (order of StepLayout), lane 3 + kNA copies g n^2; read from the instance's
-// descriptor in global memory at the parity of its control block.
+// descriptor in global memory at the parity of its control block.  Both buffers'
+// pointers and the parity are read independently (one memory round trip).
+template <typename P>
+__device__ __forceinline__ P ldg_ptr(const P* p) {
+  return reinterpret_cast<P>(__ldg(reinterpret_cast<const unsigned long long*>(p)));
+}
 template <typename T>
 __device__ __forceinline__ const T* slice_src(const PipeItem& it, int lane) {
   using SL = StepLayout<T>;
   const InstDesc<T>* d = static_cast<const InstDesc<T>*>(it.desc);
-  const int par = it.ctl->parity;
   const int j = lane - 3;
+  T* const* pair = nullptr;  // double-buffered arrays
+  const T* const* one = nullptr;
   if constexpr (SL::k64) {
-    switch (j) {
-      case 0: return d->H[par];
-      case 1: return d->qx[par];
-      case 2: return d->qy[par];
-      case 3: return d->z;
-      case 4: return d->gn2;
-      default: return nullptr;
-    }
+    pair = j == 0 ? d->H : j == 1 ? d->qx : j == 2 ? d->qy : nullptr;
+    one = j == 3 ? &d->z : j == 4 ? &d->gn2 : nullptr;
   } else {
-    switch (j) {
-      case 0: return d->H[par];
-      case 1: return d->Hlo[par];
-      case 2: return d->qx[par];
-      case 3: return d->qy[par];
-      case 4: return d->z;
-      case 5: return d->gn2;
-      default: return nullptr;
-    }
+    pair = j == 0 ? d->H : j == 1 ? d->Hlo : j == 2 ? d->qx : j == 3 ? d->qy : nullptr;
+    one = j == 4 ? &d->z : j == 5 ? &d->gn2 : nullptr;
   }
+  if (one != nullptr) return ldg_ptr(one);
+  if (pair == nullptr) return nullptr;
+  const int par = it.ctl->parity;
+  const T* p0 = ldg_ptr(pair);
+  const T* p1 = ldg_ptr(pair + 1);
+  return par ? p1 : p0;
 }
 
 // Group A of a tile into a slot (all lanes of the copy warp; src = this lane's slice
@@ -293,7 +297,9 @@ template <typename T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 3;
 
 // One step (prime = 0) or prime pass (prime = 1: no update; derived data, inflow
-// weights and the dt of the current state) over a work list.  sched: [0] next ticket,
+// weights and the dt of the current state) over a work list.  sched: [0] tickets handed out by the counter
+// (a CTA's first two tickets are blockIdx.x and gridDim.x + blockIdx.x, the counter's
+// start at 2 gridDim.x),
 // [1] CTAs done taking items (both zero at launch; the last CTA to finish taking zeroes
 // them), [2] launch stamp s, [3] early items listed for launch s + 1, [4] early items
 // listed for this launch (E), [5] items finished.  Ticket t < E takes early[s & 1][t];
@@ -340,6 +346,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     // copy warp never waits on a value in the iteration that asked for it: a ticket
     // (atomic) -> the item read -> promotion to "next to issue" (instance pointers and
     // halo indices read) -> issue.  FP64 tickets map through the early list first.
+    // FP64: the early list and marks are the previous step's
+    if constexpr (SL::k64) grid_dep_wait();
     int stamp = 0, n_early = 0;
     if (SL::k64 && lane == 0) {
       stamp = *reinterpret_cast<volatile int*>(&sched[2]);
@@ -368,9 +376,12 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       if (idx >= 0) it = items[idx];
       return it;
     };
-    auto take = [&]() -> int {  // the next ticket, synchronously (start-up and skips)
+    // tickets blockIdx.x and gridDim.x + blockIdx.x are this CTA's without asking; the
+    // counter hands out the tickets from 2 gridDim.x on
+    const int t_dyn = 2 * static_cast<int>(gridDim.x);
+    auto take = [&]() -> int {  // the next ticket, synchronously (skips)
       int t = 0;
-      if (lane == 0) t = atomicAdd(&sched[0], 1);
+      if (lane == 0) t = atomicAdd(&sched[0], 1) + t_dyn;
       return __shfl_sync(0xffffffffu, t, 0);
     };
     auto next_idx = [&](int t) -> int {  // a ticket's item, taking more tickets past skips
@@ -378,17 +389,26 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       while (idx == -1) idx = item_of(take());
       return idx;
     };
-    // start-up: item a (next to issue), item b (read), ticket c (requested)
-    int idx_a = next_idx(take());
+    // start-up: item a (next to issue), item b (read), ticket c (requested); a and b
+    // are read together.  Both static tickets are always claimed (an FP64 skip past
+    // the first can end at the counter's end while the second still holds an item).
+    int idx_a = next_idx(static_cast<int>(blockIdx.x));
+    int idx_b = next_idx(static_cast<int>(gridDim.x + blockIdx.x));
+    if (idx_a < 0 && idx_b >= 0) {
+      idx_a = idx_b;
+      idx_b = next_idx(take());
+    }
     PipeItem pa = fetch(idx_a);
-    int idx_b = pa.tile >= 0 ? next_idx(take()) : -2;
     PipeItem pb = fetch(idx_b);
-    int tc = 0;  // lane 0: the pending ticket
-    bool tc_live = pb.tile >= 0;
-    if (tc_live && lane == 0) tc = atomicAdd(&sched[0], 1);
-    const T* src = pa.tile >= 0 ? slice_src<T>(pa, lane) : nullptr;
     int hv_a[kHaloPre];
     load_halo<T>(pa, lane, hv_a);
+    // FP32-bulk: items and records are the mesh's, read before the previous step has
+    // ended; the ticket counter, control blocks and state are the previous step's
+    if constexpr (!SL::k64) grid_dep_wait();
+    int tc = 0;  // lane 0: the pending ticket
+    bool tc_live = idx_b >= 0;
+    if (tc_live && lane == 0) tc = atomicAdd(&sched[0], 1) + t_dyn;
+    const T* src = pa.tile >= 0 ? slice_src<T>(pa, lane) : nullptr;
     int a_next = 0;      // next tile (in this CTA's order) whose groups are issued
     bool ended = false;  // the end marker has been issued
     long long idle0 = clock64();
@@ -413,7 +433,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
             idx_b = next_idx(__shfl_sync(0xffffffffu, tc, 0));
             pb = fetch(idx_b);
             tc_live = pb.tile >= 0;
-            if (tc_live && lane == 0) tc = atomicAdd(&sched[0], 1);
+            if (tc_live && lane == 0) tc = atomicAdd(&sched[0], 1) + t_dyn;
           } else {
             pb.tile = -1;
             idx_b = -2;
@@ -426,6 +446,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           }
           cp_async_arrive(&mb_h[a_next % S]);  // end marker: nothing to gather
           ended = true;
+          grid_dep_launch();  // this CTA takes no more items
         }
         ++a_next;
         progress = true;
@@ -461,6 +482,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
   }
 
   // ------------------------------------------------------------------ compute warps
+  grid_dep_wait();
   T* Fs = reinterpret_cast<T*>(smem + L.F);
   unsigned char* dry = smem + L.dry;
   unsigned char* skip = smem + L.skip;
