@@ -286,6 +286,18 @@ bm_status bm_server_stats(bm_server* sv, int64_t* queued, int64_t* running, int6
 bm_status bm_volume_noalloc(const double* H, const double* z, const double* area, int64_t n_cells, double* volume,
                             void* cuda_stream);
 
+/* Diagnostics: evaluate one of the step kernel's hand-written elementary functions, or
+ * the CUDA library function it stands in for, on n host values (copied to the device
+ * and back; synchronous).  fn: 0 x^(-1/3) as the FP64 step computes it (Newton steps
+ * from a single-precision estimate), 1 the library's 1/cbrt(x), 2 1/x as the FP64 step
+ * computes it (Newton steps from the hardware reciprocal estimate), 3 the IEEE
+ * division 1/x, 4 x^(-1/3) as the FP32-bulk step computes it (hardware base-2
+ * logarithm and exponent), 5 the library's rcbrtf, 6 x^(1/3) as the FP64 step computes
+ * it, 7 the library's cbrt.  x, y: n doubles each (host memory, caller-owned; FP32
+ * functions see x rounded to float).  BM_EINVAL for fn outside [0, 7], n outside
+ * [0, 2^28] or NULL arrays; BM_ECUDA / BM_ENOMEM from the device. */
+bm_status bm_math_eval(int32_t fn, const double* x, double* y, int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

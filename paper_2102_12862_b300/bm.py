@@ -75,6 +75,7 @@ SIGNATURES = {
     "bm_state_autotune": (C.c_int, [_vp, C.c_int, _P(C.c_int), _P(_d)]),
     "bm_batch_autotune": (C.c_int, [_vp, C.c_int, _P(C.c_int), _P(_d)]),
     "bm_volume_noalloc": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
+    "bm_math_eval": (C.c_int, [C.c_int32, _vp, _vp, _i64]),
     "bm_server_opts_default": (None, [_P(bm_server_opts)]),
     "bm_server_create": (C.c_int, [_P(bm_server_opts), _P(_vp)]),
     "bm_server_destroy": (None, [_vp]),
@@ -243,6 +244,18 @@ def bm_state_set_launch(state: int, ctas_per_sm: int):
 def bm_volume_noalloc(H_dev: int, z_dev: int, area_dev: int, n_cells: int, volume_dev: int, stream_ptr: int = 0):
     """Volume of caller-owned device arrays (raw device pointers), no device allocation."""
     _check(load_library().bm_volume_noalloc(H_dev, z_dev, area_dev, int(n_cells), volume_dev, stream_ptr or None))
+
+
+MATH_FUNCTIONS = {"rcbrt": 0, "rcbrt_lib": 1, "rcp": 2, "rcp_lib": 3, "rcbrt32": 4, "rcbrt32_lib": 5,
+                  "cbrt": 6, "cbrt_lib": 7}
+
+
+def bm_math_eval(fn: str, x) -> np.ndarray:
+    """One of the step kernel's elementary functions (or the CUDA library's) on x."""
+    xs = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    y = np.empty_like(xs)
+    _check(load_library().bm_math_eval(MATH_FUNCTIONS[fn], xs.ctypes.data, y.ctypes.data, xs.size))
+    return y
 
 
 def bm_state_autotune(state: int, steps_per_trial: int = 20) -> tuple[int, float]:

@@ -785,6 +785,51 @@ bm_status bm_step_timed(bm_state* s, int64_t n, double* step_kernel_ms, double* 
 
 }  // extern "C"
 
+namespace bm {
+namespace {
+// The step kernel's elementary functions (and the CUDA library's counterparts) on an
+// array, for tests of the hand-written ones.
+__global__ void math_eval(int fn, const double* x, double* y, int64_t n) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  double r = 0.0;
+  switch (fn) {
+    case 0: r = f_rcbrt(v); break;
+    case 1: r = 1.0 / cbrt(v); break;
+    case 2: r = f_rcp(v); break;
+    case 3: r = 1.0 / v; break;
+    case 4: r = static_cast<double>(f_rcbrt(static_cast<float>(v))); break;
+    case 5: r = static_cast<double>(rcbrtf(static_cast<float>(v))); break;
+    case 6: r = f_cbrt(v); break;
+    case 7: r = cbrt(v); break;
+    default: r = 0.0;
+  }
+  y[i] = r;
+}
+}  // namespace
+}  // namespace bm
+
+extern "C" {
+
+bm_status bm_math_eval(int32_t fn, const double* x, double* y, int64_t n) {
+  clear_error();
+  if (fn < 0 || fn > 7) return fail(BM_EINVAL, "bm_math_eval: fn must be in [0, 7]");
+  if (n < 0 || n > (int64_t(1) << 28)) return fail(BM_EINVAL, "bm_math_eval: n must be in [0, 2^28]");
+  if (n == 0) return BM_OK;
+  if (!x || !y) return fail(BM_EINVAL, "bm_math_eval: NULL array");
+  DBuf<double> dx, dy;
+  BM_CUDA(dx.alloc(static_cast<size_t>(n)));
+  BM_CUDA(dy.alloc(static_cast<size_t>(n)));
+  BM_CUDA(cudaMemcpy(dx.p, x, static_cast<size_t>(n) * sizeof(double), cudaMemcpyHostToDevice));
+  math_eval<<<static_cast<unsigned>((n + 255) / 256), 256>>>(fn, dx.p, dy.p, n);
+  BM_CUDA(cudaGetLastError());
+  BM_CUDA(cudaMemcpy(y, dy.p, static_cast<size_t>(n) * sizeof(double), cudaMemcpyDeviceToHost));
+  return BM_OK;
+}
+
+}  // extern "C"
+
 // ---------------------------------------------------------------- autotuner
 
 namespace bm {

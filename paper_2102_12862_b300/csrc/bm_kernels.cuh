@@ -135,13 +135,27 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-// Elementary functions.  FP64: the IEEE-rounded library square root and division;
-// cube roots through f_rcbrt below.  FP32-bulk: the hardware approximations (MUFU
-// reciprocal square root, reciprocal, base-2 logarithm and exponent), a few ulp each --
-// far inside that mode's 1e-4 m accuracy target and deterministic, so both sides of an
-// edge still compute identical values.
+// Elementary functions.  FP64: the IEEE-rounded library square root; division as a
+// times the Newton-refined reciprocal f_rcp below; cube roots through f_rcbrt below.
+// FP32-bulk: the hardware approximations (MUFU reciprocal square root, reciprocal,
+// base-2 logarithm and exponent), a few ulp each -- far inside that mode's 1e-4 m
+// accuracy target.  All are deterministic, so both sides of an edge still compute
+// identical values.
+//
+// 1/x for FP64 by Newton-Raphson on f(r) = 1/r - x: from the hardware estimate
+// (rcp.approx.ftz.f64), e = 1 - x r, r <- r + r e, which squares the relative error at
+// each step (two steps reach the double's precision); within 2 ulp of the rounded
+// reciprocal for normal x (no special-case path: 0 and infinities give NaN).
+__device__ __forceinline__ double f_rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
 __device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ double f_div(double a, double b) { return a / b; }
+__device__ __forceinline__ double f_div(double a, double b) { return a * f_rcp(b); }
 __device__ __forceinline__ float f_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 __device__ __forceinline__ float f_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ float f_exp2(float x) {

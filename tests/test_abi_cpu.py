@@ -109,3 +109,11 @@ def test_mesh_layout_on_the_host(make):
     assert lay64["max_tile_edges"] == lay32["max_tile_edges"] and lay64["max_tile_halo"] == lay32["max_tile_halo"]
     with pytest.raises(bm.BMError, match="precision"):
         bm.bm_mesh_layout(m.handle, 7)
+
+
+def test_math_eval_validates_before_any_device_work():
+    lib = bm.load_library()
+    assert lib.bm_math_eval(9, None, None, 1) == bm.BM_EINVAL
+    assert lib.bm_math_eval(0, None, None, 4) == bm.BM_EINVAL
+    assert lib.bm_math_eval(0, None, None, -1) == bm.BM_EINVAL
+    assert lib.bm_math_eval(0, None, None, 0) == bm.BM_OK
