@@ -357,28 +357,28 @@ def tri_areas(s):
 
 def run_stress(args, ws, rank, torch, bm, W):
     """Precision stress: (1) the 1,000,000-triangle lake at rest on fractal relief
-    (surface 403 m over a 400 m datum, partially dry) for args.stress_steps FP32-bulk
-    steps -- largest velocity, surface drift and relative mass defect; (2) Thacker's
+    (surface 403 m over a 400 m datum, partially dry) for args.stress_steps steps in
+    FP32-bulk and FP64 -- largest velocity, surface drift and relative mass defect; (2) Thacker's
     planar sloshing in a paraboloid on 250k cells for one period, FP64 and FP32-bulk --
     errors against the closed form, between the two precisions, and mass defects."""
     out = {"metric": "precision stress", "n_gpus": ws, "data": "synthetic"}
     s = W.fractal_lake()
-    area = tri_areas(s)
-    st = bm.State.from_scenario(s, precision="fp32")
-    v0 = st.stats()["volume"]
-    t0 = time.perf_counter()
-    st.step(args.stress_steps)
-    wall = time.perf_counter() - t0
-    H, qx, qy, _ = st.download()
-    h = H - s.z
-    wet = h > 1e-3
-    v1 = st.stats()["volume"]
-    out["lake_fp32"] = {"workload": "lake at rest, 1,000,000 triangles, z = 400 m + fractal relief (5 m), "
-                                    "surface 403 m", "steps": args.stress_steps, "wall_s": wall,
-                        "max_speed_ms": float(np.max(np.hypot(qx[wet], qy[wet]) / h[wet])),
-                        "max_surface_drift_m": float(np.max(np.abs(H - s.H))),
-                        "rel_mass_defect": abs(v1 - v0) / abs(v0)}
-    st.close()
+    for prec in ("fp32", "fp64"):
+        st = bm.State.from_scenario(s, precision=prec)
+        v0 = st.stats()["volume"]
+        t0 = time.perf_counter()
+        st.step(args.stress_steps)
+        wall = time.perf_counter() - t0
+        H, qx, qy, _ = st.download()
+        h = H - s.z
+        wet = h > 1e-3
+        v1 = st.stats()["volume"]
+        out[f"lake_{prec}"] = {"workload": "lake at rest, 1,000,000 triangles, z = 400 m + fractal relief (5 m), "
+                                           "surface 403 m", "steps": args.stress_steps, "wall_s": wall,
+                               "max_speed_ms": float(np.max(np.hypot(qx[wet], qy[wet]) / h[wet])),
+                               "max_surface_drift_m": float(np.max(np.abs(H - s.H))),
+                               "rel_mass_defect": abs(v1 - v0) / abs(v0)}
+        st.close()
     s = W.thacker()
     area = tri_areas(s)
     c = s.xy[s.tri].mean(axis=1)
