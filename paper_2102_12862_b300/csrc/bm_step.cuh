@@ -295,11 +295,15 @@ __device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* s
 
 template <typename T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 3;
+// Share of a launch's tickets handed out statically: kStaticNum / kStaticDen (FP64,
+// with its wide spread of tile costs, leaves more to the counter).
+constexpr int kStaticDen = 16;
+template <typename T>
+constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M floodplain
 
 // One step (prime = 0) or prime pass (prime = 1: no update; derived data, inflow
 // weights and the dt of the current state) over a work list.  sched: [0] tickets handed out by the counter
-// (a CTA's first two tickets are blockIdx.x and gridDim.x + blockIdx.x, the counter's
-// start at 2 gridDim.x),
+// (after each CTA's static tickets),
 // [1] CTAs done taking items (both zero at launch; the last CTA to finish taking zeroes
 // them), [2] launch stamp s, [3] early items listed for launch s + 1, [4] early items
 // listed for this launch (E), [5] items finished.  Ticket t < E takes early[s & 1][t];
@@ -357,18 +361,21 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     n_early = min(__shfl_sync(0xffffffffu, n_early, 0), n_items);
     const int* ord = early + static_cast<size_t>(stamp & 1) * n_items;
     const int n_tickets = n_early + n_items;
-    // ticket -> work item (-1: taken in the early pass; -2: past the end).  An item
+    // ticket -> work item (-1: taken in the early pass; -2: past the end), in two
+    // parts so the load can be issued a step ahead: map_load reads what the ticket
+    // needs (its early-list entry, or the item's mark), resolve decides.  An item
     // listed with stamp s, or finished in the early pass and re-listed with s + 1, was
     // taken early (an item only finishes after it was taken).
-    auto item_of = [&](int t) -> int {
+    auto map_load = [&](int t) -> int {
       if (t < n_early) return ord[t];
+      if (n_early > 0 && t < n_tickets) return __ldcg(&mark[t - n_early]);
+      return 0;
+    };
+    auto resolve = [&](int t, int v) -> int {
+      if (t < n_early) return v;
       if (t >= n_tickets) return -2;
-      const int idx = t - n_early;
-      if (n_early > 0) {
-        const int m = __ldcg(&mark[idx]);
-        if (m == stamp || m == stamp + 1) return -1;
-      }
-      return idx;
+      if (n_early > 0 && (v == stamp || v == stamp + 1)) return -1;
+      return t - n_early;
     };
     auto fetch = [&](int idx) -> PipeItem {
       PipeItem it{};
@@ -376,28 +383,38 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       if (idx >= 0) it = items[idx];
       return it;
     };
-    // tickets blockIdx.x and gridDim.x + blockIdx.x are this CTA's without asking; the
-    // counter hands out the tickets from 2 gridDim.x on
-    const int t_dyn = 2 * static_cast<int>(gridDim.x);
-    auto take = [&]() -> int {  // the next ticket, synchronously (skips)
-      int t = 0;
-      if (lane == 0) t = atomicAdd(&sched[0], 1) + t_dyn;
-      return __shfl_sync(0xffffffffu, t, 0);
+    // Tickets: first this CTA's static ones, blockIdx.x + m gridDim.x for m < m_static
+    // (known without asking, so their items are looked up a step ahead without
+    // waiting; a share of all tickets, so that the counter's rest evens out the CTAs),
+    // then the launch's counter from n_static on, one ticket requested a step ahead.
+    // A CTA's tickets increase, so once one is past the end every later one is too.
+    const int G = static_cast<int>(gridDim.x);
+    const int m_static = max(2, n_tickets / kStaticDen * kStaticNum<T> / G);
+    const int n_static = m_static * G;
+    int m_next = 0;
+    int tc = 0;  // lane 0: the requested counter ticket
+    bool tc_pending = false;
+    auto request = [&]() {
+      if (lane == 0) tc = atomicAdd(&sched[0], 1) + n_static;
+      tc_pending = true;
     };
-    auto next_idx = [&](int t) -> int {  // a ticket's item, taking more tickets past skips
-      int idx = item_of(t);
-      while (idx == -1) idx = item_of(take());
+    auto next_ticket = [&]() -> int {
+      if (m_next < m_static) return static_cast<int>(blockIdx.x) + (m_next++) * G;
+      if (!tc_pending) request();
+      tc_pending = false;
+      return __shfl_sync(0xffffffffu, tc, 0);
+    };
+    auto next_idx = [&]() -> int {  // the next ticket's item, past skipped tickets (waits)
+      int idx;
+      do {
+        const int t = next_ticket();
+        idx = resolve(t, map_load(t));
+      } while (idx == -1);
       return idx;
     };
-    // start-up: item a (next to issue), item b (read), ticket c (requested); a and b
-    // are read together.  Both static tickets are always claimed (an FP64 skip past
-    // the first can end at the counter's end while the second still holds an item).
-    int idx_a = next_idx(static_cast<int>(blockIdx.x));
-    int idx_b = next_idx(static_cast<int>(gridDim.x + blockIdx.x));
-    if (idx_a < 0 && idx_b >= 0) {
-      idx_a = idx_b;
-      idx_b = next_idx(take());
-    }
+    // start-up: item a (next to issue) and item b (read), read together
+    int idx_a = next_idx();
+    int idx_b = idx_a >= 0 ? next_idx() : -2;
     PipeItem pa = fetch(idx_a);
     PipeItem pb = fetch(idx_b);
     int hv_a[kHaloPre];
@@ -405,9 +422,14 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     // FP32-bulk: items and records are the mesh's, read before the previous step has
     // ended; the ticket counter, control blocks and state are the previous step's
     if constexpr (!SL::k64) grid_dep_wait();
-    int tc = 0;  // lane 0: the pending ticket
     bool tc_live = idx_b >= 0;
-    if (tc_live && lane == 0) tc = atomicAdd(&sched[0], 1) + t_dyn;
+    // the ticket after b and its lookup, resolved at the first promotion
+    int tn = -2, tv = 0;
+    if (tc_live) {
+      tn = next_ticket();
+      tv = map_load(tn);
+      if (m_next >= m_static && !tc_pending) request();
+    }
     const T* src = pa.tile >= 0 ? slice_src<T>(pa, lane) : nullptr;
     int a_next = 0;      // next tile (in this CTA's order) whose groups are issued
     bool ended = false;  // the end marker has been issued
@@ -430,10 +452,17 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           load_halo<T>(pa, lane, hv_a);
           // the pending ticket becomes the next read; request a new ticket
           if (pa.tile >= 0 && tc_live) {
-            idx_b = next_idx(__shfl_sync(0xffffffffu, tc, 0));
+            // the ticket looked up a step ago; past a skipped one, the next ones now
+            int idx = resolve(tn, tv);
+            if (idx == -1) idx = next_idx();
+            idx_b = idx;
             pb = fetch(idx_b);  // used at the next promotion: its load is not waited for here
             tc_live = idx_b >= 0;
-            if (tc_live && lane == 0) tc = atomicAdd(&sched[0], 1) + t_dyn;
+            if (tc_live) {
+              tn = next_ticket();
+              tv = map_load(tn);
+              if (m_next >= m_static && !tc_pending) request();
+            }
           } else {
             pb.tile = -1;
             idx_b = -2;
