@@ -89,10 +89,15 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the step kernel's sources with comments and blank lines removed, so that
+    a profile stays attached to the code it was taken on across comment edits."""
     h = hashlib.sha256()
     for f in ("bm_kernels.cuh", "bm_step.cuh", "bm_internal.h"):
-        with open(os.path.join(ROOT, "paper_2102_12862_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2102_12862_b300", "csrc", f), encoding="utf-8") as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -1,9 +1,10 @@
 // bm_step.cuh -- the fused step kernel (sm_103a): persistent CTAs of eight compute
 // warps and one copy warp, a shared-memory pipeline fed by bulk asynchronous copies.
 //
-// CTAs take work items (tiles of 256 Hilbert-ordered cells of some instance) from a
-// launch-wide counter, so a CTA that meets expensive wet tiles simply takes fewer;
-// in FP64, where a wet tile costs many times a dry one (B300's FP64 rate), the tiles
+// CTAs take work items (tiles of 256 Hilbert-ordered cells of some instance) by
+// ticket: a share of each CTA's tickets is static (known ahead, no atomic), the rest
+// come from a launch-wide counter, so a CTA that meets expensive wet tiles simply takes
+// fewer; in FP64, where a wet tile costs many times a dry one (B300's FP64 rate), the tiles
 // the previous launch found wet, or that have boundary or inflow edges, are taken
 // first so the expensive tiles do not come last; the others (all tiles in FP32-bulk,
 // which is bound by memory traffic and profits from spatial order) follow in the work
