@@ -212,7 +212,9 @@ bm_status bm_batch_step(bm_batch* b, int64_t n_steps);
 bm_status bm_batch_step_async(bm_batch* b, int64_t n_steps);
 bm_status bm_batch_sync(bm_batch* b);
 /* Member k runs until exactly t_end[k] (n_states finite values); finished members
- * idle while the others continue. */
+ * idle while the others continue (once a quarter of the listed members have
+ * finished, the launches list only the running ones; blocks, allocating a work list
+ * each time). */
 bm_status bm_batch_run_until(bm_batch* b, const double* t_end);
 
 /*

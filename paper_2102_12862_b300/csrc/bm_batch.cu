@@ -11,6 +11,7 @@
 #include <functional>
 #include <limits>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -21,7 +22,14 @@ struct bm_batch {
   std::vector<bm_state*> members;
   int prec = BM_FP64;
   bm::DBuf<unsigned char> descs;  // member descriptors, one after another
+  size_t dsz = 0;                 // bytes per descriptor
   bm::StepList list;
+  // run_until: a work list of the members still running, once enough have finished
+  // (a finished member's tiles would still be staged by every launch)
+  std::unique_ptr<bm::StepList> sub;
+  std::map<int, cudaGraphExec_t> sub_graphs;
+  int sub_grid = 0;
+  int shape = 0;                  // the launch shape (CTAs per SM; 0 = occupancy)
   bm::DBuf<bm::Ctl*> ctlp;        // device pointers to the members' control blocks
   bm::DBuf<double> t_end;         // per-member end times (run_until)
   bm::DBuf<int> flags;            // per member: active | status << 1
@@ -32,6 +40,7 @@ struct bm_batch {
   int grid = 0;
   ~bm_batch() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : sub_graphs) cudaGraphExecDestroy(kv.second);
     if (hflags) cudaFreeHost(hflags);
     if (own) cudaStreamDestroy(own);
   }
@@ -68,12 +77,16 @@ __global__ void batch_flags(Ctl* const* ctl, int n, int* flags) {
 }
 
 void launch_batch(bm_batch* b, cudaStream_t st) {
-  launch_work(b->prec, b->list, b->grid, 0, st);
+  if (b->sub)
+    launch_work(b->prec, *b->sub, b->sub_grid, 0, st);
+  else
+    launch_work(b->prec, b->list, b->grid, 0, st);
 }
 
 bm_status batch_graph(bm_batch* b, int k, cudaGraphExec_t* out) {
-  auto it = b->graphs.find(k);
-  if (it != b->graphs.end()) {
+  auto& graphs = b->sub ? b->sub_graphs : b->graphs;
+  auto it = graphs.find(k);
+  if (it != graphs.end()) {
     *out = it->second;
     return BM_OK;
   }
@@ -85,8 +98,35 @@ bm_status batch_graph(bm_batch* b, int k, cudaGraphExec_t* out) {
   cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(BM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-  b->graphs[k] = ge;
+  graphs[k] = ge;
   *out = ge;
+  return BM_OK;
+}
+
+// Drop the run_until work list (the stream must be idle).
+void drop_sub(bm_batch* b) {
+  for (auto& kv : b->sub_graphs) cudaGraphExecDestroy(kv.second);
+  b->sub_graphs.clear();
+  b->sub.reset();
+}
+
+// Step only the members whose flag (b->hflags, as batch_read left it) is active.
+bm_status use_active_members(bm_batch* b) {
+  std::vector<bm_state*> act;
+  std::vector<const void*> dptr;
+  for (size_t k = 0; k < b->members.size(); ++k)
+    if (b->hflags[k] & 1) {
+      act.push_back(b->members[k]);
+      dptr.push_back(b->descs.p + k * b->dsz);
+    }
+  drop_sub(b);
+  if (act.empty()) return BM_OK;
+  std::unique_ptr<StepList> l(new (std::nothrow) StepList());
+  if (!l) return fail(BM_ENOMEM, "bm_batch_run_until: out of host memory");
+  bm_status st = build_step_list(act, dptr, l.get());
+  if (st != BM_OK) return st;
+  b->sub_grid = step_grid(*l, b->shape);
+  b->sub = std::move(l);
   return BM_OK;
 }
 
@@ -187,6 +227,7 @@ bm_status bm_batch_create(bm_state* const* states, int32_t n, bm_batch** out) {
     ctls[k] = s->ctl;
   }
   const size_t dsz = one.size();  // a multiple of 16: members' descriptors stay aligned
+  b->dsz = dsz;
   cudaError_t e = b->descs.upload(all);
   if (e == cudaSuccess) {
     std::vector<const void*> dptr(n);
@@ -237,6 +278,7 @@ bm_status bm_batch_set_launch(bm_batch* b, int ctas_per_sm) {
   if (!b) return fail(BM_EINVAL, "bm_batch_set_launch: batch is NULL");
   if (ctas_per_sm < 0 || ctas_per_sm > 64) return fail(BM_EINVAL, "bm_batch_set_launch: ctas_per_sm in [0, 64]");
   const int grid = step_grid(b->list, ctas_per_sm);
+  b->shape = ctas_per_sm;
   if (grid != b->grid) {
     BM_CUDA(cudaStreamSynchronize(b->stream));
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
@@ -283,14 +325,26 @@ bm_status bm_batch_run_until(bm_batch* b, const double* t_end) {
   st = batch_read(b, &active);
   int64_t chunk = 16;
   int64_t launched = 0;
+  int listed = static_cast<int>(b->members.size());  // members of the launches' work list
   while (st == BM_OK && active > 0) {
+    // once a quarter of the listed members have finished, list only the running ones
+    if (4 * active <= 3 * listed) {
+      st = use_active_members(b);
+      if (st != BM_OK) break;
+      listed = active;
+    }
     st = batch_enqueue(b, chunk);
-    if (st != BM_OK) return st;
+    if (st != BM_OK) break;
     launched += chunk;
     st = batch_read(b, &active);
     if (chunk < 512) chunk *= 2;
-    if (launched > (int64_t(1) << 40)) return fail(BM_ETIMEOUT, "bm_batch_run_until: no progress");
+    if (launched > (int64_t(1) << 40)) {
+      st = fail(BM_ETIMEOUT, "bm_batch_run_until: no progress");
+      break;
+    }
   }
+  cudaStreamSynchronize(b->stream);
+  drop_sub(b);
   return st;
 }
 
