@@ -193,8 +193,8 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
     nh4 = std::max(nh4, R.nh4_max);
   }
   cudaError_t e = out->items.upload(items);
-  if (e == cudaSuccess) e = out->sched.alloc(6);
-  if (e == cudaSuccess) e = cudaMemset(out->sched.p, 0, 6 * sizeof(int));
+  if (e == cudaSuccess) e = out->sched.alloc(8);
+  if (e == cudaSuccess) e = cudaMemset(out->sched.p, 0, 8 * sizeof(int));
   if (e == cudaSuccess) e = out->early.alloc(2 * items.size());
   if (e == cudaSuccess) e = out->mark.alloc(items.size());
   if (e == cudaSuccess) e = cudaMemset(out->mark.p, 0xff, items.size() * sizeof(int));  // stamp -1: none

@@ -303,18 +303,20 @@ template <typename T>
 constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M floodplain
 
 // One step (prime = 0) or prime pass (prime = 1: no update; derived data, inflow
-// weights and the dt of the current state) over a work list.  sched: [0] tickets handed out by the counter
-// (after each CTA's static tickets),
-// [1] CTAs done taking items (both zero at launch; the last CTA to finish taking zeroes
-// them), [2] launch stamp s, [3] early items listed for launch s + 1, [4] early items
-// listed for this launch (E), [5] items finished.  Ticket t < E takes early[s & 1][t];
-// t < E + n_items takes item t - E unless mark[t - E] == s (it was early).  Finished
-// early items are listed in early[(s + 1) & 1] and marked s + 1; the last item to
-// finish moves [3] to [4], zeroes [3] and [5] and increments s.  early: 2 x n_items,
-// mark: n_items.  ne4max / nh4max: the largest record of the list (they fix the
-// shared-memory layout).  A single state is
-// a list of one instance's tiles, so a run executes the same machine code alone and in
-// a batch and gives bitwise the same result.
+// weights and the dt of the current state) over a work list.  sched: [0] tickets
+// handed out by the counter (after each CTA's static tickets), [1] CTAs done taking
+// items (both zero at launch; the last CTA to finish taking zeroes them), [2] launch
+// stamp s, [3] / [6] boundary-or-inflow / other wet items listed for launch s + 1,
+// [4] / [7] the same listed for this launch (F, W; E = F + W early items), [5] items
+// finished.  Ticket t < F takes early[s & 1][t], t < E takes
+// early[s & 1][n_items - 1 - (t - F)]; t < E + n_items takes item t - E unless
+// mark[t - E] == s (it was early).  Finished items are listed in early[(s + 1) & 1]
+// (from the front or the back) and marked s + 1; the last item to finish moves [3],
+// [6] to [4], [7], zeroes [3], [5], [6] and increments s.  early: 2 x n_items, mark:
+// n_items.  ne4max / nh4max: the largest record of the list (they fix the
+// shared-memory layout).  A single state is a list of one instance's tiles, so a run
+// executes the same machine code alone and in a batch and gives bitwise the same
+// result.
 template <typename T>
 __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const PipeItem* __restrict__ items,
                                                                          int n_items, int* __restrict__ sched,
@@ -347,19 +349,27 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     // ---------------------------------------------------------------- copy warp
     const int lane = tid - kTile;
     volatile int* abort_flag = &s_abort;
-    // Work items come from the launch's counter through a three-stage pipeline, so the
-    // copy warp never waits on a value in the iteration that asked for it: a ticket
-    // (atomic) -> the item read -> promotion to "next to issue" (instance pointers and
-    // halo indices read) -> issue.  FP64 tickets map through the early list first.
+    // Work items reach the issue through a pipeline, so the copy warp seldom waits on a
+    // value in the iteration that asked for it: the ticket (static, or requested from
+    // the counter a step ahead) and its lookup -> the item read -> promotion to "next
+    // to issue" (instance pointers and halo indices read) -> issue.  FP64 tickets map
+    // through the early list first.
     // FP64: the early list and marks are the previous step's
     if constexpr (SL::k64) grid_dep_wait();
-    int stamp = 0, n_early = 0;
+    // The early list: the tiles with boundary or inflow edges (front part, in the order
+    // they finished; the per-instance boundary and inflow work follows the last of
+    // them), then the other tiles the previous launch found wet (stored from the end
+    // of the array).
+    int stamp = 0, n_front = 0, n_back = 0;
     if (SL::k64 && lane == 0) {
       stamp = *reinterpret_cast<volatile int*>(&sched[2]);
-      n_early = *reinterpret_cast<volatile int*>(&sched[4]);
+      n_front = *reinterpret_cast<volatile int*>(&sched[4]);
+      n_back = *reinterpret_cast<volatile int*>(&sched[7]);
     }
     stamp = __shfl_sync(0xffffffffu, stamp, 0);
-    n_early = min(__shfl_sync(0xffffffffu, n_early, 0), n_items);
+    n_front = min(__shfl_sync(0xffffffffu, n_front, 0), n_items);
+    n_back = min(__shfl_sync(0xffffffffu, n_back, 0), n_items - n_front);
+    const int n_early = n_front + n_back;
     const int* ord = early + static_cast<size_t>(stamp & 1) * n_items;
     const int n_tickets = n_early + n_items;
     // ticket -> work item (-1: taken in the early pass; -2: past the end), in two
@@ -368,7 +378,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     // listed with stamp s, or finished in the early pass and re-listed with s + 1, was
     // taken early (an item only finishes after it was taken).
     auto map_load = [&](int t) -> int {
-      if (t < n_early) return ord[t];
+      if (t < n_early) return t < n_front ? ord[t] : ord[n_items - 1 - (t - n_front)];
       if (n_early > 0 && t < n_tickets) return __ldcg(&mark[t - n_early]);
       return 0;
     };
@@ -814,14 +824,21 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       rrun = 0.0;
       cnt = 0;
     }
-    // FP64: wet, boundary and inflow tiles are taken early in the next launch (only the
-    // next launch reads the list, so no fence)
+    // FP64: boundary, inflow and wet tiles are taken early in the next launch (only the
+    // next launch reads the list, so no fence); every item finishes once per launch, so
+    // the two parts never meet
     if (SL::k64 && tid == 0) {
       ++n_done;
-      if (!quiet || (inf.flags & 3u)) {
+      if (inf.flags & 3u) {
         const int pos = atomicAdd(&sched[3], 1);
         if (pos < n_items) {
           next_early[pos] = inf.item;
+          mark[inf.item] = stamp + 1;
+        }
+      } else if (!quiet) {
+        const int pos = atomicAdd(&sched[6], 1);
+        if (pos < n_items) {
+          next_early[n_items - 1 - pos] = inf.item;
           mark[inf.item] = stamp + 1;
         }
       }
@@ -836,7 +853,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     __threadfence();
     if (atomicAdd(&sched[5], n_done) + n_done == n_items) {
       __threadfence();
-      atomicExch(&sched[4], min(atomicExch(&sched[3], 0), n_items));
+      atomicExch(&sched[4], atomicExch(&sched[3], 0));
+      atomicExch(&sched[7], atomicExch(&sched[6], 0));
       atomicExch(&sched[5], 0);
       atomicExch(&sched[2], stamp + 1);
     }
