@@ -66,15 +66,16 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
 }
 // Test for completion of the phase with the given parity; the thread may sleep in
-// the instruction meanwhile (suspend-time hint 0.1 ms).
+// the instruction meanwhile, for a system-dependent time (no hint: measured faster
+// on the floodplain than a 0.1 ms or 1 us hint).
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(saddr(b)), "r"(parity), "r"(100000u)
+      : "r"(saddr(b)), "r"(parity)
       : "memory");
   return ok != 0;
 }

@@ -69,6 +69,11 @@ def test_batch_run_until_per_member_end_times():
     rel = np.max(np.abs(H - o.H)) / np.max(np.abs(o.H))
     assert rel < 1e-11
     assert sts[1].stats()["steps"] == o.steps
+    # run_until listed only the running members towards the end; plain steps take
+    # every member again
+    before = [st.stats()["steps"] for st in sts]
+    b.step(3)
+    assert [st.stats()["steps"] for st in sts] == [n + 3 for n in before]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
