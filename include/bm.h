@@ -176,8 +176,9 @@ bm_status bm_step_timed(bm_state* s, int64_t n_steps, double* step_kernel_ms, do
 /*
  * Launch shape of the state's step kernel, whose CTAs stay resident and loop over
  * the 256-cell tiles: ctas_per_sm = 0 launches as many CTAs per SM as fit (the
- * default), k > 0 launches k per SM.  Results do not depend on it.  Chosen by the
- * autotuner or by hand.
+ * default), k > 0 launches k per SM, at most as many as fit (every CTA of the launch
+ * is resident from its start: a share of the tiles is assigned to CTAs statically).
+ * Results do not depend on it.  Chosen by the autotuner or by hand.
  */
 bm_status bm_state_set_launch(bm_state* s, int ctas_per_sm);
 

@@ -215,8 +215,10 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
   return BM_OK;
 }
 
+// CTAs of a step launch: all resident at once (a share of the tiles is assigned to
+// CTAs statically, so a CTA that waited for another to exit would finish late).
 int step_grid(const StepList& l, int ctas_per_sm) {
-  const int per = ctas_per_sm > 0 ? ctas_per_sm : l.occupancy;
+  const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, l.occupancy) : l.occupancy;
   const long long g = static_cast<long long>(per) * sm_count();
   return static_cast<int>(std::max(1LL, std::min<long long>(g, l.n)));
 }
