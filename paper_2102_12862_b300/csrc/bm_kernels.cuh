@@ -245,11 +245,11 @@ __device__ __forceinline__ void cell_derived(T h, T qx, T qy, T hmin, T g, T& u,
 // The free surface H of an FP32-bulk cell is the unevaluated sum hi + lo of two
 // floats (offset from the FP64 datum); FP64 cells have lo = 0.  Depths are formed
 // as (hi - z) + lo, so near-equal hi and z cancel exactly (Sterbenz) and the lo
-// part keeps what a single float would round away.
-template <typename T>
-__device__ __forceinline__ T depth_of(T hi, T lo, T z) {
-  return (hi - z) + lo;
-}
+// part keeps what a single float would round away; FP64 forms H - z, as the
+// oracle does (adding a zero lo would cost an instruction and could flip the sign
+// of a zero depth).
+__device__ __forceinline__ float depth_of(float hi, float lo, float z) { return (hi - z) + lo; }
+__device__ __forceinline__ double depth_of(double hi, double, double z) { return hi - z; }
 
 // (hi, lo) += d without rounding error in the pair: Knuth's TwoSum of hi and d,
 // then Dekker's Fast2Sum renormalisation (|s| >= |lo + e| holds for these

@@ -739,8 +739,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
             // |q1| = |q*| / (1 + a), q2 = q1 / (1 + dt k(q1)) = q* / (1 + 2a); so
             // (q* + q2) / 2 = q* (1 + a) / (1 + 2a) -- one square root and one
             // division instead of two each (equal up to rounding)
-            const T r3 = f_rcbrt(h), r6 = r3 * r3 * r3 * r3 * r3 * r3;  // h^(-1/3), h^(-2)
-            const T cf = gn2 * (r6 * r3);                                 // g n^2 / h^(7/3)
+            const T r3 = f_rcbrt(h), r32 = r3 * r3;                      // h^(-1/3), h^(-2/3)
+            const T cf = gn2 * (r32 * r32 * r32 * r3);                    // g n^2 / h^(7/3)
             const T a1 = dt * (cf * f_sqrt(ux * ux + uy * uy));
             const T fr = f_div(T(1) + a1, T(1) + T(2) * a1);
             ux = ux * fr;
