@@ -79,6 +79,10 @@ def _lib():
         lib.orc_n_edges.restype = i64
         lib.orc_cell_area.argtypes = [C.c_void_p, P(d)]
         lib.orc_edges.argtypes = [C.c_void_p, P(i64), P(i64), P(d), P(d), P(d)]
+        lib.orc_track.argtypes = [C.c_void_p, P(d), P(d), P(d), d, d, d, C.c_int, P(d), P(d), P(d), P(d), P(d)]
+        lib.orc_run_tracked.argtypes = [C.c_void_p, P(d), P(d), P(d), P(d), d, i64, P(d), d, d, P(d), P(d), P(d),
+                                        P(d), P(d)]
+        lib.orc_run_tracked.restype = i64
         _libs["serial"] = lib
     return _libs["serial"]
 
@@ -127,6 +131,7 @@ class Oracle:
         self.t = C.c_double(0.0)
         self.bvol = C.c_double(0.0)
         self.steps = 0
+        self.tracking = None  # flood tracking record (see track())
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -134,10 +139,28 @@ class Oracle:
             _lib().orc_destroy(h)
             self._h = None
 
+    def track(self, h_arrival: float, rho: float = 1000.0):
+        """Start flood tracking from the current state (updated after every step):
+        arrays t_arrival (NaN: not reached), h_max, u_max, q_max, tau_max."""
+        n = self.n_cells
+        self.tracking = {k: np.empty(n) for k in ("t_arrival", "h_max", "u_max", "q_max", "tau_max")}
+        self._track_args = (float(h_arrival), float(rho))
+        tr = self.tracking
+        _lib().orc_track(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), self.t.value, float(h_arrival),
+                         float(rho), 1, _dp(tr["t_arrival"]), _dp(tr["h_max"]), _dp(tr["u_max"]),
+                         _dp(tr["q_max"]), _dp(tr["tau_max"]))
+
     def step(self, n: int = 1, t_end: float = math.inf) -> int:
         lib = _lib()
-        k = lib.orc_run(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), C.byref(self.t), float(t_end), int(n),
-                        C.byref(self.bvol))
+        if self.tracking is not None:
+            tr = self.tracking
+            k = lib.orc_run_tracked(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), C.byref(self.t),
+                                    float(t_end), int(n), C.byref(self.bvol), *self._track_args,
+                                    _dp(tr["t_arrival"]), _dp(tr["h_max"]), _dp(tr["u_max"]), _dp(tr["q_max"]),
+                                    _dp(tr["tau_max"]))
+        else:
+            k = lib.orc_run(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), C.byref(self.t), float(t_end),
+                            int(n), C.byref(self.bvol))
         self.steps += k
         return k
 

@@ -24,6 +24,7 @@
  *   4. Manning friction (Eq. 2, Table 1) split off and integrated with a
  *      two-stage semi-implicit Runge-Kutta (Heun) step.
  *   5. q := 0 on cells whose depth is below the minimum water depth.
+ * Optional flood tracking after each step (orc_track below).
  *
  * Readings where the paper is silent are the same as in the design notes:
  * modified-state form, Toro wave speeds, h_min, friction stages, rho_ij, the
@@ -462,6 +463,55 @@ int64_t orc_run(orc_mesh* m, double* H, double* qx, double* qy, double* t, doubl
   for (; s < n_steps; ++s) {
     if (!(*t < t_end)) break;
     orc_step(m, H, qx, qy, t, t_end, bvol);
+  }
+  return s;
+}
+
+/*
+ * Flood tracking (the hydrodynamic module's "Flood" outputs: water front arrival
+ * time, maximum water depth, maximum flow velocity, maximum specific discharge and
+ * maximum bed shear stress), updated from the state (H, qx, qy) at time t.  Per cell:
+ *   h = H - z,  |q| = sqrt(qx^2 + qy^2),
+ *   |u| = |q| / h and tau = rho g n^2 |u|^2 / h^(1/3) where h > h_min, else 0
+ *   (Manning, Eq. 2 / Table 1: the bed shear stress rho g h S_f with
+ *   S_f = n^2 |u|^2 / h^(4/3)),
+ *   arrival = the first t at which h > h_arr (NaN until then),
+ *   the maxima of h, |u|, |q|, tau over the calls.
+ * init != 0 starts the record from this state.
+ */
+void orc_track(const orc_mesh* m, const double* H, const double* qx, const double* qy, double t, double h_arr,
+               double rho, int init, double* arr, double* hmax, double* umax, double* qmax, double* taumax) {
+  const double g = m->p.g, hmin = m->p.h_min;
+  for (int64_t i = 0; i < m->n_cells; ++i) {
+    const double h = H[i] - m->z[i];
+    const double q = sqrt(qx[i] * qx[i] + qy[i] * qy[i]);
+    double u = 0, tau = 0;
+    if (h > hmin) {
+      u = q / h;
+      tau = rho * g * m->man[i] * m->man[i] * u * u / cbrt(h);
+    }
+    if (init) {
+      arr[i] = h > h_arr ? t : NAN;
+      hmax[i] = h; umax[i] = u; qmax[i] = q; taumax[i] = tau;
+    } else {
+      if (isnan(arr[i]) && h > h_arr) arr[i] = t;
+      if (h > hmax[i]) hmax[i] = h;
+      if (u > umax[i]) umax[i] = u;
+      if (q > qmax[i]) qmax[i] = q;
+      if (tau > taumax[i]) taumax[i] = tau;
+    }
+  }
+}
+
+/* orc_run with flood tracking after every step */
+int64_t orc_run_tracked(orc_mesh* m, double* H, double* qx, double* qy, double* t, double t_end, int64_t n_steps,
+                        double* bvol, double h_arr, double rho, double* arr, double* hmax, double* umax, double* qmax,
+                        double* taumax) {
+  int64_t s = 0;
+  for (; s < n_steps; ++s) {
+    if (!(*t < t_end)) break;
+    orc_step(m, H, qx, qy, t, t_end, bvol);
+    orc_track(m, H, qx, qy, *t, h_arr, rho, 0, arr, hmax, umax, qmax, taumax);
   }
   return s;
 }

@@ -37,11 +37,22 @@ MUTANTS = [
     ("hll_state_jump", "double H0 = FL0 - SL * ((FR0 - FL0) - SR * (hR - hL)) / d;",
      "double H0 = FL0 - SL * ((FR0 - FL0) - SR * (hL - hR)) / d;"),
 ]
+# flood tracking, caught by tests/test_oracle_tracking.py
+TRACK_MUTANTS = [
+    ("track_shear_exponent", "u * u / cbrt(h);", "u * u / sqrt(h);"),
+    ("track_arrival_threshold", "if (isnan(arr[i]) && h > h_arr) arr[i] = t;",
+     "if (isnan(arr[i]) && h > hmin) arr[i] = t;"),
+    ("track_max_of_surface", "if (h > hmax[i]) hmax[i] = h;", "if (H[i] > hmax[i]) hmax[i] = H[i];"),
+    ("track_discharge_as_velocity", "u = q / h;", "u = q;"),
+]
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("name,orig,mut", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_mutant(name, orig, mut, tmp_path):
+@pytest.mark.parametrize("name,orig,mut,pins",
+                         [m + ("test_oracle_pins.py",) for m in MUTANTS]
+                         + [m + ("test_oracle_tracking.py",) for m in TRACK_MUTANTS],
+                         ids=[m[0] for m in MUTANTS + TRACK_MUTANTS])
+def test_pins_catch_mutant(name, orig, mut, pins, tmp_path):
     src = open(SRC).read()
     assert src.count(orig) == 1, f"mutation site for {name} not unique"
     msrc = tmp_path / "bm_oracle_mutant.c"
@@ -49,6 +60,6 @@ def test_pins_catch_mutant(name, orig, mut, tmp_path):
     env = dict(os.environ, ORACLE_MUTANT_SRC=str(msrc), ORACLE_MUTANT_LIB=str(tmp_path / "libmut.so"),
                PYTHONPATH=ROOT)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
