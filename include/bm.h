@@ -157,6 +157,27 @@ bm_status bm_state_upload(bm_state* s, const double* H, const double* qx, const 
 bm_status bm_state_download(bm_state* s, double* H, double* qx, double* qy, double* t);
 
 /*
+ * Flood tracking (the hydrodynamic module's "Flood" outputs), updated in the step
+ * kernel with every step from the call on, per cell: the water front arrival time
+ * (the first t^{n+1} at which the depth h = H - z exceeds h_arrival; NaN until then)
+ * and the running maxima of h, of the flow velocity |u| = |q| / h, of the specific
+ * discharge |q| = sqrt(q_x^2 + q_y^2) and of the bed shear stress
+ * rho g n^2 |u|^2 / h^(1/3) (Manning, Eq. 2; rho = 1000 kg/m^3; |u| and the stress
+ * are 0 where h <= h_min).
+ * bm_state_track starts (or restarts) the record from the current state: arrival = t
+ * where h > h_arrival, maxima = the current values.  It allocates the five tracking
+ * arrays on first use (5 values per cell) and blocks.  h_arrival must be finite and
+ * >= 0 (BM_EINVAL).  Uploading a state does not restart the record; batches created
+ * after the call track their member (the batch copies the member's descriptor).
+ * bm_state_download_track copies the record to host arrays in the caller's cell order
+ * (any pointer may be NULL); BM_EINVAL while tracking was never started.  FP32-bulk
+ * states keep the maxima in single precision (the arrival time in double).
+ */
+bm_status bm_state_track(bm_state* s, double h_arrival);
+bm_status bm_state_download_track(bm_state* s, double* t_arrival, double* h_max, double* u_max, double* q_max,
+                                  double* tau_max);
+
+/*
  * Scalars of the state: time, the dt the next step will take, steps taken,
  * water volume V = sum |Omega_i| (H_i - z_i) (FP64, fixed summation order), and
  * the net volume that entered through the boundary since init/upload.

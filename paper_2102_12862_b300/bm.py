@@ -76,6 +76,8 @@ SIGNATURES = {
     "bm_batch_autotune": (C.c_int, [_vp, C.c_int, _P(C.c_int), _P(_d)]),
     "bm_volume_noalloc": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "bm_math_eval": (C.c_int, [C.c_int32, _vp, _vp, _i64]),
+    "bm_state_track": (C.c_int, [_vp, C.c_double]),
+    "bm_state_download_track": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "bm_server_opts_default": (None, [_P(bm_server_opts)]),
     "bm_server_create": (C.c_int, [_P(bm_server_opts), _P(_vp)]),
     "bm_server_destroy": (None, [_vp]),
@@ -219,6 +221,20 @@ def bm_state_download(state: int, n_cells: int, H=None, qx=None, qy=None):
     t = _d()
     _check(load_library().bm_state_download(state, _dp(H), _dp(qx), _dp(qy), C.byref(t)))
     return H, qx, qy, t.value
+
+
+TRACK_FIELDS = ("t_arrival", "h_max", "u_max", "q_max", "tau_max")
+
+
+def bm_state_track(state: int, h_arrival: float):
+    _check(load_library().bm_state_track(state, float(h_arrival)))
+
+
+def bm_state_download_track(state: int, n_cells: int) -> dict:
+    """The flood-tracking record in the caller's cell order (see bm_state_track)."""
+    out = {k: np.empty(n_cells) for k in TRACK_FIELDS}
+    _check(load_library().bm_state_download_track(state, *(_dp(out[k]) for k in TRACK_FIELDS)))
+    return out
 
 
 def bm_state_stats(state: int, volume: bool = True) -> dict:
@@ -372,6 +388,13 @@ class State:
 
     def download(self):
         return bm_state_download(self.handle, self.n_cells)
+
+    def track(self, h_arrival: float = 0.01):
+        """Start flood tracking from the current state (updated with every step)."""
+        bm_state_track(self.handle, h_arrival)
+
+    def download_track(self) -> dict:
+        return bm_state_download_track(self.handle, self.n_cells)
 
     def stats(self, volume: bool = True) -> dict:
         return bm_state_stats(self.handle, volume)

@@ -321,6 +321,14 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
   }
   d.z = b.z.p;
   d.gn2 = b.gn2.p;
+  if (b.trk_t.p) {
+    d.trk_t = b.trk_t.p;
+    d.trk_h = b.trk[0].p;
+    d.trk_u = b.trk[1].p;
+    d.trk_q = b.trk[2].p;
+    d.trk_tau = b.trk[3].p;
+    d.trk_harr = static_cast<T>(s->trk_harr);
+  }
   d.in_pw = b.in_pw.p;
   d.in_hs = b.in_hs.p;
   if constexpr (sizeof(T) == 8) {
@@ -720,6 +728,61 @@ bm_status bm_state_download(bm_state* s, double* H, double* qx, double* qy, doub
   return BM_OK;
 }
 
+bm_status bm_state_track(bm_state* s, double h_arrival) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_track: state is NULL");
+  if (!std::isfinite(h_arrival) || h_arrival < 0.0)
+    return fail(BM_EINVAL, "bm_state_track: h_arrival must be finite and >= 0");
+  const HostMesh& h = s->mesh->h;
+  const size_t Np = static_cast<size_t>(h.n_tiles) * kTile;
+  cudaError_t e = s->prec == BM_FP64 ? s->b64.alloc_tracking(Np) : s->b32.alloc_tracking(Np);
+  if (e != cudaSuccess) return dev_fail(e, "bm_state_track: tracking arrays");
+  s->trk_harr = h_arrival;
+  // the step kernels read the descriptor in place: rewrite it (same size, same address)
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  state_desc_bytes(s, &s->hdesc);
+  BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
+  const int n = static_cast<int>(h.n_cells);
+  const int nb = (n + 255) / 256;
+  if (s->prec == BM_FP64)
+    track_init<double><<<nb, 256, 0, s->stream>>>(reinterpret_cast<const InstDesc<double>*>(s->desc.p), s->ctl, n);
+  else
+    track_init<float><<<nb, 256, 0, s->stream>>>(reinterpret_cast<const InstDesc<float>*>(s->desc.p), s->ctl, n);
+  BM_CUDA(cudaGetLastError());
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  return BM_OK;
+}
+
+bm_status bm_state_download_track(bm_state* s, double* t_arrival, double* h_max, double* u_max, double* q_max,
+                                  double* tau_max) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_download_track: state is NULL");
+  const bool on = s->prec == BM_FP64 ? s->b64.trk_t.p != nullptr : s->b32.trk_t.p != nullptr;
+  if (!on) return fail(BM_EINVAL, "bm_state_download_track: tracking is off (bm_state_track starts it)");
+  const int n = static_cast<int>(s->mesh->h.n_cells);
+  const int nb = (n + 255) / 256;
+  const size_t bytes = static_cast<size_t>(n) * sizeof(double);
+  double* outs[5] = {t_arrival, h_max, u_max, q_max, tau_max};
+  for (int k = 0; k < 5; ++k) {
+    if (!outs[k]) continue;
+    double* stage = s->stage[k % 3].p;  // reused in stream order after its copy-out
+    if (k == 0) {
+      const double* src = s->prec == BM_FP64 ? s->b64.trk_t.p : s->b32.trk_t.p;
+      scatter_to_user<double><<<nb, 256, 0, s->stream>>>(src, nullptr, s->mesh->perm.p, n, stage, 0.0);
+    } else if (s->prec == BM_FP64) {
+      scatter_to_user<double><<<nb, 256, 0, s->stream>>>(s->b64.trk[k - 1].p, nullptr, s->mesh->perm.p, n, stage,
+                                                          0.0);
+    } else {
+      scatter_to_user<float><<<nb, 256, 0, s->stream>>>(s->b32.trk[k - 1].p, nullptr, s->mesh->perm.p, n, stage,
+                                                         0.0);
+    }
+    BM_CUDA(cudaGetLastError());
+    BM_CUDA(cudaMemcpyAsync(outs[k], stage, bytes, cudaMemcpyDeviceToHost, s->stream));
+  }
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  return BM_OK;
+}
+
 bm_status bm_state_stats(bm_state* s, double* t, double* dt_next, int64_t* steps, double* volume,
                          double* boundary_volume) {
   clear_error();
@@ -867,6 +930,8 @@ cudaError_t snapshot_buffers(Buffers<T>& b, Snapshot* sn, cudaStream_t st) {
   }
   if (e == cudaSuccess) e = sn->take(b.in_pw.p, b.in_pw.bytes(), st);
   if (e == cudaSuccess) e = sn->take(b.in_hs.p, b.in_hs.bytes(), st);
+  if (e == cudaSuccess) e = sn->take(b.trk_t.p, b.trk_t.bytes(), st);
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = sn->take(b.trk[k].p, b.trk[k].bytes(), st);
   return e;
 }
 

@@ -22,6 +22,14 @@ struct alignas(16) InstDesc {
   T* Hlo[2];  // FP32-bulk only: lo part of the free surface
   T* qx[2];
   T* qy[2];
+  // flood tracking (null when off): front arrival time, maxima of depth, |u|, |q|
+  // and bed shear stress per cell; the arrival threshold depth
+  double* trk_t;
+  T* trk_h;
+  T* trk_u;
+  T* trk_q;
+  T* trk_tau;
+  T trk_harr;
   const T* z;
   const T* gn2;       // g n^2
   const T* inv_area;  // 1 / |Omega_i|
@@ -279,6 +287,70 @@ __device__ __forceinline__ T cell_rate(const T* nxs, const T* nys, const T* ls, 
     ssum += ll;
   }
   return cfl_mode == 1 ? ssum * ia : rmax;
+}
+
+// ------------------------------------------------------------------ flood tracking
+
+// The hydrodynamic module's "Flood" outputs per cell: the time the water front
+// arrives (the first time the depth exceeds a threshold) and the running maxima of
+// the depth h, the flow velocity |u| = |q| / h, the specific discharge |q| and the
+// bed shear stress, Manning's rho g n^2 |u|^2 / h^(1/3) (= rho g h S_f with Eq. 2's
+// friction slope; |u| and the stress are 0 at or below h_min).
+constexpr double kRhoWater = 1000.0;  // density of water, kg / m^3
+
+template <typename T>
+__device__ __forceinline__ void track_values(T h, T qx, T qy, T gn2, T hmin, T& q, T& u, T& tau) {
+  q = f_sqrt(qx * qx + qy * qy);
+  u = T(0);
+  tau = T(0);
+  if (h > hmin) {
+    u = f_div(q, h);
+    tau = static_cast<T>(kRhoWater) * gn2 * u * u * f_rcbrt(h);
+  }
+}
+
+// A cell's record before this step's update (loaded early, so the loads overlap the
+// update's arithmetic).
+template <typename T>
+struct TrackRecord {
+  double t;
+  T h, u, q, tau;
+};
+template <typename T>
+__device__ __forceinline__ TrackRecord<T> track_load(const InstDesc<T>& a, int i) {
+  return TrackRecord<T>{a.trk_t[i], a.trk_h[i], a.trk_u[i], a.trk_q[i], a.trk_tau[i]};
+}
+// Fold the cell's state U^{n+1} (depth h, discharge qx, qy) at time t into its record;
+// stores only what changes.
+template <typename T>
+__device__ __forceinline__ void track_update(const InstDesc<T>& a, int i, const TrackRecord<T>& r, T h, T qx, T qy,
+                                             T gn2, T hmin, double t) {
+  T q, u, tau;
+  track_values<T>(h, qx, qy, gn2, hmin, q, u, tau);
+  if (isnan(r.t) && h > a.trk_harr) a.trk_t[i] = t;
+  if (h > r.h) a.trk_h[i] = h;
+  if (u > r.u) a.trk_u[i] = u;
+  if (q > r.q) a.trk_q[i] = q;
+  if (tau > r.tau) a.trk_tau[i] = tau;
+}
+
+// Start the record from the instance's current state (cells 0..n-1, tile order).
+template <typename T>
+__global__ void track_init(const InstDesc<T>* d, const Ctl* ctl, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const InstDesc<T>& a = *d;
+  const int par = ctl->parity;
+  const T lo = sizeof(T) == 4 ? a.Hlo[par][i] : T(0);
+  const T h = depth_of(a.H[par][i], lo, a.z[i]);
+  const T hmin = sizeof(T) == 8 ? static_cast<T>(a.p.h_min) : static_cast<T>(a.p.hmin_f);
+  T q, u, tau;
+  track_values<T>(h, a.qx[par][i], a.qy[par][i], a.gn2[i], hmin, q, u, tau);
+  a.trk_t[i] = h > a.trk_harr ? ctl->t : static_cast<double>(NAN);
+  a.trk_h[i] = h;
+  a.trk_u[i] = u;
+  a.trk_q[i] = q;
+  a.trk_tau[i] = tau;
 }
 
 // The per-instance work at the end of a step is split three ways so that little of

@@ -56,6 +56,14 @@ template <typename T>
 struct Buffers {
   DBuf<T> H[2], Hlo[2], qx[2], qy[2];
   DBuf<T> z, gn2, in_pw, in_hs;
+  DBuf<double> trk_t;  // flood tracking (bm_state_track): front arrival time,
+  DBuf<T> trk[4];      // maxima of depth, |u|, |q|, bed shear stress
+  cudaError_t alloc_tracking(size_t np) {
+    cudaError_t e = trk_t.p ? cudaSuccess : trk_t.alloc(np);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+      if (!trk[k].p) e = trk[k].alloc(np);
+    return e;
+  }
   cudaError_t alloc(size_t np, size_t n_inflow, bool pair) {
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
@@ -78,7 +86,8 @@ struct Buffers {
     return e;
   }
   size_t bytes() const {
-    size_t b = z.bytes() + gn2.bytes() + in_pw.bytes() + in_hs.bytes();
+    size_t b = z.bytes() + gn2.bytes() + in_pw.bytes() + in_hs.bytes() + trk_t.bytes();
+    for (int k = 0; k < 4; ++k) b += trk[k].bytes();
     for (int k = 0; k < 2; ++k)
       b += H[k].bytes() + Hlo[k].bytes() + qx[k].bytes() + qy[k].bytes();
     return b;
@@ -144,6 +153,8 @@ struct bm_state {
   double cur_t_end = 0.0;
   int grid = 0;         // CTAs of the persistent step launch
   int ctas_per_sm = 0;  // launch shape (0: as many as fit)
+  double trk_harr = 0.0;  // flood tracking: arrival threshold depth (tracking is on
+                          // once the tracking arrays exist)
   template <typename T>
   bm::Buffers<T>& buf();
   ~bm_state() {

@@ -710,6 +710,11 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       } else {
         T h = depth_of(Hh, Hl, zi), ux = qxi, uy = qyi;
         if (!prime) {
+          // flood tracking: the cell's record, loaded ahead of the update (a cell
+          // copied through, dry and at rest, cannot change its record)
+          const bool trk = a.trk_t != nullptr;
+          TrackRecord<T> rec{};
+          if (trk) rec = track_load(a, i);
           T s0 = zero, s1 = zero, s2 = zero;
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
@@ -758,6 +763,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           // negative depth: below -h_min, beyond the rounding of the FP32 bed offset in FP32-bulk
           const T negtol = kPair ? hmin + T(4) * static_cast<T>(FLT_EPSILON) * fabs(zi) : hmin;
           if (h < -negtol) atomicOr(&a.ctl->status, 2);
+          if (trk) track_update<T>(a, i, rec, h, ux, uy, gn2, hmin, new_time(cs, 1));
         }
         T u, v, c;
         cell_derived<T>(h, ux, uy, hmin, g, u, v, c);

@@ -117,3 +117,9 @@ def test_math_eval_validates_before_any_device_work():
     assert lib.bm_math_eval(0, None, None, 4) == bm.BM_EINVAL
     assert lib.bm_math_eval(0, None, None, -1) == bm.BM_EINVAL
     assert lib.bm_math_eval(0, None, None, 0) == bm.BM_OK
+
+
+def test_tracking_validates_before_any_device_work():
+    lib = bm.load_library()
+    assert lib.bm_state_track(None, 0.01) == bm.BM_EINVAL
+    assert lib.bm_state_download_track(None, None, None, None, None, None) == bm.BM_EINVAL
