@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--precisions", default="fp64,fp32")
     ap.add_argument("--lake-steps", type=int, default=500,
                     help="steps of the mostly wet lake-at-rest line (0: skip it)")
+    ap.add_argument("--track-steps", type=int, default=500,
+                    help="steps of the flood-tracking cost line (0: skip it)")
     ap.add_argument("--stress-steps", type=int, default=100000, help="stress: lake-at-rest steps")
     ap.add_argument("--workload", choices=["floodplain", "ensemble", "serve", "stress"], default="floodplain",
                     help="floodplain: the default line; ensemble: batched uneven meshes; serve: request loop")
@@ -355,6 +357,43 @@ def measure_lake(args, torch, bm, W):
     return out
 
 
+def measure_tracking(args, torch, bm, W):
+    """Flood tracking's cost on the floodplain: the same args.track_steps steps from
+    t = 0 with and without the per-cell record (arrival time of 0.05 m, maxima of
+    depth, velocity, discharge and bed shear stress) updated in the step kernel."""
+    s = W.floodplain()
+    mesh = bm.Mesh.from_scenario(s)
+    out = {"workload": "floodplain 2,000,000 triangles, steps from t = 0, arrival threshold 0.05 m",
+           "steps": args.track_steps}
+    for prec in [p for p in args.precisions.split(",") if p]:
+        res = {}
+        for tracked in (False, True):
+            st = bm.State.from_scenario(s, mesh=mesh, precision=prec)
+            stream = torch.cuda.Stream()
+            torch.cuda.set_stream(stream)
+            st.set_stream(stream.cuda_stream)
+            if tracked:
+                st.track(0.05)
+            st.step(args.warmup)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st.step_async(args.track_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st.sync()
+            res[tracked] = e0.elapsed_time(e1) / args.track_steps
+            if tracked:
+                rec = st.download_track()
+                res["arrived"] = int(np.sum(~np.isnan(rec["t_arrival"])))
+            st.close()
+        out["fp32_bulk" if prec == "fp32" else prec] = {
+            "ms_per_step": res[False], "ms_per_step_tracked": res[True],
+            "overhead": res[True] / res[False] - 1.0, "cells_arrived": res["arrived"]}
+    return out
+
+
 def tri_areas(s):
     a, b, c = s.xy[s.tri[:, 0]], s.xy[s.tri[:, 1]], s.xy[s.tri[:, 2]]
     return 0.5 * np.abs((b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (c[:, 0] - a[:, 0]) * (b[:, 1] - a[:, 1]))
@@ -535,6 +574,7 @@ def main():
         res[p], finals[p] = measure(args, p, s, mesh, torch, bm, dist, ws, rank)
 
     lake = measure_lake(args, torch, bm, W) if (rank == 0 and args.lake_steps > 0) else None
+    tracking = measure_tracking(args, torch, bm, W) if (rank == 0 and args.track_steps > 0) else None
 
     cpu, acc = None, {}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -574,6 +614,8 @@ def main():
                          "wet_fraction_first_last": q["wet_fraction"], "accuracy_vs_oracle": acc.get(p)}
         if lake is not None:
             line["wet_lake"] = lake
+        if tracking is not None:
+            line["flood_tracking"] = tracking
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

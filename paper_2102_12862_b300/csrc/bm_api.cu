@@ -83,10 +83,12 @@ int step_smem_limit() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, step_pipe<T>);
+    cudaFuncGetAttributes(&fa, step_pipe<T, false>);
     const int l = optin - static_cast<int>(fa.sharedSizeBytes);
-    if (cudaFuncSetAttribute(step_pipe<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, l) != cudaSuccess ||
-        cudaFuncSetAttribute(step_pipe<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) {
+    if (cudaFuncSetAttribute(step_pipe<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, l) != cudaSuccess ||
+        cudaFuncSetAttribute(step_pipe<T, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess ||
+        cudaFuncSetAttribute(step_pipe<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, l) != cudaSuccess ||
+        cudaFuncSetAttribute(step_pipe<T, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) {
       (void)cudaGetLastError();  // leave no sticky error behind; launches check the size
       return 48 * 1024 - static_cast<int>(fa.sharedSizeBytes);
     }
@@ -205,13 +207,23 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
   out->smem = prec == BM_FP64 ? StepLayout<double>(ne4, nh4).total : StepLayout<float>(ne4, nh4).total;
   const int lim = prec == BM_FP64 ? step_smem_limit<double>() : step_smem_limit<float>();
   if (out->smem > static_cast<size_t>(lim)) return fail(BM_EINVAL, "tile layout exceeds the device's shared memory");
+  out->track = false;
+  for (bm_state* m : members) out->track |= (prec == BM_FP64 ? m->b64.trk_t.p : m->b32.trk_t.p) != nullptr;
+  return list_occupancy(prec, out);
+}
+
+// Resident CTAs per SM of the list's kernel (with or without tracking).
+bm_status list_occupancy(int prec, StepList* l) {
   int occ = 0;
+  cudaError_t e;
   if (prec == BM_FP64)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_pipe<double>, kStepThreads, out->smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, l->track ? step_pipe<double, true> : step_pipe<double, false>, kStepThreads, l->smem);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_pipe<float>, kStepThreads, out->smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, l->track ? step_pipe<float, true> : step_pipe<float, false>, kStepThreads, l->smem);
   if (e != cudaSuccess) return dev_fail(e, "occupancy query");
-  out->occupancy = std::max(1, occ);
+  l->occupancy = std::max(1, occ);
   return BM_OK;
 }
 
@@ -241,12 +253,13 @@ void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const int ne4 = static_cast<int>(l.ne4), nh4 = static_cast<int>(l.nh4);
+  const PipeItem* items = static_cast<const PipeItem*>(l.items.p);
   if (prec == BM_FP64)
-    (void)cudaLaunchKernelEx(&cfg, step_pipe<double>, static_cast<const PipeItem*>(l.items.p), l.n, l.sched.p,
-                             l.early.p, l.mark.p, ne4, nh4, prime);
+    (void)cudaLaunchKernelEx(&cfg, l.track ? step_pipe<double, true> : step_pipe<double, false>, items, l.n,
+                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime);
   else
-    (void)cudaLaunchKernelEx(&cfg, step_pipe<float>, static_cast<const PipeItem*>(l.items.p), l.n, l.sched.p,
-                             l.early.p, l.mark.p, ne4, nh4, prime);
+    (void)cudaLaunchKernelEx(&cfg, l.track ? step_pipe<float, true> : step_pipe<float, false>, items, l.n,
+                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime);
 }
 
 namespace {
@@ -750,6 +763,14 @@ bm_status bm_state_track(bm_state* s, double h_arrival) {
     track_init<float><<<nb, 256, 0, s->stream>>>(reinterpret_cast<const InstDesc<float>*>(s->desc.p), s->ctl, n);
   BM_CUDA(cudaGetLastError());
   BM_CUDA(cudaStreamSynchronize(s->stream));
+  // from now on the state's launches run the tracking kernel
+  if (!s->list.track) {
+    s->list.track = true;
+    bm_status st = list_occupancy(s->prec, &s->list);
+    if (st != BM_OK) return st;
+    s->grid = step_grid(s->list, s->ctas_per_sm);
+    drop_graphs(s);
+  }
   return BM_OK;
 }
 

@@ -123,6 +123,7 @@ struct StepList {
   uint32_t ne4 = 4, nh4 = 4;
   size_t smem = 0;
   int occupancy = 1;  // resident CTAs per SM at this shared-memory size
+  bool track = false;  // a member keeps a flood-tracking record (the tracking kernel)
 };
 }  // namespace bm
 
@@ -185,6 +186,7 @@ bm_status mesh_on_device(bm_mesh* m, int prec);
 bm_status build_step_list(const std::vector<bm_state*>& members, const std::vector<const void*>& descs,
                           StepList* out);
 // Grid of a step launch for a launch shape (ctas_per_sm = 0: all that fit).
+bm_status list_occupancy(int prec, StepList* l);
 int step_grid(const StepList& l, int ctas_per_sm);
 void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st);
 }  // namespace bm

@@ -317,8 +317,10 @@ constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M flood
 // n_items.  ne4max / nh4max: the largest record of the list (they fix the
 // shared-memory layout).  A single state is a list of one instance's tiles, so a run
 // executes the same machine code alone and in a batch and gives bitwise the same
-// result.
-template <typename T>
+// result.  kTrack: the instantiation that also updates the flood-tracking records of
+// the instances that have them (launched only when one does; the other carries no
+// tracking code at all).
+template <typename T, bool kTrack>
 __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const PipeItem* __restrict__ items,
                                                                          int n_items, int* __restrict__ sched,
                                                                          int* __restrict__ early, int* __restrict__ mark,
@@ -712,9 +714,12 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         if (!prime) {
           // flood tracking: the cell's record, loaded ahead of the update (a cell
           // copied through, dry and at rest, cannot change its record)
-          const bool trk = a.trk_t != nullptr;
+          bool trk = false;
           TrackRecord<T> rec{};
-          if (trk) rec = track_load(a, i);
+          if constexpr (kTrack) {
+            trk = a.trk_t != nullptr;
+            if (trk) rec = track_load(a, i);
+          }
           T s0 = zero, s1 = zero, s2 = zero;
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
@@ -763,7 +768,9 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           // negative depth: below -h_min, beyond the rounding of the FP32 bed offset in FP32-bulk
           const T negtol = kPair ? hmin + T(4) * static_cast<T>(FLT_EPSILON) * fabs(zi) : hmin;
           if (h < -negtol) atomicOr(&a.ctl->status, 2);
-          if (trk) track_update<T>(a, i, rec, h, ux, uy, gn2, hmin, new_time(cs, 1));
+          if constexpr (kTrack) {
+            if (trk) track_update<T>(a, i, rec, h, ux, uy, gn2, hmin, new_time(cs, 1));
+          }
         }
         T u, v, c;
         cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
