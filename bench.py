@@ -52,7 +52,7 @@ METRIC = "cell-updates/s"
 BYTES_PER_CELL = {"fp64": 2 * 24 + 3 * 8 + 4, "fp32": 2 * 16 + 3 * 4 + 4}
 BYTES_PER_EDGE = {"fp64": 4 + 3 * 8, "fp32": 4 + 3 * 4}
 HBM_FALLBACK_GBS = 6400.0
-KERNEL_NAME = {"fp64": "step_pipe<double>", "fp32": "step_pipe<float>"}
+KERNEL_NAME = {"fp64": "step_pipe<double, 0>", "fp32": "step_pipe<float, 0>"}  # without flood tracking
 
 
 def parse():
