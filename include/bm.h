@@ -280,6 +280,18 @@ bm_status bm_submit(bm_server* sv, const bm_mesh* mesh, const bm_params* p, cons
  * completion, forgets the ticket and returns BM_OK, or the run's failure status.
  */
 bm_status bm_poll(bm_server* sv, uint64_t ticket, double* H, double* qx, double* qy, double* latency_s);
+/*
+ * bm_submit with flood tracking (see bm_state_track): h_arrival >= 0 starts the record
+ * when the run is admitted (its footprint counts the record); h_arrival < 0 is
+ * bm_submit.  bm_poll_track copies the finished run's record (caller order, any
+ * pointer may be NULL) and leaves the ticket for bm_poll: call it first.  BM_EAGAIN
+ * while the run is not finished, BM_EINVAL for an unknown ticket or a run submitted
+ * without tracking, the run's error if it failed.
+ */
+bm_status bm_submit_tracked(bm_server* sv, const bm_mesh* mesh, const bm_params* p, const double* H,
+                            const double* qx, const double* qy, double t_end, double h_arrival, uint64_t* ticket);
+bm_status bm_poll_track(bm_server* sv, uint64_t ticket, double* t_arrival, double* h_max, double* u_max,
+                        double* q_max, double* tau_max);
 /* Block until the run has finished (or timeout_s elapsed: BM_ETIMEOUT); then bm_poll. */
 bm_status bm_server_wait(bm_server* sv, uint64_t ticket, double timeout_s);
 /* Queued, running and completed runs, cell-updates done, device bytes admitted. */

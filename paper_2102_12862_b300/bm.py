@@ -83,6 +83,8 @@ SIGNATURES = {
     "bm_server_destroy": (None, [_vp]),
     "bm_submit": (C.c_int, [_vp, _vp, _P(bm_params), _P(_d), _P(_d), _P(_d), _d, _P(C.c_uint64)]),
     "bm_poll": (C.c_int, [_vp, C.c_uint64, _P(_d), _P(_d), _P(_d), _P(_d)]),
+    "bm_submit_tracked": (C.c_int, [_vp, _vp, _P(bm_params), _P(_d), _P(_d), _P(_d), _d, _d, _P(C.c_uint64)]),
+    "bm_poll_track": (C.c_int, [_vp, C.c_uint64, _P(_d), _P(_d), _P(_d), _P(_d), _P(_d)]),
     "bm_server_wait": (C.c_int, [_vp, C.c_uint64, _d]),
     "bm_server_stats": (C.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_d), _P(_d)]),
 }
@@ -497,6 +499,25 @@ def bm_submit(server: int, mesh: int, params: bm_params, H, qx=None, qy=None, t_
     return tk.value
 
 
+def bm_submit_tracked(server: int, mesh: int, params: bm_params, H, qx=None, qy=None, t_end: float = 1.0,
+                      h_arrival: float = 0.01) -> int:
+    H, qx, qy = _f64(H), _f64(qx), _f64(qy)
+    tk = C.c_uint64()
+    _check(load_library().bm_submit_tracked(server, mesh, C.byref(params), _dp(H), _dp(qx), _dp(qy), float(t_end),
+                                            float(h_arrival), C.byref(tk)))
+    return tk.value
+
+
+def bm_poll_track(server: int, ticket: int, n_cells: int):
+    """The finished run's flood-tracking record (dict), None while BM_EAGAIN."""
+    out = {k: np.empty(n_cells) for k in TRACK_FIELDS}
+    st = load_library().bm_poll_track(server, int(ticket), *(_dp(out[k]) for k in TRACK_FIELDS))
+    if st == BM_EAGAIN:
+        return None
+    _check(st)
+    return out
+
+
 def bm_poll(server: int, ticket: int, n_cells: int):
     """(H, qx, qy, latency_s) when finished, None while BM_EAGAIN; raises on failure."""
     H, qx, qy = np.empty(n_cells), np.empty(n_cells), np.empty(n_cells)
@@ -528,12 +549,20 @@ class Server:
         self.precision = precision
         self._keep = {}
 
-    def submit(self, mesh: Mesh, H, qx=None, qy=None, t_end: float = 1.0, **params) -> int:
+    def submit(self, mesh: Mesh, H, qx=None, qy=None, t_end: float = 1.0, track=None, **params) -> int:
+        """track: the flood-tracking arrival threshold (None: no tracking)."""
         params.setdefault("precision", self.precision)
         p, keep = make_params(**params)
-        tk = bm_submit(self.handle, mesh.handle, p, H, qx, qy, t_end)
+        if track is None:
+            tk = bm_submit(self.handle, mesh.handle, p, H, qx, qy, t_end)
+        else:
+            tk = bm_submit_tracked(self.handle, mesh.handle, p, H, qx, qy, t_end, track)
         self._keep[tk] = (mesh, p, keep)
         return tk
+
+    def poll_track(self, ticket: int):
+        """The finished run's tracking record; call before poll() / wait()."""
+        return bm_poll_track(self.handle, ticket, self._keep[ticket][0].n_cells)
 
     def poll(self, ticket: int):
         mesh = self._keep[ticket][0]

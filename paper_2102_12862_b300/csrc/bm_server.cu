@@ -40,6 +40,8 @@ struct Request {
   std::vector<double> hydro_t, hydro_q;
   std::vector<double> H, qx, qy;  // input, then result (caller order)
   double t_end = 0.0;
+  double h_arrival = -1.0;        // flood tracking threshold (< 0: no tracking)
+  std::vector<double> track[5];   // the tracking record at the end (caller order)
   size_t footprint = 0;
   Clock::time_point submitted, finished;
   bm_state* state = nullptr;
@@ -92,6 +94,11 @@ void finish(bm_server* sv, const std::shared_ptr<Request>& r, bm_status st, cons
   if (r->state) {
     if (st == BM_OK) {
       bm_status d = bm_state_download(r->state, r->H.data(), r->qx.data(), r->qy.data(), nullptr);
+      if (d == BM_OK && r->h_arrival >= 0.0) {
+        for (auto& v : r->track) v.assign(r->H.size(), 0.0);
+        d = bm_state_download_track(r->state, r->track[0].data(), r->track[1].data(), r->track[2].data(),
+                                    r->track[3].data(), r->track[4].data());
+      }
       if (d != BM_OK) {
         st = d;
       }
@@ -146,6 +153,11 @@ void worker_loop(bm_server* sv) {
       p.hydro_q = r->hydro_q.data();
       bm_state* s = nullptr;
       bm_status st = bm_state_init(r->mesh, &p, r->H.data(), r->qx.data(), r->qy.data(), &s);
+      if (st == BM_OK && r->h_arrival >= 0.0) st = bm_state_track(s, r->h_arrival);
+      if (st != BM_OK && s) {
+        bm_state_destroy(s);
+        s = nullptr;
+      }
       if (st == BM_OK) {
         r->state = s;
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -292,7 +304,14 @@ void bm_server_destroy(bm_server* sv) {
 
 bm_status bm_submit(bm_server* sv, const bm_mesh* mesh, const bm_params* prm, const double* H, const double* qx,
                     const double* qy, double t_end, uint64_t* ticket) {
+  return bm_submit_tracked(sv, mesh, prm, H, qx, qy, t_end, -1.0, ticket);
+}
+
+bm_status bm_submit_tracked(bm_server* sv, const bm_mesh* mesh, const bm_params* prm, const double* H,
+                            const double* qx, const double* qy, double t_end, double h_arrival, uint64_t* ticket) {
   clear_error();
+  if (std::isnan(h_arrival) || std::isinf(h_arrival))
+    return fail(BM_EINVAL, "bm_submit_tracked: h_arrival must be finite (< 0: no tracking)");
   if (!sv || !mesh || !H || !ticket) return fail(BM_EINVAL, "bm_submit: NULL argument");
   bm_status st = check_params(prm);
   if (st != BM_OK) return st;
@@ -310,7 +329,10 @@ bm_status bm_submit(bm_server* sv, const bm_mesh* mesh, const bm_params* prm, co
   if (qx) std::copy(qx, qx + n, r->qx.begin());
   if (qy) std::copy(qy, qy + n, r->qy.begin());
   r->t_end = t_end;
+  r->h_arrival = h_arrival;
   r->footprint = state_footprint(mesh, prm->precision);
+  if (h_arrival >= 0.0)  // the record: arrival time (double) and four maxima per padded cell
+    r->footprint += static_cast<size_t>(mesh->h.n_tiles) * kTile * (8 + 4 * (prm->precision == BM_FP64 ? 8 : 4));
   r->submitted = Clock::now();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -344,6 +366,26 @@ bm_status bm_poll(bm_server* sv, uint64_t ticket, double* H, double* qx, double*
   if (H) std::copy(r->H.begin(), r->H.end(), H);
   if (qx) std::copy(r->qx.begin(), r->qx.begin() + n, qx);
   if (qy) std::copy(r->qy.begin(), r->qy.begin() + n, qy);
+  return BM_OK;
+}
+
+bm_status bm_poll_track(bm_server* sv, uint64_t ticket, double* t_arrival, double* h_max, double* u_max,
+                        double* q_max, double* tau_max) {
+  clear_error();
+  if (!sv) return fail(BM_EINVAL, "bm_poll_track: server is NULL");
+  std::shared_ptr<Request> r;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return fail(BM_EINVAL, "bm_poll_track: unknown or already collected ticket");
+    r = it->second;
+    if (!r->done) return fail(BM_EAGAIN, "bm_poll_track: not finished yet");
+  }
+  if (r->status != BM_OK) return fail(r->status, "bm_poll_track: run failed: " + r->error);
+  if (r->h_arrival < 0.0) return fail(BM_EINVAL, "bm_poll_track: the run was submitted without tracking");
+  double* outs[5] = {t_arrival, h_max, u_max, q_max, tau_max};
+  for (int k = 0; k < 5; ++k)
+    if (outs[k]) std::copy(r->track[k].begin(), r->track[k].end(), outs[k]);
   return BM_OK;
 }
 

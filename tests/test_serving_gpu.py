@@ -50,6 +50,35 @@ def test_results_same_alone_and_in_the_mix(precision):
     sv.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_tracked_runs_in_the_mix(precision):
+    """Flood tracking as a serving output: tracked and untracked runs share the batches;
+    each tracked run's record equals the same run alone, bitwise."""
+    scs = scenarios()[:4]
+    meshes = [bm.Mesh.from_scenario(s) for s in scs]
+    t_ends = [25.0, 10.0, 40.0, 15.0]
+    track = [0.05, None, 0.02, 0.1]
+    sv = bm.Server(precision=precision, steps_per_round=16)
+    tickets = [sv.submit(meshes[k], s.H, s.qx, s.qy, t_end=t_ends[k], track=track[k], **dict(s.params))
+               for k, s in enumerate(scs)]
+    for k, (s, tk) in enumerate(zip(scs, tickets)):
+        bm.bm_server_wait(sv.handle, tk, 300.0)
+        if track[k] is None:
+            with pytest.raises(bm.BMError, match="without tracking"):
+                sv.poll_track(tk)
+        else:
+            rec = sv.poll_track(tk)
+            st = bm.State.from_scenario(s, mesh=meshes[k], precision=precision)
+            st.track(track[k])
+            st.run_until(t_ends[k])
+            ref = st.download_track()
+            for f in ref:
+                assert np.array_equal(rec[f], ref[f], equal_nan=True), f"run {k}: {f}"
+            assert np.nanmax(rec["t_arrival"]) > 0  # the flood front moved
+        assert sv.poll(tk) is not None
+    sv.close()
+
+
 def test_admission_by_budget_and_slots():
     scs = scenarios()
     meshes = [bm.Mesh.from_scenario(s) for s in scs]
