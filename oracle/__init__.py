@@ -83,6 +83,8 @@ def _lib():
         lib.orc_run_tracked.argtypes = [C.c_void_p, P(d), P(d), P(d), P(d), d, i64, P(d), d, d, P(d), P(d), P(d),
                                         P(d), P(d)]
         lib.orc_run_tracked.restype = i64
+        lib.orc_run_scalars.argtypes = [C.c_void_p, P(d), P(d), P(d), P(d), d, i64, P(d), C.c_int, P(d), P(d)]
+        lib.orc_run_scalars.restype = i64
         _libs["serial"] = lib
     return _libs["serial"]
 
@@ -132,6 +134,7 @@ class Oracle:
         self.bvol = C.c_double(0.0)
         self.steps = 0
         self.tracking = None  # flood tracking record (see track())
+        self.hc = None  # passive species q_c = h phi_c, K x n (see set_scalars())
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -150,8 +153,29 @@ class Oracle:
                          float(rho), 1, _dp(tr["t_arrival"]), _dp(tr["h_max"]), _dp(tr["u_max"]),
                          _dp(tr["q_max"]), _dp(tr["tau_max"]))
 
+    def set_scalars(self, hc, c_in=None):
+        """Advect K passive species with the water: hc (K x n) is q_c = h phi_c; c_in
+        the inflow concentrations (K, default 0)."""
+        self.hc = np.array(hc, dtype=np.float64, copy=True).reshape(-1, self.n_cells)
+        k = self.hc.shape[0]
+        self.c_in = np.zeros(k) if c_in is None else np.array(c_in, dtype=np.float64).reshape(k)
+
+    def concentration(self):
+        h = self.depth()
+        return np.where(h > 0, self.hc / np.where(h > 0, h, 1.0), 0.0)
+
     def step(self, n: int = 1, t_end: float = math.inf) -> int:
         lib = _lib()
+        if self.hc is not None:
+            if self.tracking is not None:
+                raise OracleError("scalars and flood tracking together are not supported by the oracle")
+            k = lib.orc_run_scalars(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), C.byref(self.t),
+                                    float(t_end), int(n), C.byref(self.bvol), self.hc.shape[0], _dp(self.hc),
+                                    _dp(self.c_in))
+            if k < 0:
+                raise OracleError("orc_run_scalars: out of memory")
+            self.steps += k
+            return k
         if self.tracking is not None:
             tr = self.tracking
             k = lib.orc_run_tracked(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), C.byref(self.t),

@@ -516,6 +516,79 @@ int64_t orc_run_tracked(orc_mesh* m, double* H, double* qx, double* qy, double* 
   return s;
 }
 
+/*
+ * Passive scalar advection (Section "Scalar advection-diffusion", Eq. 8 without the
+ * diffusion and source terms): K species with unknowns q_c = h phi_c (hc: K x n,
+ * species-major).  The advective flux of a species is HLLC's contact-wave flux, the
+ * formula the tangential momentum uses with phi_c in place of the tangential velocity:
+ * F_c = F_h phi_c of the upwind side of the contact (S* >= 0: left) -- the scheme the
+ * "Scalar advection-diffusion" numerics subsection names for the advective part.
+ * phi_c = q_c / h where h = H - z > 0, else 0.  Walls carry nothing; a transmissive
+ * edge carries F_h phi_c of the inside cell; an inflow edge brings q_e l c_in[c].
+ * A cell that ends the step dry (h <= 0) keeps no scalar.  One step of the water
+ * (orc_step) and the species together; returns the number of steps taken.
+ */
+int64_t orc_run_scalars(orc_mesh* m, double* H, double* qx, double* qy, double* t, double t_end, int64_t n_steps,
+                        double* bvol, int K, double* hc, const double* c_in) {
+  const double g = m->p.g;
+  const int64_t n = m->n_cells, ne = m->n_edges;
+  double* phi = (double*)malloc(sizeof(double) * (size_t)(K * n + K * ne + 1));
+  if (!phi) return -1;
+  double* fl = phi + K * n; /* per edge and species: l * F_c (outward from the left cell) */
+  int64_t s = 0;
+  for (; s < n_steps; ++s) {
+    if (!(*t < t_end)) break;
+    for (int64_t i = 0; i < n; ++i) {
+      double h = H[i] - m->z[i];
+      for (int c = 0; c < K; ++c) phi[c * n + i] = h > 0 ? hc[c * n + i] / h : 0.0;
+    }
+    inflow_discharge(m, H, *t); /* q_e of this step (orc_step computes the same) */
+    for (int64_t e = 0; e < ne; ++e) {
+      int64_t L = m->eL[e], R = m->eR[e];
+      double nx = m->nx[e], ny = m->ny[e], l = m->len[e];
+      double uL, vL; cell_velocity(m, H, qx, qy, L, &uL, &vL);
+      double unL = uL * nx + vL * ny;
+      for (int c = 0; c < K; ++c) {
+        double F[3], f;
+        double pL = phi[c * n + L];
+        if (R >= 0) {
+          double zs = fmax(m->z[L], m->z[R]);
+          double hLs = fmax(0.0, H[L] - zs), hRs = fmax(0.0, H[R] - zs);
+          double uR, vR; cell_velocity(m, H, qx, qy, R, &uR, &vR);
+          double unR = uR * nx + vR * ny;
+          orc_hllc(hLs, unL, pL, hRs, unR, phi[c * n + R], g, F);
+          f = F[2];
+        } else if (R == -1) {
+          f = 0; /* wall */
+        } else if (R == -2) {
+          double hs = fmax(0.0, H[L] - m->z[L]);
+          orc_hllc(hs, unL, pL, hs, unL, pL, g, F);
+          f = F[2];
+        } else {
+          double q = m->qin[e];
+          f = q > 0 ? -q * c_in[c] : 0.0;
+        }
+        fl[c * ne + e] = l * f;
+      }
+    }
+    double dt = orc_step(m, H, qx, qy, t, t_end, bvol);
+    for (int64_t i = 0; i < n; ++i) {
+      double r = dt / m->area[i];
+      for (int c = 0; c < K; ++c) {
+        double sum = 0;
+        for (int k = 0; k < 3; ++k) {
+          int64_t e = m->cedge[3 * i + k];
+          sum += (m->eL[e] == i) ? fl[c * ne + e] : -fl[c * ne + e];
+        }
+        double v = hc[c * n + i] - r * sum;
+        hc[c * n + i] = (H[i] - m->z[i] > 0) ? v : 0.0;
+      }
+    }
+  }
+  free(phi);
+  return s;
+}
+
 /* V = sum_i |Omega_i| (H_i - z_i), fixed order */
 double orc_volume(const orc_mesh* m, const double* H) {
   double v = 0;

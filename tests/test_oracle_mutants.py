@@ -45,13 +45,23 @@ TRACK_MUTANTS = [
     ("track_max_of_surface", "if (h > hmax[i]) hmax[i] = h;", "if (H[i] > hmax[i]) hmax[i] = H[i];"),
     ("track_discharge_as_velocity", "u = q / h;", "u = q;"),
 ]
+# passive scalars, caught by tests/test_oracle_scalars.py
+SCALAR_MUTANTS = [
+    ("scalar_contact_side", "orc_hllc(hLs, unL, pL, hRs, unR, phi[c * n + R], g, F);",
+     "orc_hllc(hLs, unL, phi[c * n + R], hRs, unR, pL, g, F);"),
+    ("scalar_update_sign", "double v = hc[c * n + i] - r * sum;", "double v = hc[c * n + i] + r * sum;"),
+    ("scalar_inflow_sign", "f = q > 0 ? -q * c_in[c] : 0.0;", "f = q > 0 ? q * c_in[c] : 0.0;"),
+    ("scalar_concentration_of_surface", "double h = H[i] - m->z[i];\n      for (int c = 0; c < K; ++c) phi",
+     "double h = H[i];\n      for (int c = 0; c < K; ++c) phi"),
+]
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name,orig,mut,pins",
                          [m + ("test_oracle_pins.py",) for m in MUTANTS]
-                         + [m + ("test_oracle_tracking.py",) for m in TRACK_MUTANTS],
-                         ids=[m[0] for m in MUTANTS + TRACK_MUTANTS])
+                         + [m + ("test_oracle_tracking.py",) for m in TRACK_MUTANTS]
+                         + [m + ("test_oracle_scalars.py",) for m in SCALAR_MUTANTS],
+                         ids=[m[0] for m in MUTANTS + TRACK_MUTANTS + SCALAR_MUTANTS])
 def test_pins_catch_mutant(name, orig, mut, pins, tmp_path):
     src = open(SRC).read()
     assert src.count(orig) == 1, f"mutation site for {name} not unique"
