@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--lake-steps", type=int, default=500,
                     help="steps of the mostly wet lake-at-rest line (0: skip it)")
     ap.add_argument("--track-steps", type=int, default=500,
-                    help="steps of the flood-tracking cost line (0: skip it)")
+                    help="steps of the flood-tracking and passive-species cost line (0: skip it)")
     ap.add_argument("--stress-steps", type=int, default=100000, help="stress: lake-at-rest steps")
     ap.add_argument("--workload", choices=["floodplain", "ensemble", "serve", "stress"], default="floodplain",
                     help="floodplain: the default line; ensemble: batched uneven meshes; serve: request loop")
@@ -358,22 +358,29 @@ def measure_lake(args, torch, bm, W):
 
 
 def measure_tracking(args, torch, bm, W):
-    """Flood tracking's cost on the floodplain: the same args.track_steps steps from
-    t = 0 with and without the per-cell record (arrival time of 0.05 m, maxima of
-    depth, velocity, discharge and bed shear stress) updated in the step kernel."""
+    """The optional outputs' cost on the floodplain: the same args.track_steps steps
+    from t = 0 plain, with flood tracking (arrival time of 0.05 m, maxima of depth,
+    velocity, discharge and bed shear stress, updated in the step kernel) and with two
+    passive species (one entering with the inflow at c = 1, one filling the initially
+    wet river at c = 0.5; the step kernel exports its edge mass fluxes, the species
+    kernel advects them after each step)."""
     s = W.floodplain()
     mesh = bm.Mesh.from_scenario(s)
-    out = {"workload": "floodplain 2,000,000 triangles, steps from t = 0, arrival threshold 0.05 m",
+    h0 = np.maximum(s.H - s.z, 0.0)
+    out = {"workload": "floodplain 2,000,000 triangles, steps from t = 0, arrival threshold 0.05 m; "
+                       "2 passive species (inflow c = 1; river c = 0.5)",
            "steps": args.track_steps}
     for prec in [p for p in args.precisions.split(",") if p]:
         res = {}
-        for tracked in (False, True):
+        for mode in ("plain", "tracked", "species"):
             st = bm.State.from_scenario(s, mesh=mesh, precision=prec)
             stream = torch.cuda.Stream()
             torch.cuda.set_stream(stream)
             st.set_stream(stream.cuda_stream)
-            if tracked:
+            if mode == "tracked":
                 st.track(0.05)
+            elif mode == "species":
+                st.set_scalars(np.stack([np.zeros_like(h0), 0.5 * h0]), c_in=[1.0, 0.0])
             st.step(args.warmup)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -383,14 +390,19 @@ def measure_tracking(args, torch, bm, W):
             e1.record(stream)
             torch.cuda.synchronize()
             st.sync()
-            res[tracked] = e0.elapsed_time(e1) / args.track_steps
-            if tracked:
+            res[mode] = e0.elapsed_time(e1) / args.track_steps
+            if mode == "tracked":
                 rec = st.download_track()
                 res["arrived"] = int(np.sum(~np.isnan(rec["t_arrival"])))
+            elif mode == "species":
+                hc = st.download_scalars()
+                res["inflow_species_volume"] = float(hc[0] @ tri_areas(s))
             st.close()
         out["fp32_bulk" if prec == "fp32" else prec] = {
-            "ms_per_step": res[False], "ms_per_step_tracked": res[True],
-            "overhead": res[True] / res[False] - 1.0, "cells_arrived": res["arrived"]}
+            "ms_per_step": res["plain"], "ms_per_step_tracked": res["tracked"],
+            "overhead": res["tracked"] / res["plain"] - 1.0, "cells_arrived": res["arrived"],
+            "ms_per_step_2_species": res["species"], "overhead_2_species": res["species"] / res["plain"] - 1.0,
+            "inflow_species_volume_m3": res["inflow_species_volume"]}
     return out
 
 

@@ -178,6 +178,30 @@ bm_status bm_state_download_track(bm_state* s, double* t_arrival, double* h_max,
                                   double* tau_max);
 
 /*
+ * Passive species (Section "Scalar advection-diffusion", Eq. 8 with the diffusion and
+ * source terms off): up to 5 concentrations phi_c carried by the water, advected with
+ * every step from the call on.  The unknowns are q_c = h phi_c per cell; the flux of
+ * a species through an edge is the edge's HLLC mass flux times phi_c of the upwind
+ * side of the contact wave (the step kernel's own decision), phi_c = q_c / h where
+ * h > 0, else 0; walls carry nothing, a transmissive edge carries the inside value,
+ * and the water entering through inflow edges carries c_in[c].  A cell that ends a
+ * step dry keeps no species (q_c = 0).
+ * bm_state_set_scalars sets the species: hc holds n_species * n_cells values of q_c
+ * (species-major, caller cell order, finite; BM_EINVAL otherwise), c_in n_species
+ * inflow concentrations (NULL: 0).  n_species in [0, 5]; 0 removes them.  It
+ * allocates 2 * n_species values per cell plus, per tile edge, one exported flux and
+ * one byte, and blocks.  From then on every step launches a second kernel after the
+ * step kernel (one CTA per tile).  A state with species steps alone:
+ * bm_batch_create refuses it (BM_EINVAL); do not set species on a state that is a
+ * member of a live batch (the batch keeps a copy of its descriptor).  Uploading a
+ * state keeps the species' values.  bm_state_download_scalars copies q_c back
+ * (n_species * n_cells, caller order); BM_EINVAL when the state carries none.
+ * FP32-bulk states keep q_c in single precision.
+ */
+bm_status bm_state_set_scalars(bm_state* s, int32_t n_species, const double* hc, const double* c_in);
+bm_status bm_state_download_scalars(bm_state* s, double* hc);
+
+/*
  * Scalars of the state: time, the dt the next step will take, steps taken,
  * water volume V = sum |Omega_i| (H_i - z_i) (FP64, fixed summation order), and
  * the net volume that entered through the boundary since init/upload.

@@ -552,7 +552,7 @@ int64_t orc_run_scalars(orc_mesh* m, double* H, double* qx, double* qy, double* 
         double F[3], f;
         double pL = phi[c * n + L];
         if (R >= 0) {
-          double zs = fmax(m->z[L], m->z[R]);
+          double zs = fmax(m->z[R], m->z[L]); /* the higher bed of the two */
           double hLs = fmax(0.0, H[L] - zs), hRs = fmax(0.0, H[R] - zs);
           double uR, vR; cell_velocity(m, H, qx, qy, R, &uR, &vR);
           double unR = uR * nx + vR * ny;

@@ -78,6 +78,8 @@ SIGNATURES = {
     "bm_math_eval": (C.c_int, [C.c_int32, _vp, _vp, _i64]),
     "bm_state_track": (C.c_int, [_vp, C.c_double]),
     "bm_state_download_track": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "bm_state_set_scalars": (C.c_int, [_vp, C.c_int32, _vp, _vp]),
+    "bm_state_download_scalars": (C.c_int, [_vp, _vp]),
     "bm_server_opts_default": (None, [_P(bm_server_opts)]),
     "bm_server_create": (C.c_int, [_P(bm_server_opts), _P(_vp)]),
     "bm_server_destroy": (None, [_vp]),
@@ -239,6 +241,25 @@ def bm_state_download_track(state: int, n_cells: int) -> dict:
     return out
 
 
+def bm_state_set_scalars(state: int, hc, c_in=None):
+    """Passive species q_c = h phi_c: hc of shape (K, n_cells), K <= 5 (0 rows: none);
+    c_in: K inflow concentrations (None: 0)."""
+    hc = np.ascontiguousarray(np.atleast_2d(np.asarray(hc, dtype=np.float64)))
+    k = hc.shape[0] if hc.size else 0
+    ci = None if c_in is None else np.ascontiguousarray(np.asarray(c_in, dtype=np.float64).reshape(-1))
+    if ci is not None and ci.size != k:
+        raise ValueError("c_in needs one value per species")
+    _check(load_library().bm_state_set_scalars(state, k, _dp(hc) if k else None, _dp(ci) if ci is not None else None))
+    return hc, ci
+
+
+def bm_state_download_scalars(state: int, n_species: int, n_cells: int) -> np.ndarray:
+    """q_c of the state's species, shape (K, n_cells), caller cell order."""
+    out = np.empty((n_species, n_cells))
+    _check(load_library().bm_state_download_scalars(state, _dp(out)))
+    return out
+
+
 def bm_state_stats(state: int, volume: bool = True) -> dict:
     t, dt, vol, bv = _d(), _d(), _d(), _d()
     steps = _i64()
@@ -336,6 +357,7 @@ def bm_batch_run_until(batch: int, t_end):
 class Mesh:
     def __init__(self, xy, tri, z_bed, manning_n, edge_tag):
         self.handle = bm_mesh_create(xy, tri, z_bed, manning_n, edge_tag)
+        self.z_bed = np.array(z_bed, dtype=np.float64)  # caller order (species concentrations)
         self.info = bm_mesh_info(self.handle)
         self.n_cells = self.info["n_cells"]
 
@@ -366,6 +388,7 @@ class State:
         self._p, self._keep = make_params(**params)
         self.handle = bm_state_init(mesh.handle, self._p, H, qx, qy)
         self.n_cells = mesh.n_cells
+        self.n_species = 0
 
     @classmethod
     def from_scenario(cls, s, mesh: Mesh | None = None, **overrides) -> "State":
@@ -397,6 +420,22 @@ class State:
 
     def download_track(self) -> dict:
         return bm_state_download_track(self.handle, self.n_cells)
+
+    def set_scalars(self, hc, c_in=None):
+        """Carry passive species q_c = h phi_c (shape (K, n_cells), K <= 5), advected
+        with every step from now on; c_in: their inflow concentrations."""
+        hc, _ = bm_state_set_scalars(self.handle, hc, c_in)
+        self.n_species = hc.shape[0] if hc.size else 0
+
+    def download_scalars(self) -> np.ndarray:
+        return bm_state_download_scalars(self.handle, self.n_species, self.n_cells)
+
+    def concentration(self) -> np.ndarray:
+        """phi_c = q_c / h where h > 0, else 0 (shape (K, n_cells))."""
+        hc = self.download_scalars()
+        H, _, _, _ = self.download()
+        h = H - self.mesh.z_bed
+        return np.where(h > 0, hc / np.where(h > 0, h, 1.0), 0.0)
 
     def stats(self, volume: bool = True) -> dict:
         return bm_state_stats(self.handle, volume)

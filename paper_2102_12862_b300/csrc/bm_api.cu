@@ -18,6 +18,7 @@
 #include "bm_internal.h"
 #include "bm_kernels.cuh"
 #include "bm_step.cuh"
+#include "bm_species.cuh"
 #include "bm_state.h"
 
 namespace bm {
@@ -207,9 +208,14 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
   out->smem = prec == BM_FP64 ? StepLayout<double>(ne4, nh4).total : StepLayout<float>(ne4, nh4).total;
   const int lim = prec == BM_FP64 ? step_smem_limit<double>() : step_smem_limit<float>();
   if (out->smem > static_cast<size_t>(lim)) return fail(BM_EINVAL, "tile layout exceeds the device's shared memory");
-  out->track = false;
-  for (bm_state* m : members) out->track |= (prec == BM_FP64 ? m->b64.trk_t.p : m->b32.trk_t.p) != nullptr;
+  out->extra = false;
+  for (bm_state* m : members) out->extra |= state_has_extras(m);
   return list_occupancy(prec, out);
+}
+
+bool state_has_extras(const bm_state* s) {
+  const bool trk = s->prec == BM_FP64 ? s->b64.trk_t.p != nullptr : s->b32.trk_t.p != nullptr;
+  return trk || s->n_species > 0;
 }
 
 // Resident CTAs per SM of the list's kernel (with or without tracking).
@@ -218,10 +224,10 @@ bm_status list_occupancy(int prec, StepList* l) {
   cudaError_t e;
   if (prec == BM_FP64)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, l->track ? step_pipe<double, true> : step_pipe<double, false>, kStepThreads, l->smem);
+        &occ, l->extra ? step_pipe<double, true> : step_pipe<double, false>, kStepThreads, l->smem);
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, l->track ? step_pipe<float, true> : step_pipe<float, false>, kStepThreads, l->smem);
+        &occ, l->extra ? step_pipe<float, true> : step_pipe<float, false>, kStepThreads, l->smem);
   if (e != cudaSuccess) return dev_fail(e, "occupancy query");
   l->occupancy = std::max(1, occ);
   return BM_OK;
@@ -255,10 +261,10 @@ void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t 
   const int ne4 = static_cast<int>(l.ne4), nh4 = static_cast<int>(l.nh4);
   const PipeItem* items = static_cast<const PipeItem*>(l.items.p);
   if (prec == BM_FP64)
-    (void)cudaLaunchKernelEx(&cfg, l.track ? step_pipe<double, true> : step_pipe<double, false>, items, l.n,
+    (void)cudaLaunchKernelEx(&cfg, l.extra ? step_pipe<double, true> : step_pipe<double, false>, items, l.n,
                              l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime);
   else
-    (void)cudaLaunchKernelEx(&cfg, l.track ? step_pipe<float, true> : step_pipe<float, false>, items, l.n,
+    (void)cudaLaunchKernelEx(&cfg, l.extra ? step_pipe<float, true> : step_pipe<float, false>, items, l.n,
                              l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime);
 }
 
@@ -270,8 +276,54 @@ bm_status read_status(bm_state* s) {
   return status_of(*s->hctl);
 }
 
+// The species kernel after a step: one CTA per tile of the state's work list.
+template <typename T>
+void launch_species(bm_state* s, cudaStream_t st) {
+  Buffers<T>& b = s->buf<T>();
+  const TileRecords& R = s->mesh->rec[sizeof(T) == 8 ? 0 : 1];
+  const size_t np = static_cast<size_t>(s->mesh->h.n_tiles) * kTile;
+  SpeciesArgs<T> a{};
+  a.items = static_cast<const PipeItem*>(s->list.items.p);
+  for (int c = 0; c < s->n_species; ++c) {
+    a.hc[c][0] = b.hc[0].p + c * np;
+    a.hc[c][1] = b.hc[1].p + c * np;
+    a.c_in[c] = static_cast<T>(s->c_in[c]);
+  }
+  for (int k = 0; k < 2; ++k) {
+    a.H[k] = b.H[k].p;
+    a.Hlo[k] = b.Hlo[k].p;
+  }
+  a.z = b.z.p;
+  a.ctl = s->ctl;
+  a.ex_flux = b.ex_flux.p;
+  a.ex_right = b.ex_right.p;
+  a.ex_valid = b.ex_valid.p;
+  a.ex_dt = b.ex_dt.p;
+  a.zmask = b.zmask.p;
+  a.ex_stride = static_cast<int>(R.ne4_max);
+  a.n_species = s->n_species;
+  a.n_cells = static_cast<int>(s->mesh->h.n_cells);
+  const int nloc = kTile + static_cast<int>(R.nh4_max);
+  const size_t smem = (2 * static_cast<size_t>(nloc) + R.ne4_max) * sizeof(T);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(s->list.n));
+  cfg.blockDim = dim3(kTile);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, species_step<T>, a, nloc);
+}
+
 void launch_state(bm_state* s, cudaStream_t st, int prime) {
   launch_work(s->prec, s->list, s->grid, prime, st);
+  if (!prime && s->n_species > 0) {
+    if (s->prec == BM_FP64) launch_species<double>(s, st);
+    else launch_species<float>(s, st);
+  }
 }
 
 bm_status get_graph(bm_state* s, int k, cudaGraphExec_t* out) {
@@ -341,6 +393,13 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
     d.trk_q = b.trk[2].p;
     d.trk_tau = b.trk[3].p;
     d.trk_harr = static_cast<T>(s->trk_harr);
+  }
+  if (s->n_species > 0) {
+    d.ex_flux = b.ex_flux.p;
+    d.ex_right = b.ex_right.p;
+    d.ex_valid = b.ex_valid.p;
+    d.ex_dt = b.ex_dt.p;
+    d.ex_stride = static_cast<int>(m->rec[sizeof(T) == 8 ? 0 : 1].ne4_max);
   }
   d.in_pw = b.in_pw.p;
   d.in_hs = b.in_hs.p;
@@ -710,7 +769,19 @@ bm_status bm_state_upload(bm_state* s, const double* H, const double* qx, const 
   clear_error();
   if (!s) return fail(BM_EINVAL, "bm_state_upload: state is NULL");
   BM_CUDA(cudaStreamSynchronize(s->stream));
-  return load_state(s, H, qx, qy, t);
+  BM_CUDA(cudaMemcpy(s->hctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const int par = s->hctl->parity;
+  bm_status st = load_state(s, H, qx, qy, t);
+  if (st != BM_OK || s->n_species == 0 || par == 0) return st;
+  // the state restarts in buffer 0: the species keep their values
+  if (s->prec == BM_FP64) {
+    BM_CUDA(cudaMemcpy(s->b64.hc[0].p, s->b64.hc[1].p, s->b64.hc[1].bytes(), cudaMemcpyDeviceToDevice));
+    BM_CUDA(cudaMemset(s->b64.zmask.p, 0, s->b64.zmask.bytes()));
+  } else {
+    BM_CUDA(cudaMemcpy(s->b32.hc[0].p, s->b32.hc[1].p, s->b32.hc[1].bytes(), cudaMemcpyDeviceToDevice));
+    BM_CUDA(cudaMemset(s->b32.zmask.p, 0, s->b32.zmask.bytes()));
+  }
+  return BM_OK;
 }
 
 bm_status bm_state_download(bm_state* s, double* H, double* qx, double* qy, double* t) {
@@ -764,8 +835,8 @@ bm_status bm_state_track(bm_state* s, double h_arrival) {
   BM_CUDA(cudaGetLastError());
   BM_CUDA(cudaStreamSynchronize(s->stream));
   // from now on the state's launches run the tracking kernel
-  if (!s->list.track) {
-    s->list.track = true;
+  if (!s->list.extra) {
+    s->list.extra = true;
     bm_status st = list_occupancy(s->prec, &s->list);
     if (st != BM_OK) return st;
     s->grid = step_grid(s->list, s->ctas_per_sm);
@@ -799,6 +870,88 @@ bm_status bm_state_download_track(bm_state* s, double* t_arrival, double* h_max,
     }
     BM_CUDA(cudaGetLastError());
     BM_CUDA(cudaMemcpyAsync(outs[k], stage, bytes, cudaMemcpyDeviceToHost, s->stream));
+  }
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  return BM_OK;
+}
+
+bm_status bm_state_set_scalars(bm_state* s, int32_t n_species, const double* hc, const double* c_in) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_set_scalars: state is NULL");
+  if (n_species < 0 || n_species > kMaxSpecies) return fail(BM_EINVAL, "bm_state_set_scalars: n_species in [0, 5]");
+  const HostMesh& h = s->mesh->h;
+  const int n = static_cast<int>(h.n_cells);
+  if (n_species > 0 && !hc) return fail(BM_EINVAL, "bm_state_set_scalars: hc is NULL");
+  for (int64_t i = 0; i < static_cast<int64_t>(n_species) * n; ++i)
+    if (!std::isfinite(hc[i])) return fail(BM_EINVAL, "bm_state_set_scalars: hc has a non-finite value");
+  for (int c = 0; c < n_species && c_in; ++c)
+    if (!std::isfinite(c_in[c])) return fail(BM_EINVAL, "bm_state_set_scalars: c_in has a non-finite value");
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  BM_CUDA(cudaMemcpyAsync(s->hctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  const int par = s->hctl->parity;
+  const size_t np = static_cast<size_t>(h.n_tiles) * kTile;
+  const TileRecords& R = s->mesh->rec[s->prec == BM_FP64 ? 0 : 1];
+  const size_t stride = R.ne4_max;
+  if (n_species == 0) {
+    s->b64.free_species();
+    s->b32.free_species();
+  } else {
+    cudaError_t e = s->prec == BM_FP64 ? s->b64.alloc_species(np, n_species, h.n_tiles, stride)
+                                       : s->b32.alloc_species(np, n_species, h.n_tiles, stride);
+    if (e != cudaSuccess) return dev_fail(e, "bm_state_set_scalars: species arrays");
+    const int nb = (n + 255) / 256;
+    const size_t bytes = static_cast<size_t>(n) * sizeof(double);
+    for (int c = 0; c < n_species; ++c) {
+      double* stage = s->stage[c % 3].p;  // reused in stream order after its gather
+      BM_CUDA(cudaMemcpyAsync(stage, hc + static_cast<size_t>(c) * n, bytes, cudaMemcpyHostToDevice, s->stream));
+      if (s->prec == BM_FP64)
+        gather_from_user<double><<<nb, 256, 0, s->stream>>>(stage, s->mesh->perm.p, n, s->b64.hc[par].p + c * np);
+      else
+        gather_from_user<float><<<nb, 256, 0, s->stream>>>(stage, s->mesh->perm.p, n, s->b32.hc[par].p + c * np);
+      BM_CUDA(cudaGetLastError());
+    }
+  }
+  s->n_species = n_species;
+  for (int c = 0; c < kMaxSpecies; ++c) s->c_in[c] = (c < n_species && c_in) ? c_in[c] : 0.0;
+  // the step kernels read the descriptor in place: rewrite it (same size, same address)
+  state_desc_bytes(s, &s->hdesc);
+  BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  // the launch sequence changes (kernel instantiation, species kernel after each step)
+  const bool extra = state_has_extras(s);
+  if (extra != s->list.extra) {
+    s->list.extra = extra;
+    bm_status st = list_occupancy(s->prec, &s->list);
+    if (st != BM_OK) return st;
+    s->grid = step_grid(s->list, s->ctas_per_sm);
+  }
+  drop_graphs(s);
+  return BM_OK;
+}
+
+bm_status bm_state_download_scalars(bm_state* s, double* hc) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_download_scalars: state is NULL");
+  if (s->n_species == 0) return fail(BM_EINVAL, "bm_state_download_scalars: the state carries no species");
+  if (!hc) return fail(BM_EINVAL, "bm_state_download_scalars: hc is NULL");
+  BM_CUDA(cudaMemcpyAsync(s->hctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  const int par = s->hctl->parity;
+  const int n = static_cast<int>(s->mesh->h.n_cells);
+  const int nb = (n + 255) / 256;
+  const size_t np = static_cast<size_t>(s->mesh->h.n_tiles) * kTile;
+  const size_t bytes = static_cast<size_t>(n) * sizeof(double);
+  for (int c = 0; c < s->n_species; ++c) {
+    double* stage = s->stage[c % 3].p;
+    if (s->prec == BM_FP64)
+      scatter_to_user<double><<<nb, 256, 0, s->stream>>>(s->b64.hc[par].p + c * np, nullptr, s->mesh->perm.p, n,
+                                                          stage, 0.0);
+    else
+      scatter_to_user<float><<<nb, 256, 0, s->stream>>>(s->b32.hc[par].p + c * np, nullptr, s->mesh->perm.p, n,
+                                                         stage, 0.0);
+    BM_CUDA(cudaGetLastError());
+    BM_CUDA(cudaMemcpyAsync(hc + static_cast<size_t>(c) * n, stage, bytes, cudaMemcpyDeviceToHost, s->stream));
   }
   BM_CUDA(cudaStreamSynchronize(s->stream));
   return BM_OK;
@@ -953,6 +1106,8 @@ cudaError_t snapshot_buffers(Buffers<T>& b, Snapshot* sn, cudaStream_t st) {
   if (e == cudaSuccess) e = sn->take(b.in_hs.p, b.in_hs.bytes(), st);
   if (e == cudaSuccess) e = sn->take(b.trk_t.p, b.trk_t.bytes(), st);
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = sn->take(b.trk[k].p, b.trk[k].bytes(), st);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = sn->take(b.hc[k].p, b.hc[k].bytes(), st);
+  if (e == cudaSuccess) e = sn->take(b.zmask.p, b.zmask.bytes(), st);
   return e;
 }
 

@@ -15,6 +15,8 @@ namespace bm {
 // its cells, so one CTA evaluates each of those edges once (edges shared with
 // another tile are evaluated by both; about 12 % of them on large meshes).
 constexpr int kTile = 256;
+// Passive species a state can carry (Section "Scalar advection-diffusion").
+constexpr int kMaxSpecies = 5;
 constexpr int kMaxTileEdges = 3 * kTile;
 
 // Boundary codes stored in place of the right cell of an edge; inflow edge j of

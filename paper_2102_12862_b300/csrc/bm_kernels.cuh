@@ -48,6 +48,14 @@ struct alignas(16) InstDesc {
   int n_in_tiles;          // tiles with inflow edges
   int n_cells;
   int n_tiles;
+  // passive species (null when none): the step exports, per tile edge, l F_h and
+  // whether the contact's right side is upwind; per tile whether it had fluxes (0:
+  // quiet); the step's dt.  A second kernel advects the species with them.
+  T* ex_flux;
+  unsigned char* ex_right;
+  unsigned char* ex_valid;
+  double* ex_dt;
+  int ex_stride;  // edges per tile in ex_flux / ex_right (the mesh's largest, rounded to 4)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -203,10 +211,11 @@ __device__ __forceinline__ T pow53(T h) {
 // celerities cL = sqrt(g hL), cR = sqrt(g hR); un/ut are normal/tangential
 // velocities.  Wave speeds: two-rarefaction star estimates when both sides are
 // wet, exact dry-front speeds when one side is dry.  pL, pR = g/2 h^2 are
-// returned so the caller subtracts exactly the same values.
+// returned so the caller subtracts exactly the same values; right: the flux carries
+// the right side's tangential velocity (and passive species), else the left's.
 template <typename T>
 __device__ __forceinline__ void hllc(T hL, T unL, T utL, T cL, T hR, T unR, T utR, T cR, T hg, T& F0, T& F1,
-                                     T& F2, T& pL, T& pR) {
+                                     T& F2, T& pL, T& pR, bool& right) {
   const T half = T(0.5), quarter = T(0.25), two = T(2), zero = T(0);
   const T us = half * (unL + unR) + cL - cR;
   const T cs = half * (cL + cR) + quarter * (unL - unR);
@@ -225,6 +234,8 @@ __device__ __forceinline__ void hllc(T hL, T unL, T utL, T cL, T hR, T unR, T ut
   // sign of the contact speed S* = num / den with den < 0 whenever a side is wet
   const T num = SL * hR * (unR - SR) - SR * hL * (unL - SL);
   const T H2 = H0 * (num <= zero ? utL : utR);
+  // the side whose tangential velocity (and passive species) the flux carries
+  right = SL >= zero ? false : (SR <= zero ? true : !(num <= zero));
   if (SL >= zero) {
     F0 = FL0; F1 = FL1; F2 = FL2;
   } else if (SR <= zero) {

@@ -64,6 +64,32 @@ struct Buffers {
       if (!trk[k].p) e = trk[k].alloc(np);
     return e;
   }
+  // passive species (bm_state_set_scalars): q_c = h phi_c of K species per state
+  // buffer (species c at c * np), and the step kernel's exports per tile edge
+  DBuf<T> hc[2];
+  DBuf<T> ex_flux;
+  DBuf<unsigned char> ex_right, ex_valid, zmask;  // zmask: per tile, species all zero per buffer
+  DBuf<double> ex_dt;
+  cudaError_t alloc_species(size_t np, int k, size_t n_tiles, size_t stride) {
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = hc[b].alloc(np * static_cast<size_t>(k));
+      if (e == cudaSuccess) e = cudaMemset(hc[b].p, 0, hc[b].bytes());
+    }
+    if (e == cudaSuccess && !ex_flux.p) e = ex_flux.alloc(n_tiles * stride);
+    if (e == cudaSuccess && !ex_right.p) e = ex_right.alloc(n_tiles * stride);
+    if (e == cudaSuccess && !ex_valid.p) e = ex_valid.alloc(n_tiles);
+    if (e == cudaSuccess && !ex_dt.p) e = ex_dt.alloc(1);
+    if (e == cudaSuccess && !zmask.p) e = zmask.alloc(n_tiles);
+    if (e == cudaSuccess) e = cudaMemset(zmask.p, 0, zmask.bytes());  // not known to be zero
+    if (e == cudaSuccess) e = cudaMemset(ex_valid.p, 0, ex_valid.bytes());
+    if (e == cudaSuccess) e = cudaMemset(ex_dt.p, 0xff, sizeof(double));  // -NaN: no step exported
+    return e;
+  }
+  void free_species() {
+    hc[0].release(); hc[1].release();
+    ex_flux.release(); ex_right.release(); ex_valid.release(); ex_dt.release(); zmask.release();
+  }
   cudaError_t alloc(size_t np, size_t n_inflow, bool pair) {
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
@@ -88,6 +114,7 @@ struct Buffers {
   size_t bytes() const {
     size_t b = z.bytes() + gn2.bytes() + in_pw.bytes() + in_hs.bytes() + trk_t.bytes();
     for (int k = 0; k < 4; ++k) b += trk[k].bytes();
+    b += hc[0].bytes() + hc[1].bytes() + ex_flux.bytes() + ex_right.bytes() + ex_valid.bytes() + ex_dt.bytes() + zmask.bytes();
     for (int k = 0; k < 2; ++k)
       b += H[k].bytes() + Hlo[k].bytes() + qx[k].bytes() + qy[k].bytes();
     return b;
@@ -123,7 +150,8 @@ struct StepList {
   uint32_t ne4 = 4, nh4 = 4;
   size_t smem = 0;
   int occupancy = 1;  // resident CTAs per SM at this shared-memory size
-  bool track = false;  // a member keeps a flood-tracking record (the tracking kernel)
+  bool extra = false;  // a member keeps a flood-tracking record or passive species
+                       // (the step kernel with the optional outputs)
 };
 }  // namespace bm
 
@@ -156,6 +184,8 @@ struct bm_state {
   int ctas_per_sm = 0;  // launch shape (0: as many as fit)
   double trk_harr = 0.0;  // flood tracking: arrival threshold depth (tracking is on
                           // once the tracking arrays exist)
+  int n_species = 0;                    // passive species carried (0: none)
+  double c_in[bm::kMaxSpecies] = {};    // their concentration in the inflow
   template <typename T>
   bm::Buffers<T>& buf();
   ~bm_state() {
@@ -187,6 +217,8 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
                           StepList* out);
 // Grid of a step launch for a launch shape (ctas_per_sm = 0: all that fit).
 bm_status list_occupancy(int prec, StepList* l);
+// The state needs the step kernel with the optional outputs (tracking or species).
+bool state_has_extras(const bm_state* s);
 int step_grid(const StepList& l, int ctas_per_sm);
 void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st);
 }  // namespace bm

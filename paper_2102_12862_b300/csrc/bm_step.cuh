@@ -317,10 +317,11 @@ constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M flood
 // n_items.  ne4max / nh4max: the largest record of the list (they fix the
 // shared-memory layout).  A single state is a list of one instance's tiles, so a run
 // executes the same machine code alone and in a batch and gives bitwise the same
-// result.  kTrack: the instantiation that also updates the flood-tracking records of
-// the instances that have them (launched only when one does; the other carries no
-// tracking code at all).
-template <typename T, bool kTrack>
+// result.  kExtra: the instantiation with the optional outputs -- it updates the
+// flood-tracking records and exports each tile's edge mass fluxes for the passive
+// species of the instances that have them (launched only when one does; the other
+// carries none of that code).
+template <typename T, bool kExtra>
 __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const PipeItem* __restrict__ items,
                                                                          int n_items, int* __restrict__ sched,
                                                                          int* __restrict__ early, int* __restrict__ mark,
@@ -608,6 +609,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         const int lR = R >= 0 ? R : lL;
         const bool inflow = R <= kInflow;
         T f0 = zero, f1 = zero, f2 = zero, f3 = zero, f4 = zero;
+        bool right = false;  // the contact's right side is upwind (passive species)
         unsigned char skipped = 1;
         if (!(dry[lL] && dry[lR]) || inflow) {
           const T HLh = sH[lL], HLl = kPair ? sHl[lL] : zero, zL = sZ[lL];
@@ -643,7 +645,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
               ut2 = utL;
             }
             T F0, F1, F2, pL, pR;
-            hllc<T>(h1, unL, utL, c1, h2, un2, ut2, c2, hg, F0, F1, F2, pL, pR);
+            hllc<T>(h1, unL, utL, c1, h2, un2, ut2, c2, hg, F0, F1, F2, pL, pR, right);
             T GL = F1 - pL;
             const T GR = F1 - pR;
             if (R == kWall) {
@@ -677,6 +679,23 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         Fs[3 * L.ne4 + k2] = f3;
         Fs[4 * L.ne4 + k2] = f4;
         skip[k2] = skipped;
+        if constexpr (kExtra) {
+          // passive species: this edge's l F_h (inflow: l (-q); 0 on walls and skipped
+          // edges) and its upwind side, for the species kernel after the step
+          if (a.ex_flux != nullptr) {
+            const size_t o = static_cast<size_t>(tile) * static_cast<size_t>(a.ex_stride) + k2;
+            a.ex_flux[o] = f0;
+            a.ex_right[o] = right ? 1 : 0;
+          }
+        }
+      }
+    }
+    if constexpr (kExtra) {
+      // passive species: whether this tile exported fluxes (a quiet tile has none) and,
+      // from tile 0, the step's dt (-1: the instance did not step)
+      if (tid == 0 && a.ex_flux != nullptr && !prime) {
+        a.ex_valid[tile] = (run && !quiet) ? 1 : 0;
+        if (tile == 0) *a.ex_dt = run ? static_cast<double>(cs.dt) : -1.0;
       }
     }
     nbar<kTile>();
@@ -716,7 +735,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           // copied through, dry and at rest, cannot change its record)
           bool trk = false;
           TrackRecord<T> rec{};
-          if constexpr (kTrack) {
+          if constexpr (kExtra) {
             trk = a.trk_t != nullptr;
             if (trk) rec = track_load(a, i);
           }
@@ -768,7 +787,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           // negative depth: below -h_min, beyond the rounding of the FP32 bed offset in FP32-bulk
           const T negtol = kPair ? hmin + T(4) * static_cast<T>(FLT_EPSILON) * fabs(zi) : hmin;
           if (h < -negtol) atomicOr(&a.ctl->status, 2);
-          if constexpr (kTrack) {
+          if constexpr (kExtra) {
             if (trk) track_update<T>(a, i, rec, h, ux, uy, gn2, hmin, new_time(cs, 1));
           }
         }
