@@ -148,3 +148,21 @@ def test_species_follow_upload_and_removal():
     with pytest.raises(bm.BMError, match="n_species"):
         st.set_scalars(np.zeros((6, st.n_cells)))
     st.step(2)  # the state steps on without species
+
+
+def test_t6_three_humps_fp64():
+    """Section T6's two species (Eq. 24) in the dam break over three humps: wet/dry
+    fronts over the humps, friction, walls; element-wise parity after 30 s and the
+    paper's mixed values (species mass over water volume) kept."""
+    s = W.three_humps(nx=75, ny=30)
+    x = s.centroids()[:, 0]
+    h0 = np.maximum(s.H - s.z, 0.0)
+    hc = np.stack([np.where(x < 16.0, 0.5, 0.0) * h0, np.where(x < 16.0, 0.0, 0.1) * h0])
+    st, o = both(s, hc)
+    st.run_until(30.0)
+    o.run_until(30.0)
+    g = compare_fp64(st, o)
+    area = o.area()
+    H, _, _, _ = st.download()
+    mean = (g @ area) / np.sum(area * (H - s.z))
+    assert abs(mean[0] - 0.386) <= 5e-4 and abs(mean[1] - 0.023) <= 5e-4
