@@ -85,6 +85,11 @@ def _lib():
         lib.orc_run_tracked.restype = i64
         lib.orc_run_scalars.argtypes = [C.c_void_p, P(d), P(d), P(d), P(d), d, i64, P(d), C.c_int, P(d), P(d)]
         lib.orc_run_scalars.restype = i64
+        i32 = C.c_int32
+        lib.orc_set_sources.argtypes = [C.c_void_p, i32, P(i32), P(i32), P(i32), P(i64), P(d), P(d)]
+        lib.orc_set_sources.restype = C.c_int
+        lib.orc_source_volume.argtypes = [C.c_void_p]
+        lib.orc_source_volume.restype = d
         _libs["serial"] = lib
     return _libs["serial"]
 
@@ -160,6 +165,34 @@ class Oracle:
         k = self.hc.shape[0]
         self.c_in = np.zeros(k) if c_in is None else np.array(c_in, dtype=np.float64).reshape(k)
 
+    def set_sources(self, region, kind, mode, series):
+        """External sources / sinks S_h (see orc_set_sources): region (n,) of each
+        cell (-1: none); per region kind (0: total discharge m^3/s, 1: intensity mm/h),
+        mode (0: Exact, 1: Available, 2: Infinity) and series (t, v): points of v(t)."""
+        reg = np.ascontiguousarray(region, dtype=np.int32).reshape(self.n_cells)
+        kind = np.ascontiguousarray(kind, dtype=np.int32).reshape(-1)
+        mode = np.ascontiguousarray(mode, dtype=np.int32).reshape(-1)
+        nr = len(kind)
+        if len(mode) != nr or len(series) != nr:
+            raise OracleError("kind, mode and series need one entry per region")
+        off = np.zeros(nr + 1, np.int64)
+        for r, (t, v) in enumerate(series):
+            off[r + 1] = off[r] + len(t)
+        tt = np.ascontiguousarray(np.concatenate([np.asarray(t, float) for t, _ in series]) if nr else np.zeros(1))
+        vv = np.ascontiguousarray(np.concatenate([np.asarray(v, float) for _, v in series]) if nr else np.zeros(1))
+        rc = _lib().orc_set_sources(self._h, nr, reg.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    kind.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    mode.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    off.ctypes.data_as(C.POINTER(C.c_int64)), _dp(tt), _dp(vv))
+        if rc != 0:
+            raise OracleError(f"orc_set_sources failed with code {rc}")
+        self.n_sources = nr
+
+    @property
+    def source_volume(self) -> float:
+        """Volume the sources added (negative: sinks removed) since set_sources."""
+        return _lib().orc_source_volume(self._h)
+
     def concentration(self):
         h = self.depth()
         return np.where(h > 0, self.hc / np.where(h > 0, h, 1.0), 0.0)
@@ -167,6 +200,8 @@ class Oracle:
     def step(self, n: int = 1, t_end: float = math.inf) -> int:
         lib = _lib()
         if self.hc is not None:
+            if getattr(self, "n_sources", 0):
+                raise OracleError("passive species with external sources are not modelled")
             if self.tracking is not None:
                 raise OracleError("scalars and flood tracking together are not supported by the oracle")
             k = lib.orc_run_scalars(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), C.byref(self.t),

@@ -24,7 +24,8 @@
  *   4. Manning friction (Eq. 2, Table 1) split off and integrated with a
  *      two-stage semi-implicit Runge-Kutta (Heun) step.
  *   5. q := 0 on cells whose depth is below the minimum water depth.
- * Optional flood tracking after each step (orc_track below).
+ * Optional: external sources in step 3 (orc_set_sources), flood tracking after each
+ * step (orc_track), passive species advected with each step (orc_run_scalars).
  *
  * Readings where the paper is silent are the same as in the design notes:
  * modified-state form, Toro wave speeds, h_min, friction stages, rho_ij, the
@@ -70,6 +71,13 @@ typedef struct {
   double inflow_len;     /* total length of the inflow boundary */
   orc_params p;
   double *ht, *hq;
+  /* external sources (orc_set_sources): region of each cell (-1: none); per region
+   * kind, mode, area and a piecewise-linear series (src_off[r] .. src_off[r+1]) */
+  int32_t src_n;
+  int32_t *src_reg, *src_kind, *src_mode;
+  int64_t *src_off;
+  double *src_t, *src_v, *src_area, *src_rate;
+  double src_vol; /* volume the sources added (negative: removed) since they were set */
 } orc_mesh;
 
 /* ---------- mesh topology (independent, plain) ---------- */
@@ -90,6 +98,8 @@ void orc_destroy(orc_mesh* m) {
   free(m->eL); free(m->eR); free(m->nx); free(m->ny); free(m->len);
   free(m->area); free(m->z); free(m->man); free(m->cedge);
   free(m->cL); free(m->cR); free(m->qin); free(m->ht); free(m->hq);
+  free(m->src_reg); free(m->src_kind); free(m->src_mode); free(m->src_off);
+  free(m->src_t); free(m->src_v); free(m->src_area); free(m->src_rate);
   free(m);
 }
 
@@ -374,6 +384,70 @@ double orc_cfl(const orc_mesh* m, const double* H, const double* qx, const doubl
 }
 
 /*
+ * External sources and sinks (Section "External inflow/outflow discharge"): S_h [m/s]
+ * over regions of cells, added explicitly to the continuity equation (the S term of
+ * Eq. 12, evaluated at t^n).  Region r has a series v_r(t), piecewise linear through
+ * its points and constant beyond the ends; kind 0: a total discharge [m^3/s] spread
+ * over the region's area A_r, S_h = v / A_r; kind 1: an intensity [mm/h] per square
+ * metre, S_h = v / 3.6e6.  v > 0 adds water, v < 0 takes it.  mode 0 (Exact): the
+ * depth changes by dt S_h as prescribed (it may fall below zero: the run then fails);
+ * mode 1 (Available): a sink takes at most the water the cell holds after the
+ * fluxes (the depth stops at 0); mode 2 (Infinity): the region takes all water its
+ * cells hold (depth 0, whatever v).  Sources add mass only, no momentum.
+ * n_regions = 0 removes them.  Returns ORC_EINVAL on malformed input.
+ */
+int orc_set_sources(orc_mesh* m, int32_t n_regions, const int32_t* reg, const int32_t* kind, const int32_t* mode,
+                    const int64_t* off, const double* t, const double* v) {
+  free(m->src_reg); free(m->src_kind); free(m->src_mode); free(m->src_off);
+  free(m->src_t); free(m->src_v); free(m->src_area); free(m->src_rate);
+  m->src_reg = NULL; m->src_kind = NULL; m->src_mode = NULL; m->src_off = NULL;
+  m->src_t = NULL; m->src_v = NULL; m->src_area = NULL; m->src_rate = NULL;
+  m->src_n = 0;
+  m->src_vol = 0.0;
+  if (n_regions <= 0) return ORC_OK;
+  const int64_t n = m->n_cells, np = off[n_regions];
+  m->src_reg = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  m->src_kind = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_regions);
+  m->src_mode = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_regions);
+  m->src_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_regions + 1));
+  m->src_t = (double*)malloc(sizeof(double) * (size_t)(np + 1));
+  m->src_v = (double*)malloc(sizeof(double) * (size_t)(np + 1));
+  m->src_area = (double*)calloc((size_t)n_regions, sizeof(double));
+  m->src_rate = (double*)calloc((size_t)n_regions, sizeof(double));
+  if (!m->src_reg || !m->src_kind || !m->src_mode || !m->src_off || !m->src_t || !m->src_v || !m->src_area ||
+      !m->src_rate)
+    return ORC_ENOMEM;
+  memcpy(m->src_reg, reg, sizeof(int32_t) * (size_t)n);
+  memcpy(m->src_kind, kind, sizeof(int32_t) * (size_t)n_regions);
+  memcpy(m->src_mode, mode, sizeof(int32_t) * (size_t)n_regions);
+  memcpy(m->src_off, off, sizeof(int64_t) * (size_t)(n_regions + 1));
+  memcpy(m->src_t, t, sizeof(double) * (size_t)np);
+  memcpy(m->src_v, v, sizeof(double) * (size_t)np);
+  for (int64_t i = 0; i < n; ++i)
+    if (reg[i] >= 0) m->src_area[reg[i]] += m->area[i];
+  m->src_n = n_regions;
+  return ORC_OK;
+}
+
+/* S_h of every region at time t (m/s) */
+static void source_rates(orc_mesh* m, double t) {
+  for (int32_t r = 0; r < m->src_n; ++r) {
+    const int64_t a = m->src_off[r], b = m->src_off[r + 1];
+    double v = m->src_v[a];
+    if (t > m->src_t[a]) {
+      v = m->src_v[b - 1];
+      for (int64_t k = a + 1; k < b; ++k)
+        if (t <= m->src_t[k]) {
+          double w = (t - m->src_t[k - 1]) / (m->src_t[k] - m->src_t[k - 1]);
+          v = m->src_v[k - 1] + w * (m->src_v[k] - m->src_v[k - 1]);
+          break;
+        }
+    }
+    m->src_rate[r] = m->src_kind[r] == 0 ? v / m->src_area[r] : v / 3.6e6;
+  }
+}
+
+/*
  * One explicit step from (t, H, qx, qy) to t + dt, in place.  t_end clips dt
  * (pass +inf for none).  bvol accumulates the net volume that entered through
  * the boundary (positive = inflow).  Returns dt (0 if t >= t_end).
@@ -434,7 +508,8 @@ double orc_step(orc_mesh* m, double* H, double* qx, double* qy, double* t, doubl
       bflux += l * Fh;
     }
   }
-  /* 3.-5. cell update (Eq. 12), friction, dry clean-up */
+  /* 3.-5. cell update (Eq. 12 with the external source), friction, dry clean-up */
+  if (m->src_n > 0) source_rates(m, *t);
   for (int64_t i = 0; i < m->n_cells; ++i) {
     double s0 = 0, s1 = 0, s2 = 0;
     for (int k = 0; k < 3; ++k) {
@@ -446,6 +521,15 @@ double orc_step(orc_mesh* m, double* H, double* qx, double* qy, double* t, doubl
     double Hn = H[i] - r * s0;
     double ux = qx[i] - r * s1;
     double uy = qy[i] - r * s2;
+    if (m->src_n > 0 && m->src_reg[i] >= 0) {
+      const int32_t rg = m->src_reg[i];
+      const double Hf = Hn, add = dt * m->src_rate[rg];
+      if (m->src_mode[rg] == 2 || (m->src_mode[rg] == 1 && (Hn - m->z[i]) + add < 0))
+        Hn = m->z[i]; /* the sink empties the cell */
+      else
+        Hn = Hn + add;
+      m->src_vol += m->area[i] * (Hn - Hf);
+    }
     double h = Hn - m->z[i];
     orc_friction(h, m->man[i], g, dt, hmin, &ux, &uy);
     if (!(h > hmin)) { ux = 0; uy = 0; }
@@ -588,6 +672,8 @@ int64_t orc_run_scalars(orc_mesh* m, double* H, double* qx, double* qy, double* 
   free(phi);
   return s;
 }
+
+double orc_source_volume(const orc_mesh* m) { return m->src_vol; }
 
 /* V = sum_i |Omega_i| (H_i - z_i), fixed order */
 double orc_volume(const orc_mesh* m, const double* H) {

@@ -161,6 +161,27 @@ def three_humps(nx: int = 150, ny: int = 60, seed: int = 0, jitter: float = 0.1)
 # terrains
 # ----------------------------------------------------------------------------------------------
 
+def rained_plane(nx: int = 100, ny: int = 5, L: float = 200.0, Wd: float = 10.0, slope: float = 0.01,
+                 manning: float = 0.03, seed: int = 0, jitter: float = 0.1) -> Scenario:
+    """Tilted plane (the overland-flow setting of the "External inflow/outflow
+    discharge" source): bed z = slope (L - x), initially dry, walls at x = 0 and at the
+    sides, a transmissive outlet at x = L.  The rain is set separately (a source region
+    covering every cell)."""
+    xy, tri, tag = rect_mesh(nx, ny, L, Wd, jitter=jitter, seed=seed, side_tags=(WALL, TRANSMISSIVE, WALL, WALL))
+    c = _centroids(xy, tri)
+    z = slope * (L - c[:, 0])
+    n = len(tri)
+    return Scenario("rained_plane", xy, tri, z, np.full(n, manning), tag, z.copy(), np.zeros(n), np.zeros(n),
+                    default_params())
+
+
+def disk_region(s: Scenario, x0: float, y0: float, r: float) -> np.ndarray:
+    """Source region 0 on the cells whose centroid lies within r of (x0, y0), -1
+    elsewhere."""
+    c = _centroids(s.xy, s.tri)
+    return np.where(np.hypot(c[:, 0] - x0, c[:, 1] - y0) <= r, 0, -1).astype(np.int32)
+
+
 def _sinusoid_bed(rng, x, y, n_waves=8, amp=(0.5, 3.0), wl=(200.0, 2000.0)):
     A = rng.uniform(*amp, size=n_waves)
     L = rng.uniform(*wl, size=n_waves)

@@ -55,13 +55,21 @@ SCALAR_MUTANTS = [
      "double h = H[i];\n      for (int c = 0; c < K; ++c) phi"),
 ]
 
+SOURCE_MUTANTS = [
+    ("source_mm_per_hour", "v / 3.6e6;", "v / 3.6e3;"),
+    ("source_region_area", "m->src_area[reg[i]] += m->area[i];", "m->src_area[reg[i]] = m->area[i];"),
+    ("source_sign", "Hn = Hn + add;", "Hn = Hn - add;"),
+    ("sink_available_test", "(Hn - m->z[i]) + add < 0", "(Hn - m->z[i]) - add < 0"),
+]
+
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name,orig,mut,pins",
                          [m + ("test_oracle_pins.py",) for m in MUTANTS]
                          + [m + ("test_oracle_tracking.py",) for m in TRACK_MUTANTS]
-                         + [m + ("test_oracle_scalars.py",) for m in SCALAR_MUTANTS],
-                         ids=[m[0] for m in MUTANTS + TRACK_MUTANTS + SCALAR_MUTANTS])
+                         + [m + ("test_oracle_scalars.py",) for m in SCALAR_MUTANTS]
+                         + [m + ("test_oracle_sources.py",) for m in SOURCE_MUTANTS],
+                         ids=[m[0] for m in MUTANTS + TRACK_MUTANTS + SCALAR_MUTANTS + SOURCE_MUTANTS])
 def test_pins_catch_mutant(name, orig, mut, pins, tmp_path):
     src = open(SRC).read()
     assert src.count(orig) == 1, f"mutation site for {name} not unique"
