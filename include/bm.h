@@ -202,6 +202,28 @@ bm_status bm_state_set_scalars(bm_state* s, int32_t n_species, const double* hc,
 bm_status bm_state_download_scalars(bm_state* s, double* hc);
 
 /*
+ * External sources and sinks (Section "External inflow/outflow discharge"): S_h [m/s]
+ * over regions of cells, added explicitly to the continuity equation (the S term of
+ * Eq. 12, evaluated at t^n) with every step from the call on.
+ * region: n_cells entries (caller order), the region of each cell in [0, n_regions)
+ * or -1.  Per region r: kind[r] 0 = total discharge [m^3/s] spread over the region's
+ * area (S_h = v / A_r), 1 = intensity [mm/h] (S_h = v / 3.6e6); mode[r] 0 = Exact
+ * (the depth changes by dt S_h as prescribed; a sink larger than the water ends the
+ * run with BM_ENEGDEPTH), 1 = Available (a sink takes at most the
+ * water the cell holds after the step's fluxes), 2 = Infinity (the region takes all
+ * the water its cells hold, whatever v); its series v(t) is the points
+ * (t[k], v[k]) for k in [offsets[r], offsets[r+1]) (times strictly increasing),
+ * piecewise linear and constant beyond the ends; v > 0 adds water, v < 0 takes it.
+ * Sources add mass, not momentum.  n_regions in [0, 65536]; 0 removes them.  BM_EINVAL
+ * on malformed input, on a total-discharge region with no cell, and when the state
+ * carries passive species (not modelled together; bm_state_set_scalars refuses the
+ * converse).  A state with sources steps alone (bm_batch_create refuses it).  Blocks.
+ * Every step launches a one-block kernel before the step kernel (S_h at t^n).
+ */
+bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* region, const int32_t* kind,
+                               const int32_t* mode, const int64_t* offsets, const double* t, const double* v);
+
+/*
  * Scalars of the state: time, the dt the next step will take, steps taken,
  * water volume V = sum |Omega_i| (H_i - z_i) (FP64, fixed summation order), and
  * the net volume that entered through the boundary since init/upload.

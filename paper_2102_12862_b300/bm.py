@@ -80,6 +80,7 @@ SIGNATURES = {
     "bm_state_download_track": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "bm_state_set_scalars": (C.c_int, [_vp, C.c_int32, _vp, _vp]),
     "bm_state_download_scalars": (C.c_int, [_vp, _vp]),
+    "bm_state_set_sources": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "bm_server_opts_default": (None, [_P(bm_server_opts)]),
     "bm_server_create": (C.c_int, [_P(bm_server_opts), _P(_vp)]),
     "bm_server_destroy": (None, [_vp]),
@@ -251,6 +252,32 @@ def bm_state_set_scalars(state: int, hc, c_in=None):
         raise ValueError("c_in needs one value per species")
     _check(load_library().bm_state_set_scalars(state, k, _dp(hc) if k else None, _dp(ci) if ci is not None else None))
     return hc, ci
+
+
+SOURCE_TOTAL, SOURCE_INTENSITY = 0, 1          # kind: m^3/s over the region, mm/h
+SINK_EXACT, SINK_AVAILABLE, SINK_INFINITY = 0, 1, 2
+
+
+def bm_state_set_sources(state: int, region, kind, mode, series):
+    """External sources / sinks: region (n_cells,) of each cell (-1: none); per region
+    kind, mode and series (t, v) of v(t)."""
+    i32 = C.c_int32
+    kind = np.ascontiguousarray(kind, dtype=np.int32).reshape(-1)
+    mode = np.ascontiguousarray(mode, dtype=np.int32).reshape(-1)
+    nr = len(kind)
+    if len(mode) != nr or len(series) != nr:
+        raise ValueError("kind, mode and series need one entry per region")
+    reg = np.ascontiguousarray(region, dtype=np.int32).reshape(-1)
+    off = np.zeros(nr + 1, np.int64)
+    for r, (t, _) in enumerate(series):
+        off[r + 1] = off[r] + len(t)
+    tt = np.ascontiguousarray(np.concatenate([np.asarray(t, float) for t, _ in series]) if nr else np.zeros(1))
+    vv = np.ascontiguousarray(np.concatenate([np.asarray(v, float) for _, v in series]) if nr else np.zeros(1))
+    keep = (reg, kind, mode, off, tt, vv)
+    _check(load_library().bm_state_set_sources(state, nr, reg.ctypes.data_as(_P(i32)), kind.ctypes.data_as(_P(i32)),
+                                               mode.ctypes.data_as(_P(i32)), off.ctypes.data_as(_P(C.c_int64)),
+                                               _dp(tt), _dp(vv)))
+    return keep
 
 
 def bm_state_download_scalars(state: int, n_species: int, n_cells: int) -> np.ndarray:
@@ -426,6 +453,13 @@ class State:
         with every step from now on; c_in: their inflow concentrations."""
         hc, _ = bm_state_set_scalars(self.handle, hc, c_in)
         self.n_species = hc.shape[0] if hc.size else 0
+
+    def set_sources(self, region, kind, mode, series):
+        """External sources / sinks S_h over regions (see bm_state_set_sources):
+        region (n_cells,) of each cell (-1: none); per region kind (SOURCE_TOTAL m^3/s,
+        SOURCE_INTENSITY mm/h), mode (SINK_EXACT / SINK_AVAILABLE / SINK_INFINITY) and
+        series (t, v) of v(t); no regions removes them."""
+        bm_state_set_sources(self.handle, region, kind, mode, series)
 
     def download_scalars(self) -> np.ndarray:
         return bm_state_download_scalars(self.handle, self.n_species, self.n_cells)

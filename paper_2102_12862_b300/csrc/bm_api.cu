@@ -189,6 +189,7 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
       it.ne_nh = R.ne_nh[t];
       it.inst = static_cast<int32_t>(k);
       it.flags = R.flags[t];
+      if (!members[k]->src_tile.empty() && members[k]->src_tile[t]) it.flags |= 4u;  // source cells
       it.bidx = brank_of[t];
       items.push_back(it);
     }
@@ -215,7 +216,7 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
 
 bool state_has_extras(const bm_state* s) {
   const bool trk = s->prec == BM_FP64 ? s->b64.trk_t.p != nullptr : s->b32.trk_t.p != nullptr;
-  return trk || s->n_species > 0;
+  return trk || s->n_species > 0 || s->n_src > 0;
 }
 
 // Resident CTAs per SM of the list's kernel (with or without tracking).
@@ -319,6 +320,14 @@ void launch_species(bm_state* s, cudaStream_t st) {
 }
 
 void launch_state(bm_state* s, cudaStream_t st, int prime) {
+  if (!prime && s->n_src > 0) {
+    if (s->prec == BM_FP64)
+      source_rates<double><<<1, 128, 0, st>>>(s->ctl, s->n_src, s->src_kind.p, s->src_off.p, s->src_t.p, s->src_v.p,
+                                               s->src_area.p, s->src_rate64.p);
+    else
+      source_rates<float><<<1, 128, 0, st>>>(s->ctl, s->n_src, s->src_kind.p, s->src_off.p, s->src_t.p, s->src_v.p,
+                                              s->src_area.p, s->src_rate32.p);
+  }
   launch_work(s->prec, s->list, s->grid, prime, st);
   if (!prime && s->n_species > 0) {
     if (s->prec == BM_FP64) launch_species<double>(s, st);
@@ -400,6 +409,12 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
     d.ex_valid = b.ex_valid.p;
     d.ex_dt = b.ex_dt.p;
     d.ex_stride = static_cast<int>(m->rec[sizeof(T) == 8 ? 0 : 1].ne4_max);
+  }
+  if (s->n_src > 0) {
+    d.src_reg = s->src_reg.p;
+    d.src_mode = s->src_mode.p;
+    if constexpr (sizeof(T) == 8) d.src_rate = s->src_rate64.p;
+    else d.src_rate = s->src_rate32.p;
   }
   d.in_pw = b.in_pw.p;
   d.in_hs = b.in_hs.p;
@@ -882,6 +897,7 @@ bm_status bm_state_set_scalars(bm_state* s, int32_t n_species, const double* hc,
   const HostMesh& h = s->mesh->h;
   const int n = static_cast<int>(h.n_cells);
   if (n_species > 0 && !hc) return fail(BM_EINVAL, "bm_state_set_scalars: hc is NULL");
+  if (n_species > 0 && s->n_src > 0) return fail(BM_EINVAL, "bm_state_set_scalars: the state has external sources");
   for (int64_t i = 0; i < static_cast<int64_t>(n_species) * n; ++i)
     if (!std::isfinite(hc[i])) return fail(BM_EINVAL, "bm_state_set_scalars: hc has a non-finite value");
   for (int c = 0; c < n_species && c_in; ++c)
@@ -954,6 +970,77 @@ bm_status bm_state_download_scalars(bm_state* s, double* hc) {
     BM_CUDA(cudaMemcpyAsync(hc + static_cast<size_t>(c) * n, stage, bytes, cudaMemcpyDeviceToHost, s->stream));
   }
   BM_CUDA(cudaStreamSynchronize(s->stream));
+  return BM_OK;
+}
+
+bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* region, const int32_t* kind,
+                               const int32_t* mode, const int64_t* offsets, const double* t, const double* v) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_set_sources: state is NULL");
+  if (n_regions < 0 || n_regions > 65536) return fail(BM_EINVAL, "bm_state_set_sources: n_regions in [0, 65536]");
+  const HostMesh& h = s->mesh->h;
+  const int64_t n = h.n_cells;
+  if (n_regions > 0) {
+    if (s->n_species > 0) return fail(BM_EINVAL, "bm_state_set_sources: the state carries passive species");
+    if (!region || !kind || !mode || !offsets || !t || !v) return fail(BM_EINVAL, "bm_state_set_sources: NULL array");
+    if (offsets[0] != 0) return fail(BM_EINVAL, "bm_state_set_sources: offsets[0] must be 0");
+    for (int32_t r = 0; r < n_regions; ++r) {
+      if (kind[r] != 0 && kind[r] != 1) return fail(BM_EINVAL, "bm_state_set_sources: kind must be 0 or 1");
+      if (mode[r] < 0 || mode[r] > 2) return fail(BM_EINVAL, "bm_state_set_sources: mode must be 0, 1 or 2");
+      if (offsets[r + 1] <= offsets[r] || offsets[r + 1] - offsets[r] > 1000000)
+        return fail(BM_EINVAL, "bm_state_set_sources: every series needs 1 to 1e6 points");
+      for (int64_t k = offsets[r]; k < offsets[r + 1]; ++k) {
+        if (!std::isfinite(t[k]) || !std::isfinite(v[k]))
+          return fail(BM_EINVAL, "bm_state_set_sources: series values must be finite");
+        if (k > offsets[r] && !(t[k] > t[k - 1]))
+          return fail(BM_EINVAL, "bm_state_set_sources: series times must increase strictly");
+      }
+    }
+  }
+  std::vector<int32_t> reg_new(static_cast<size_t>(h.n_tiles) * kTile, -1);
+  std::vector<double> area(static_cast<size_t>(n_regions), 0.0);
+  std::vector<uint8_t> tiles(static_cast<size_t>(h.n_tiles), 0);
+  for (int64_t i = 0; i < n && n_regions > 0; ++i) {
+    const int32_t r = region[h.perm[i]];
+    if (r < -1 || r >= n_regions) return fail(BM_EINVAL, "bm_state_set_sources: region index out of range");
+    reg_new[i] = r;
+    if (r >= 0) {
+      area[r] += h.area[i];
+      tiles[i / kTile] = 1;
+    }
+  }
+  for (int32_t r = 0; r < n_regions; ++r)
+    if (kind[r] == 0 && !(area[r] > 0.0))
+      return fail(BM_EINVAL, "bm_state_set_sources: a total-discharge region holds no cell");
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  cudaError_t e = cudaSuccess;
+  if (n_regions > 0) {
+    const int64_t np = offsets[n_regions];
+    e = s->src_reg.upload(reg_new);
+    if (e == cudaSuccess) e = s->src_kind.upload(std::vector<int32_t>(kind, kind + n_regions));
+    if (e == cudaSuccess) e = s->src_mode.upload(std::vector<int32_t>(mode, mode + n_regions));
+    if (e == cudaSuccess) e = s->src_off.upload(std::vector<long long>(offsets, offsets + n_regions + 1));
+    if (e == cudaSuccess) e = s->src_t.upload(std::vector<double>(t, t + np));
+    if (e == cudaSuccess) e = s->src_v.upload(std::vector<double>(v, v + np));
+    if (e == cudaSuccess) e = s->src_area.upload(area);
+    if (e == cudaSuccess) e = s->src_rate64.alloc(static_cast<size_t>(n_regions));
+    if (e == cudaSuccess) e = s->src_rate32.alloc(static_cast<size_t>(n_regions));
+    if (e != cudaSuccess) return dev_fail(e, "bm_state_set_sources: source arrays");
+    s->src_tile = tiles;
+  } else {
+    s->src_reg.release(); s->src_kind.release(); s->src_mode.release(); s->src_off.release();
+    s->src_t.release(); s->src_v.release(); s->src_area.release(); s->src_rate64.release(); s->src_rate32.release();
+    s->src_tile.clear();
+  }
+  s->n_src = n_regions;
+  // the descriptor (read in place) and the work list (tile flags, kernel instantiation)
+  state_desc_bytes(s, &s->hdesc);
+  BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  drop_graphs(s);
+  bm_status st = build_step_list({s}, {static_cast<const void*>(s->desc.p)}, &s->list);
+  if (st != BM_OK) return st;
+  s->grid = step_grid(s->list, s->ctas_per_sm);
   return BM_OK;
 }
 

@@ -56,6 +56,12 @@ struct alignas(16) InstDesc {
   unsigned char* ex_valid;
   double* ex_dt;
   int ex_stride;  // edges per tile in ex_flux / ex_right (the mesh's largest, rounded to 4)
+  // external sources (null when none): region of each cell (-1: none), S_h of each
+  // region at t^n (m/s, written before each step), its sink mode (0 Exact, 1
+  // Available, 2 Infinity)
+  const int32_t* src_reg;
+  const T* src_rate;
+  const int32_t* src_mode;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -578,6 +584,31 @@ __global__ void set_t_end(Ctl* ctl, double t_end) {
   ctl->dt_f = static_cast<float>(dt);
   ctl->clipped = clipped;
   ctl->active = t < t_end ? 1 : 0;
+}
+
+// External sources (Section "External inflow/outflow discharge"): S_h of every region
+// at t^n -- its series v(t), piecewise linear through its points and constant beyond
+// the ends, as a total discharge over the region's area (kind 0, m^3/s) or an
+// intensity (kind 1, mm/h).  Launched before each step; nothing once the run ended.
+template <typename T>
+__global__ void source_rates(const Ctl* ctl, int n_regions, const int32_t* kind, const long long* off,
+                             const double* ts, const double* vs, const double* area, T* rate) {
+  if (!ctl->active) return;
+  const double t = ctl->t;
+  for (int r = threadIdx.x; r < n_regions; r += blockDim.x) {
+    const long long a = off[r], b = off[r + 1];
+    double v = vs[a];
+    if (t > ts[a]) {
+      v = vs[b - 1];
+      for (long long k = a + 1; k < b; ++k)
+        if (t <= ts[k]) {
+          const double w = (t - ts[k - 1]) / (ts[k] - ts[k - 1]);
+          v = vs[k - 1] + w * (vs[k] - vs[k - 1]);
+          break;
+        }
+    }
+    rate[r] = static_cast<T>(kind[r] == 0 ? v / area[r] : v / 3.6e6);
+  }
 }
 
 // V = sum |Omega_i| (H_i - z_i): per-tile partials, then one block in fixed order.

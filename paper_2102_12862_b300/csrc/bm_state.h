@@ -184,6 +184,15 @@ struct bm_state {
   int ctas_per_sm = 0;  // launch shape (0: as many as fit)
   double trk_harr = 0.0;  // flood tracking: arrival threshold depth (tracking is on
                           // once the tracking arrays exist)
+  // external sources (bm_state_set_sources): region of each cell (new numbering),
+  // per region kind, mode, series and area; S_h per region (T of the precision);
+  // per tile whether it holds a source cell (never quiet)
+  int n_src = 0;
+  bm::DBuf<int32_t> src_reg, src_kind, src_mode;
+  bm::DBuf<long long> src_off;
+  bm::DBuf<double> src_t, src_v, src_area, src_rate64;
+  bm::DBuf<float> src_rate32;
+  std::vector<uint8_t> src_tile;
   int n_species = 0;                    // passive species carried (0: none)
   double c_in[bm::kMaxSpecies] = {};    // their concentration in the inflow
   template <typename T>

@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         C[j] = c;
       }
     }
-    const bool quiet = nbar_and<kTile>(tq) && !prime && !(inf.flags & 2u);
+    const bool quiet = nbar_and<kTile>(tq) && !prime && !(inf.flags & 6u);  // no inflow or source
 
     // phase F: edges
     double bsum = 0.0;
@@ -713,8 +713,12 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         side[q] = (sLR[idx[q]] & (kMaxLocal - 1)) != static_cast<uint32_t>(tid) ? 1 : 0;
       }
       const int dst = par ^ 1;
-      if (quiet ||
-          (!prime && skip[idx[0]] && skip[idx[1]] && skip[idx[2]] && dry[tid] && is_zero(qxi) && is_zero(qyi))) {
+      int src = -1;  // the cell's source region
+      if constexpr (kExtra) {
+        if (a.src_reg != nullptr) src = a.src_reg[i];
+      }
+      if (quiet || (src < 0 && !prime && skip[idx[0]] && skip[idx[1]] && skip[idx[2]] && dry[tid] && is_zero(qxi) &&
+                    is_zero(qyi))) {
         // no flux, dry and at rest: U^{n+1} = U^n, velocity and celerity zero
         a.H[dst][i] = Hh;
         if constexpr (kPair) a.Hlo[dst][i] = Hl;
@@ -761,6 +765,21 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           }
           ux = qxi - r * s1;
           uy = qyi - r * s2;
+          if constexpr (kExtra) {
+            // external source / sink, explicit in continuity (the S term of Eq. 12)
+            if (src >= 0) {
+              const T add = dt * a.src_rate[src];
+              const int md = a.src_mode[src];
+              if (md == 2 || (md == 1 && depth_of(Hh, Hl, zi) + add < zero)) {
+                Hh = zi;  // the sink empties the cell
+                if constexpr (kPair) Hl = zero;
+              } else if constexpr (kPair) {
+                pair_add(Hh, Hl, add);
+              } else {
+                Hh = Hh + add;
+              }
+            }
+          }
           h = depth_of(Hh, Hl, zi);
           if (h > hmin && gn2 > zero) {
             // split friction: two semi-implicit stages, Heun average.  With
