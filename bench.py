@@ -358,21 +358,24 @@ def measure_lake(args, torch, bm, W):
 
 
 def measure_tracking(args, torch, bm, W):
-    """The optional outputs' cost on the floodplain: the same args.track_steps steps
+    """The optional features' cost on the floodplain: the same args.track_steps steps
     from t = 0 plain, with flood tracking (arrival time of 0.05 m, maxima of depth,
     velocity, discharge and bed shear stress, updated in the step kernel) and with two
     passive species (one entering with the inflow at c = 1, one filling the initially
     wet river at c = 0.5; the step kernel exports its edge mass fluxes, the species
-    kernel advects them after each step)."""
+    kernel advects them after each step) and with rain on a disk (a source region: the
+    rate kernel before each step, the S term in the step kernel)."""
     s = W.floodplain()
     mesh = bm.Mesh.from_scenario(s)
     h0 = np.maximum(s.H - s.z, 0.0)
+    rain_region = W.disk_region(s, 2500.0, 1000.0, 500.0)
     out = {"workload": "floodplain 2,000,000 triangles, steps from t = 0, arrival threshold 0.05 m; "
-                       "2 passive species (inflow c = 1; river c = 0.5)",
+                       "2 passive species (inflow c = 1; river c = 0.5); rain 50 mm/h on a 500 m disk "
+                       f"({int((rain_region >= 0).sum())} cells, 9 % wet at t = 0)",
            "steps": args.track_steps}
     for prec in [p for p in args.precisions.split(",") if p]:
         res = {}
-        for mode in ("plain", "tracked", "species"):
+        for mode in ("plain", "tracked", "species", "sources"):
             st = bm.State.from_scenario(s, mesh=mesh, precision=prec)
             stream = torch.cuda.Stream()
             torch.cuda.set_stream(stream)
@@ -381,6 +384,9 @@ def measure_tracking(args, torch, bm, W):
                 st.track(0.05)
             elif mode == "species":
                 st.set_scalars(np.stack([np.zeros_like(h0), 0.5 * h0]), c_in=[1.0, 0.0])
+            elif mode == "sources":
+                st.set_sources(rain_region, [bm.SOURCE_INTENSITY], [bm.SINK_EXACT],
+                               [(np.array([0.0]), np.array([50.0]))])
             st.step(args.warmup)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -402,7 +408,8 @@ def measure_tracking(args, torch, bm, W):
             "ms_per_step": res["plain"], "ms_per_step_tracked": res["tracked"],
             "overhead": res["tracked"] / res["plain"] - 1.0, "cells_arrived": res["arrived"],
             "ms_per_step_2_species": res["species"], "overhead_2_species": res["species"] / res["plain"] - 1.0,
-            "inflow_species_volume_m3": res["inflow_species_volume"]}
+            "inflow_species_volume_m3": res["inflow_species_volume"],
+            "ms_per_step_rain": res["sources"], "overhead_rain": res["sources"] / res["plain"] - 1.0}
     return out
 
 
