@@ -254,6 +254,12 @@ def bm_state_set_scalars(state: int, hc, c_in=None):
     return hc, ci
 
 
+def manning_from_strickler(k_str):
+    """Strickler's coefficient k_str [m^(1/3)/s] as the Manning n the library takes:
+    Table 1's Strickler law is Manning's with n = 1 / k_str."""
+    return 1.0 / np.asarray(k_str, dtype=np.float64)
+
+
 SOURCE_TOTAL, SOURCE_INTENSITY = 0, 1          # kind: m^3/s over the region, mm/h
 SINK_EXACT, SINK_AVAILABLE, SINK_INFINITY = 0, 1, 2
 
