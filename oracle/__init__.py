@@ -90,6 +90,11 @@ def _lib():
         lib.orc_set_sources.restype = C.c_int
         lib.orc_source_volume.argtypes = [C.c_void_p]
         lib.orc_source_volume.restype = d
+        lib.orc_set_morpho.argtypes = [C.c_void_p, C.c_int, d, d, d, d, d, d]
+        lib.orc_set_morpho.restype = C.c_int
+        lib.orc_bed_outflow.argtypes = [C.c_void_p]
+        lib.orc_bed_outflow.restype = d
+        lib.orc_bed.argtypes = [C.c_void_p, P(d)]
         _libs["serial"] = lib
     return _libs["serial"]
 
@@ -188,6 +193,20 @@ class Oracle:
             raise OracleError(f"orc_set_sources failed with code {rc}")
         self.n_sources = nr
 
+    def set_morpho(self, porosity=0.4, s=2.65, d=0.001, alpha=8.0, m=1.5, theta_cr=0.047, on=True):
+        """Bed evolution (Exner, Eq. 3 / Eq. 13-16) with the MPM-like closure (Table 2),
+        stepped with the water; z changes and H moves with it."""
+        rc = _lib().orc_set_morpho(self._h, int(on), float(porosity), float(s), float(d), float(alpha), float(m),
+                                   float(theta_cr))
+        if rc != 0:
+            raise OracleError(f"orc_set_morpho failed with code {rc}")
+        self.morpho = bool(on)
+
+    @property
+    def bed_outflow(self) -> float:
+        """Solid sediment volume that left through the boundary (negative: entered)."""
+        return _lib().orc_bed_outflow(self._h)
+
     @property
     def source_volume(self) -> float:
         """Volume the sources added (negative: sinks removed) since set_sources."""
@@ -210,6 +229,7 @@ class Oracle:
             if k < 0:
                 raise OracleError("orc_run_scalars: out of memory")
             self.steps += k
+            self._sync_bed()
             return k
         if self.tracking is not None:
             tr = self.tracking
@@ -221,10 +241,15 @@ class Oracle:
             k = lib.orc_run(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), C.byref(self.t), float(t_end),
                             int(n), C.byref(self.bvol))
         self.steps += k
+        self._sync_bed()
         return k
 
     def run_until(self, t_end: float, max_steps: int = 10**9) -> int:
         return self.step(max_steps, t_end)
+
+    def _sync_bed(self):
+        if getattr(self, "morpho", False):
+            _lib().orc_bed(self._h, _dp(self.z))
 
     def next_dt(self) -> float:
         return _lib().orc_next_dt(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), self.t.value)

@@ -24,8 +24,9 @@
  *   4. Manning friction (Eq. 2, Table 1) split off and integrated with a
  *      two-stage semi-implicit Runge-Kutta (Heun) step.
  *   5. q := 0 on cells whose depth is below the minimum water depth.
- * Optional: external sources in step 3 (orc_set_sources), flood tracking after each
- * step (orc_track), passive species advected with each step (orc_run_scalars).
+ * Optional: external sources in step 3 (orc_set_sources), the bed update of the
+ * morphodynamic module (orc_set_morpho), flood tracking after each step (orc_track),
+ * passive species advected with each step (orc_run_scalars).
  *
  * Readings where the paper is silent are the same as in the design notes:
  * modified-state form, Toro wave speeds, h_min, friction stages, rho_ij, the
@@ -78,6 +79,13 @@ typedef struct {
   int64_t *src_off;
   double *src_t, *src_v, *src_area, *src_rate;
   double src_vol; /* volume the sources added (negative: removed) since they were set */
+  /* morphodynamics (orc_set_morpho): on/off, porosity p, relative density s, grain
+   * diameter d, MPM-like alpha, m, theta_cr; per cell bedload vector and dq_B/dq; per
+   * edge l q_Bij (outward from the left cell); bed volume through the boundary */
+  int morpho;
+  double mp_p, mp_s, mp_d, mp_alpha, mp_m, mp_thcr;
+  double *qbx, *qby, *qbd, *fb;
+  double bed_bvol;
 } orc_mesh;
 
 /* ---------- mesh topology (independent, plain) ---------- */
@@ -100,6 +108,7 @@ void orc_destroy(orc_mesh* m) {
   free(m->cL); free(m->cR); free(m->qin); free(m->ht); free(m->hq);
   free(m->src_reg); free(m->src_kind); free(m->src_mode); free(m->src_off);
   free(m->src_t); free(m->src_v); free(m->src_area); free(m->src_rate);
+  free(m->qbx); free(m->qby); free(m->qbd); free(m->fb);
   free(m);
 }
 
@@ -429,6 +438,91 @@ int orc_set_sources(orc_mesh* m, int32_t n_regions, const int32_t* reg, const in
   return ORC_OK;
 }
 
+/*
+ * Morphodynamics (Section "Morphodynamics", Eq. 3 with S_b = 0, solved with the update
+ * of Eq. 13 and the HLL sediment flux of Eq. 14-16, synchronous-decoupled: the same dt,
+ * every term from U^n and z^n).  Bedload magnitude from the MPM-like closure (Table 2):
+ *   |q_B| = alpha (theta - theta_cr)^m sqrt((s - 1) g d^3)  (0 for theta <= theta_cr),
+ *   theta = tau_b / ((rho_s - rho) g d) = n^2 |u|^2 / ((s - 1) d h^(1/3))
+ * (Manning's bed shear stress rho g n^2 |u|^2 / h^(1/3)), directed along the flow
+ * (no slope or curvature corrections).  dq_B,n/dq_n of Eq. 16 is taken along the
+ * flow at fixed depth: d|q_B|/d|u| / h = alpha m (theta - theta_cr)^(m-1)
+ * sqrt((s - 1) g d^3) (2 theta / |u|) / h.  u_n and c = sqrt(g h) of each cell on the
+ * edge; walls carry no sediment, other boundary edges the inside cell's normal bedload.
+ * The bed change moves the free surface with it (H += dz): the water depth, hence the
+ * water volume, is kept.  on = 0 turns it off.
+ */
+int orc_set_morpho(orc_mesh* m, int on, double porosity, double s, double d, double alpha, double mexp,
+                   double theta_cr) {
+  m->morpho = 0;
+  if (!on) return ORC_OK;
+  if (!(porosity >= 0 && porosity < 1) || !(s > 1) || !(d > 0) || !(alpha >= 0) || !(mexp >= 1)) return ORC_EINVAL;
+  if (!m->qbx) {
+    m->qbx = (double*)calloc((size_t)m->n_cells, sizeof(double));
+    m->qby = (double*)calloc((size_t)m->n_cells, sizeof(double));
+    m->qbd = (double*)calloc((size_t)m->n_cells, sizeof(double));
+    m->fb = (double*)calloc((size_t)m->n_edges, sizeof(double));
+    if (!m->qbx || !m->qby || !m->qbd || !m->fb) return ORC_ENOMEM;
+  }
+  m->mp_p = porosity; m->mp_s = s; m->mp_d = d; m->mp_alpha = alpha; m->mp_m = mexp; m->mp_thcr = theta_cr;
+  m->morpho = 1;
+  return ORC_OK;
+}
+
+/* bedload vector and dq_B/dq of every cell from U^n, z^n */
+static void morpho_cells(orc_mesh* m, const double* H, const double* qx, const double* qy) {
+  const double g = m->p.g, sd = m->mp_s - 1.0, d = m->mp_d;
+  const double scale = sqrt(sd * g * d * d * d);
+  for (int64_t i = 0; i < m->n_cells; ++i) {
+    double u, v;
+    cell_velocity(m, H, qx, qy, i, &u, &v);
+    const double h = H[i] - m->z[i];
+    const double sp = sqrt(u * u + v * v);
+    m->qbx[i] = 0; m->qby[i] = 0; m->qbd[i] = 0;
+    if (!(h > m->p.h_min) || sp == 0) continue;
+    const double theta = m->man[i] * m->man[i] * sp * sp / (sd * d * cbrt(h));
+    if (!(theta > m->mp_thcr)) continue;
+    const double qb = m->mp_alpha * pow(theta - m->mp_thcr, m->mp_m) * scale;
+    m->qbx[i] = qb * u / sp;
+    m->qby[i] = qb * v / sp;
+    m->qbd[i] = m->mp_alpha * m->mp_m * pow(theta - m->mp_thcr, m->mp_m - 1.0) * scale * (2.0 * theta / sp) / h;
+  }
+}
+
+/* the two speeds of Eq. 16 for one cell on an edge */
+static void morpho_speeds(double un, double c, double dqb, double* l1, double* l2) {
+  const double a = un - c;
+  const double r = sqrt(a * a + 4.0 * dqb * c * c);
+  *l1 = 0.5 * (a - r);
+  *l2 = 0.5 * (a + r);
+}
+
+/* l q_Bij of every edge (Eq. 14, 15), outward from the left cell */
+static void morpho_edges(orc_mesh* m, const double* H, const double* qx, const double* qy) {
+  const double g = m->p.g;
+  for (int64_t e = 0; e < m->n_edges; ++e) {
+    const int64_t L = m->eL[e], R = m->eR[e];
+    const double nx = m->nx[e], ny = m->ny[e];
+    const double qL = m->qbx[L] * nx + m->qby[L] * ny;
+    double f;
+    if (R >= 0) {
+      double uL, vL, uR, vR;
+      cell_velocity(m, H, qx, qy, L, &uL, &vL);
+      cell_velocity(m, H, qx, qy, R, &uR, &vR);
+      const double cL = sqrt(g * fmax(0.0, H[L] - m->z[L])), cR = sqrt(g * fmax(0.0, H[R] - m->z[R]));
+      double a1, a2, b1, b2;
+      morpho_speeds(uL * nx + vL * ny, cL, m->qbd[L], &a1, &a2);
+      morpho_speeds(uR * nx + vR * ny, cR, m->qbd[R], &b1, &b2);
+      const double lm = fmin(a1, b1), lp = fmax(a2, b2);
+      const double qR = m->qbx[R] * nx + m->qby[R] * ny;
+      f = lp - lm > 0 ? (lp * qL - lm * qR + lp * lm * (m->z[R] - m->z[L])) / (lp - lm) : 0.0;
+    } else {
+      f = R == -1 ? 0.0 : qL; /* wall; transmissive / inflow: the inside cell's bedload */
+    }
+    m->fb[e] = m->len[e] * f;
+  }
+}
+
 /* S_h of every region at time t (m/s) */
 static void source_rates(orc_mesh* m, double t) {
   for (int32_t r = 0; r < m->src_n; ++r) {
@@ -508,6 +602,11 @@ double orc_step(orc_mesh* m, double* H, double* qx, double* qy, double* t, doubl
       bflux += l * Fh;
     }
   }
+  /* morphodynamics: bedload fluxes from U^n, z^n (before the state is overwritten) */
+  if (m->morpho) {
+    morpho_cells(m, H, qx, qy);
+    morpho_edges(m, H, qx, qy);
+  }
   /* 3.-5. cell update (Eq. 12 with the external source), friction, dry clean-up */
   if (m->src_n > 0) source_rates(m, *t);
   for (int64_t i = 0; i < m->n_cells; ++i) {
@@ -534,6 +633,21 @@ double orc_step(orc_mesh* m, double* H, double* qx, double* qy, double* t, doubl
     orc_friction(h, m->man[i], g, dt, hmin, &ux, &uy);
     if (!(h > hmin)) { ux = 0; uy = 0; }
     H[i] = Hn; qx[i] = ux; qy[i] = uy;
+  }
+  if (m->morpho) {
+    /* Eq. 13 (S_b = 0); the free surface moves with the bed */
+    for (int64_t i = 0; i < m->n_cells; ++i) {
+      double sum = 0;
+      for (int k = 0; k < 3; ++k) {
+        int64_t e = m->cedge[3 * i + k];
+        sum += (m->eL[e] == i) ? m->fb[e] : -m->fb[e];
+      }
+      const double dz = -(dt / m->area[i] * sum) / (1.0 - m->mp_p);
+      m->z[i] += dz;
+      H[i] += dz;
+    }
+    for (int64_t e = 0; e < m->n_edges; ++e)
+      if (m->eR[e] < 0) m->bed_bvol += dt * m->fb[e];
   }
   *bvol += -dt * bflux;
   *t = clipped ? t_end : *t + dt;
@@ -674,6 +788,9 @@ int64_t orc_run_scalars(orc_mesh* m, double* H, double* qx, double* qy, double* 
 }
 
 double orc_source_volume(const orc_mesh* m) { return m->src_vol; }
+/* sediment volume (solid, per Eq. 3's flux) that left through the boundary */
+double orc_bed_outflow(const orc_mesh* m) { return m->bed_bvol; }
+void orc_bed(const orc_mesh* m, double* z) { memcpy(z, m->z, m->n_cells * sizeof(double)); }
 
 /* V = sum_i |Omega_i| (H_i - z_i), fixed order */
 double orc_volume(const orc_mesh* m, const double* H) {

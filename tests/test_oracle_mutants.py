@@ -62,14 +62,23 @@ SOURCE_MUTANTS = [
     ("sink_available_test", "(Hn - m->z[i]) + add < 0", "(Hn - m->z[i]) - add < 0"),
 ]
 
+MORPHO_MUTANTS = [
+    ("bed_update_sign", "const double dz = -(dt / m->area[i] * sum)", "const double dz = +(dt / m->area[i] * sum)"),
+    ("bed_porosity", "* sum) / (1.0 - m->mp_p);", "* sum) / (1.0 + m->mp_p);"),
+    ("bed_keeps_surface", "      H[i] += dz;", "      H[i] += 0.0 * dz;"),
+    ("shields_depth_power", "(sd * d * cbrt(h))", "(sd * d * h)"),
+]
+
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name,orig,mut,pins",
                          [m + ("test_oracle_pins.py",) for m in MUTANTS]
                          + [m + ("test_oracle_tracking.py",) for m in TRACK_MUTANTS]
                          + [m + ("test_oracle_scalars.py",) for m in SCALAR_MUTANTS]
-                         + [m + ("test_oracle_sources.py",) for m in SOURCE_MUTANTS],
-                         ids=[m[0] for m in MUTANTS + TRACK_MUTANTS + SCALAR_MUTANTS + SOURCE_MUTANTS])
+                         + [m + ("test_oracle_sources.py",) for m in SOURCE_MUTANTS]
+                         + [m + ("test_oracle_morpho.py",) for m in MORPHO_MUTANTS],
+                         ids=[m[0] for m in MUTANTS + TRACK_MUTANTS + SCALAR_MUTANTS + SOURCE_MUTANTS
+                              + MORPHO_MUTANTS])
 def test_pins_catch_mutant(name, orig, mut, pins, tmp_path):
     src = open(SRC).read()
     assert src.count(orig) == 1, f"mutation site for {name} not unique"
