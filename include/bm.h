@@ -224,6 +224,25 @@ bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* re
                                const int32_t* mode, const int64_t* offsets, const double* t, const double* v);
 
 /*
+ * Bed evolution (Section "Morphodynamics": Exner, Eq. 3 with S_b = 0, updated by Eq. 13
+ * with the HLL sediment flux of Eq. 14-16), stepped with the water from the call on
+ * (synchronous-decoupled: the same dt, every term from U^n and z^n).  Bedload from
+ * Table 2's MPM-like closure: |q_B| = alpha (theta - theta_cr)^m sqrt((s - 1) g d^3),
+ * theta = n^2 |u|^2 / ((s - 1) d h^(1/3)) (Manning's bed shear stress), along the flow;
+ * dq_B,n/dq_n of Eq. 16 along the flow at fixed depth.  Walls carry no sediment, other
+ * boundary edges the inside cell's normal bedload.  The free surface moves with the
+ * bed, so the water depth and volume are kept.  on = 0 stops it (the bed stays as it
+ * is).  FP64 states only; 0 <= porosity < 1, s > 1, d > 0 [m], alpha >= 0, m >= 1,
+ * theta_cr finite (BM_EINVAL otherwise).  A state with morphodynamics steps alone
+ * (bm_batch_create refuses it).  Every step launches three more kernels (the step's
+ * dt saved before it; the bed fluxes, one CTA per tile, and the update after it).
+ * Blocks.  bm_state_download_bed copies the bed elevation (caller order) to z.
+ */
+bm_status bm_state_set_morpho(bm_state* s, int32_t on, double porosity, double s_rel, double d, double alpha,
+                              double m, double theta_cr);
+bm_status bm_state_download_bed(bm_state* s, double* z);
+
+/*
  * Scalars of the state: time, the dt the next step will take, steps taken,
  * water volume V = sum |Omega_i| (H_i - z_i) (FP64, fixed summation order), and
  * the net volume that entered through the boundary since init/upload.

@@ -81,6 +81,8 @@ SIGNATURES = {
     "bm_state_set_scalars": (C.c_int, [_vp, C.c_int32, _vp, _vp]),
     "bm_state_download_scalars": (C.c_int, [_vp, _vp]),
     "bm_state_set_sources": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "bm_state_set_morpho": (C.c_int, [_vp, C.c_int32, _d, _d, _d, _d, _d, _d]),
+    "bm_state_download_bed": (C.c_int, [_vp, _vp]),
     "bm_server_opts_default": (None, [_P(bm_server_opts)]),
     "bm_server_create": (C.c_int, [_P(bm_server_opts), _P(_vp)]),
     "bm_server_destroy": (None, [_vp]),
@@ -466,6 +468,18 @@ class State:
         SOURCE_INTENSITY mm/h), mode (SINK_EXACT / SINK_AVAILABLE / SINK_INFINITY) and
         series (t, v) of v(t); no regions removes them."""
         bm_state_set_sources(self.handle, region, kind, mode, series)
+
+    def set_morpho(self, porosity=0.4, s=2.65, d=0.001, alpha=8.0, m=1.5, theta_cr=0.047, on=True):
+        """Bed evolution (Exner with the HLL sediment flux and the MPM-like closure;
+        see bm_state_set_morpho), stepped with the water from now on (FP64 states)."""
+        _check(load_library().bm_state_set_morpho(self.handle, int(on), float(porosity), float(s), float(d),
+                                                  float(alpha), float(m), float(theta_cr)))
+
+    def download_bed(self) -> np.ndarray:
+        """The bed elevation z (caller cell order)."""
+        z = np.empty(self.n_cells)
+        _check(load_library().bm_state_download_bed(self.handle, _dp(z)))
+        return z
 
     def download_scalars(self) -> np.ndarray:
         return bm_state_download_scalars(self.handle, self.n_species, self.n_cells)

@@ -19,6 +19,7 @@
 #include "bm_kernels.cuh"
 #include "bm_step.cuh"
 #include "bm_species.cuh"
+#include "bm_morpho.cuh"
 #include "bm_state.h"
 
 namespace bm {
@@ -319,7 +320,35 @@ void launch_species(bm_state* s, cudaStream_t st) {
   (void)cudaLaunchKernelEx(&cfg, species_step<T>, a, nloc);
 }
 
+// The bed update after a step (and after the species, which read z^n).
+void launch_morpho(bm_state* s, cudaStream_t st) {
+  const TileRecords& R = s->mesh->rec[0];
+  MorphoArgs a{};
+  a.items = static_cast<const PipeItem*>(s->list.items.p);
+  for (int k = 0; k < 2; ++k) {
+    a.H[k] = s->b64.H[k].p;
+    a.qx[k] = s->b64.qx[k].p;
+    a.qy[k] = s->b64.qy[k].p;
+  }
+  a.z = s->b64.z.p;
+  a.gn2 = s->b64.gn2.p;
+  a.ctl = s->ctl;
+  a.step_dt = s->mo_dt.p;
+  a.dz = s->mo_dz.p;
+  a.mp = MorphoParams{s->mo_par[0], s->mo_par[1], s->mo_par[2], s->mo_par[3], s->mo_par[4], s->mo_par[5]};
+  a.g = s->p.g;
+  a.h_min = s->p.h_min;
+  a.n_cells = static_cast<int>(s->mesh->h.n_cells);
+  const int nloc = kTile + static_cast<int>(R.nh4_max);
+  const size_t smem = (8 * static_cast<size_t>(nloc) + R.ne4_max) * sizeof(double);
+  morpho_flux<<<s->list.n, kTile, smem, st>>>(a, nloc);
+  const int nb = (a.n_cells + 255) / 256;
+  morpho_apply<<<nb, 256, 0, st>>>(s->mo_dz.p, s->mo_dt.p, s->ctl, s->b64.z.p, s->b64.H[0].p, s->b64.H[1].p,
+                                   a.n_cells);
+}
+
 void launch_state(bm_state* s, cudaStream_t st, int prime) {
+  if (!prime && s->morpho) morpho_save_dt<<<1, 32, 0, st>>>(s->ctl, s->mo_dt.p);
   if (!prime && s->n_src > 0) {
     if (s->prec == BM_FP64)
       source_rates<double><<<1, 128, 0, st>>>(s->ctl, s->n_src, s->src_kind.p, s->src_off.p, s->src_t.p, s->src_v.p,
@@ -333,6 +362,7 @@ void launch_state(bm_state* s, cudaStream_t st, int prime) {
     if (s->prec == BM_FP64) launch_species<double>(s, st);
     else launch_species<float>(s, st);
   }
+  if (!prime && s->morpho) launch_morpho(s, st);
 }
 
 bm_status get_graph(bm_state* s, int k, cudaGraphExec_t* out) {
@@ -1044,6 +1074,51 @@ bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* re
   return BM_OK;
 }
 
+bm_status bm_state_set_morpho(bm_state* s, int32_t on, double porosity, double s_rel, double d, double alpha,
+                              double m, double theta_cr) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_set_morpho: state is NULL");
+  if (on) {
+    if (s->prec != BM_FP64) return fail(BM_EINVAL, "bm_state_set_morpho: morphodynamics needs an FP64 state");
+    if (!(porosity >= 0.0 && porosity < 1.0) || !(s_rel > 1.0) || !(d > 0.0) || !(alpha >= 0.0) || !(m >= 1.0) ||
+        !std::isfinite(theta_cr) || !std::isfinite(d) || !std::isfinite(alpha) || !std::isfinite(m) ||
+        !std::isfinite(s_rel))
+      return fail(BM_EINVAL,
+                  "bm_state_set_morpho: need 0 <= porosity < 1, s > 1, d > 0, alpha >= 0, m >= 1, finite theta_cr");
+  }
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  if (on) {
+    const size_t np = static_cast<size_t>(s->mesh->h.n_tiles) * kTile;
+    cudaError_t e = s->mo_dz.p ? cudaSuccess : s->mo_dz.alloc(np);
+    if (e == cudaSuccess && !s->mo_dt.p) e = s->mo_dt.alloc(1);
+    if (e == cudaSuccess) e = cudaMemset(s->mo_dz.p, 0, s->mo_dz.bytes());
+    if (e != cudaSuccess) return dev_fail(e, "bm_state_set_morpho");
+    const double par[6] = {porosity, s_rel, d, alpha, m, theta_cr};
+    for (int k = 0; k < 6; ++k) s->mo_par[k] = par[k];
+  }
+  s->morpho = on != 0;
+  drop_graphs(s);  // the launch sequence changes
+  return BM_OK;
+}
+
+bm_status bm_state_download_bed(bm_state* s, double* z) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_download_bed: state is NULL");
+  if (!z) return fail(BM_EINVAL, "bm_state_download_bed: z is NULL");
+  const int n = static_cast<int>(s->mesh->h.n_cells);
+  const int nb = (n + 255) / 256;
+  if (s->prec == BM_FP64)
+    scatter_to_user<double><<<nb, 256, 0, s->stream>>>(s->b64.z.p, nullptr, s->mesh->perm.p, n, s->stage[0].p, 0.0);
+  else
+    scatter_to_user<float><<<nb, 256, 0, s->stream>>>(s->b32.z.p, nullptr, s->mesh->perm.p, n, s->stage[0].p,
+                                                       s->datum);
+  BM_CUDA(cudaGetLastError());
+  BM_CUDA(cudaMemcpyAsync(z, s->stage[0].p, static_cast<size_t>(n) * sizeof(double), cudaMemcpyDeviceToHost,
+                          s->stream));
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  return BM_OK;
+}
+
 bm_status bm_state_stats(bm_state* s, double* t, double* dt_next, int64_t* steps, double* volume,
                          double* boundary_volume) {
   clear_error();
@@ -1195,6 +1270,7 @@ cudaError_t snapshot_buffers(Buffers<T>& b, Snapshot* sn, cudaStream_t st) {
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = sn->take(b.trk[k].p, b.trk[k].bytes(), st);
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = sn->take(b.hc[k].p, b.hc[k].bytes(), st);
   if (e == cudaSuccess) e = sn->take(b.zmask.p, b.zmask.bytes(), st);
+  if (e == cudaSuccess) e = sn->take(b.z.p, b.z.bytes(), st);  // the bed moves with morphodynamics
   return e;
 }
 

@@ -210,6 +210,8 @@ bm_status bm_batch_create(bm_state* const* states, int32_t n, bm_batch** out) {
   for (int k = 0; k < n; ++k) {
     if (!states[k]) return fail(BM_EINVAL, "bm_batch_create: NULL state");
     if (states[k]->prec != prec) return fail(BM_EINVAL, "bm_batch_create: members must share one precision");
+    if (states[k]->morpho)
+      return fail(BM_EINVAL, "bm_batch_create: a state with morphodynamics steps alone (bm_step)");
     if (states[k]->n_src > 0)
       return fail(BM_EINVAL, "bm_batch_create: a state with external sources steps alone (bm_step)");
     if (states[k]->n_species > 0)

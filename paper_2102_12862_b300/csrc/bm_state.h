@@ -193,6 +193,11 @@ struct bm_state {
   bm::DBuf<double> src_t, src_v, src_area, src_rate64;
   bm::DBuf<float> src_rate32;
   std::vector<uint8_t> src_tile;
+  // bed evolution (bm_state_set_morpho; FP64): parameters, per-cell bed change of the
+  // step, the dt of the step being taken
+  bool morpho = false;
+  double mo_par[6] = {};  // porosity, s, d, alpha, m, theta_cr
+  bm::DBuf<double> mo_dz, mo_dt;
   int n_species = 0;                    // passive species carried (0: none)
   double c_in[bm::kMaxSpecies] = {};    // their concentration in the inflow
   template <typename T>
