@@ -363,19 +363,21 @@ def measure_tracking(args, torch, bm, W):
     velocity, discharge and bed shear stress, updated in the step kernel) and with two
     passive species (one entering with the inflow at c = 1, one filling the initially
     wet river at c = 0.5; the step kernel exports its edge mass fluxes, the species
-    kernel advects them after each step) and with rain on a disk (a source region: the
-    rate kernel before each step, the S term in the step kernel)."""
+    kernel advects them after each step), with rain on a disk (a source region: the
+    rate kernel before each step, the S term in the step kernel) and, in FP64, with bed
+    evolution (sand: d = 1 mm, MPM-like closure; the bed-flux and update kernels)."""
     s = W.floodplain()
     mesh = bm.Mesh.from_scenario(s)
     h0 = np.maximum(s.H - s.z, 0.0)
     rain_region = W.disk_region(s, 2500.0, 1000.0, 500.0)
     out = {"workload": "floodplain 2,000,000 triangles, steps from t = 0, arrival threshold 0.05 m; "
-                       "2 passive species (inflow c = 1; river c = 0.5); rain 50 mm/h on a 500 m disk "
+                       "2 passive species (inflow c = 1; river c = 0.5); bed evolution (sand d = 1 mm, MPM-like, FP64); "
+                       "rain 50 mm/h on a 500 m disk "
                        f"({int((rain_region >= 0).sum())} cells, 9 % wet at t = 0)",
            "steps": args.track_steps}
     for prec in [p for p in args.precisions.split(",") if p]:
         res = {}
-        for mode in ("plain", "tracked", "species", "sources"):
+        for mode in ("plain", "tracked", "species", "sources") + (("morpho",) if prec == "fp64" else ()):
             st = bm.State.from_scenario(s, mesh=mesh, precision=prec)
             stream = torch.cuda.Stream()
             torch.cuda.set_stream(stream)
@@ -384,6 +386,8 @@ def measure_tracking(args, torch, bm, W):
                 st.track(0.05)
             elif mode == "species":
                 st.set_scalars(np.stack([np.zeros_like(h0), 0.5 * h0]), c_in=[1.0, 0.0])
+            elif mode == "morpho":
+                st.set_morpho(porosity=0.4, s=2.65, d=0.001, alpha=8.0, m=1.5, theta_cr=0.047)
             elif mode == "sources":
                 st.set_sources(rain_region, [bm.SOURCE_INTENSITY], [bm.SINK_EXACT],
                                [(np.array([0.0]), np.array([50.0]))])
@@ -410,6 +414,9 @@ def measure_tracking(args, torch, bm, W):
             "ms_per_step_2_species": res["species"], "overhead_2_species": res["species"] / res["plain"] - 1.0,
             "inflow_species_volume_m3": res["inflow_species_volume"],
             "ms_per_step_rain": res["sources"], "overhead_rain": res["sources"] / res["plain"] - 1.0}
+        if "morpho" in res:
+            out["fp64"].update({"ms_per_step_morpho": res["morpho"],
+                                "overhead_morpho": res["morpho"] / res["plain"] - 1.0})
     return out
 
 
@@ -634,7 +641,7 @@ def main():
         if lake is not None:
             line["wet_lake"] = lake
         if tracking is not None:
-            line["flood_tracking"] = tracking
+            line["optional_features"] = tracking
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
