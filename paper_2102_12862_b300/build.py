@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libbm.so")
 SOURCES = ["bm_api.cu", "bm_batch.cu", "bm_server.cu", "bm_mesh.cpp"]
-HEADERS = ["bm_internal.h", "bm_kernels.cuh", "bm_step.cuh", "bm_state.h", os.path.join("..", "..", "include", "bm.h")]
+HEADERS = sorted(f for f in os.listdir(os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc"))
+                 if f.endswith((".h", ".cuh"))) + [os.path.join("..", "..", "include", "bm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -335,7 +335,9 @@ void launch_morpho(bm_state* s, cudaStream_t st) {
   a.ctl = s->ctl;
   a.step_dt = s->mo_dt.p;
   a.dz = s->mo_dz.p;
-  a.mp = MorphoParams{s->mo_par[0], s->mo_par[1], s->mo_par[2], s->mo_par[3], s->mo_par[4], s->mo_par[5]};
+  const double* q = s->mo_par;
+  a.mp = MorphoParams{q[0], q[1], q[2], q[3], q[4], q[5], 1.0 / s->p.g, 1.0 / ((q[1] - 1.0) * q[2]),
+                      std::sqrt((q[1] - 1.0) * s->p.g * q[2] * q[2] * q[2]), 1.0 / (1.0 - q[0])};
   a.g = s->p.g;
   a.h_min = s->p.h_min;
   a.n_cells = static_cast<int>(s->mesh->h.n_cells);

@@ -19,6 +19,8 @@ namespace bm {
 
 struct MorphoParams {
   double porosity, s, d, alpha, m, theta_cr;
+  // derived on the host: 1 / g, 1 / ((s - 1) d), sqrt((s - 1) g d^3), 1 / (1 - porosity)
+  double inv_g, inv_sdd, scale, inv_solid;
 };
 
 struct MorphoArgs {
@@ -48,17 +50,30 @@ __device__ __forceinline__ void bedload(const MorphoArgs& a, double h, double qx
   by = 0.0;
   bd = 0.0;
   if (!(h > a.h_min)) return;
-  const double u = qx / h, v = qy / h;
+  // FP64 transcendentals are slow on this part: divisions as a times a refined
+  // reciprocal, h^(-1/3) by Newton steps, and for the usual exponent 3/2 the powers
+  // as x sqrt(x) and sqrt(x) (the library power for any other exponent)
+  const double rh = f_rcp(h);
+  const double u = qx * rh, v = qy * rh;
   const double sp = sqrt(u * u + v * v);
   if (sp == 0.0) return;
-  const double sd = a.mp.s - 1.0;
-  const double theta = (gn2 / a.g) * sp * sp / (sd * a.mp.d * cbrt(h));
+  const double theta = gn2 * a.mp.inv_g * sp * sp * f_rcbrt(h) * a.mp.inv_sdd;
   if (!(theta > a.mp.theta_cr)) return;
-  const double scale = sqrt(sd * a.g * a.mp.d * a.mp.d * a.mp.d);
-  const double qb = a.mp.alpha * pow(theta - a.mp.theta_cr, a.mp.m) * scale;
-  bx = qb * u / sp;
-  by = qb * v / sp;
-  bd = a.mp.alpha * a.mp.m * pow(theta - a.mp.theta_cr, a.mp.m - 1.0) * scale * (2.0 * theta / sp) / h;
+  const double scale = a.mp.scale;
+  const double x = theta - a.mp.theta_cr;
+  double xm, xm1;  // x^m, x^(m-1)
+  if (a.mp.m == 1.5) {
+    xm1 = sqrt(x);
+    xm = x * xm1;
+  } else {
+    xm = pow(x, a.mp.m);
+    xm1 = pow(x, a.mp.m - 1.0);
+  }
+  const double qb = a.mp.alpha * xm * scale;
+  const double rsp = f_rcp(sp);
+  bx = qb * u * rsp;
+  by = qb * v * rsp;
+  bd = a.mp.alpha * a.mp.m * xm1 * scale * (2.0 * theta * rsp) * rh;
 }
 
 // Eq. 16's two speeds for one cell on an edge.
@@ -96,6 +111,7 @@ __global__ void __launch_bounds__(kTile) morpho_flux(const MorphoArgs a, int nlo
   const double* eny = reinterpret_cast<const double*>(rec + RL::ny(ne4));
   const double* eln = reinterpret_cast<const double*>(rec + RL::len(ne4));
   const int po = a.ctl->parity ^ 1;  // U^n
+  bool wet = false;  // a tile or halo cell above h_min (else no edge of the tile moves sediment)
   for (int j = tid; j < kTile + nh; j += kTile) {
     const int g = j < kTile ? tile * kTile + j : hidx[j - kTile];
     double h = 0.0, u = 0.0, v = 0.0, c = 0.0, bx = 0.0, by = 0.0, bd = 0.0, zz = 0.0;
@@ -104,15 +120,23 @@ __global__ void __launch_bounds__(kTile) morpho_flux(const MorphoArgs a, int nlo
       h = a.H[po][g] - zz;
       const double qx = a.qx[po][g], qy = a.qy[po][g];
       if (h > a.h_min) {
-        u = qx / h;
-        v = qy / h;
+        const double rh = f_rcp(h);
+        u = qx * rh;
+        v = qy * rh;
+        wet = true;
+        bedload(a, h, qx, qy, a.gn2[g], bx, by, bd);
       }
-      c = sqrt(a.g * fmax(0.0, h));
-      bedload(a, h, qx, qy, a.gn2[g], bx, by, bd);
+      if (h > 0.0) c = sqrt(a.g * h);
     }
     sh[j] = h; su[j] = u; sv[j] = v; sc[j] = c; sbx[j] = bx; sby[j] = by; sbd[j] = bd; sz[j] = zz;
   }
-  __syncthreads();
+  const int i = tile * kTile + tid;
+  // every cell at or below h_min: u_n - c <= 0 and no bedload on both sides of every
+  // edge, so lambda+ = 0 and every flux of Eq. 14 is zero
+  if (!__syncthreads_or(wet)) {
+    if (i < a.n_cells) a.dz[i] = 0.0;
+    return;
+  }
   for (int k = tid; k < ne; k += kTile) {
     const uint32_t w = lr[k];
     const int lL = static_cast<int>(w & (kMaxLocal - 1));
@@ -121,19 +145,26 @@ __global__ void __launch_bounds__(kTile) morpho_flux(const MorphoArgs a, int nlo
     const double qL = sbx[lL] * nx + sby[lL] * ny;
     double f;
     if (R >= 0) {
-      double a1, a2, b1, b2;
-      morpho_speeds(su[lL] * nx + sv[lL] * ny, sc[lL], sbd[lL], a1, a2);
-      morpho_speeds(su[R] * nx + sv[R] * ny, sc[R], sbd[R], b1, b2);
-      const double lm = fmin(a1, b1), lp = fmax(a2, b2);
+      const double unL = su[lL] * nx + sv[lL] * ny, unR = su[R] * nx + sv[R] * ny;
       const double qR = sbx[R] * nx + sby[R] * ny;
-      f = lp - lm > 0.0 ? (lp * qL - lm * qR + lp * lm * (sz[R] - sz[lL])) / (lp - lm) : 0.0;
+      const double aL = unL - sc[lL], aR = unR - sc[R];
+      if (sbd[lL] == 0.0 && sbd[R] == 0.0 && qL == 0.0 && qR == 0.0 && !(fmin(aL, aR) < 0.0 && fmax(aL, aR) > 0.0)) {
+        // no transport on either side: Eq. 16 gives min(a, 0) and max(a, 0) exactly,
+        // so one of lambda+, lambda- is zero unless a changes sign across the edge
+        f = 0.0;
+      } else {
+        double a1, a2, b1, b2;
+        morpho_speeds(unL, sc[lL], sbd[lL], a1, a2);
+        morpho_speeds(unR, sc[R], sbd[R], b1, b2);
+        const double lm = fmin(a1, b1), lp = fmax(a2, b2);
+        f = lp - lm > 0.0 ? (lp * qL - lm * qR + lp * lm * (sz[R] - sz[lL])) * f_rcp(lp - lm) : 0.0;
+      }
     } else {
       f = R == kWall ? 0.0 : qL;
     }
     fs[k] = eln[k] * f;
   }
   __syncthreads();
-  const int i = tile * kTile + tid;
   if (i < a.n_cells) {
     const double ia = reinterpret_cast<const double*>(rec + RL::ia())[tid];
     const uint32_t sl = reinterpret_cast<const uint32_t*>(rec + RL::slot())[tid];
@@ -144,7 +175,7 @@ __global__ void __launch_bounds__(kTile) morpho_flux(const MorphoArgs a, int nlo
       const bool left = (lr[e] & (kMaxLocal - 1)) == static_cast<uint32_t>(tid);
       sum += left ? fs[e] : -fs[e];
     }
-    a.dz[i] = -(dt * ia * sum) / (1.0 - a.mp.porosity);
+    a.dz[i] = -(dt * ia * sum) * a.mp.inv_solid;
   }
 }
 
