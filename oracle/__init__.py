@@ -95,6 +95,10 @@ def _lib():
         lib.orc_bed_outflow.argtypes = [C.c_void_p]
         lib.orc_bed_outflow.restype = d
         lib.orc_bed.argtypes = [C.c_void_p, P(d)]
+        lib.orc_set_friction.argtypes = [C.c_void_p, C.c_int, P(d)]
+        lib.orc_set_friction.restype = C.c_int
+        lib.orc_cf.argtypes = [C.c_int, d, d]
+        lib.orc_cf.restype = d
         _libs["serial"] = lib
     return _libs["serial"]
 
@@ -202,6 +206,14 @@ class Oracle:
             raise OracleError(f"orc_set_morpho failed with code {rc}")
         self.morpho = bool(on)
 
+    def set_friction(self, law: int, coef):
+        """Friction closure of Table 1: 0 Manning (coef = n), 1 Chezy (coef = K_s),
+        2 Bezzola (coef = y_R); coef per cell."""
+        c = np.ascontiguousarray(np.broadcast_to(np.asarray(coef, dtype=np.float64), (self.n_cells,)))
+        rc = _lib().orc_set_friction(self._h, int(law), _dp(c))
+        if rc != 0:
+            raise OracleError(f"orc_set_friction failed with code {rc}")
+
     @property
     def bed_outflow(self) -> float:
         """Solid sediment volume that left through the boundary (negative: entered)."""
@@ -303,6 +315,11 @@ def friction(h, n, dt, qx, qy, g=9.81, h_min=1e-6):
     a, b = C.c_double(qx), C.c_double(qy)
     _lib().orc_friction(h, n, g, dt, h_min, C.byref(a), C.byref(b))
     return a.value, b.value
+
+
+def friction_cf(law, h, r):
+    """c_f of a Table 1 closure (1 Chezy with K_s = r, 2 Bezzola with y_R = r)."""
+    return _lib().orc_cf(int(law), float(h), float(r))
 
 
 def hydrograph(t_pts, q_pts, t):

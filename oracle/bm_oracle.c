@@ -86,6 +86,9 @@ typedef struct {
   double mp_p, mp_s, mp_d, mp_alpha, mp_m, mp_thcr;
   double *qbx, *qby, *qbd, *fb;
   double bed_bvol;
+  /* friction closure (orc_set_friction): 0 Manning (man = n), 1 Chezy (man = K_s),
+   * 2 Bezzola (man = y_R) */
+  int fr_law;
 } orc_mesh;
 
 /* ---------- mesh topology (independent, plain) ---------- */
@@ -312,6 +315,47 @@ void orc_friction(double h, double n, double g, double dt, double h_min, double*
   double q2x = q1x / (1 + dt * k1), q2y = q1y / (1 + dt * k1);
   *qx = 0.5 * (q0x + q2x);
   *qy = 0.5 * (q0y + q2y);
+}
+
+/*
+ * The friction closures of Table 1 as the dimensionless coefficient c_f of Eq. 2
+ * (S_f = u |u| / (g h c_f^2)): Chezy c_f = 6.25 + ln(h / K_s) for h > K_s, else 6.25;
+ * Bezzola c_f = 2.5 sqrt(1 - y_R / h) ln(10.9 h / y_R) for h / y_R > 2,
+ * 1.25 sqrt(h / y_R) ln(10.9 h / y_R) for 0.5 <= h / y_R <= 2, 1.5 below.  (Manning,
+ * c_f = h^(1/6) / (n sqrt(g)), and Strickler, the same with n = 1 / k_str, go through
+ * orc_friction's own form.)
+ */
+double orc_cf(int law, double h, double r) {
+  if (law == 1) return h > r ? 6.25 + log(h / r) : 6.25;
+  const double x = h / r;
+  if (x > 2.0) return 2.5 * sqrt(1.0 - r / h) * log(10.9 * h / r);
+  if (x >= 0.5) return 1.25 * sqrt(x) * log(10.9 * h / r);
+  return 1.5;
+}
+
+/* the friction split step of orc_friction with a Table 1 closure other than Manning:
+ * k(q) = |q| / (h^2 c_f^2), the same two semi-implicit stages */
+void orc_friction_cf(double h, double cf, double dt, double h_min, double* qx, double* qy) {
+  if (!(h > h_min)) return;
+  double c = 1.0 / (h * h * cf * cf);
+  double q0x = *qx, q0y = *qy;
+  double k0 = c * sqrt(q0x * q0x + q0y * q0y);
+  double q1x = q0x / (1 + dt * k0), q1y = q0y / (1 + dt * k0);
+  double k1 = c * sqrt(q1x * q1x + q1y * q1y);
+  double q2x = q1x / (1 + dt * k1), q2y = q1y / (1 + dt * k1);
+  *qx = 0.5 * (q0x + q2x);
+  *qy = 0.5 * (q0y + q2y);
+}
+
+/* select the friction closure; coef (n_cells, caller order) replaces the per-cell
+ * coefficient: n (Manning), K_s (Chezy) or y_R (Bezzola), all > 0 or 0 for none */
+int orc_set_friction(orc_mesh* m, int law, const double* coef) {
+  if (law < 0 || law > 2) return ORC_EINVAL;
+  for (int64_t i = 0; i < m->n_cells; ++i)
+    if (!(coef[i] >= 0)) return ORC_EINVAL;
+  memcpy(m->man, coef, sizeof(double) * (size_t)m->n_cells);
+  m->fr_law = law;
+  return ORC_OK;
 }
 
 /* cell velocity of the unmodified state: q/h where h > h_min, else 0 */
@@ -630,7 +674,10 @@ double orc_step(orc_mesh* m, double* H, double* qx, double* qy, double* t, doubl
       m->src_vol += m->area[i] * (Hn - Hf);
     }
     double h = Hn - m->z[i];
-    orc_friction(h, m->man[i], g, dt, hmin, &ux, &uy);
+    if (m->fr_law == 0)
+      orc_friction(h, m->man[i], g, dt, hmin, &ux, &uy);
+    else if (m->man[i] > 0 && h > hmin)
+      orc_friction_cf(h, orc_cf(m->fr_law, h, m->man[i]), dt, hmin, &ux, &uy);
     if (!(h > hmin)) { ux = 0; uy = 0; }
     H[i] = Hn; qx[i] = ux; qy[i] = uy;
   }

@@ -69,6 +69,12 @@ MORPHO_MUTANTS = [
     ("shields_depth_power", "(sd * d * cbrt(h))", "(sd * d * h)"),
 ]
 
+FRICTION_MUTANTS = [
+    ("chezy_constant", "return h > r ? 6.25 + log(h / r) : 6.25;", "return h > r ? 6.5 + log(h / r) : 6.25;"),
+    ("bezzola_branch", "if (x > 2.0) return", "if (x > 1.0) return"),
+    ("closure_cf_squared", "double c = 1.0 / (h * h * cf * cf);", "double c = 1.0 / (h * h * cf);"),
+]
+
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name,orig,mut,pins",
@@ -76,9 +82,10 @@ MORPHO_MUTANTS = [
                          + [m + ("test_oracle_tracking.py",) for m in TRACK_MUTANTS]
                          + [m + ("test_oracle_scalars.py",) for m in SCALAR_MUTANTS]
                          + [m + ("test_oracle_sources.py",) for m in SOURCE_MUTANTS]
-                         + [m + ("test_oracle_morpho.py",) for m in MORPHO_MUTANTS],
+                         + [m + ("test_oracle_morpho.py",) for m in MORPHO_MUTANTS]
+                         + [m + ("test_oracle_friction.py",) for m in FRICTION_MUTANTS],
                          ids=[m[0] for m in MUTANTS + TRACK_MUTANTS + SCALAR_MUTANTS + SOURCE_MUTANTS
-                              + MORPHO_MUTANTS])
+                              + MORPHO_MUTANTS + FRICTION_MUTANTS])
 def test_pins_catch_mutant(name, orig, mut, pins, tmp_path):
     src = open(SRC).read()
     assert src.count(orig) == 1, f"mutation site for {name} not unique"
