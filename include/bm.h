@@ -238,6 +238,19 @@ bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* re
  * dt saved before it; the bed fluxes, one CTA per tile, and the update after it).
  * Blocks.  bm_state_download_bed copies the bed elevation (caller order) to z.
  */
+/*
+ * Friction closure (Table 1, used in Eq. 2's S_f = u |u| / (g h c_f^2) by the split
+ * friction step): law 0 Manning with coef = n (the default, set from bm_params at
+ * init; Strickler is Manning with n = 1 / k_str), 1 Chezy with coef = K_s [m]
+ * (c_f = 6.25 + ln(h / K_s) for h > K_s, else 6.25), 2 Bezzola with coef = y_R [m]
+ * (c_f = 2.5 sqrt(1 - y_R/h) ln(10.9 h / y_R) for h / y_R > 2, 1.25 sqrt(h / y_R)
+ * ln(10.9 h / y_R) for 0.5 <= h / y_R <= 2, 1.5 below).  coef: n_cells values,
+ * caller order, finite and >= 0 (0: no friction in that cell).  Laws 1 and 2 run in
+ * the step kernel's optional-output instantiation; flood tracking and bed evolution
+ * take Manning's law only (BM_EINVAL either way round).  Blocks.
+ */
+bm_status bm_state_set_friction(bm_state* s, int32_t law, const double* coef);
+
 bm_status bm_state_set_morpho(bm_state* s, int32_t on, double porosity, double s_rel, double d, double alpha,
                               double m, double theta_cr);
 bm_status bm_state_download_bed(bm_state* s, double* z);

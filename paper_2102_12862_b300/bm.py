@@ -83,6 +83,7 @@ SIGNATURES = {
     "bm_state_set_sources": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "bm_state_set_morpho": (C.c_int, [_vp, C.c_int32, _d, _d, _d, _d, _d, _d]),
     "bm_state_download_bed": (C.c_int, [_vp, _vp]),
+    "bm_state_set_friction": (C.c_int, [_vp, C.c_int32, _vp]),
     "bm_server_opts_default": (None, [_P(bm_server_opts)]),
     "bm_server_create": (C.c_int, [_P(bm_server_opts), _P(_vp)]),
     "bm_server_destroy": (None, [_vp]),
@@ -262,6 +263,7 @@ def manning_from_strickler(k_str):
     return 1.0 / np.asarray(k_str, dtype=np.float64)
 
 
+FRICTION_MANNING, FRICTION_CHEZY, FRICTION_BEZZOLA = 0, 1, 2
 SOURCE_TOTAL, SOURCE_INTENSITY = 0, 1          # kind: m^3/s over the region, mm/h
 SINK_EXACT, SINK_AVAILABLE, SINK_INFINITY = 0, 1, 2
 
@@ -474,6 +476,12 @@ class State:
         see bm_state_set_morpho), stepped with the water from now on (FP64 states)."""
         _check(load_library().bm_state_set_morpho(self.handle, int(on), float(porosity), float(s), float(d),
                                                   float(alpha), float(m), float(theta_cr)))
+
+    def set_friction(self, law: int, coef):
+        """Friction closure of Table 1: FRICTION_MANNING (coef = n), FRICTION_CHEZY
+        (coef = K_s), FRICTION_BEZZOLA (coef = y_R); coef scalar or per cell."""
+        c = np.ascontiguousarray(np.broadcast_to(np.asarray(coef, dtype=np.float64), (self.n_cells,)))
+        _check(load_library().bm_state_set_friction(self.handle, int(law), _dp(c)))
 
     def download_bed(self) -> np.ndarray:
         """The bed elevation z (caller cell order)."""

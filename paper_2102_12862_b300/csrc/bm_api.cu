@@ -217,7 +217,7 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
 
 bool state_has_extras(const bm_state* s) {
   const bool trk = s->prec == BM_FP64 ? s->b64.trk_t.p != nullptr : s->b32.trk_t.p != nullptr;
-  return trk || s->n_species > 0 || s->n_src > 0;
+  return trk || s->n_species > 0 || s->n_src > 0 || s->fr_law != 0;
 }
 
 // Resident CTAs per SM of the list's kernel (with or without tracking).
@@ -442,6 +442,7 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
     d.ex_dt = b.ex_dt.p;
     d.ex_stride = static_cast<int>(m->rec[sizeof(T) == 8 ? 0 : 1].ne4_max);
   }
+  d.fr_law = s->fr_law;
   if (s->n_src > 0) {
     d.src_reg = s->src_reg.p;
     d.src_mode = s->src_mode.p;
@@ -864,6 +865,7 @@ bm_status bm_state_track(bm_state* s, double h_arrival) {
   if (!s) return fail(BM_EINVAL, "bm_state_track: state is NULL");
   if (!std::isfinite(h_arrival) || h_arrival < 0.0)
     return fail(BM_EINVAL, "bm_state_track: h_arrival must be finite and >= 0");
+  if (s->fr_law != 0) return fail(BM_EINVAL, "bm_state_track: tracking takes Manning's law only");
   const HostMesh& h = s->mesh->h;
   const size_t Np = static_cast<size_t>(h.n_tiles) * kTile;
   cudaError_t e = s->prec == BM_FP64 ? s->b64.alloc_tracking(Np) : s->b32.alloc_tracking(Np);
@@ -1082,6 +1084,7 @@ bm_status bm_state_set_morpho(bm_state* s, int32_t on, double porosity, double s
   if (!s) return fail(BM_EINVAL, "bm_state_set_morpho: state is NULL");
   if (on) {
     if (s->prec != BM_FP64) return fail(BM_EINVAL, "bm_state_set_morpho: morphodynamics needs an FP64 state");
+    if (s->fr_law != 0) return fail(BM_EINVAL, "bm_state_set_morpho: morphodynamics takes Manning's law only");
     if (!(porosity >= 0.0 && porosity < 1.0) || !(s_rel > 1.0) || !(d > 0.0) || !(alpha >= 0.0) || !(m >= 1.0) ||
         !std::isfinite(theta_cr) || !std::isfinite(d) || !std::isfinite(alpha) || !std::isfinite(m) ||
         !std::isfinite(s_rel))
@@ -1100,6 +1103,43 @@ bm_status bm_state_set_morpho(bm_state* s, int32_t on, double porosity, double s
   }
   s->morpho = on != 0;
   drop_graphs(s);  // the launch sequence changes
+  return BM_OK;
+}
+
+bm_status bm_state_set_friction(bm_state* s, int32_t law, const double* coef) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_set_friction: state is NULL");
+  if (law < 0 || law > 2) return fail(BM_EINVAL, "bm_state_set_friction: law must be 0, 1 or 2");
+  if (!coef) return fail(BM_EINVAL, "bm_state_set_friction: coef is NULL");
+  const bool trk = s->prec == BM_FP64 ? s->b64.trk_t.p != nullptr : s->b32.trk_t.p != nullptr;
+  if (law != 0 && (trk || s->morpho))
+    return fail(BM_EINVAL, "bm_state_set_friction: tracking and morphodynamics take Manning's law only");
+  const HostMesh& h = s->mesh->h;
+  const int64_t n = h.n_cells;
+  std::vector<double> v(static_cast<size_t>(h.n_tiles) * kTile, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    const double c = coef[h.perm[i]];
+    if (!(c >= 0.0) || !std::isfinite(c)) return fail(BM_EINVAL, "bm_state_set_friction: coef must be finite and >= 0");
+    v[i] = law == 0 ? s->prm.g * c * c : c;
+  }
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  cudaError_t e = s->prec == BM_FP64 ? cudaMemcpy(s->b64.gn2.p, v.data(), v.size() * sizeof(double),
+                                                  cudaMemcpyHostToDevice)
+                                     : cudaMemcpy(s->b32.gn2.p, narrow<float>(v).data(), v.size() * sizeof(float),
+                                                  cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return dev_fail(e, "bm_state_set_friction");
+  s->fr_law = law;
+  state_desc_bytes(s, &s->hdesc);
+  BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  const bool extra = state_has_extras(s);
+  if (extra != s->list.extra) {
+    s->list.extra = extra;
+    bm_status st = list_occupancy(s->prec, &s->list);
+    if (st != BM_OK) return st;
+    s->grid = step_grid(s->list, s->ctas_per_sm);
+  }
+  drop_graphs(s);
   return BM_OK;
 }
 

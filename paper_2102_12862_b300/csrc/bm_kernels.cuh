@@ -62,6 +62,9 @@ struct alignas(16) InstDesc {
   const int32_t* src_reg;
   const T* src_rate;
   const int32_t* src_mode;
+  // friction closure of Table 1: 0 Manning (gn2 = g n^2), 1 Chezy (gn2 holds K_s),
+  // 2 Bezzola (gn2 holds y_R)
+  int fr_law;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -584,6 +587,19 @@ __global__ void set_t_end(Ctl* ctl, double t_end) {
   ctl->dt_f = static_cast<float>(dt);
   ctl->clipped = clipped;
   ctl->active = t < t_end ? 1 : 0;
+}
+
+// The dimensionless friction coefficient c_f of Table 1's logarithmic closures (Eq. 2:
+// S_f = u |u| / (g h c_f^2)): Chezy (r = K_s) c_f = 6.25 + ln(h / K_s) for h > K_s,
+// else 6.25; Bezzola (r = y_R) 2.5 sqrt(1 - y_R / h) ln(10.9 h / y_R) for h / y_R > 2,
+// 1.25 sqrt(h / y_R) ln(10.9 h / y_R) for 0.5 <= h / y_R <= 2, 1.5 below.
+template <typename T>
+__device__ __forceinline__ T closure_cf(int law, T h, T r) {
+  if (law == 1) return h > r ? T(6.25) + log(h / r) : T(6.25);
+  const T x = h / r;
+  if (x > T(2)) return T(2.5) * sqrt(T(1) - r / h) * log(T(10.9) * h / r);
+  if (x >= T(0.5)) return T(1.25) * sqrt(x) * log(T(10.9) * h / r);
+  return T(1.5);
 }
 
 // External sources (Section "External inflow/outflow discharge"): S_h of every region

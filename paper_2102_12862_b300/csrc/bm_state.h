@@ -195,6 +195,7 @@ struct bm_state {
   std::vector<uint8_t> src_tile;
   // bed evolution (bm_state_set_morpho; FP64): parameters, per-cell bed change of the
   // step, the dt of the step being taken
+  int fr_law = 0;  // friction closure (bm_state_set_friction): 0 Manning, 1 Chezy, 2 Bezzola
   bool morpho = false;
   double mo_par[6] = {};  // porosity, s, d, alpha, m, theta_cr
   bm::DBuf<double> mo_dz, mo_dt;

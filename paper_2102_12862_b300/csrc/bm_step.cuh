@@ -787,8 +787,16 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
             // |q1| = |q*| / (1 + a), q2 = q1 / (1 + dt k(q1)) = q* / (1 + 2a); so
             // (q* + q2) / 2 = q* (1 + a) / (1 + 2a) -- one square root and one
             // division instead of two each (equal up to rounding)
-            const T r3 = f_rcbrt(h), r32 = r3 * r3;                      // h^(-1/3), h^(-2/3)
-            const T cf = gn2 * (r32 * r32 * r32 * r3);                    // g n^2 / h^(7/3)
+            T cf;  // k(q) / |q|: g n^2 / h^(7/3) (Manning), 1 / (h c_f)^2 (Table 1's log laws)
+            bool manning = true;
+            if constexpr (kExtra) manning = a.fr_law == 0;
+            if (manning) {
+              const T r3 = f_rcbrt(h), r32 = r3 * r3;  // h^(-1/3), h^(-2/3)
+              cf = gn2 * (r32 * r32 * r32 * r3);
+            } else {
+              const T hc = h * closure_cf<T>(a.fr_law, h, gn2);
+              cf = T(1) / (hc * hc);
+            }
             const T a1 = dt * (cf * f_sqrt(ux * ux + uy * uy));
             const T fr = f_div(T(1) + a1, T(1) + T(2) * a1);
             ux = ux * fr;
