@@ -87,3 +87,22 @@ def test_friction_api_rules():
     st.set_friction(bm.FRICTION_MANNING, 0.02)  # back to the default law
     st.track(0.1)
     st.step(5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_with_a_log_law_member_equals_solo(precision):
+    """A batch of a Chezy member, a Bezzola member and a Manning member steps each
+    bitwise as it steps alone (the descriptor carries the law)."""
+    scs = [W.dam_break(manning=0.02, seed=s) for s in (1, 2, 3)]
+    laws = [(bm.FRICTION_CHEZY, 0.05), (bm.FRICTION_BEZZOLA, 0.1), (bm.FRICTION_MANNING, 0.03)]
+    solo = [bm.State.from_scenario(s, precision=precision) for s in scs]
+    members = [bm.State.from_scenario(s, precision=precision) for s in scs]
+    for st_list in (solo, members):
+        for st, (law, r) in zip(st_list, laws):
+            st.set_friction(law, r)
+    for st in solo:
+        st.step(60)
+    bm.Batch(members).step(60)
+    for a, b in zip(solo, members):
+        for x, y in zip(a.download(), b.download()):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
