@@ -305,9 +305,8 @@ void orc_hllc(double hL, double uL, double vL, double hR, double uR, double vR, 
  * Euler stages combined as Heun's RK2: q1 = q0/(1+dt k(q0)), q2 = q1/(1+dt k(q1)),
  * q = (q0 + q2)/2.  Skipped when h <= h_min or n = 0.
  */
-void orc_friction(double h, double n, double g, double dt, double h_min, double* qx, double* qy) {
-  if (!(h > h_min) || n == 0) return;
-  double c = g * n * n / pow(h, 7.0 / 3.0);
+/* the two semi-implicit stages and their Heun average for dq/dt = -c |q| q */
+static void friction_stages(double c, double dt, double* qx, double* qy) {
   double q0x = *qx, q0y = *qy;
   double k0 = c * sqrt(q0x * q0x + q0y * q0y);
   double q1x = q0x / (1 + dt * k0), q1y = q0y / (1 + dt * k0);
@@ -315,6 +314,12 @@ void orc_friction(double h, double n, double g, double dt, double h_min, double*
   double q2x = q1x / (1 + dt * k1), q2y = q1y / (1 + dt * k1);
   *qx = 0.5 * (q0x + q2x);
   *qy = 0.5 * (q0y + q2y);
+}
+
+void orc_friction(double h, double n, double g, double dt, double h_min, double* qx, double* qy) {
+  if (!(h > h_min) || n == 0) return;
+  double c = g * n * n / pow(h, 7.0 / 3.0);
+  friction_stages(c, dt, qx, qy);
 }
 
 /*
@@ -338,13 +343,7 @@ double orc_cf(int law, double h, double r) {
 void orc_friction_cf(double h, double cf, double dt, double h_min, double* qx, double* qy) {
   if (!(h > h_min)) return;
   double c = 1.0 / (h * h * cf * cf);
-  double q0x = *qx, q0y = *qy;
-  double k0 = c * sqrt(q0x * q0x + q0y * q0y);
-  double q1x = q0x / (1 + dt * k0), q1y = q0y / (1 + dt * k0);
-  double k1 = c * sqrt(q1x * q1x + q1y * q1y);
-  double q2x = q1x / (1 + dt * k1), q2y = q1y / (1 + dt * k1);
-  *qx = 0.5 * (q0x + q2x);
-  *qy = 0.5 * (q0y + q2y);
+  friction_stages(c, dt, qx, qy);
 }
 
 /* select the friction closure; coef (n_cells, caller order) replaces the per-cell
