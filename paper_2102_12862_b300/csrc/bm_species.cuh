@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kTile) species_step(const SpeciesArgs<T> a, in
   if (!valid && (zm & 3u) == 3u) return;
   using RL = RecLayout<sizeof(T)>;
   extern __shared__ __align__(16) unsigned char smem_sp[];
-  T* hs = reinterpret_cast<T*>(smem_sp);  // h^n of the tile's and halo cells
+  T* hs = reinterpret_cast<T*>(smem_sp);  // 1 / h^n of the tile's and halo cells (0 where dry)
   T* ph = hs + nloc_max;                   // phi of the species being advected
   T* fs = ph + nloc_max;                   // its edge fluxes
   const PipeItem& it = a.items[blockIdx.x];
@@ -69,9 +69,12 @@ __global__ void __launch_bounds__(kTile) species_step(const SpeciesArgs<T> a, in
     return depth_of(a.H[buf][g], lo, a.z[g]);
   };
   auto cell = [&](int j) -> int { return j < kTile ? tile * kTile + j : hidx[j - kTile]; };
+  // one reciprocal per cell for all species (FP64 division is slow on this part: a
+  // Newton-refined hardware reciprocal, within 2 ulp of the quotient)
   for (int j = tid; j < kTile + nh; j += kTile) {
     const int g = cell(j);
-    hs[j] = g < a.n_cells ? depth(po, g) : T(0);
+    const T h = g < a.n_cells ? depth(po, g) : T(0);
+    hs[j] = h > T(0) ? f_div(T(1), h) : T(0);
   }
   const int i = tile * kTile + tid;
   const bool own = i < a.n_cells;
@@ -88,8 +91,8 @@ __global__ void __launch_bounds__(kTile) species_step(const SpeciesArgs<T> a, in
   for (int c = 0; c < a.n_species; ++c) {
     for (int j = tid; j < kTile + nh; j += kTile) {
       const int g = cell(j);
-      const T h = hs[j];
-      ph[j] = (g < a.n_cells && h > T(0)) ? a.hc[c][po][g] / h : T(0);
+      const T rh = hs[j];
+      ph[j] = (g < a.n_cells && rh > T(0)) ? a.hc[c][po][g] * rh : T(0);
     }
     __syncthreads();
     for (int k = tid; k < ne; k += kTile) {
