@@ -85,12 +85,13 @@ int step_smem_limit() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, step_pipe<T, false>);
+    cudaFuncGetAttributes(&fa, step_pipe<T, 0>);
     const int l = optin - static_cast<int>(fa.sharedSizeBytes);
-    if (cudaFuncSetAttribute(step_pipe<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, l) != cudaSuccess ||
-        cudaFuncSetAttribute(step_pipe<T, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess ||
-        cudaFuncSetAttribute(step_pipe<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, l) != cudaSuccess ||
-        cudaFuncSetAttribute(step_pipe<T, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) {
+    bool ok = true;
+    for (auto k : {step_pipe<T, 0>, step_pipe<T, 1>, step_pipe<T, 2>})
+      ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, l) == cudaSuccess &&
+           cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
+    if (!ok) {
       (void)cudaGetLastError();  // leave no sticky error behind; launches check the size
       return 48 * 1024 - static_cast<int>(fa.sharedSizeBytes);
     }
@@ -210,14 +211,21 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
   out->smem = prec == BM_FP64 ? StepLayout<double>(ne4, nh4).total : StepLayout<float>(ne4, nh4).total;
   const int lim = prec == BM_FP64 ? step_smem_limit<double>() : step_smem_limit<float>();
   if (out->smem > static_cast<size_t>(lim)) return fail(BM_EINVAL, "tile layout exceeds the device's shared memory");
-  out->extra = false;
-  for (bm_state* m : members) out->extra |= state_has_extras(m);
+  out->extra = 0;
+  for (bm_state* m : members) out->extra = std::max(out->extra, state_extra_level(m));
   return list_occupancy(prec, out);
 }
 
-bool state_has_extras(const bm_state* s) {
+int state_extra_level(const bm_state* s) {
+  if (s->n_src > 0 || s->fr_law != 0) return 2;
   const bool trk = s->prec == BM_FP64 ? s->b64.trk_t.p != nullptr : s->b32.trk_t.p != nullptr;
-  return trk || s->n_species > 0 || s->n_src > 0 || s->fr_law != 0;
+  return (trk || s->n_species > 0) ? 1 : 0;
+}
+
+// The step kernel of a feature level.
+template <typename T>
+auto step_kernel(int level) {
+  return level >= 2 ? step_pipe<T, 2> : (level == 1 ? step_pipe<T, 1> : step_pipe<T, 0>);
 }
 
 // Resident CTAs per SM of the list's kernel (with or without tracking).
@@ -226,10 +234,10 @@ bm_status list_occupancy(int prec, StepList* l) {
   cudaError_t e;
   if (prec == BM_FP64)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, l->extra ? step_pipe<double, true> : step_pipe<double, false>, kStepThreads, l->smem);
+        &occ, step_kernel<double>(l->extra), kStepThreads, l->smem);
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, l->extra ? step_pipe<float, true> : step_pipe<float, false>, kStepThreads, l->smem);
+        &occ, step_kernel<float>(l->extra), kStepThreads, l->smem);
   if (e != cudaSuccess) return dev_fail(e, "occupancy query");
   l->occupancy = std::max(1, occ);
   return BM_OK;
@@ -263,10 +271,10 @@ void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t 
   const int ne4 = static_cast<int>(l.ne4), nh4 = static_cast<int>(l.nh4);
   const PipeItem* items = static_cast<const PipeItem*>(l.items.p);
   if (prec == BM_FP64)
-    (void)cudaLaunchKernelEx(&cfg, l.extra ? step_pipe<double, true> : step_pipe<double, false>, items, l.n,
+    (void)cudaLaunchKernelEx(&cfg, step_kernel<double>(l.extra), items, l.n,
                              l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime);
   else
-    (void)cudaLaunchKernelEx(&cfg, l.extra ? step_pipe<float, true> : step_pipe<float, false>, items, l.n,
+    (void)cudaLaunchKernelEx(&cfg, step_kernel<float>(l.extra), items, l.n,
                              l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime);
 }
 
@@ -884,8 +892,8 @@ bm_status bm_state_track(bm_state* s, double h_arrival) {
   BM_CUDA(cudaGetLastError());
   BM_CUDA(cudaStreamSynchronize(s->stream));
   // from now on the state's launches run the tracking kernel
-  if (!s->list.extra) {
-    s->list.extra = true;
+  if (state_extra_level(s) != s->list.extra) {
+    s->list.extra = state_extra_level(s);
     bm_status st = list_occupancy(s->prec, &s->list);
     if (st != BM_OK) return st;
     s->grid = step_grid(s->list, s->ctas_per_sm);
@@ -969,7 +977,7 @@ bm_status bm_state_set_scalars(bm_state* s, int32_t n_species, const double* hc,
   BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
   BM_CUDA(cudaStreamSynchronize(s->stream));
   // the launch sequence changes (kernel instantiation, species kernel after each step)
-  const bool extra = state_has_extras(s);
+  const int extra = state_extra_level(s);
   if (extra != s->list.extra) {
     s->list.extra = extra;
     bm_status st = list_occupancy(s->prec, &s->list);
@@ -1132,7 +1140,7 @@ bm_status bm_state_set_friction(bm_state* s, int32_t law, const double* coef) {
   state_desc_bytes(s, &s->hdesc);
   BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
   BM_CUDA(cudaStreamSynchronize(s->stream));
-  const bool extra = state_has_extras(s);
+  const int extra = state_extra_level(s);
   if (extra != s->list.extra) {
     s->list.extra = extra;
     bm_status st = list_occupancy(s->prec, &s->list);

@@ -150,8 +150,8 @@ struct StepList {
   uint32_t ne4 = 4, nh4 = 4;
   size_t smem = 0;
   int occupancy = 1;  // resident CTAs per SM at this shared-memory size
-  bool extra = false;  // a member keeps a flood-tracking record or passive species
-                       // (the step kernel with the optional outputs)
+  int extra = 0;  // the step kernel's feature level the members need (0 none; 1 tracking or
+                 // species; 2 also sources or log-law friction)
 };
 }  // namespace bm
 
@@ -232,8 +232,8 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
                           StepList* out);
 // Grid of a step launch for a launch shape (ctas_per_sm = 0: all that fit).
 bm_status list_occupancy(int prec, StepList* l);
-// The state needs the step kernel with the optional outputs (tracking or species).
-bool state_has_extras(const bm_state* s);
+// The step kernel's feature level a state needs (see StepList::extra).
+int state_extra_level(const bm_state* s);
 int step_grid(const StepList& l, int ctas_per_sm);
 void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st);
 }  // namespace bm

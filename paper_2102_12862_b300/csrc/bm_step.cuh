@@ -317,15 +317,17 @@ constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M flood
 // n_items.  ne4max / nh4max: the largest record of the list (they fix the
 // shared-memory layout).  A single state is a list of one instance's tiles, so a run
 // executes the same machine code alone and in a batch and gives bitwise the same
-// result.  kExtra: the instantiation with the optional outputs -- it updates the
-// flood-tracking records and exports each tile's edge mass fluxes for the passive
-// species of the instances that have them (launched only when one does; the other
-// carries none of that code).
-template <typename T, bool kExtra>
+// result.  kX: which optional features the instantiation carries -- 0 none; 1 the
+// flood-tracking records and the edge mass fluxes exported for passive species; 2 also
+// external sources and the logarithmic friction closures (a list launches the lowest
+// level its members need, so the plain step carries none of that code).
+template <typename T, int kX>
 __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const PipeItem* __restrict__ items,
                                                                          int n_items, int* __restrict__ sched,
                                                                          int* __restrict__ early, int* __restrict__ mark,
                                                                          int ne4max, int nh4max, int prime) {
+  constexpr bool kExtra = kX >= 1;  // tracking, species exports
+  constexpr bool kFull = kX >= 2;   // sources, log-law friction
   using SL = StepLayout<T>;
   using RL = RecLayout<SL::S>;
   constexpr bool kPair = !SL::k64;
@@ -714,7 +716,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       }
       const int dst = par ^ 1;
       int src = -1;  // the cell's source region
-      if constexpr (kExtra) {
+      if constexpr (kFull) {
         if (a.src_reg != nullptr) src = a.src_reg[i];
       }
       if (quiet || (src < 0 && !prime && skip[idx[0]] && skip[idx[1]] && skip[idx[2]] && dry[tid] && is_zero(qxi) &&
@@ -765,7 +767,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           }
           ux = qxi - r * s1;
           uy = qyi - r * s2;
-          if constexpr (kExtra) {
+          if constexpr (kFull) {
             // external source / sink, explicit in continuity (the S term of Eq. 12)
             if (src >= 0) {
               const T add = dt * a.src_rate[src];
@@ -789,7 +791,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
             // division instead of two each (equal up to rounding)
             T cf;  // k(q) / |q|: g n^2 / h^(7/3) (Manning), 1 / (h c_f)^2 (Table 1's log laws)
             bool manning = true;
-            if constexpr (kExtra) manning = a.fr_law == 0;
+            if constexpr (kFull) manning = a.fr_law == 0;
             if (manning) {
               const T r3 = f_rcbrt(h), r32 = r3 * r3;  // h^(-1/3), h^(-2/3)
               cf = gn2 * (r32 * r32 * r32 * r3);
