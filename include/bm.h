@@ -246,8 +246,9 @@ bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* re
  * (c_f = 2.5 sqrt(1 - y_R/h) ln(10.9 h / y_R) for h / y_R > 2, 1.25 sqrt(h / y_R)
  * ln(10.9 h / y_R) for 0.5 <= h / y_R <= 2, 1.5 below).  coef: n_cells values,
  * caller order, finite and >= 0 (0: no friction in that cell).  Laws 1 and 2 run in
- * the step kernel's optional-output instantiation; flood tracking and bed evolution
- * take Manning's law only (BM_EINVAL either way round).  Blocks.
+ * the step kernel's optional-feature instantiation; flood tracking records the bed
+ * shear stress of the law in force (rho u^2 / c_f^2); bed evolution takes Manning's law
+ * only (BM_EINVAL either way round).  Blocks.
  */
 bm_status bm_state_set_friction(bm_state* s, int32_t law, const double* coef);
 

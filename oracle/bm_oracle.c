@@ -718,7 +718,7 @@ int64_t orc_run(orc_mesh* m, double* H, double* qx, double* qy, double* t, doubl
  *   h = H - z,  |q| = sqrt(qx^2 + qy^2),
  *   |u| = |q| / h and tau = rho g n^2 |u|^2 / h^(1/3) where h > h_min, else 0
  *   (Manning, Eq. 2 / Table 1: the bed shear stress rho g h S_f with
- *   S_f = n^2 |u|^2 / h^(4/3)),
+ *   S_f = n^2 |u|^2 / h^(4/3); under a logarithmic closure rho |u|^2 / c_f^2),
  *   arrival = the first t at which h > h_arr (NaN until then),
  *   the maxima of h, |u|, |q|, tau over the calls.
  * init != 0 starts the record from this state.
@@ -732,7 +732,12 @@ void orc_track(const orc_mesh* m, const double* H, const double* qx, const doubl
     double u = 0, tau = 0;
     if (h > hmin) {
       u = q / h;
-      tau = rho * g * m->man[i] * m->man[i] * u * u / cbrt(h);
+      if (m->fr_law == 0) {
+        tau = rho * g * m->man[i] * m->man[i] * u * u / cbrt(h);
+      } else { /* rho g h S_f = rho u^2 / c_f^2 (Eq. 2) with the law's c_f */
+        double cf = orc_cf(m->fr_law, h, m->man[i]);
+        tau = rho * u * u / (cf * cf);
+      }
     }
     if (init) {
       arr[i] = h > h_arr ? t : NAN;

@@ -873,7 +873,6 @@ bm_status bm_state_track(bm_state* s, double h_arrival) {
   if (!s) return fail(BM_EINVAL, "bm_state_track: state is NULL");
   if (!std::isfinite(h_arrival) || h_arrival < 0.0)
     return fail(BM_EINVAL, "bm_state_track: h_arrival must be finite and >= 0");
-  if (s->fr_law != 0) return fail(BM_EINVAL, "bm_state_track: tracking takes Manning's law only");
   const HostMesh& h = s->mesh->h;
   const size_t Np = static_cast<size_t>(h.n_tiles) * kTile;
   cudaError_t e = s->prec == BM_FP64 ? s->b64.alloc_tracking(Np) : s->b32.alloc_tracking(Np);
@@ -1119,9 +1118,8 @@ bm_status bm_state_set_friction(bm_state* s, int32_t law, const double* coef) {
   if (!s) return fail(BM_EINVAL, "bm_state_set_friction: state is NULL");
   if (law < 0 || law > 2) return fail(BM_EINVAL, "bm_state_set_friction: law must be 0, 1 or 2");
   if (!coef) return fail(BM_EINVAL, "bm_state_set_friction: coef is NULL");
-  const bool trk = s->prec == BM_FP64 ? s->b64.trk_t.p != nullptr : s->b32.trk_t.p != nullptr;
-  if (law != 0 && (trk || s->morpho))
-    return fail(BM_EINVAL, "bm_state_set_friction: tracking and morphodynamics take Manning's law only");
+  if (law != 0 && s->morpho)
+    return fail(BM_EINVAL, "bm_state_set_friction: morphodynamics takes Manning's law only");
   const HostMesh& h = s->mesh->h;
   const int64_t n = h.n_cells;
   std::vector<double> v(static_cast<size_t>(h.n_tiles) * kTile, 0.0);

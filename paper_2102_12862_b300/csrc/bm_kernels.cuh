@@ -318,14 +318,32 @@ __device__ __forceinline__ T cell_rate(const T* nxs, const T* nys, const T* ls, 
 // friction slope; |u| and the stress are 0 at or below h_min).
 constexpr double kRhoWater = 1000.0;  // density of water, kg / m^3
 
+// The dimensionless friction coefficient c_f of Table 1's logarithmic closures (Eq. 2:
+// S_f = u |u| / (g h c_f^2)): Chezy (r = K_s) c_f = 6.25 + ln(h / K_s) for h > K_s,
+// else 6.25; Bezzola (r = y_R) 2.5 sqrt(1 - y_R / h) ln(10.9 h / y_R) for h / y_R > 2,
+// 1.25 sqrt(h / y_R) ln(10.9 h / y_R) for 0.5 <= h / y_R <= 2, 1.5 below.
 template <typename T>
-__device__ __forceinline__ void track_values(T h, T qx, T qy, T gn2, T hmin, T& q, T& u, T& tau) {
+__device__ __forceinline__ T closure_cf(int law, T h, T r) {
+  if (law == 1) return h > r ? T(6.25) + log(h / r) : T(6.25);
+  const T x = h / r;
+  if (x > T(2)) return T(2.5) * sqrt(T(1) - r / h) * log(T(10.9) * h / r);
+  if (x >= T(0.5)) return T(1.25) * sqrt(x) * log(T(10.9) * h / r);
+  return T(1.5);
+}
+
+template <typename T>
+__device__ __forceinline__ void track_values(T h, T qx, T qy, T gn2, T hmin, int law, T& q, T& u, T& tau) {
   q = f_sqrt(qx * qx + qy * qy);
   u = T(0);
   tau = T(0);
   if (h > hmin) {
     u = f_div(q, h);
-    tau = static_cast<T>(kRhoWater) * gn2 * u * u * f_rcbrt(h);
+    if (law == 0) {
+      tau = static_cast<T>(kRhoWater) * gn2 * u * u * f_rcbrt(h);  // rho g n^2 u^2 / h^(1/3)
+    } else {
+      const T cf = closure_cf<T>(law, h, gn2);  // gn2 holds K_s or y_R
+      tau = static_cast<T>(kRhoWater) * u * u / (cf * cf);  // rho u^2 / c_f^2
+    }
   }
 }
 
@@ -342,11 +360,11 @@ __device__ __forceinline__ TrackRecord<T> track_load(const InstDesc<T>& a, int i
 }
 // Fold the cell's state U^{n+1} (depth h, discharge qx, qy) at time t into its record;
 // stores only what changes.
-template <typename T>
+template <typename T, bool kLaws>
 __device__ __forceinline__ void track_update(const InstDesc<T>& a, int i, const TrackRecord<T>& r, T h, T qx, T qy,
                                              T gn2, T hmin, double t) {
   T q, u, tau;
-  track_values<T>(h, qx, qy, gn2, hmin, q, u, tau);
+  track_values<T>(h, qx, qy, gn2, hmin, kLaws ? a.fr_law : 0, q, u, tau);
   if (isnan(r.t) && h > a.trk_harr) a.trk_t[i] = t;
   if (h > r.h) a.trk_h[i] = h;
   if (u > r.u) a.trk_u[i] = u;
@@ -365,7 +383,7 @@ __global__ void track_init(const InstDesc<T>* d, const Ctl* ctl, int n) {
   const T h = depth_of(a.H[par][i], lo, a.z[i]);
   const T hmin = sizeof(T) == 8 ? static_cast<T>(a.p.h_min) : static_cast<T>(a.p.hmin_f);
   T q, u, tau;
-  track_values<T>(h, a.qx[par][i], a.qy[par][i], a.gn2[i], hmin, q, u, tau);
+  track_values<T>(h, a.qx[par][i], a.qy[par][i], a.gn2[i], hmin, a.fr_law, q, u, tau);
   a.trk_t[i] = h > a.trk_harr ? ctl->t : static_cast<double>(NAN);
   a.trk_h[i] = h;
   a.trk_u[i] = u;
@@ -587,19 +605,6 @@ __global__ void set_t_end(Ctl* ctl, double t_end) {
   ctl->dt_f = static_cast<float>(dt);
   ctl->clipped = clipped;
   ctl->active = t < t_end ? 1 : 0;
-}
-
-// The dimensionless friction coefficient c_f of Table 1's logarithmic closures (Eq. 2:
-// S_f = u |u| / (g h c_f^2)): Chezy (r = K_s) c_f = 6.25 + ln(h / K_s) for h > K_s,
-// else 6.25; Bezzola (r = y_R) 2.5 sqrt(1 - y_R / h) ln(10.9 h / y_R) for h / y_R > 2,
-// 1.25 sqrt(h / y_R) ln(10.9 h / y_R) for 0.5 <= h / y_R <= 2, 1.5 below.
-template <typename T>
-__device__ __forceinline__ T closure_cf(int law, T h, T r) {
-  if (law == 1) return h > r ? T(6.25) + log(h / r) : T(6.25);
-  const T x = h / r;
-  if (x > T(2)) return T(2.5) * sqrt(T(1) - r / h) * log(T(10.9) * h / r);
-  if (x >= T(0.5)) return T(1.25) * sqrt(x) * log(T(10.9) * h / r);
-  return T(1.5);
 }
 
 // External sources (Section "External inflow/outflow discharge"): S_h of every region

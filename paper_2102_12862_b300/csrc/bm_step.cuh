@@ -817,7 +817,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           const T negtol = kPair ? hmin + T(4) * static_cast<T>(FLT_EPSILON) * fabs(zi) : hmin;
           if (h < -negtol) atomicOr(&a.ctl->status, 2);
           if constexpr (kExtra) {
-            if (trk) track_update<T>(a, i, rec, h, ux, uy, gn2, hmin, new_time(cs, 1));
+            if (trk) track_update<T, kFull>(a, i, rec, h, ux, uy, gn2, hmin, new_time(cs, 1));
           }
         }
         T u, v, c;

@@ -80,8 +80,6 @@ def test_friction_api_rules():
         st.set_friction(1, -1.0)
     st.set_friction(bm.FRICTION_CHEZY, 0.05)
     with pytest.raises(bm.BMError, match="Manning"):
-        st.track(0.1)
-    with pytest.raises(bm.BMError, match="Manning"):
         st.set_morpho()
     st.step(5)
     st.set_friction(bm.FRICTION_MANNING, 0.02)  # back to the default law
@@ -106,3 +104,22 @@ def test_batch_with_a_log_law_member_equals_solo(precision):
     for a, b in zip(solo, members):
         for x, y in zip(a.download(), b.download()):
             assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_tracking_under_a_log_law_fp64():
+    """Flood tracking on a dam break with Chezy friction: the record (shear stress
+    rho u^2 / c_f^2) matches the oracle's."""
+    s = W.dam_break(manning=0.02, seed=4)
+    st = bm.State.from_scenario(s)
+    o = oracle.Oracle(s)
+    for x in (st, o):
+        x.set_friction(bm.FRICTION_CHEZY, 0.01)
+        x.track(0.2)
+    st.step(200)
+    o.step(200)
+    g, r = st.download_track(), o.tracking
+    for k in ("h_max", "q_max"):
+        assert rel_linf(g[k], r[k]) <= 1e-11, k
+    for k in ("u_max", "tau_max"):
+        assert rel_linf(g[k], r[k]) <= 1e-9, k
+    assert g["tau_max"].max() > 0

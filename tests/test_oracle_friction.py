@@ -61,7 +61,8 @@ def test_one_step_in_a_box_is_the_friction_split(law, h, r):
 @pytest.mark.parametrize("law,r", [(1, 0.02), (2, 0.05)])
 def test_normal_depth_on_a_slope(law, r):
     """Uniform flow q = 2 m^2/s on S = 0.002: the depth settles where friction balances
-    gravity, q = h c_f(h) (g h S)^(1/2) (bisection here), within 2 %."""
+    gravity, q = h c_f(h) (g h S)^(1/2) (bisection here), within 2 %; the tracked bed shear stress rho u^2 / c_f^2 equals
+    rho g h S there within 5 %."""
     L, Wd, S, q = 1000.0, 20.0, 0.002, 2.0
     lo, hi = 1e-3, 10.0
     for _ in range(100):
@@ -82,3 +83,8 @@ def test_normal_depth_on_a_slope(law, r):
     o.run_until(1500.0)
     up = (c[:, 0] > 200) & (c[:, 0] < 600)
     assert abs(np.mean(o.depth()[up]) / hn - 1.0) < 0.02
+    # the tracked bed shear stress under the law: rho g h S in uniform flow
+    o.track(0.01)
+    o.run_until(1600.0)
+    tau = 1000.0 * G * hn * S
+    assert abs(np.mean(o.tracking["tau_max"][up]) / tau - 1.0) < 0.05
