@@ -10,8 +10,10 @@ modified-state bed treatment (Section "Numerical solution", "Hydrodynamics"),
 Manning friction (Eq. 2, Table 1) split off with a semi-implicit two-stage RK,
 and the time step of Eq. 21.
 
-Parity unpinned: the discharge-inflow distribution and the wet/dry threshold
-heuristics are pinned only by mass balance and agreement with the CUDA path.
+The discharge-inflow split and boundary wave speed are pinned by
+tests/test_oracle_inflow.py, the speeds of Eq. 16 by the coupled-system bracket in
+tests/test_oracle_morpho.py; the wet/dry threshold logic by Ritter's dry-bed dam
+break, the lake at rest with dry islands and wet/dry mass conservation.
 """
 from __future__ import annotations
 
@@ -99,6 +101,8 @@ def _lib():
         lib.orc_set_friction.restype = C.c_int
         lib.orc_cf.argtypes = [C.c_int, d, d]
         lib.orc_cf.restype = d
+        lib.orc_morpho_speeds.argtypes = [C.c_void_p, P(d), P(d), P(d), i64, d, d, P(d), P(d)]
+        lib.orc_morpho_speeds.restype = C.c_int
         _libs["serial"] = lib
     return _libs["serial"]
 
@@ -213,6 +217,16 @@ class Oracle:
         rc = _lib().orc_set_friction(self._h, int(law), _dp(c))
         if rc != 0:
             raise OracleError(f"orc_set_friction failed with code {rc}")
+
+    def morpho_speeds(self, i: int, nx: float, ny: float):
+        """Eq. 16's (lambda_1, lambda_2) of cell i for the unit normal (nx, ny) at the
+        current state, as the bed flux of the next step uses them (needs set_morpho)."""
+        a, b = C.c_double(), C.c_double()
+        rc = _lib().orc_morpho_speeds(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), int(i), float(nx), float(ny),
+                                      C.byref(a), C.byref(b))
+        if rc != 0:
+            raise OracleError("orc_morpho_speeds: bed evolution is off or the cell index is out of range")
+        return a.value, b.value
 
     @property
     def bed_outflow(self) -> float:

@@ -32,9 +32,11 @@
  * modified-state form, Toro wave speeds, h_min, friction stages, rho_ij, the
  * inflow distribution, wall mass flux exactly zero.
  *
- * Pinned by tests/test_oracle_*.py (closed forms, invariants, paper values).
- * The Q-inflow distribution and the threshold heuristics are "parity unpinned"
- * beyond mass balance.
+ * Pinned by tests/test_oracle_*.py (closed forms, invariants, paper values; the
+ * inflow split by a channel held at its normal flow and hand-computed boundary wave
+ * speeds; the speeds of Eq. 16 by the waves of the coupled shallow-water-Exner
+ * system); the wet/dry threshold logic by Ritter's dry-bed dam break, the lake at rest
+ * with dry islands and wet/dry mass conservation (h_min's value is a reading).
  */
 #include <math.h>
 #include <stdint.h>
@@ -365,6 +367,12 @@ static void cell_velocity(const orc_mesh* m, const double* H, const double* qx, 
   else { *u = 0; *w = 0; }
 }
 
+/* conveyance weight of an inflow edge of length l whose cell holds depth h: l h^(5/3)
+ * (Manning's uniform-flow discharge per unit width grows as h^(5/3)), 0 when dry */
+static double inflow_weight(double l, double h, double h_min) {
+  return h > h_min ? l * pow(h, 5.0 / 3.0) : 0.0;
+}
+
 /* inflow: unit discharge per inflow edge at time t, conveyance-weighted */
 static void inflow_discharge(orc_mesh* m, const double* H, double t) {
   double Q = orc_hydrograph(&m->p, t);
@@ -372,14 +380,13 @@ static void inflow_discharge(orc_mesh* m, const double* H, double t) {
   for (int64_t e = 0; e < m->n_edges; ++e) {
     if (m->eR[e] != -3) continue;
     double h = H[m->eL[e]] - m->z[m->eL[e]];
-    double w = h > m->p.h_min ? m->len[e] * pow(h, 5.0 / 3.0) : 0.0;
-    W += w;
+    W += inflow_weight(m->len[e], h, m->p.h_min);
   }
   for (int64_t e = 0; e < m->n_edges; ++e) {
     if (m->eR[e] != -3) { m->qin[e] = 0; continue; }
     double h = H[m->eL[e]] - m->z[m->eL[e]];
     if (W > 0) {
-      double w = h > m->p.h_min ? m->len[e] * pow(h, 5.0 / 3.0) : 0.0;
+      double w = inflow_weight(m->len[e], h, m->p.h_min);
       m->qin[e] = Q * w / (m->len[e] * W);
     } else {
       m->qin[e] = m->inflow_len > 0 ? Q / m->inflow_len : 0.0;
@@ -540,22 +547,27 @@ static void morpho_speeds(double un, double c, double dqb, double* l1, double* l
   *l2 = 0.5 * (a + r);
 }
 
+/* the speeds of Eq. 16 of cell i on an edge of unit normal (nx, ny): u_n = u.n and
+ * c = sqrt(g h) of the cell's own (unmodified) state, dq_B,n/dq_n from morpho_cells */
+static void cell_edge_speeds(const orc_mesh* m, const double* H, const double* qx, const double* qy, int64_t i,
+                             double nx, double ny, double* l1, double* l2) {
+  double u, v;
+  cell_velocity(m, H, qx, qy, i, &u, &v);
+  const double c = sqrt(m->p.g * fmax(0.0, H[i] - m->z[i]));
+  morpho_speeds(u * nx + v * ny, c, m->qbd[i], l1, l2);
+}
+
 /* l q_Bij of every edge (Eq. 14, 15), outward from the left cell */
 static void morpho_edges(orc_mesh* m, const double* H, const double* qx, const double* qy) {
-  const double g = m->p.g;
   for (int64_t e = 0; e < m->n_edges; ++e) {
     const int64_t L = m->eL[e], R = m->eR[e];
     const double nx = m->nx[e], ny = m->ny[e];
     const double qL = m->qbx[L] * nx + m->qby[L] * ny;
     double f;
     if (R >= 0) {
-      double uL, vL, uR, vR;
-      cell_velocity(m, H, qx, qy, L, &uL, &vL);
-      cell_velocity(m, H, qx, qy, R, &uR, &vR);
-      const double cL = sqrt(g * fmax(0.0, H[L] - m->z[L])), cR = sqrt(g * fmax(0.0, H[R] - m->z[R]));
       double a1, a2, b1, b2;
-      morpho_speeds(uL * nx + vL * ny, cL, m->qbd[L], &a1, &a2);
-      morpho_speeds(uR * nx + vR * ny, cR, m->qbd[R], &b1, &b2);
+      cell_edge_speeds(m, H, qx, qy, L, nx, ny, &a1, &a2);
+      cell_edge_speeds(m, H, qx, qy, R, nx, ny, &b1, &b2);
       const double lm = fmin(a1, b1), lp = fmax(a2, b2);
       const double qR = m->qbx[R] * nx + m->qby[R] * ny;
       f = lp - lm > 0 ? (lp * qL - lm * qR + lp * lm * (m->z[R] - m->z[L])) / (lp - lm) : 0.0;
@@ -859,6 +871,17 @@ double orc_next_dt(orc_mesh* m, const double* H, const double* qx, const double*
 }
 
 /* accessors for tests */
+
+/* Eq. 16's (lambda_1, lambda_2) of cell i for the unit normal (nx, ny) at the state
+ * (H, qx, qy), as the bed flux of a step from that state uses them (bed evolution must
+ * be on: orc_set_morpho).  Returns ORC_EINVAL when it is off or i is out of range. */
+int orc_morpho_speeds(orc_mesh* m, const double* H, const double* qx, const double* qy, int64_t i, double nx,
+                      double ny, double* l1, double* l2) {
+  if (!m->morpho || i < 0 || i >= m->n_cells) return ORC_EINVAL;
+  morpho_cells(m, H, qx, qy);
+  cell_edge_speeds(m, H, qx, qy, i, nx, ny, l1, l2);
+  return ORC_OK;
+}
 int64_t orc_n_edges(const orc_mesh* m) { return m->n_edges; }
 void orc_cell_area(const orc_mesh* m, double* out) { memcpy(out, m->area, m->n_cells * sizeof(double)); }
 void orc_edges(const orc_mesh* m, int64_t* L, int64_t* R, double* nx, double* ny, double* len) {

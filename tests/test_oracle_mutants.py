@@ -3,8 +3,9 @@ each one: a pin suite that passes a mutated oracle would not be pinning anything
 
 Each mutant is a one-token change of oracle/bm_oracle.c compiled into a private
 library; the pin tests run against it in a subprocess and must fail.  The
-discharge-inflow boundary depth is not in the list: it is "parity unpinned"
-(only mass balance and agreement with the CUDA path check it).
+discharge-inflow boundary (its conveyance split, momentum flux, critical depth and
+wave speed) is caught by tests/test_oracle_inflow.py, the speeds of Eq. 16 by the
+coupled-system bracket in tests/test_oracle_morpho.py.
 """
 import os
 import subprocess
@@ -67,6 +68,22 @@ MORPHO_MUTANTS = [
     ("bed_porosity", "* sum) / (1.0 - m->mp_p);", "* sum) / (1.0 + m->mp_p);"),
     ("bed_keeps_surface", "      H[i] += dz;", "      H[i] += 0.0 * dz;"),
     ("shields_depth_power", "(sd * d * cbrt(h))", "(sd * d * h)"),
+    ("eq16_root_sign", "const double r = sqrt(a * a + 4.0 * dqb * c * c);",
+     "const double r = sqrt(a * a - 4.0 * dqb * c * c);"),
+    ("eq16_root_factor", "const double r = sqrt(a * a + 4.0 * dqb * c * c);",
+     "const double r = sqrt(a * a + 2.0 * dqb * c * c);"),
+    ("eq16_celerity_sign", "const double a = un - c;", "const double a = un + c;"),
+    ("eq16_bedload_derivative", "(2.0 * theta / sp) / h;", "(theta / sp) / h;"),
+]
+
+# discharge inflow, caught by tests/test_oracle_inflow.py
+INFLOW_MUTANTS = [
+    ("inflow_weight_by_depth", "return h > h_min ? l * pow(h, 5.0 / 3.0) : 0.0;", "return h > h_min ? l * h : 0.0;"),
+    ("inflow_momentum_factor", "Gn = q * q / hb + 0.5 * g * hb * hb - p;", "Gn = q * q / hb + g * hb * hb - p;"),
+    ("inflow_wave_speed", "double lb = m->qin[e] / hb + sqrt(g * hb);", "double lb = sqrt(g * hb);"),
+    ("inflow_critical_depth", "double hcr = cbrt(q * q / g);", "double hcr = sqrt(q * q / g);"),
+    ("inflow_dry_split_per_edge", "m->qin[e] = m->inflow_len > 0 ? Q / m->inflow_len : 0.0;",
+     "m->qin[e] = m->inflow_len > 0 ? Q * m->len[e] / m->inflow_len : 0.0;"),
 ]
 
 FRICTION_MUTANTS = [
@@ -83,9 +100,10 @@ FRICTION_MUTANTS = [
                          + [m + ("test_oracle_scalars.py",) for m in SCALAR_MUTANTS]
                          + [m + ("test_oracle_sources.py",) for m in SOURCE_MUTANTS]
                          + [m + ("test_oracle_morpho.py",) for m in MORPHO_MUTANTS]
-                         + [m + ("test_oracle_friction.py",) for m in FRICTION_MUTANTS],
+                         + [m + ("test_oracle_friction.py",) for m in FRICTION_MUTANTS]
+                         + [m + ("test_oracle_inflow.py",) for m in INFLOW_MUTANTS],
                          ids=[m[0] for m in MUTANTS + TRACK_MUTANTS + SCALAR_MUTANTS + SOURCE_MUTANTS
-                              + MORPHO_MUTANTS + FRICTION_MUTANTS])
+                              + MORPHO_MUTANTS + FRICTION_MUTANTS + INFLOW_MUTANTS])
 def test_pins_catch_mutant(name, orig, mut, pins, tmp_path):
     src = open(SRC).read()
     assert src.count(orig) == 1, f"mutation site for {name} not unique"
