@@ -161,9 +161,10 @@ bm_status bm_state_download(bm_state* s, double* H, double* qx, double* qy, doub
  * kernel with every step from the call on, per cell: the water front arrival time
  * (the first t^{n+1} at which the depth h = H - z exceeds h_arrival; NaN until then)
  * and the running maxima of h, of the flow velocity |u| = |q| / h, of the specific
- * discharge |q| = sqrt(q_x^2 + q_y^2) and of the bed shear stress
- * rho g n^2 |u|^2 / h^(1/3) (Manning, Eq. 2; rho = 1000 kg/m^3; |u| and the stress
- * are 0 where h <= h_min).
+ * discharge |q| = sqrt(q_x^2 + q_y^2) and of the bed shear stress of the friction law
+ * in force (Eq. 2; rho = 1000 kg/m^3): rho g n^2 |u|^2 / h^(1/3) under Manning's law
+ * (law 0, the default), rho |u|^2 / c_f^2 under Chezy's or Bezzola's (laws 1 and 2, see
+ * bm_state_set_friction); |u| and the stress are 0 where h <= h_min.
  * bm_state_track starts (or restarts) the record from the current state: arrival = t
  * where h > h_arrival, maxima = the current values.  It allocates the five tracking
  * arrays on first use (5 values per cell) and blocks.  h_arrival must be finite and
@@ -272,6 +273,17 @@ bm_status bm_state_stats(bm_state* s, double* t, double* dt_next, int64_t* steps
  * state advances exactly as bm_step would.
  */
 bm_status bm_step_timed(bm_state* s, int64_t n_steps, double* step_kernel_ms, double* total_ms);
+
+/*
+ * Diagnostics for tests of the failure path (the paper has no counterpart: the bounded
+ * waits belong to this library's step kernel): one step launch in
+ * which every CTA's copy warp withholds the halo copies of its first tile, so the
+ * compute warps' bounded wait for them runs out after about a second.  Every CTA then
+ * retires the copies it did issue and exits without writing the state; the call blocks
+ * and returns BM_ETIMEOUT with the state, time and step count unchanged.  The status
+ * stays set in the state: re-upload it (bm_state_upload) before stepping it again.
+ */
+bm_status bm_state_test_timeout(bm_state* s);
 
 /*
  * Launch shape of the state's step kernel, whose CTAs stay resident and loop over

@@ -62,6 +62,7 @@ SIGNATURES = {
     "bm_state_download": (C.c_int, [_vp, _P(_d), _P(_d), _P(_d), _P(_d)]),
     "bm_state_stats": (C.c_int, [_vp, _P(_d), _P(_d), _P(_i64), _P(_d), _P(_d)]),
     "bm_step_timed": (C.c_int, [_vp, _i64, _P(_d), _P(_d)]),
+    "bm_state_test_timeout": (C.c_int, [_vp]),
     "bm_state_set_launch": (C.c_int, [_vp, C.c_int]),
     "bm_batch_create": (C.c_int, [_P(_vp), C.c_int32, _P(_vp)]),
     "bm_batch_destroy": (None, [_vp]),
@@ -313,6 +314,12 @@ def bm_step_timed(state: int, n_steps: int) -> tuple[float, float]:
     return k.value, t.value
 
 
+def bm_state_test_timeout(state: int):
+    """One step launch whose bounded data wait runs out on purpose (diagnostics of the
+    failure path); raises BMError(BM_ETIMEOUT).  Re-upload the state afterwards."""
+    _check(load_library().bm_state_test_timeout(state))
+
+
 def bm_state_set_launch(state: int, ctas_per_sm: int):
     _check(load_library().bm_state_set_launch(state, int(ctas_per_sm)))
 
@@ -504,6 +511,9 @@ class State:
 
     def step_timed(self, n: int) -> tuple[float, float]:
         return bm_step_timed(self.handle, n)
+
+    def test_timeout(self):
+        bm_state_test_timeout(self.handle)
 
     def set_stream(self, stream_ptr: int):
         bm_state_set_stream(self.handle, stream_ptr)

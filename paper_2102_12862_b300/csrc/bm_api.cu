@@ -255,7 +255,7 @@ int step_grid(const StepList& l, int ctas_per_sm) {
 // Launched as a programmatic dependent of the previous kernel in the stream: its CTAs
 // may start while that kernel's last CTAs finish and wait (griddepcontrol.wait) before
 // touching anything the previous kernel writes.
-void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st) {
+void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st, int withhold) {
   if (l.n <= 0) return;
   grid = std::max(1, std::min(grid, l.n));
   cudaLaunchConfig_t cfg = {};
@@ -272,10 +272,10 @@ void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t 
   const PipeItem* items = static_cast<const PipeItem*>(l.items.p);
   if (prec == BM_FP64)
     (void)cudaLaunchKernelEx(&cfg, step_kernel<double>(l.extra), items, l.n,
-                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime);
+                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime, withhold);
   else
     (void)cudaLaunchKernelEx(&cfg, step_kernel<float>(l.extra), items, l.n,
-                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime);
+                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime, withhold);
 }
 
 namespace {
@@ -1193,6 +1193,15 @@ bm_status bm_state_stats(bm_state* s, double* t, double* dt_next, int64_t* steps
   if (steps) *steps = s->hctl->steps;
   if (boundary_volume) *boundary_volume = s->hctl->bvol;
   return BM_OK;
+}
+
+bm_status bm_state_test_timeout(bm_state* s) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_test_timeout: state is NULL");
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  launch_work(s->prec, s->list, s->grid, 0, s->stream, 1);
+  BM_CUDA(cudaGetLastError());
+  return read_status(s);
 }
 
 bm_status bm_step_timed(bm_state* s, int64_t n, double* step_kernel_ms, double* total_ms) {

@@ -235,5 +235,5 @@ bm_status list_occupancy(int prec, StepList* l);
 // The step kernel's feature level a state needs (see StepList::extra).
 int state_extra_level(const bm_state* s);
 int step_grid(const StepList& l, int ctas_per_sm);
-void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st);
+void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st, int withhold = 0);
 }  // namespace bm

@@ -320,12 +320,16 @@ constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M flood
 // result.  kX: which optional features the instantiation carries -- 0 none; 1 the
 // flood-tracking records and the edge mass fluxes exported for passive species; 2 also
 // external sources and the logarithmic friction closures (a list launches the lowest
-// level its members need, so the plain step carries none of that code).
+// level its members need, so the plain step carries none of that code).  withhold != 0
+// (diagnostics of the failure path only): every CTA's copy warp withholds group H of
+// its first tile, so the compute warps' bounded wait for it runs out; the launch then
+// takes the timeout path below (status bit 2, issued copies retired, no state written).
 template <typename T, int kX>
 __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const PipeItem* __restrict__ items,
                                                                          int n_items, int* __restrict__ sched,
                                                                          int* __restrict__ early, int* __restrict__ mark,
-                                                                         int ne4max, int nh4max, int prime) {
+                                                                         int ne4max, int nh4max, int prime,
+                                                                         int withhold) {
   constexpr bool kExtra = kX >= 1;  // tracking, species exports
   constexpr bool kFull = kX >= 2;   // sources, log-law friction
   using SL = StepLayout<T>;
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       if (__shfl_sync(0xffffffffu, free_slot, 0)) {
         if (pa.tile >= 0) {
           issue_a<T>(L, slot(a_next), pa, idx_a, pb.tile >= 0 ? pb.inst : -1, src, &mb_a[a_next % S], lane);
-          issue_h<T>(L, slot(a_next), pa, src, hv_a, &mb_h[a_next % S], lane);
+          if (!(withhold && a_next == 0)) issue_h<T>(L, slot(a_next), pa, src, hv_a, &mb_h[a_next % S], lane);
           // promote b (read one iteration ago); read its instance pointers and halo
           // indices (used at the next issue)
           if (pb.tile >= 0 && pb.inst != pa.inst) src = slice_src<T>(pb, lane);
@@ -537,7 +541,10 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
   volatile int* abort_flag = &s_abort;
   const int stamp = *reinterpret_cast<volatile int*>(&sched[2]);  // read before any item can finish
   int* next_early = early + static_cast<size_t>((stamp + 1) & 1) * n_items;
-  double rrun = 0.0;  // this CTA's max Eq. 21 rate over the current instance's tiles
+  // this CTA's max Eq. 21 rate over the current instance's tiles, in the working
+  // precision (FP32-bulk: no FP64 instruction per cell; the max of the floats, converted
+  // once, equals the max of the converted values)
+  T rrun = T(0);
   unsigned cnt = 0;   // tiles of the current instance this CTA completed
   int n_done = 0;     // FP64: tiles this CTA completed in the launch
   for (int k = 0;; ++k) {
@@ -822,7 +829,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         }
         T u, v, c;
         cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
-        if (h > hmin) rrun = fmax(rrun, static_cast<double>(cell_rate<T>(sNx, sNy, sLn, idx, u, v, c, ia, a.p.cfl_mode)));
+        if (h > hmin) rrun = fmax(rrun, cell_rate<T>(sNx, sNy, sLn, idx, u, v, c, ia, a.p.cfl_mode));
         // inflow cells: conveyance weight and depth of the new state
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -871,7 +878,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     }
     const bool leave = inf.next_inst != inf.inst;
     if (leave && cnt > 0) {
-      const double r = block_max_nonneg_all<kTile>(rrun, reinterpret_cast<unsigned long long*>(red));
+      const double r = block_max_nonneg_all<kTile>(static_cast<double>(rrun), reinterpret_cast<unsigned long long*>(red));
       int is_last = 0;
       if (tid == 0) {
         if (r > 0.0) atomicMax(&a.ctl->rmax_bits, static_cast<unsigned long long>(__double_as_longlong(r)));
@@ -883,7 +890,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         __threadfence();
         finalize_step<T>(a, cs, prime ? 0 : 1);
       }
-      rrun = 0.0;
+      rrun = T(0);
       cnt = 0;
     }
     // FP64: boundary, inflow and wet tiles are taken early in the next launch (only the

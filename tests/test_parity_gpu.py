@@ -199,3 +199,48 @@ def test_floodplain_full_size():
     st2.step(3)
     o2.step(3)
     compare(r, st2, o2)
+
+
+def test_floodplain_full_size_mid_run_window():
+    """The 2,000,000-cell floodplain mid-run (moving wet/dry fronts, the inflow at its
+    500 m^3/s plateau): the FP64 GPU run to t = 1,800 s is downloaded, the oracle
+    starts from that snapshot (same time, so the same Q(t)), and both take 20 steps;
+    every cell compared (h, hu, hv) at the 1e-11 bar."""
+    s = W.floodplain()
+    st = bm.State.from_scenario(s)
+    st.run_until(1800.0)
+    H, qx, qy, t = st.download()
+    assert t == 1800.0
+    wet = float(np.mean(H - s.z > 1e-6))
+    assert wet > 0.08, wet  # well past the initial 4 % wet channel
+    snap = s.copy()
+    snap.H, snap.qx, snap.qy = H, qx, qy
+    o = oracle.Oracle(snap)
+    o.t.value = t
+    st.step(20)
+    o.step(20)
+    compare(s, st, o)
+
+
+def test_non_finite_state_is_flagged_and_the_mesh_stays_usable():
+    """A total-discharge source of 1e308 m^3/s on one cell of 0.25 m^2 makes S_h overflow
+    to infinity: the step returns BM_ENONFINITE (the device's status word, no fault),
+    the state still downloads, and a fresh state on the same mesh steps and matches the
+    oracle."""
+    s = W.dam_break(manning=0.02)
+    mesh = bm.Mesh.from_scenario(s)
+    for prec in ("fp64", "fp32"):
+        st = bm.State.from_scenario(s, mesh=mesh, precision=prec)
+        region = np.full(s.n_cells, -1, np.int32)
+        region[1234] = 0
+        st.set_sources(region, [bm.SOURCE_TOTAL], [bm.SINK_EXACT], [(np.array([0.0]), np.array([1e308]))])
+        with pytest.raises(bm.BMError) as ei:
+            st.step(3)
+        assert ei.value.status == bm.BM_ENONFINITE, ei.value
+        H, qx, qy, t = st.download()
+        assert not np.isfinite(H[1234])
+        st.close()
+    st, o = bm.State.from_scenario(s, mesh=mesh), oracle.Oracle(s)
+    st.step(20)
+    o.step(20)
+    compare(s, st, o)

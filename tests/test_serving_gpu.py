@@ -6,6 +6,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 from paper_2102_12862_b300 import bm
 from paper_2102_12862_b300 import workloads as W
 
@@ -44,6 +45,18 @@ def test_results_same_alone_and_in_the_mix(precision):
         Hs, qxs, qys = solo(meshes[k], s, t_ends[k], precision)
         assert np.array_equal(H, Hs), f"run {k}: H differs from the solo run"
         assert np.array_equal(qx, qxs) and np.array_equal(qy, qys), f"run {k}: q differs"
+        # and the served result against the FP64 oracle run to the same end time:
+        # FP64 element by element (relative L-inf of h, hu, hv), FP32-bulk at its
+        # L1 depth bar
+        o = oracle.Oracle(s)
+        o.run_until(t_ends[k])
+        if precision == "fp64":
+            tol = 1e-11 if o.steps <= 400 else 1e-10
+            for a, b in ((H - s.z, o.depth()), (qx, o.qx), (qy, o.qy)):
+                assert np.max(np.abs(a - b)) <= tol * max(np.max(np.abs(b)), 1e-300), f"run {k} vs oracle"
+        else:
+            area = o.area()
+            assert np.sum(area * np.abs((H - s.z) - o.depth())) / area.sum() <= 1e-4, f"run {k} vs oracle"
     st = sv.stats()
     assert st["completed"] == len(scs) and st["running"] == 0 and st["queued"] == 0
     assert st["cell_updates"] > 0
