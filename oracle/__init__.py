@@ -103,6 +103,10 @@ def _lib():
         lib.orc_cf.restype = d
         lib.orc_morpho_speeds.argtypes = [C.c_void_p, P(d), P(d), P(d), i64, d, d, P(d), P(d)]
         lib.orc_morpho_speeds.restype = C.c_int
+        lib.orc_set_outflow.argtypes = [C.c_void_p, i64, P(d), P(d), d, d]
+        lib.orc_set_outflow.restype = C.c_int
+        lib.orc_boundary_discharge.argtypes = [C.c_void_p, P(d), d, P(d), P(d)]
+        lib.orc_boundary_discharge.restype = None
         _libs["serial"] = lib
     return _libs["serial"]
 
@@ -217,6 +221,26 @@ class Oracle:
         rc = _lib().orc_set_friction(self._h, int(law), _dp(c))
         if rc != 0:
             raise OracleError(f"orc_set_friction failed with code {rc}")
+
+    def set_outflow(self, hq_stage=(), hq_discharge=(), weir_crest: float = 0.0, weir_poleni: float = 0.0):
+        """Outflow laws of the h-Q edges (tag 3: rating curve through the (stage,
+        discharge) table) and of the weir edges (tag 4: crest elevation, Poleni
+        coefficient)."""
+        s_ = np.ascontiguousarray(hq_stage, dtype=np.float64)
+        q_ = np.ascontiguousarray(hq_discharge, dtype=np.float64)
+        if s_.shape != q_.shape:
+            raise OracleError("set_outflow: stage and discharge differ in length")
+        rc = _lib().orc_set_outflow(self._h, len(s_), _dp(s_), _dp(q_), float(weir_crest), float(weir_poleni))
+        if rc != 0:
+            raise OracleError(f"orc_set_outflow failed with code {rc}")
+
+    def boundary_discharge(self):
+        """Per edge, the unit discharge entering through an inflow edge and the one
+        leaving through an outflow edge at the current state (0 elsewhere)."""
+        ne = _lib().orc_n_edges(self._h)
+        qi, qo = np.empty(ne), np.empty(ne)
+        _lib().orc_boundary_discharge(self._h, _dp(self.H), self.t.value, _dp(qi), _dp(qo))
+        return qi, qo
 
     def morpho_speeds(self, i: int, nx: float, ny: float):
         """Eq. 16's (lambda_1, lambda_2) of cell i for the unit normal (nx, ny) at the

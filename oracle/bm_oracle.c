@@ -19,7 +19,8 @@
  *      flux (Toro 2001 ch. 10, named in the same subsection) in the edge frame,
  *      pre-balanced pressure correction 1/2 g h*^2 of each side.
  *   2. boundary edges: wall (mirror), transmissive (zero gradient), discharge
- *      inflow (Section "Boundary conditions": standard inflow / wall).
+ *      inflow, and the outflows h-Q relation (rating curve) and weir (Poleni)
+ *      (Section "Boundary conditions": standard inflow / outflow / wall).
  *   3. conservative update, Eq. 12.
  *   4. Manning friction (Eq. 2, Table 1) split off and integrated with a
  *      two-stage semi-implicit Runge-Kutta (Heun) step.
@@ -72,6 +73,13 @@ typedef struct {
   double *cL, *cR;       /* 3 per edge */
   double *qin;           /* per edge: imposed unit discharge on inflow edges */
   double inflow_len;     /* total length of the inflow boundary */
+  /* outflow boundaries (orc_set_outflow): the h-Q relation's table of stage (strictly
+   * increasing) and discharge (tag 3); the weir's crest elevation and Poleni
+   * coefficient (tag 4); per edge the unit discharge leaving through it */
+  int64_t hq_n;
+  double *hq_s, *hq_q;
+  double weir_crest, weir_mu;
+  double *qout;
   orc_params p;
   double *ht, *hq;
   /* external sources (orc_set_sources): region of each cell (-1: none); per region
@@ -111,6 +119,7 @@ void orc_destroy(orc_mesh* m) {
   free(m->eL); free(m->eR); free(m->nx); free(m->ny); free(m->len);
   free(m->area); free(m->z); free(m->man); free(m->cedge);
   free(m->cL); free(m->cR); free(m->qin); free(m->ht); free(m->hq);
+  free(m->qout); free(m->hq_s); free(m->hq_q);
   free(m->src_reg); free(m->src_kind); free(m->src_mode); free(m->src_off);
   free(m->src_t); free(m->src_v); free(m->src_area); free(m->src_rate);
   free(m->qbx); free(m->qby); free(m->qbd); free(m->fb);
@@ -122,7 +131,9 @@ void orc_destroy(orc_mesh* m) {
  * triangles, l_ij and n_ij (unit, pointing from i to j) per edge, |Omega_i| per
  * cell.  Clockwise triangles are reoriented; their edge tags follow the edges.
  * edge_tag[3t+k] tags edge (v_k, v_{k+1}) of the triangle as given: 0 wall,
- * 1 transmissive, 2 inflow.  Returns ORC_EINVAL on any malformed input.
+ * 1 transmissive, 2 inflow, 3 h-Q outflow, 4 weir outflow (their laws are set by
+ * orc_set_outflow; until then they let nothing out).  Returns ORC_EINVAL on any
+ * malformed input.
  */
 int orc_create(int64_t n_nodes, const double* xy, int64_t n_tri, const int32_t* tri,
                const double* z, const double* man, const uint8_t* edge_tag,
@@ -192,7 +203,8 @@ int orc_create(int64_t n_nodes, const double* xy, int64_t n_tri, const int32_t* 
   m->cL = (double*)malloc(3 * ne * sizeof(double));
   m->cR = (double*)malloc(3 * ne * sizeof(double));
   m->qin = (double*)calloc(ne, sizeof(double));
-  if (!m->eL || !m->eR || !m->nx || !m->ny || !m->len || !m->cL || !m->cR || !m->qin) {
+  m->qout = (double*)calloc(ne, sizeof(double));
+  if (!m->eL || !m->eR || !m->nx || !m->ny || !m->len || !m->cL || !m->cR || !m->qin || !m->qout) {
     free(v); free(tg); free(hs); orc_destroy(m); return ORC_ENOMEM;
   }
   int64_t e = 0;
@@ -219,7 +231,7 @@ int orc_create(int64_t n_nodes, const double* xy, int64_t n_tri, const int32_t* 
       m->cedge[3 * tr + kr] = e;
     } else {
       uint8_t tag = tg[3 * tl + kl];
-      if (tag > 2) rc = ORC_EINVAL;
+      if (tag > 4) rc = ORC_EINVAL;
       m->eR[e] = -1 - (int64_t)tag;
       if (tag == 2) m->inflow_len += l;
     }
@@ -400,9 +412,138 @@ static double inflow_depth(double hc, double q, double g) {
   return hc > hcr ? hc : hcr;
 }
 
+/*
+ * Outflow laws (Section "Boundary conditions", standard outflows; the appendix's
+ * parameter list: the h-Q relation's table, the weir's height and Poleni factor).
+ *
+ * h-Q relation: the discharge Q leaving through the whole h-Q boundary is the rating
+ * curve at its stage S, the length-weighted mean free surface over its edges whose
+ * cell is wet; Q is split over those edges like the inflow, by conveyance l h^(5/3).
+ * Rating curve: piecewise linear through (hq_s[k], hq_q[k]), constant beyond the ends.
+ *
+ * Weir: Poleni's law per unit crest width, q = (2/3) mu sqrt(2 g) eta^(3/2), with eta
+ * the head of the cell's free surface over the crest; a crest below the cell's bed is
+ * taken at the bed (free overfall), so eta never exceeds the depth.
+ *
+ * Either way the edge's flux is the physical flux of a boundary state that lets q leave
+ * (outflow_state): the depth h_b on the outgoing characteristic of the cell (Riemann
+ * invariant u_n + 2 sqrt(g h) of the cell, subcritical branch) that carries q at u_b =
+ * q / h_b, and the cell's tangential velocity: (q, q u_b + g h_b^2 / 2, q u_t), less
+ * the cell's own pressure g h^2 / 2 (pre-balanced form).  Water at rest sees a lower
+ * boundary depth and accelerates towards the outlet; water arriving faster than the law
+ * lets it out sees a higher one and is partly reflected.  An edge that lets nothing out
+ * (head at or below the crest, dry cell) is a wall.
+ */
+static double rating(const orc_mesh* m, double S) {
+  if (m->hq_n <= 0) return 0.0;
+  if (S <= m->hq_s[0]) return m->hq_q[0];
+  for (int64_t k = 1; k < m->hq_n; ++k) {
+    if (S <= m->hq_s[k]) {
+      double w = (S - m->hq_s[k - 1]) / (m->hq_s[k] - m->hq_s[k - 1]);
+      return m->hq_q[k - 1] + w * (m->hq_q[k] - m->hq_q[k - 1]);
+    }
+  }
+  return m->hq_q[m->hq_n - 1];
+}
+
+/* The boundary depth h_b of an outflow edge whose cell holds depth h and outward normal
+ * velocity un, for a unit discharge *q > 0 leaving: q / h_b + 2 sqrt(g h_b) = w with
+ * w = un + 2 sqrt(g h), on the subcritical branch (u_b <= sqrt(g h_b)).  *q is first
+ * capped at the critical discharge w^3 / (27 g), the largest the invariant admits (then
+ * h_b is the critical depth, (w / 3)^2 / g).  Returns h_b, or -1 if nothing can leave
+ * (w <= 0: then *q = 0).  Newton's method on s = sqrt(h_b), from the right of the root
+ * or stepping past it to the right (f(s) = 2 sqrt(g) s + q / s^2 - w is convex). */
+static double outflow_state(double h, double un, double g, double* q) {
+  const double w = un + 2.0 * sqrt(g * h), sg = sqrt(g);
+  if (!(w > 0)) { *q = 0; return -1.0; }
+  const double qmax = w * w * w / (27.0 * g);
+  if (*q >= qmax) { *q = qmax; return (w / 3.0) * (w / 3.0) / g; }
+  const double sm = cbrt(*q / sg); /* f's minimum */
+  double s = sqrt(h) > sm ? sqrt(h) : sm;
+  for (int it = 0; it < 100; ++it) {
+    double f = 2.0 * sg * s + *q / (s * s) - w;
+    double df = 2.0 * sg - 2.0 * *q / (s * s * s);
+    if (!(df > 0)) break;
+    double ds = f / df;
+    s -= ds;
+    if (fabs(ds) <= 1e-16 * s) break;
+  }
+  return s * s;
+}
+
+static double poleni(double mu, double g, double eta) {
+  return (2.0 / 3.0) * mu * sqrt(2.0 * g) * eta * sqrt(eta);
+}
+
+static void outflow_discharge(orc_mesh* m, const double* H) {
+  const double hmin = m->p.h_min;
+  double sl = 0, sH = 0, W = 0;
+  for (int64_t e = 0; e < m->n_edges; ++e) {
+    if (m->eR[e] != -4) continue;
+    int64_t i = m->eL[e];
+    double h = H[i] - m->z[i];
+    if (!(h > hmin)) continue;
+    sl += m->len[e];
+    sH += m->len[e] * H[i];
+    W += inflow_weight(m->len[e], h, hmin);
+  }
+  double Q = sl > 0 ? rating(m, sH / sl) : 0.0;
+  for (int64_t e = 0; e < m->n_edges; ++e) {
+    m->qout[e] = 0;
+    int64_t i = m->eL[e];
+    double h = H[i] - m->z[i];
+    if (!(h > hmin)) continue;
+    if (m->eR[e] == -4 && W > 0) {
+      m->qout[e] = Q * inflow_weight(m->len[e], h, hmin) / (m->len[e] * W);
+    } else if (m->eR[e] == -5) {
+      double crest = m->weir_crest > m->z[i] ? m->weir_crest : m->z[i];
+      double eta = H[i] - crest;
+      if (eta > 0) m->qout[e] = poleni(m->weir_mu, m->p.g, eta);
+    }
+  }
+}
+
+/*
+ * The outflow laws of a mesh with h-Q (tag 3) or weir (tag 4) edges: n_hq >= 2
+ * (stage, discharge) pairs, stage strictly increasing, discharge >= 0 (n_hq = 0: the
+ * h-Q edges let nothing out); the weir's crest elevation and Poleni coefficient
+ * mu >= 0.  Returns ORC_EINVAL on a malformed table.
+ */
+int orc_set_outflow(orc_mesh* m, int64_t n_hq, const double* stage, const double* q, double crest, double mu) {
+  if (n_hq < 0 || n_hq == 1 || !(mu >= 0) || !isfinite(crest)) return ORC_EINVAL;
+  for (int64_t k = 0; k < n_hq; ++k) {
+    if (!isfinite(stage[k]) || !(q[k] >= 0) || !isfinite(q[k])) return ORC_EINVAL;
+    if (k > 0 && !(stage[k] > stage[k - 1])) return ORC_EINVAL;
+  }
+  free(m->hq_s); free(m->hq_q);
+  m->hq_s = m->hq_q = NULL;
+  m->hq_n = 0;
+  if (n_hq > 0) {
+    m->hq_s = (double*)malloc(n_hq * sizeof(double));
+    m->hq_q = (double*)malloc(n_hq * sizeof(double));
+    if (!m->hq_s || !m->hq_q) return ORC_ENOMEM;
+    memcpy(m->hq_s, stage, n_hq * sizeof(double));
+    memcpy(m->hq_q, q, n_hq * sizeof(double));
+  }
+  m->hq_n = n_hq;
+  m->weir_crest = crest;
+  m->weir_mu = mu;
+  return ORC_OK;
+}
+
+/* unit discharge through every edge at the state H and time t (>0 entering on inflow
+ * edges, >0 leaving on outflow edges, 0 elsewhere) -- exported for the pins */
+void orc_boundary_discharge(orc_mesh* m, const double* H, double t, double* q_in, double* q_out) {
+  inflow_discharge(m, H, t);
+  outflow_discharge(m, H);
+  memcpy(q_in, m->qin, m->n_edges * sizeof(double));
+  memcpy(q_out, m->qout, m->n_edges * sizeof(double));
+}
+
 /* Eq. 21: dt = CFL * min_i min_j rho_ij / lambda_ij on wet cells (or, cfl_mode 1,
- * CFL * min_i |Omega_i| / sum_j l_ij lambda_ij); inflow edges add their own
- * boundary wave speed.  Returns +inf if nothing constrains dt.  Requires qin. */
+ * CFL * min_i |Omega_i| / sum_j l_ij lambda_ij); inflow and outflow edges add their
+ * own boundary wave speed.  Returns +inf if nothing constrains dt.  Requires qin and
+ * qout. */
 double orc_cfl(const orc_mesh* m, const double* H, const double* qx, const double* qy) {
   const double g = m->p.g;
   double best = INFINITY;
@@ -420,6 +561,19 @@ double orc_cfl(const orc_mesh* m, const double* H, const double* qx, const doubl
       if (m->eR[e] == -3 && m->qin[e] > 0) {
         double hb = inflow_depth(h > 0 ? h : 0.0, m->qin[e], g);
         double lb = m->qin[e] / hb + sqrt(g * hb);
+        if (m->p.cfl_mode == 0) {
+          double rho = 4.0 * m->area[i] / (3.0 * m->len[e]);
+          if (rho / lb < best) best = rho / lb;
+        } else {
+          double r = m->area[i] / (m->len[e] * lb);
+          if (r < best) best = r;
+        }
+      }
+      if ((m->eR[e] == -4 || m->eR[e] == -5) && m->qout[e] > 0) {
+        /* outflow edge: the boundary state's u_b + sqrt(g h_b) */
+        double q = m->qout[e];
+        double hb = outflow_state(h, u * nx + w * ny, g, &q);
+        double lb = hb > 0 ? q / hb + sqrt(g * hb) : 0.0;
         if (m->p.cfl_mode == 0) {
           double rho = 4.0 * m->area[i] / (3.0 * m->len[e]);
           if (rho / lb < best) best = rho / lb;
@@ -572,7 +726,7 @@ static void morpho_edges(orc_mesh* m, const double* H, const double* qx, const d
       const double qR = m->qbx[R] * nx + m->qby[R] * ny;
       f = lp - lm > 0 ? (lp * qL - lm * qR + lp * lm * (m->z[R] - m->z[L])) / (lp - lm) : 0.0;
     } else {
-      f = R == -1 ? 0.0 : qL; /* wall; transmissive / inflow: the inside cell's bedload */
+      f = R == -1 ? 0.0 : qL; /* wall; transmissive / inflow / outflow: the inside cell's bedload */
     }
     m->fb[e] = m->len[e] * f;
   }
@@ -607,6 +761,7 @@ double orc_step(orc_mesh* m, double* H, double* qx, double* qy, double* t, doubl
   if (!(*t < t_end)) return 0.0;
   /* 0. time step from U^n (Eq. 21) */
   inflow_discharge(m, H, *t);
+  outflow_discharge(m, H);
   double mcfl = orc_cfl(m, H, qx, qy);
   double dt = isinf(mcfl) ? m->p.dt_max : m->p.cfl * mcfl;
   if (dt > m->p.dt_max) dt = m->p.dt_max;
@@ -638,18 +793,25 @@ double orc_step(orc_mesh* m, double* H, double* qx, double* qy, double* t, doubl
       double hs = fmax(0.0, H[L] - m->z[L]);
       double p = 0.5 * g * hs * hs;
       double Fh, Gn, Ft;
-      if (R == -1) { /* wall: mirrored normal velocity, impermeable */
+      /* an outflow edge (h-Q, weir) lets q_e leave through its boundary state */
+      double qo = R <= -4 ? m->qout[e] : 0.0;
+      double hbo = qo > 0 ? outflow_state(hs, unL, g, &qo) : -1.0;
+      if (R == -1 || (R <= -4 && !(hbo > 0))) {
+        /* wall: mirrored normal velocity, impermeable (also an outflow edge that lets
+         * nothing out) */
         orc_hllc(hs, unL, utL, hs, -unL, utL, g, F);
         Fh = 0; Gn = F[1] - p; Ft = 0;
       } else if (R == -2) { /* transmissive: the outside state equals the inside state */
         orc_hllc(hs, unL, utL, hs, unL, utL, g, F);
         Fh = F[0]; Gn = F[1] - p; Ft = F[2];
-      } else { /* inflow: imposed unit discharge q_e entering along -n */
+      } else if (R == -3) { /* inflow: imposed unit discharge q_e entering along -n */
         double q = m->qin[e];
         if (q > 0) {
           double hb = inflow_depth(hs, q, g);
           Fh = -q; Gn = q * q / hb + 0.5 * g * hb * hb - p; Ft = 0;
         } else { Fh = 0; Gn = 0; Ft = 0; }
+      } else { /* outflow: q_e leaves along n at the boundary state's depth */
+        Fh = qo; Gn = qo * (qo / hbo) + 0.5 * g * hbo * hbo - p; Ft = qo * utL;
       }
       m->cL[3 * e] = l * Fh;
       m->cL[3 * e + 1] = l * (Gn * nx - Ft * ny);
@@ -785,7 +947,8 @@ int64_t orc_run_tracked(orc_mesh* m, double* H, double* qx, double* qy, double* 
  * F_c = F_h phi_c of the upwind side of the contact (S* >= 0: left) -- the scheme the
  * "Scalar advection-diffusion" numerics subsection names for the advective part.
  * phi_c = q_c / h where h = H - z > 0, else 0.  Walls carry nothing; a transmissive
- * edge carries F_h phi_c of the inside cell; an inflow edge brings q_e l c_in[c].
+ * edge carries F_h phi_c of the inside cell; an inflow edge brings q_e l c_in[c]; an
+ * outflow edge (h-Q, weir) takes q_e l phi_c of the inside cell.
  * A cell that ends the step dry (h <= 0) keeps no scalar.  One step of the water
  * (orc_step) and the species together; returns the number of steps taken.
  */
@@ -804,6 +967,7 @@ int64_t orc_run_scalars(orc_mesh* m, double* H, double* qx, double* qy, double* 
       for (int c = 0; c < K; ++c) phi[c * n + i] = h > 0 ? hc[c * n + i] / h : 0.0;
     }
     inflow_discharge(m, H, *t); /* q_e of this step (orc_step computes the same) */
+    outflow_discharge(m, H);
     for (int64_t e = 0; e < ne; ++e) {
       int64_t L = m->eL[e], R = m->eR[e];
       double nx = m->nx[e], ny = m->ny[e], l = m->len[e];
@@ -825,9 +989,11 @@ int64_t orc_run_scalars(orc_mesh* m, double* H, double* qx, double* qy, double* 
           double hs = fmax(0.0, H[L] - m->z[L]);
           orc_hllc(hs, unL, pL, hs, unL, pL, g, F);
           f = F[2];
-        } else {
+        } else if (R == -3) {
           double q = m->qin[e];
           f = q > 0 ? -q * c_in[c] : 0.0;
+        } else {
+          f = m->qout[e] * pL; /* outflow: the inside cell's scalar leaves with q_e */
         }
         fl[c * ne + e] = l * f;
       }
@@ -865,6 +1031,7 @@ double orc_volume(const orc_mesh* m, const double* H) {
 /* next dt that orc_step would take from this state (Eq. 21 with dt_max), no clipping */
 double orc_next_dt(orc_mesh* m, const double* H, const double* qx, const double* qy, double t) {
   inflow_discharge(m, H, t);
+  outflow_discharge(m, H);
   double mcfl = orc_cfl(m, H, qx, qy);
   double dt = isinf(mcfl) ? m->p.dt_max : m->p.cfl * mcfl;
   return dt > m->p.dt_max ? m->p.dt_max : dt;

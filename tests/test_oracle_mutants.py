@@ -4,8 +4,10 @@ each one: a pin suite that passes a mutated oracle would not be pinning anything
 Each mutant is a one-token change of oracle/bm_oracle.c compiled into a private
 library; the pin tests run against it in a subprocess and must fail.  The
 discharge-inflow boundary (its conveyance split, momentum flux, critical depth and
-wave speed) is caught by tests/test_oracle_inflow.py, the speeds of Eq. 16 by the
-coupled-system bracket in tests/test_oracle_morpho.py.
+wave speed) is caught by tests/test_oracle_inflow.py, the outflow laws (Poleni's weir,
+the h-Q split and rating curve, the characteristic boundary state) by
+tests/test_oracle_outflow.py, the speeds of Eq. 16 by the coupled-system bracket in
+tests/test_oracle_morpho.py.
 """
 import os
 import subprocess
@@ -86,6 +88,27 @@ INFLOW_MUTANTS = [
      "m->qin[e] = m->inflow_len > 0 ? Q * m->len[e] / m->inflow_len : 0.0;"),
 ]
 
+# outflow boundaries (h-Q relation, weir), caught by tests/test_oracle_outflow.py
+OUTFLOW_MUTANTS = [
+    ("weir_poleni_factor", "return (2.0 / 3.0) * mu * sqrt(2.0 * g) * eta * sqrt(eta);",
+     "return (1.0 / 3.0) * mu * sqrt(2.0 * g) * eta * sqrt(eta);"),
+    ("weir_gravity", "return (2.0 / 3.0) * mu * sqrt(2.0 * g) * eta * sqrt(eta);",
+     "return (2.0 / 3.0) * mu * sqrt(g) * eta * sqrt(eta);"),
+    ("weir_head_exponent", "return (2.0 / 3.0) * mu * sqrt(2.0 * g) * eta * sqrt(eta);",
+     "return (2.0 / 3.0) * mu * sqrt(2.0 * g) * eta * cbrt(eta);"),
+    ("weir_crest_below_bed", "double crest = m->weir_crest > m->z[i] ? m->weir_crest : m->z[i];",
+     "double crest = m->weir_crest;"),
+    ("outflow_invariant_factor", "const double w = un + 2.0 * sqrt(g * h), sg = sqrt(g);",
+     "const double w = un + sqrt(g * h), sg = sqrt(g);"),
+    ("outflow_critical_cap", "const double qmax = w * w * w / (27.0 * g);", "const double qmax = w * w * w / (8.0 * g);"),
+    ("outflow_wave_speed", "double lb = hb > 0 ? q / hb + sqrt(g * hb) : 0.0;", "double lb = hb > 0 ? sqrt(g * hb) : 0.0;"),
+    ("outflow_momentum_cell_depth", "Gn = qo * (qo / hbo) + 0.5 * g * hbo * hbo - p;", "Gn = qo * (qo / hs);"),
+    ("hq_uniform_split", "m->qout[e] = Q * inflow_weight(m->len[e], h, hmin) / (m->len[e] * W);",
+     "m->qout[e] = Q / sl;"),
+    ("rating_segment", "double w = (S - m->hq_s[k - 1]) / (m->hq_s[k] - m->hq_s[k - 1]);",
+     "double w = (S - m->hq_s[k - 1]) / (m->hq_s[k] - m->hq_s[0]);"),
+]
+
 FRICTION_MUTANTS = [
     ("chezy_constant", "return h > r ? 6.25 + log(h / r) : 6.25;", "return h > r ? 6.5 + log(h / r) : 6.25;"),
     ("bezzola_branch", "if (x > 2.0) return", "if (x > 1.0) return"),
@@ -101,9 +124,10 @@ FRICTION_MUTANTS = [
                          + [m + ("test_oracle_sources.py",) for m in SOURCE_MUTANTS]
                          + [m + ("test_oracle_morpho.py",) for m in MORPHO_MUTANTS]
                          + [m + ("test_oracle_friction.py",) for m in FRICTION_MUTANTS]
-                         + [m + ("test_oracle_inflow.py",) for m in INFLOW_MUTANTS],
+                         + [m + ("test_oracle_inflow.py",) for m in INFLOW_MUTANTS]
+                         + [m + ("test_oracle_outflow.py",) for m in OUTFLOW_MUTANTS],
                          ids=[m[0] for m in MUTANTS + TRACK_MUTANTS + SCALAR_MUTANTS + SOURCE_MUTANTS
-                              + MORPHO_MUTANTS + FRICTION_MUTANTS + INFLOW_MUTANTS])
+                              + MORPHO_MUTANTS + FRICTION_MUTANTS + INFLOW_MUTANTS + OUTFLOW_MUTANTS])
 def test_pins_catch_mutant(name, orig, mut, pins, tmp_path):
     src = open(SRC).read()
     assert src.count(orig) == 1, f"mutation site for {name} not unique"
