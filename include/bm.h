@@ -92,10 +92,12 @@ const char* bm_last_error(void);
  *   manning_n n_tri Manning coefficients n >= 0 (Table 1); 0 = frictionless.
  *   edge_tag  3*n_tri tags; tag[3t+k] applies to the edge (tri[3t+k],
  *             tri[3t+(k+1)%3]) when it is on the boundary: 0 wall, 1 transmissive
- *             (zero gradient), 2 discharge inflow.  Ignored on interior edges.
+ *             (zero gradient), 2 discharge inflow, 3 h-Q relation outflow, 4 weir
+ *             outflow (the last two let nothing out until bm_state_set_outflow
+ *             sets their laws).  Ignored on interior edges.
  * Errors: BM_EINVAL for n_tri < 1, indices out of range, area <= 0, an edge
  * shared by more than two triangles or traversed twice in one direction, a tag
- * outside {0,1,2} on a boundary edge, n < 0 or a non-finite input.
+ * outside {0,1,2,3,4} on a boundary edge, n < 0 or a non-finite input.
  * *out receives the handle (NULL on failure); free with bm_mesh_destroy.
  * Host work only: the mesh is copied to the device by the first state created on
  * it (and stays on that device), so this call needs no GPU.
@@ -255,6 +257,33 @@ bm_status bm_state_set_friction(bm_state* s, int32_t law, const double* coef);
 
 bm_status bm_state_set_morpho(bm_state* s, int32_t on, double porosity, double s_rel, double d, double alpha,
                               double m, double theta_cr);
+
+/*
+ * Outflow laws of the mesh's h-Q (tag 3) and weir (tag 4) edges (Section "Boundary
+ * conditions", standard outflows; the appendix's parameter lists: the H-Q relation;
+ * the weir height and Poleni factor).
+ *   h-Q relation: the discharge Q leaving through all h-Q edges together is the rating
+ *     curve -- piecewise linear through (hq_stage[k], hq_discharge[k]), k < n_hq,
+ *     constant beyond its ends -- at the stage S, the length-weighted mean free
+ *     surface over the h-Q edges whose cell is wet (h > h_min); Q is split over those
+ *     edges by conveyance, q_e = Q h_e^(5/3) / sum_f l_f h_f^(5/3).  n_hq = 0: nothing.
+ *   weir: q_e = (2/3) mu sqrt(2 g) eta^(3/2) per unit width (Poleni), eta the head of
+ *     the cell's free surface over the crest elevation weir_crest (a crest below the
+ *     cell's bed counts from the bed: free overfall); mu = weir_poleni (0: nothing).
+ * Each outflow edge's flux is that of the boundary state on the cell's outgoing
+ * characteristic (u_n + 2 sqrt(g h) carried from the cell) that carries q_e, with q_e
+ * first capped at the critical discharge (u_n + 2 sqrt(g h))^3 / (27 g); that state's
+ * u_b + sqrt(g h_b) enters Eq. 21; an edge that lets nothing out is a wall.  Passive
+ * species leave with the inside cell's concentration, bedload as on a transmissive
+ * edge.  Stages and crest are absolute elevations [m], discharges [m^3/s] >= 0 and
+ * finite, stages strictly increasing, n_hq = 0 or >= 2, weir_poleni finite >= 0
+ * (BM_EINVAL otherwise; the arrays are copied).  Re-primes the state: the next step's
+ * dt and h-Q split follow the new laws; time and step count are kept.  Set it before
+ * bm_batch_create on a batch member (the batch copies the member's laws then); served
+ * requests (bm_submit) take none (their h-Q and weir edges are walls).  Blocks.
+ */
+bm_status bm_state_set_outflow(bm_state* s, const double* hq_stage, const double* hq_discharge, int64_t n_hq,
+                               double weir_crest, double weir_poleni);
 bm_status bm_state_download_bed(bm_state* s, double* z);
 
 /*

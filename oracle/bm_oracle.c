@@ -948,7 +948,8 @@ int64_t orc_run_tracked(orc_mesh* m, double* H, double* qx, double* qy, double* 
  * "Scalar advection-diffusion" numerics subsection names for the advective part.
  * phi_c = q_c / h where h = H - z > 0, else 0.  Walls carry nothing; a transmissive
  * edge carries F_h phi_c of the inside cell; an inflow edge brings q_e l c_in[c]; an
- * outflow edge (h-Q, weir) takes q_e l phi_c of the inside cell.
+ * outflow edge (h-Q, weir) takes its mass flux F_h (the discharge its boundary state
+ * lets out) times phi_c of the inside cell.
  * A cell that ends the step dry (h <= 0) keeps no scalar.  One step of the water
  * (orc_step) and the species together; returns the number of steps taken.
  */
@@ -992,8 +993,11 @@ int64_t orc_run_scalars(orc_mesh* m, double* H, double* qx, double* qy, double* 
         } else if (R == -3) {
           double q = m->qin[e];
           f = q > 0 ? -q * c_in[c] : 0.0;
-        } else {
-          f = m->qout[e] * pL; /* outflow: the inside cell's scalar leaves with q_e */
+        } else { /* outflow: the inside cell's scalar leaves with the edge's mass flux */
+          double q = m->qout[e];
+          double hs = fmax(0.0, H[L] - m->z[L]);
+          double hb = q > 0 ? outflow_state(hs, unL, g, &q) : -1.0;
+          f = hb > 0 ? q * pL : 0.0;
         }
         fl[c * ne + e] = l * f;
       }

@@ -85,6 +85,7 @@ SIGNATURES = {
     "bm_state_set_morpho": (C.c_int, [_vp, C.c_int32, _d, _d, _d, _d, _d, _d]),
     "bm_state_download_bed": (C.c_int, [_vp, _vp]),
     "bm_state_set_friction": (C.c_int, [_vp, C.c_int32, _vp]),
+    "bm_state_set_outflow": (C.c_int, [_vp, _vp, _vp, _i64, _d, _d]),
     "bm_server_opts_default": (None, [_P(bm_server_opts)]),
     "bm_server_create": (C.c_int, [_P(bm_server_opts), _P(_vp)]),
     "bm_server_destroy": (None, [_vp]),
@@ -489,6 +490,18 @@ class State:
         (coef = K_s), FRICTION_BEZZOLA (coef = y_R); coef scalar or per cell."""
         c = np.ascontiguousarray(np.broadcast_to(np.asarray(coef, dtype=np.float64), (self.n_cells,)))
         _check(load_library().bm_state_set_friction(self.handle, int(law), _dp(c)))
+
+    def set_outflow(self, hq_stage=(), hq_discharge=(), weir_crest: float = 0.0, weir_poleni: float = 0.0):
+        """Outflow laws of the h-Q edges (tag 3: rating curve through the (stage,
+        discharge) table) and of the weir edges (tag 4: crest elevation, Poleni
+        coefficient); see bm_state_set_outflow."""
+        st = np.ascontiguousarray(hq_stage, dtype=np.float64)
+        dq = np.ascontiguousarray(hq_discharge, dtype=np.float64)
+        if st.shape != dq.shape or st.ndim != 1:
+            raise ValueError("set_outflow: hq_stage and hq_discharge must be 1-D and of equal length")
+        _check(load_library().bm_state_set_outflow(self.handle, _dp(st) if len(st) else None,
+                                                   _dp(dq) if len(dq) else None, len(st), float(weir_crest),
+                                                   float(weir_poleni)))
 
     def download_bed(self) -> np.ndarray:
         """The bed elevation z (caller cell order)."""

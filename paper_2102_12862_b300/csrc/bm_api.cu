@@ -130,6 +130,8 @@ bm_status mesh_on_device(bm_mesh* m, int prec) {
       for (size_t j = 0; j < lia.size(); ++j) lia[j] = h.in_len[j] * h.inv_area[h.in_cell[j]];
       e = m->in_lia.upload(lia);
     }
+    if (e == cudaSuccess) e = m->in_nx.upload(h.in_nx);
+    if (e == cudaSuccess) e = m->in_ny.upload(h.in_ny);
     if (e == cudaSuccess) e = m->btiles.upload(h.btiles);
     if (e == cudaSuccess) e = m->perm.upload(h.perm);
     if (e != cudaSuccess) return dev_fail(e, "mesh upload");
@@ -217,7 +219,9 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
 }
 
 int state_extra_level(const bm_state* s) {
-  if (s->n_src > 0 || s->fr_law != 0) return 2;
+  const HostMesh& h = s->mesh->h;
+  const bool outflow = (h.n_hq > 0 && s->hq_n > 0) || (h.n_weir > 0 && s->weir_mu > 0.0);
+  if (s->n_src > 0 || s->fr_law != 0 || outflow) return 2;
   const bool trk = s->prec == BM_FP64 ? s->b64.trk_t.p != nullptr : s->b32.trk_t.p != nullptr;
   return (trk || s->n_species > 0) ? 1 : 0;
 }
@@ -272,10 +276,10 @@ void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t 
   const PipeItem* items = static_cast<const PipeItem*>(l.items.p);
   if (prec == BM_FP64)
     (void)cudaLaunchKernelEx(&cfg, step_kernel<double>(l.extra), items, l.n,
-                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime, withhold);
+                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime, withhold, l.static16);
   else
     (void)cudaLaunchKernelEx(&cfg, step_kernel<float>(l.extra), items, l.n,
-                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime, withhold);
+                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime, withhold, l.static16);
 }
 
 namespace {
@@ -312,6 +316,7 @@ void launch_species(bm_state* s, cudaStream_t st) {
   a.zmask = b.zmask.p;
   a.ex_stride = static_cast<int>(R.ne4_max);
   a.n_species = s->n_species;
+  a.n_inflow = static_cast<int>(s->mesh->h.n_inflow);
   a.n_cells = static_cast<int>(s->mesh->h.n_cells);
   const int nloc = kTile + static_cast<int>(R.nh4_max);
   const size_t smem = (2 * static_cast<size_t>(nloc) + R.ne4_max) * sizeof(T);
@@ -468,6 +473,8 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
   }
   d.in_cell = m->in_cell.p;
   d.in_lia = m->in_lia.p;
+  d.in_nx = m->in_nx.p;
+  d.in_ny = m->in_ny.p;
   d.btiles = m->btiles.p;
   d.ctl = s->ctl;
   d.part = s->part.p;
@@ -477,10 +484,22 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
   d.n_btiles = static_cast<int>(h.btiles.size());
   {
     const TileRecords& R = m->rec[sizeof(T) == 8 ? 0 : 1];
-    int nit = 0;
-    for (uint8_t f : R.flags) nit += (f & 2u) ? 1 : 0;
+    int nit = 0, nhq = 0;
+    for (uint8_t f : R.flags) {
+      nit += (f & 2u) ? 1 : 0;
+      nhq += (f & 8u) ? 1 : 0;
+    }
     d.n_in_tiles = nit;
+    d.n_hq_tiles = nhq;
   }
+  d.n_hq = static_cast<int>(h.n_hq);
+  d.n_weir = static_cast<int>(h.n_weir);
+  d.hq_n = s->hq_n;
+  d.hq_s = s->hq_s.p;
+  d.hq_q = s->hq_q.p;
+  d.datum = s->prec == BM_FP64 ? 0.0 : s->datum;
+  d.weir_crest = static_cast<T>(s->weir_crest - d.datum);
+  d.weir_k = static_cast<T>(2.0 / 3.0 * s->weir_mu * std::sqrt(2.0 * s->prm.g));
   d.n_cells = static_cast<int>(h.n_cells);
   d.n_tiles = static_cast<int>(h.n_tiles);
 }
@@ -563,11 +582,11 @@ bm_status alloc_state(bm_state* s, const bm_params* prm) {
   if (mst != BM_OK) return mst;
   cudaError_t e = cudaSuccess;
   if (f64) {
-    e = s->b64.alloc(Np, static_cast<size_t>(h.n_inflow), false);
+    e = s->b64.alloc(Np, h.in_cell.size(), false);
     if (e == cudaSuccess) e = s->b64.gn2.upload(gn2);
     if (e == cudaSuccess) e = cudaMemcpy(s->b64.z.p, h.z.data(), Np * sizeof(double), cudaMemcpyHostToDevice);
   } else {
-    e = s->b32.alloc(Np, static_cast<size_t>(h.n_inflow), true);
+    e = s->b32.alloc(Np, h.in_cell.size(), true);
     if (e == cudaSuccess) e = s->b32.gn2.upload(narrow<float>(gn2));
     if (e == cudaSuccess) {
       std::vector<float> z32 = narrow<float>(h.z, s->datum);
@@ -622,7 +641,7 @@ size_t state_footprint(const bm_mesh* m, int precision) {
   const size_t arrays = precision == BM_FP64 ? 8 : 10;  // 2 x (H [pair], q) + z, gn2
   // + caller-order staging, per tile: boundary partial, volume partial, work item
   return Np * w * arrays + 3 * static_cast<size_t>(h.n_cells) * 8 + static_cast<size_t>(h.n_tiles) * 72 +
-         static_cast<size_t>(h.n_inflow) * 2 * w + 4096;
+         h.in_cell.size() * 2 * w + 4096;
 }
 
 }  // namespace bm
@@ -1111,6 +1130,46 @@ bm_status bm_state_set_morpho(bm_state* s, int32_t on, double porosity, double s
   s->morpho = on != 0;
   drop_graphs(s);  // the launch sequence changes
   return BM_OK;
+}
+
+bm_status bm_state_set_outflow(bm_state* s, const double* hq_stage, const double* hq_discharge, int64_t n_hq,
+                               double weir_crest, double weir_poleni) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_set_outflow: state is NULL");
+  if (n_hq < 0 || n_hq == 1) return fail(BM_EINVAL, "bm_state_set_outflow: the h-Q table needs 0 or >= 2 points");
+  if (n_hq > 0 && (!hq_stage || !hq_discharge)) return fail(BM_EINVAL, "bm_state_set_outflow: table is NULL");
+  for (int64_t k = 0; k < n_hq; ++k) {
+    if (!std::isfinite(hq_stage[k]) || !std::isfinite(hq_discharge[k]) || !(hq_discharge[k] >= 0.0))
+      return fail(BM_EINVAL, "bm_state_set_outflow: stages must be finite and discharges finite and >= 0");
+    if (k > 0 && !(hq_stage[k] > hq_stage[k - 1]))
+      return fail(BM_EINVAL, "bm_state_set_outflow: stages must increase strictly");
+  }
+  if (!std::isfinite(weir_crest)) return fail(BM_EINVAL, "bm_state_set_outflow: weir_crest must be finite");
+  if (!std::isfinite(weir_poleni) || !(weir_poleni >= 0.0))
+    return fail(BM_EINVAL, "bm_state_set_outflow: weir_poleni must be finite and >= 0");
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  std::vector<double> st(hq_stage, hq_stage + n_hq), dq(hq_discharge, hq_discharge + n_hq);
+  cudaError_t e = s->hq_s.upload(st);
+  if (e == cudaSuccess) e = s->hq_q.upload(dq);
+  if (e != cudaSuccess) return dev_fail(e, "bm_state_set_outflow");
+  s->hq_n = static_cast<int>(n_hq);
+  s->weir_crest = weir_crest;
+  s->weir_mu = weir_poleni;
+  state_desc_bytes(s, &s->hdesc);
+  BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
+  const int extra = state_extra_level(s);  // laws that let water out: the full instantiation
+  if (extra != s->list.extra) {
+    s->list.extra = extra;
+    bm_status lst = list_occupancy(s->prec, &s->list);
+    if (lst != BM_OK) return lst;
+    s->grid = step_grid(s->list, s->ctas_per_sm);
+  }
+  drop_graphs(s);
+  // the next step's dt and h-Q split follow the new laws: prime again (time unchanged)
+  launch_state(s, s->stream, 1);
+  BM_CUDA(cudaGetLastError());
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  return read_status(s);
 }
 
 bm_status bm_state_set_friction(bm_state* s, int32_t law, const double* coef) {

@@ -19,11 +19,14 @@ constexpr int kTile = 256;
 constexpr int kMaxSpecies = 5;
 constexpr int kMaxTileEdges = 3 * kTile;
 
-// Boundary codes stored in place of the right cell of an edge; inflow edge j of
-// the mesh's inflow list is stored as kInflow - j.
+// Boundary codes stored in place of the right cell of an edge.  Edges with a boundary
+// law are listed -- the inflow edges first, then the h-Q outflow edges, then the weir
+// outflow edges -- and listed edge j is stored as kInflow - j.
 constexpr int32_t kWall = -1;
 constexpr int32_t kTransmissive = -2;
 constexpr int32_t kInflow = -3;
+constexpr int32_t kHqTag = -4;    // h-Q and weir edges before they are listed (mesh
+constexpr int32_t kWeirTag = -5;  // preparation only)
 
 // Set the thread-local error message and return the status.
 bm_status fail(bm_status st, const std::string& msg);
@@ -32,6 +35,7 @@ void clear_error();
 // Host-side mesh after preparation (new Hilbert numbering).
 struct HostMesh {
   int64_t n_cells = 0, n_edges = 0, n_boundary = 0, n_inflow = 0;
+  int64_t n_hq = 0, n_weir = 0;  // listed h-Q and weir outflow edges (after the inflow edges)
   int64_t n_tiles = 0;
   // per cell, new numbering (padded to n_tiles * kTile with inert cells)
   std::vector<int32_t> perm;        // new -> caller index (n_cells entries)
@@ -41,9 +45,10 @@ struct HostMesh {
   std::vector<int64_t> eoff;
   std::vector<int32_t> eL, eR;      // left cell (new id), right cell (new id) or boundary code
   std::vector<double> enx, eny, elen;
-  // inflow edges (one entry per inflow edge): cell (new id), length
+  // listed edges (inflow, h-Q, weir; one entry each): cell (new id), length, unit
+  // normal (outward)
   std::vector<int32_t> in_cell;
-  std::vector<double> in_len;
+  std::vector<double> in_len, in_nx, in_ny;
   // tiles whose edge list holds at least one boundary edge (ascending)
   std::vector<int32_t> btiles;
   double inflow_len = 0;
@@ -94,7 +99,8 @@ struct TileRecords {
   std::vector<uint64_t> off;         // byte offset of tile t's record
   std::vector<uint32_t> bytes;       // its size (multiple of 16)
   std::vector<uint32_t> ne_nh;       // edges | halo cells << 16
-  std::vector<uint8_t> flags;        // bit 0: boundary edges, bit 1: inflow edges
+  std::vector<uint8_t> flags;        // bit 0: boundary edges, bit 1: inflow edges, bit 3: h-Q edges,
+                                     // bit 4: weir edges
   uint32_t ne4_max = 0, nh4_max = 0;
 };
 
@@ -124,6 +130,9 @@ struct Ctl {
   double rb;            // max inflow-edge rate of Eq. 21 at t^{n+1} (written mid-launch)
   unsigned int in_done; // inflow tiles of the current launch that finished
   unsigned int b_done;  // boundary tiles of the current launch that finished
+  double rb_out;        // max h-Q-edge rate of Eq. 21 at t^{n+1} (written mid-launch)
+  unsigned int hq_done; // h-Q tiles of the current launch that finished
+  unsigned int pad_u;
 };
 
 static_assert(sizeof(Ctl) % 16 == 0, "Ctl is bulk-copied: its size must be a multiple of 16");
@@ -138,7 +147,8 @@ struct PipeItem {
   int32_t tile;
   uint32_t ne_nh;            // edges | halo cells << 16
   int32_t inst;              // instance index within the launch
-  uint32_t flags;            // bit 0: the tile has boundary edges, bit 1: inflow edges
+  uint32_t flags;            // bit 0: the tile has boundary edges, bit 1: inflow edges,
+                             // bit 2: source cells, bit 3: h-Q edges, bit 4: weir edges
   uint32_t bidx;             // boundary tiles: rank among the instance's boundary tiles
 };
 static_assert(sizeof(PipeItem) == 48, "PipeItem layout");

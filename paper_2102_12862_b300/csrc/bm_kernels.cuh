@@ -33,11 +33,14 @@ struct alignas(16) InstDesc {
   const T* z;
   const T* gn2;       // g n^2
   const T* inv_area;  // 1 / |Omega_i|
-  const int32_t* in_cell;  // inflow edge j: its cell
+  const int32_t* in_cell;  // listed edge j (inflow, h-Q, weir): its cell
   const double* in_lia;    //                l_j / |Omega| of its cell
   const T* in_len;         //                its length
-  T* in_pw;                //                h^(5/3) of the cell (0 at or below h_min)
-  T* in_hs;                //                max(0, h) of the cell
+  const double* in_nx;     //                its outward unit normal
+  const double* in_ny;
+  T* in_pw;                //                inflow: h^(5/3) of the cell (0 at or below h_min);
+                           //                h-Q: the unit discharge leaving (at t^n)
+  T* in_hs;                //                inflow: max(0, h) of the cell
   const int32_t* btiles;   // tiles with boundary edges (tile b's partial at part[b's rank])
   Ctl* ctl;
   TilePartial* part;
@@ -65,6 +68,19 @@ struct alignas(16) InstDesc {
   // friction closure of Table 1: 0 Manning (gn2 = g n^2), 1 Chezy (gn2 holds K_s),
   // 2 Bezzola (gn2 holds y_R)
   int fr_law;
+  // outflow laws: listed edges [n_inflow, n_inflow + n_hq) are h-Q edges, the next
+  // n_weir weir edges.  The h-Q relation's table (absolute stage, discharge; hq_n = 0:
+  // nothing leaves); the weir's crest (FP32-bulk: offset from the datum) and
+  // (2/3) mu sqrt(2 g) of its Poleni factor mu (0: nothing leaves)
+  int n_hq;
+  int n_weir;
+  int n_hq_tiles;          // tiles with h-Q edges
+  int hq_n;
+  const double* hq_s;
+  const double* hq_q;
+  double datum;            // FP32-bulk: the surface and the bed are offsets from it
+  T weir_crest;
+  T weir_k;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -538,16 +554,167 @@ __device__ __noinline__ void finalize_inflow(const InstDesc<T>& a, const Ctl& cs
   nbar<kTile>();
 }
 
+// ------------------------------------------------------------------ outflow laws
+
+// The boundary state of an outflow edge (h-Q relation, weir; Section "Boundary
+// conditions", standard outflows) that lets the unit discharge q > 0 leave a cell of
+// depth h and outward normal velocity un: the depth h_b on the cell's outgoing
+// characteristic, q / h_b + 2 sqrt(g h_b) = w = un + 2 sqrt(g h), on its subcritical
+// branch (u_b <= sqrt(g h_b)).  q is first capped at the critical discharge
+// w^3 / (27 g), the largest the invariant admits (h_b is then the critical depth
+// (w / 3)^2 / g).  Returns h_b, or -1 with q = 0 when nothing can leave (w <= 0).
+// Newton's method on s = sqrt(h_b) for f(s) = 2 sqrt(g) s + q / s^2 - w, convex in s,
+// from s = max(sqrt(h), the minimum of f): from the right of the root it descends
+// monotonically, from its left the first step lands to its right.  IEEE division and
+// square roots: the edges are few, and the iteration converges to the last bits.
+template <typename T>
+__device__ __noinline__ T outflow_state(T h, T un, T g, T& q) {
+  const T w = un + T(2) * sqrt(g * h);
+  if (!(w > T(0))) {
+    q = T(0);
+    return T(-1);
+  }
+  const T qmax = w * w * w / (T(27) * g);
+  if (q >= qmax) {
+    q = qmax;
+    const T w3 = w / T(3);
+    return w3 * w3 / g;
+  }
+  const T sg = sqrt(g);
+  T s = fmax(sqrt(h), cbrt(q / sg));
+  const T eps = sizeof(T) == 8 ? T(1e-16) : T(1e-7);
+  for (int it = 0; it < 100; ++it) {
+    const T f = T(2) * sg * s + q / (s * s) - w;
+    const T df = T(2) * sg - T(2) * q / (s * s * s);
+    if (!(df > T(0))) break;
+    const T ds = f / df;
+    s -= ds;
+    if (fabs(ds) <= eps * s) break;
+  }
+  return s * s;
+}
+
+// Poleni's weir discharge per unit crest width leaving a cell with surface (Hh, Hl),
+// bed z and depth h: (2/3) mu sqrt(2 g) eta^(3/2) = weir_k eta^(3/2), eta the head of
+// the surface over the crest, a crest below the bed taken at the bed (free overfall);
+// 0 for a dry cell or water at or below the crest.
+template <typename T>
+__device__ __forceinline__ T weir_discharge(const InstDesc<T>& a, T Hh, T Hl, T z, T h, T hmin) {
+  const T eta = depth_of(Hh, Hl, fmax(a.weir_crest, z));
+  return (h > hmin && eta > T(0)) ? a.weir_k * eta * sqrt(eta) : T(0);
+}
+
+// The largest Eq. 21 rate of a cell's weir edges at its new state (surface (Hh, Hl),
+// bed z, depth h, velocity (u, v)): the boundary state's u_b + sqrt(g h_b), times
+// l / |Omega| (and 3/4 for Eq. 21's rho = 4 |Omega| / (3 l)); 0 if nothing leaves.
+template <typename T>
+__device__ __noinline__ T weir_rate(const InstDesc<T>& a, const uint32_t* sLR, const T* sNx, const T* sNy,
+                                    const T* sLn, const int (&idx)[3], T Hh, T Hl, T z, T h, T u, T v, T ia) {
+  const T g = static_cast<T>(a.p.g), hmin = static_cast<T>(a.p.h_min);
+  T r = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int e = idx[k];
+    const int code = static_cast<int32_t>(sLR[e]) >> kLocBits;
+    if (code > kInflow || kInflow - code < a.n_inflow + a.n_hq) continue;
+    T q = weir_discharge<T>(a, Hh, Hl, z, h, hmin);
+    const T hb = q > T(0) ? outflow_state<T>(h, u * sNx[e] + v * sNy[e], g, q) : T(-1);
+    if (hb > T(0)) r = fmax(r, (q / hb + sqrt(g * hb)) * sLn[e] * ia * (a.p.cfl_mode == 0 ? T(0.75) : T(1)));
+  }
+  return r;
+}
+
+// The rating curve of the h-Q relation: piecewise linear through (hq_s, hq_q), constant
+// beyond its ends; 0 without a table.
+template <typename T>
+__device__ __forceinline__ double rating_curve(const InstDesc<T>& a, double S) {
+  const int n = a.hq_n;
+  if (n <= 0) return 0.0;
+  if (S <= a.hq_s[0]) return a.hq_q[0];
+  for (int k = 1; k < n; ++k) {
+    if (S <= a.hq_s[k]) {
+      const double w = (S - a.hq_s[k - 1]) / (a.hq_s[k] - a.hq_s[k - 1]);
+      return a.hq_q[k - 1] + w * (a.hq_q[k] - a.hq_q[k - 1]);
+    }
+  }
+  return a.hq_q[n - 1];
+}
+
+// h-Q outflow at the new time: the stage S (length-weighted mean surface over the h-Q
+// edges whose cell is wet), Q = the rating curve at S, its conveyance split over those
+// edges, q_e = Q h_e^(5/3) / sum_f l_f h_f^(5/3) (stored for the next step's fluxes),
+// and the largest h-Q-edge rate of Eq. 21 (the boundary state's u_b + sqrt(g h_b)).
+// Run, in FP64, by the CTA that completes the instance's last h-Q tile (the state of
+// every h-Q cell at the new time is in memory).  sred: 9 doubles, sbc: 4.
+template <typename T>
+__device__ __noinline__ void finalize_hq(const InstDesc<T>& a, const Ctl& cs, int advance, double* sred,
+                                         double* sbc) {
+  constexpr bool kPair = sizeof(T) == 4;
+  const int tid = threadIdx.x;
+  const int b = advance ? (cs.parity ^ 1) : cs.parity;  // the buffer holding the new state
+  const int j0 = a.n_inflow, j1 = a.n_inflow + a.n_hq;
+  const double g = a.p.g, hmin = a.p.h_min;
+  auto depth = [&](int i, double* Habs) {
+    const double Hh = static_cast<double>(__ldcg(&a.H[b][i]));
+    const double Hl = kPair ? static_cast<double>(__ldcg(&a.Hlo[b][i])) : 0.0;
+    *Habs = (a.datum + Hh) + Hl;
+    return (Hh - static_cast<double>(a.z[i])) + Hl;
+  };
+  double sl = 0.0, sH = 0.0, sw = 0.0;
+  for (int j = j0 + tid; j < j1; j += kTile) {
+    double Habs;
+    const double h = depth(a.in_cell[j], &Habs);
+    if (h > hmin) {
+      const double l = static_cast<double>(a.in_len[j]);
+      sl += l;
+      sH += l * Habs;
+      sw += l * pow53(h);
+    }
+  }
+  sl = block_sum<kTile>(sl, sred);
+  if (tid == 0) sbc[0] = sl;
+  sH = block_sum<kTile>(sH, sred);
+  if (tid == 0) sbc[1] = sH;
+  sw = block_sum<kTile>(sw, sred);
+  if (tid == 0) {
+    sbc[2] = sw;
+    sbc[3] = sbc[0] > 0.0 ? rating_curve(a, sbc[1] / sbc[0]) : 0.0;
+  }
+  nbar<kTile>();
+  const double Q = sbc[3], W = sbc[2];
+  const double fac = a.p.cfl_mode == 0 ? 0.75 : 1.0;
+  double rb = 0.0;
+  for (int j = j0 + tid; j < j1; j += kTile) {
+    const int i = a.in_cell[j];
+    double Habs;
+    const double h = depth(i, &Habs);
+    double q = (h > hmin && W > 0.0) ? Q * pow53(h) / W : 0.0;
+    a.in_pw[j] = static_cast<T>(q);
+    if (q > 0.0) {
+      const double un = (static_cast<double>(__ldcg(&a.qx[b][i])) * a.in_nx[j] +
+                         static_cast<double>(__ldcg(&a.qy[b][i])) * a.in_ny[j]) / h;
+      const double hb = outflow_state<double>(h, un, g, q);
+      if (hb > 0.0) rb = fmax(rb, (q / hb + sqrt(g * hb)) * a.in_lia[j] * fac);
+    }
+  }
+  rb = block_max_nonneg_all<kTile>(rb, reinterpret_cast<unsigned long long*>(sred));
+  if (tid == 0) {
+    a.ctl->rb_out = rb;
+    a.ctl->hq_done = 0u;
+  }
+  nbar<kTile>();
+}
+
 // The step itself: run (thread 0 only) by the CTA that completes the instance's last
-// tile, after the inflow and boundary parts (their CTAs counted their tiles after
-// them).  dt^{n+1} from the maximum cell rate and inflow rate (Eq. 21), then time,
+// tile, after the inflow, h-Q and boundary parts (their CTAs counted their tiles after
+// them).  dt^{n+1} from the maximum cell rate and inflow / h-Q rate (Eq. 21), then time,
 // parity and step count.
 template <typename T>
 __device__ __forceinline__ void finalize_step(const InstDesc<T>& a, const Ctl& cs, int advance) {
   Ctl* ctl = a.ctl;
   const double t = new_time(cs, advance);
   const double rcell = __longlong_as_double(static_cast<long long>(__ldcg(&ctl->rmax_bits)));
-  const double rb = a.n_in_tiles > 0 ? __ldcg(&ctl->rb) : 0.0;
+  const double rb = fmax(a.n_in_tiles > 0 ? __ldcg(&ctl->rb) : 0.0, a.n_hq_tiles > 0 ? __ldcg(&ctl->rb_out) : 0.0);
   if (advance) {
     ctl->t = t;
     ctl->parity = cs.parity ^ 1;

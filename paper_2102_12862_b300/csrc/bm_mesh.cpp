@@ -128,8 +128,9 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
       gr.push_back(tR);
     } else {
       uint8_t tt = tg[tkL];
-      if (tt > 2) return fail(BM_EINVAL, "bm_mesh_create: boundary edge tag outside {0,1,2}");
-      gr.push_back(tt == 0 ? kWall : (tt == 1 ? kTransmissive : kInflow));
+      if (tt > 4) return fail(BM_EINVAL, "bm_mesh_create: boundary edge tag outside {0,1,2,3,4}");
+      static const int32_t kOfTag[5] = {kWall, kTransmissive, kInflow, kHqTag, kWeirTag};
+      gr.push_back(kOfTag[tt]);
     }
     i = j;
   }
@@ -178,21 +179,33 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
     m.z_min = std::min(m.z_min, z[t]);
   }
 
-  // 4. boundary / inflow lists (inflow edge j is coded kInflow - j)
+  // 4. boundary lists: the inflow, then the h-Q, then the weir edges; listed edge j is
+  // coded kInflow - j
   std::vector<int32_t> code(E);
   for (int64_t e = 0; e < E; ++e) {
     if (gr[e] >= 0) {
       code[e] = newid[gr[e]];
-      continue;
+    } else {
+      ++m.n_boundary;
+      code[e] = static_cast<int32_t>(gr[e]);
     }
-    ++m.n_boundary;
-    if (gr[e] == kInflow) {
+  }
+  for (int32_t kind : {kInflow, kHqTag, kWeirTag}) {
+    for (int64_t e = 0; e < E; ++e) {
+      if (gr[e] != kind) continue;
       code[e] = kInflow - static_cast<int32_t>(m.in_cell.size());
       m.in_cell.push_back(newid[gl[e]]);
       m.in_len.push_back(glen[e]);
-      m.inflow_len += glen[e];
-    } else {
-      code[e] = static_cast<int32_t>(gr[e]);
+      m.in_nx.push_back(gnx[e]);
+      m.in_ny.push_back(gny[e]);
+      if (kind == kInflow) {
+        m.inflow_len += glen[e];
+        ++m.n_inflow;
+      } else if (kind == kHqTag) {
+        ++m.n_hq;
+      } else {
+        ++m.n_weir;
+      }
     }
   }
 
@@ -229,7 +242,6 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
     if (has_boundary) m.btiles.push_back(static_cast<int32_t>(tile));
   }
   m.eoff[m.n_tiles] = static_cast<int64_t>(m.eL.size());
-  m.n_inflow = static_cast<int64_t>(m.in_cell.size());
   return BM_OK;
 }
 
@@ -291,9 +303,10 @@ bm_status build_records_t(const HostMesh& m, TileRecords* out) {
       if (gR >= 0) {
         R = static_cast<int32_t>(local(gR));
       } else {
-        if (gR < kMinCode) return fail(BM_EINVAL, "tile records: too many inflow edges");
+        if (gR < kMinCode) return fail(BM_EINVAL, "tile records: too many listed boundary edges");
         R = gR;
-        r.flags[tile] |= gR <= kInflow ? 3 : 1;
+        const int64_t j = kInflow - gR;  // listed edge (j >= 0) or a wall / transmissive code
+        r.flags[tile] |= j < 0 ? 1 : (j < m.n_inflow ? 3 : (j < m.n_inflow + m.n_hq ? 9 : 17));
       }
       lr[k] = local(m.eL[e]) | (static_cast<uint32_t>(R) << kLocBits);
       put<uint32_t>(r.data, at + RL::lr() + 4 * k, lr[k]);

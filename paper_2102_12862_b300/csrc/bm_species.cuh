@@ -34,6 +34,7 @@ struct SpeciesArgs {
   int ex_stride;
   int n_species;
   int n_cells;
+  int n_inflow;                   // listed edges below n_inflow are inflow edges (outflow above)
 };
 
 // One CTA per work item (a 256-cell tile).  Dynamic shared memory: (2 nloc_max +
@@ -104,9 +105,9 @@ __global__ void __launch_bounds__(kTile) species_step(const SpeciesArgs<T> a, in
           const uint32_t w = lr[k];
           const int lL = static_cast<int>(w & (kMaxLocal - 1));
           const int R = static_cast<int32_t>(w) >> kLocBits;
-          if (R <= kInflow) {
-            f = fh * a.c_in[c];
-          } else {
+          if (R <= kInflow && kInflow - R < a.n_inflow) {
+            f = fh * a.c_in[c];  // the inflow brings its concentration
+          } else {  // an outflow edge takes the inside cell's
             const int lR = R >= 0 ? R : lL;  // transmissive: the outside equals the inside
             f = fh * (a.ex_right[o] ? ph[lR] : ph[lL]);
           }

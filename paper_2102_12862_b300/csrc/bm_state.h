@@ -129,7 +129,7 @@ struct bm_mesh {
   std::mutex mu;
   int device = -1;
   bool on_device = false;
-  bm::DBuf<double> z, inv_area, area, in_len, in_lia;
+  bm::DBuf<double> z, inv_area, area, in_len, in_lia, in_nx, in_ny;
   bm::DBuf<int32_t> in_cell, btiles, perm;
   bool has32 = false;  // FP32 copies for FP32-bulk states
   bm::DBuf<float> inv_area32, in_len32;
@@ -150,6 +150,7 @@ struct StepList {
   uint32_t ne4 = 4, nh4 = 4;
   size_t smem = 0;
   int occupancy = 1;  // resident CTAs per SM at this shared-memory size
+  int static16 = -1;  // static share of the tickets in sixteenths (-1: the precision's default)
   int extra = 0;  // the step kernel's feature level the members need (0 none; 1 tracking or
                  // species; 2 also sources or log-law friction)
 };
@@ -199,6 +200,11 @@ struct bm_state {
   bool morpho = false;
   double mo_par[6] = {};  // porosity, s, d, alpha, m, theta_cr
   bm::DBuf<double> mo_dz, mo_dt;
+  // outflow laws (bm_state_set_outflow): the h-Q relation's table (absolute stage,
+  // discharge) and the weir's crest (absolute) and Poleni factor
+  bm::DBuf<double> hq_s, hq_q;
+  int hq_n = 0;
+  double weir_crest = 0.0, weir_mu = 0.0;
   int n_species = 0;                    // passive species carried (0: none)
   double c_in[bm::kMaxSpecies] = {};    // their concentration in the inflow
   template <typename T>

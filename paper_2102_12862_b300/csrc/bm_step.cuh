@@ -297,8 +297,9 @@ __device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* s
 
 template <typename T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 3;
-// Share of a launch's tickets handed out statically: kStaticNum / kStaticDen (FP64,
-// with its wide spread of tile costs, leaves more to the counter).
+// Share of a launch's tickets handed out statically: static16 / kStaticDen, by default
+// kStaticNum (FP64, with its wide spread of tile costs, leaves more to the counter);
+// the autotuner searches it.
 constexpr int kStaticDen = 16;
 template <typename T>
 constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M floodplain
@@ -324,12 +325,14 @@ constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M flood
 // (diagnostics of the failure path only): every CTA's copy warp withholds group H of
 // its first tile, so the compute warps' bounded wait for it runs out; the launch then
 // takes the timeout path below (status bit 2, issued copies retired, no state written).
+// static16: the static share of the tickets in sixteenths (negative: kStaticNum); the
+// schedule never changes results (the reductions are order-free).
 template <typename T, int kX>
 __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const PipeItem* __restrict__ items,
                                                                          int n_items, int* __restrict__ sched,
                                                                          int* __restrict__ early, int* __restrict__ mark,
                                                                          int ne4max, int nh4max, int prime,
-                                                                         int withhold) {
+                                                                         int withhold, int static16) {
   constexpr bool kExtra = kX >= 1;  // tracking, species exports
   constexpr bool kFull = kX >= 2;   // sources, log-law friction
   using SL = StepLayout<T>;
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     // then the launch's counter from n_static on, one ticket requested a step ahead.
     // A CTA's tickets increase, so once one is past the end every later one is too.
     const int G = static_cast<int>(gridDim.x);
-    const int m_static = max(2, n_tickets / kStaticDen * kStaticNum<T> / G);
+    const int m_static = max(2, n_tickets / kStaticDen * (static16 >= 0 ? static16 : kStaticNum<T>) / G);
     const int n_static = m_static * G;
     int m_next = 0;
     int tc = 0;  // lane 0: the requested counter ticket
@@ -616,7 +619,9 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         const int lL = static_cast<int>(lr & (kMaxLocal - 1));
         const int R = static_cast<int32_t>(lr) >> kLocBits;
         const int lR = R >= 0 ? R : lL;
-        const bool inflow = R <= kInflow;
+        const bool listed = R <= kInflow;  // an edge with a boundary law
+        const bool inflow = listed && kInflow - R < a.n_inflow;
+        const bool outflow = listed && !inflow;  // h-Q relation or weir
         T f0 = zero, f1 = zero, f2 = zero, f3 = zero, f4 = zero;
         bool right = false;  // the contact's right side is upwind (passive species)
         unsigned char skipped = 1;
@@ -650,15 +655,17 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
             } else {
               c1 = cL;
               c2 = cL;
-              un2 = (R == kWall) ? -unL : unL;  // wall: mirrored normal velocity
+              // wall: mirrored normal velocity (so also an outflow edge, a wall while it
+              // lets nothing out)
+              un2 = (R == kWall || outflow) ? -unL : unL;
               ut2 = utL;
             }
             T F0, F1, F2, pL, pR;
             hllc<T>(h1, unL, utL, c1, h2, un2, ut2, c2, hg, F0, F1, F2, pL, pR, right);
             T GL = F1 - pL;
             const T GR = F1 - pR;
-            if (R == kWall) {
-              F0 = zero;  // impermeable, frictionless
+            if (R == kWall || outflow) {
+              F0 = zero;  // impermeable, frictionless (an outflow edge's law: below)
               F2 = zero;
             } else if (inflow) {
               const int j = kInflow - R;
@@ -695,6 +702,38 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
             const size_t o = static_cast<size_t>(tile) * static_cast<size_t>(a.ex_stride) + k2;
             a.ex_flux[o] = f0;
             a.ex_right[o] = right ? 1 : 0;
+          }
+        }
+      }
+      if (kFull && (inf.flags & 24u)) {
+        // outflow edges (h-Q relation, weir), walls above: where the law lets water out,
+        // the flux of the boundary state on the cell's outgoing characteristic that
+        // carries it (each thread revisits its own edges; states whose outflow laws let
+        // something out run the full instantiation)
+        for (int k2 = tid; k2 < ne; k2 += kTile) {
+          const uint32_t lr = sLR[k2];
+          const int R = static_cast<int32_t>(lr) >> kLocBits;
+          const int lL = static_cast<int>(lr & (kMaxLocal - 1));
+          if (R > kInflow || kInflow - R < a.n_inflow || dry[lL]) continue;
+          const int j = kInflow - R;
+          const T HLh = sH[lL], HLl = kPair ? sHl[lL] : zero, zL = sZ[lL];
+          const T h1 = fmax(zero, depth_of(HLh, HLl, zL));
+          const T nx = sNx[k2], ny = sNy[k2], l = sLn[k2];
+          const T unL = U[lL] * nx + V[lL] * ny, utL = -U[lL] * ny + V[lL] * nx;
+          T q = j < a.n_inflow + a.n_hq ? a.in_pw[j] : weir_discharge<T>(a, HLh, HLl, zL, h1, hmin);
+          const T hb = q > zero ? outflow_state<T>(h1, unL, g, q) : T(-1);
+          if (hb > zero) {
+            const T GL = q * (q / hb) + hg * hb * hb - hg * h1 * h1;
+            const T F2 = q * utL;
+            Fs[k2] = l * q;
+            Fs[L.ne4 + k2] = l * (GL * nx - F2 * ny);
+            Fs[2 * L.ne4 + k2] = l * (GL * ny + F2 * nx);
+            skip[k2] = 0;
+            bsum += static_cast<double>(l * q);
+            if constexpr (kExtra) {
+              if (a.ex_flux != nullptr)
+                a.ex_flux[static_cast<size_t>(tile) * static_cast<size_t>(a.ex_stride) + k2] = l * q;
+            }
           }
         }
       }
@@ -736,7 +775,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int code = static_cast<int32_t>(sLR[idx[q]]) >> kLocBits;
-          if (code <= kInflow) {
+          if (code <= kInflow && kInflow - code < a.n_inflow) {
             a.in_pw[kInflow - code] = zero;
             a.in_hs[kInflow - code] = zero;
           }
@@ -830,14 +869,21 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         T u, v, c;
         cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
         if (h > hmin) rrun = fmax(rrun, cell_rate<T>(sNx, sNy, sLn, idx, u, v, c, ia, a.p.cfl_mode));
-        // inflow cells: conveyance weight and depth of the new state
+        // inflow cells: conveyance weight and depth of the new state; weir cells: the
+        // weir edges' rates of Eq. 21 at the new state (h-Q edges: finalize_hq)
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int code = static_cast<int32_t>(sLR[idx[q]]) >> kLocBits;
           if (code <= kInflow) {
-            a.in_pw[kInflow - code] = h > hmin ? pow53(h) : zero;
-            a.in_hs[kInflow - code] = fmax(zero, h);
+            const int j = kInflow - code;
+            if (j < a.n_inflow) {
+              a.in_pw[j] = h > hmin ? pow53(h) : zero;
+              a.in_hs[j] = fmax(zero, h);
+            }
           }
+        }
+        if constexpr (kFull) {
+          if (inf.flags & 16u) rrun = fmax(rrun, weir_rate<T>(a, sLR, sNx, sNy, sLn, idx, Hh, Hl, zi, h, u, v, ia));
         }
       }
     }
@@ -861,6 +907,18 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         if (nbar_or<kTile>(last_b)) {
           __threadfence();
           finalize_boundary<T>(a, cs, scratch);
+        }
+      }
+      if (kFull && (inf.flags & 8u)) {
+        // h-Q tiles: the last one's CTA evaluates the rating curve at the new stage
+        __threadfence();
+        nbar<kTile>();  // every thread's new state is stored
+        int last_hq = 0;
+        if (tid == 0)
+          last_hq = atomicAdd(&a.ctl->hq_done, 1u) + 1u == static_cast<unsigned>(a.n_hq_tiles) ? 1 : 0;
+        if (nbar_or<kTile>(last_hq)) {
+          __threadfence();
+          finalize_hq<T>(a, cs, prime ? 0 : 1, red + 4, red);
         }
       }
       if (inf.flags & 2u) {

@@ -51,6 +51,7 @@ def _mesh_args():
     (lambda a: a[1].__setitem__((0, 0), 10_000), "out of range"),
     (lambda a: a[1].__setitem__((0, 1), a[1][0, 0]), "degenerate"),
     (lambda a: a[4].fill(7), "tag"),
+    (lambda a: a[4].fill(5), "tag"),
     (lambda a: a[3].__setitem__(0, -0.1), "n >= 0"),
     (lambda a: a[2].__setitem__(1, np.nan), "finite"),
     (lambda a: a[0].__setitem__((3, 0), np.inf), "non-finite"),
@@ -61,6 +62,18 @@ def test_mesh_validation_rejects(mutate, msg):
     with pytest.raises(bm.BMError) as ei:
         bm.bm_mesh_create(*args)
     assert ei.value.status == bm.BM_EINVAL and msg in str(ei.value)
+
+
+def test_mesh_lists_outflow_edges_after_the_inflow_edges():
+    """Tags 3 (h-Q relation) and 4 (weir) are outflow edges; the mesh lists them after
+    the inflow edges, and the tiles that hold them are boundary tiles."""
+    xy, tri, tag = W.rect_mesh(20, 4, 100.0, 20.0, jitter=0.1, seed=1,
+                               side_tags=(W.INFLOW, W.WEIR, W.HQ_OUTFLOW, W.WALL))
+    N = len(tri)
+    m = bm.Mesh(xy, tri, np.zeros(N), np.zeros(N), tag)
+    info = m.info
+    assert info["n_inflow"] == 4  # the x = 0 side
+    assert info["n_boundary"] == 4 + 4 + 20 + 20
 
 
 def test_mesh_rejects_non_manifold_and_flipped():
