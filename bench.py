@@ -6,23 +6,29 @@
 Workload: the single-floodplain configuration -- 5 km x 2 km, 1600 x 625 jittered
 quads = 2,000,000 triangles, seeded sinusoid + noise bed 400 m above datum,
 64-patch Manning map, a 2 m deep meandering main channel (the rest dry), inflow
-hydrograph 0 -> 500 m^3/s over 600 s on the upstream side, transmissive outlet,
-walls, positivity time step.  Synthetic inputs from paper_2102_12862_b300.workloads
-(seed 2).
+hydrograph 0 -> 500 m^3/s over 600 s on the upstream side, walls, positivity time
+step -- run for 3,600 simulated seconds with moving wet/dry fronts.  Synthetic
+inputs from paper_2102_12862_b300.workloads (seed 2).
 
 A step is one pass of the whole hot path over all cells (edge fluxes, update,
-friction, dt reduction, time advance: one kernel launch).  The line's `value` is
-the plain FP64 step; `fp32_bulk` repeats every measurement for the FP32-bulk
-precision mode on the same workload.  Each: W untimed warm-up steps from t = 0,
-then K steps timed with CUDA events on the stream the kernels run on.  The working
-set (0.3-0.5 GB) is larger than the 126 MB L2, so no flush is needed.  Under
-torchrun every rank steps its own replica (no exchange between independent runs:
-replicas only, weak scaling); value = all ranks' cell-updates / the slowest rank's
-time.
+friction, dt reduction, time advance: one kernel launch).  The cost of a step grows
+as the flood spreads, so the run is sampled: states at t = 0, 600, 1,800 and 3,600 s
+(made by a GPU run of the workload in the same precision, downloaded) are each
+uploaded, stepped W untimed warm-up steps and then K timed steps (CUDA events on the
+stream the kernels run on); `value` is the whole run's rate, the run's step count over
+the step-weighted time (trapezoids between the windows).  `e2e` is the user's call for the whole
+configuration through the C ABI: upload of the initial state from pinned host memory,
+bm_run_until(3,600 s), download, wall-clock.  The line's `value` is plain FP64;
+`fp32_bulk` repeats every measurement for the FP32-bulk precision mode.  The working
+set (0.3-0.5 GB) is larger than the 126 MB L2, so no flush is needed.  Under torchrun
+every rank steps its own replica (no exchange between independent runs: replicas only,
+weak scaling); value = all ranks' cell-updates / the slowest rank's time.
 
-Accuracy: the end-to-end leg (upload, E steps from t = 0, download through the C
-ABI with pinned host buffers) is compared with the FP64 CPU oracle run for the same
-E steps, which is also the timed CPU baseline.
+Also in the line: the 1,000,000-cell wet lake (the HBM / FP64-arithmetic bound
+context), a batched ensemble (FP32-bulk, one launch per step for all members) against
+FP64 plain, a bounded serving trace with p50 / p99 time-to-result, and the optional
+features' cost.  Accuracy: the first 50 steps through the C ABI against the FP64 CPU
+oracle run for the same steps, which is also the timed CPU baseline.
 
 --impl reference times that oracle alone (serial C on the host cores) on the same
 workload and metric.
@@ -45,33 +51,46 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s"
-# Algorithmic DRAM bytes of one step: every byte the step must move once.  Per cell:
+# Algorithmic DRAM bytes per cell-update (the hot-path scope table's per-unit figure):
+# the state read and written, bed, Manning coefficient, three neighbour indices, three
+# edges' geometry and the area -- FP64 156 B, FP32-bulk 84 B.
+BYTES_PER_CELL_UPDATE = {"fp64": 156, "fp32": 84}
+# The tighter count of what the tile layout moves (each mesh edge read once): per cell
 # the state read and written (FP64: H, qx, qy; FP32-bulk: H hi/lo, qx, qy), z, g n^2,
-# 1/|Omega| and the 4-byte slot word; per mesh edge (each read once): the 4-byte code
-# word and nx, ny, l.
-BYTES_PER_CELL = {"fp64": 2 * 24 + 3 * 8 + 4, "fp32": 2 * 16 + 3 * 4 + 4}
-BYTES_PER_EDGE = {"fp64": 4 + 3 * 8, "fp32": 4 + 3 * 4}
+# 1/|Omega| and the slot word; per mesh edge the code word and nx, ny, l.
+LAYOUT_BYTES_PER_CELL = {"fp64": 2 * 24 + 3 * 8 + 4, "fp32": 2 * 16 + 3 * 4 + 4}
+LAYOUT_BYTES_PER_EDGE = {"fp64": 4 + 3 * 8, "fp32": 4 + 3 * 4}
+# FP64 arithmetic per wet cell-update of the step kernel (DADD + DMUL + 2 DFMA thread
+# instructions executed, ncu counters on the 1,000,000-cell wet lake: 3.187e8 FLOP per
+# launch over 991,485 wet cells); dry cells take no FP64 instruction.
+FP64_FLOP_PER_WET_CELL = 321.4
+FP64_PEAK_TFLOPS = 1.2023  # 296 DFMA lanes per cycle (ncu peak) x 2 FLOP x 2.031 GHz
 HBM_FALLBACK_GBS = 6400.0
+T_WINDOWS = (0.0, 600.0, 1800.0, 3600.0)  # the floodplain run's sampled times [s]
 KERNEL_NAME = {"fp64": "step_pipe<double, 0>", "fp32": "step_pipe<float, 0>"}  # without flood tracking
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=200, help="timed steps of each floodplain window")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=50, help="steps per end-to-end call")
-    ap.add_argument("--e2e-iters", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=50, help="steps of the oracle accuracy check")
+    ap.add_argument("--t-end", type=float, default=3600.0, help="simulated seconds of the floodplain run")
+    ap.add_argument("--ensemble-members", type=int, default=64, help="members of the ensemble leg (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=50, help="requests of the serving leg (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle (and the accuracy check)")
     ap.add_argument("--precisions", default="fp64,fp32")
     ap.add_argument("--lake-steps", type=int, default=500,
                     help="steps of the mostly wet lake-at-rest line (0: skip it)")
-    ap.add_argument("--track-steps", type=int, default=500,
+    ap.add_argument("--track-steps", type=int, default=200,
                     help="steps of the flood-tracking and passive-species cost line (0: skip it)")
     ap.add_argument("--stress-steps", type=int, default=100000, help="stress: lake-at-rest steps")
-    ap.add_argument("--workload", choices=["floodplain", "ensemble", "serve", "stress"], default="floodplain",
-                    help="floodplain: the default line; ensemble: batched uneven meshes; serve: request loop")
+    ap.add_argument("--workload", choices=["floodplain", "ensemble", "serve", "stress", "lake"],
+                    default="floodplain",
+                    help="floodplain: the default line; ensemble: batched uneven meshes; serve: request loop; "
+                         "lake: the wet-lake leg alone")
     ap.add_argument("--instances", type=int, default=256, help="ensemble members")
     ap.add_argument("--requests", type=int, default=200, help="serving trace length")
     ap.add_argument("--rate", type=float, default=20.0, help="serving arrivals per second (Poisson)")
@@ -239,8 +258,38 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def floodplain_snapshots(s, st, t_end: float) -> list:
+    """States of the floodplain run at the sampled times (T_WINDOWS up to t_end): the
+    state st (fresh, at t = 0) runs from t = 0 and is downloaded at each, with the run's
+    step count and wet fraction.  Each precision samples its own run (the other
+    precision's state differs by its rounding: an FP32-bulk dry cell's surface lies up
+    to half an FP32 ulp of the bed offset above the FP64 bed, a film the FP64 step would
+    have to flux)."""
+    snaps = []
+    for tw in [t for t in T_WINDOWS if t <= t_end]:
+        if tw > 0:
+            st.run_until(tw)
+        H, qx, qy, t = st.download()
+        snaps.append({"t": t, "H": H, "qx": qx, "qy": qy, "steps": st.stats(volume=False)["steps"],
+                      "wet": float(np.mean(H - s.z > s.params["h_min"]))})
+    return snaps
+
+
+def step_weighted(snaps: list, ms: list) -> tuple[int, float]:
+    """The run's steps and its time from the windows' times per step: trapezoids
+    between consecutive windows, weighted by the steps the run took between them."""
+    total_ms = 0.0
+    for a in range(len(snaps) - 1):
+        total_ms += (snaps[a + 1]["steps"] - snaps[a]["steps"]) * 0.5 * (ms[a] + ms[a + 1])
+    steps = snaps[-1]["steps"] - snaps[0]["steps"]
+    if steps <= 0:  # a single window
+        return 1, ms[0]
+    return steps, total_ms
+
+
 def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
-    """Timed steps, per-kernel timing, roofline and the end-to-end leg of one precision."""
+    """The floodplain windows, the whole-run rate, the rooflines and the end-to-end run of
+    one precision."""
     def barrier():
         if dist is not None:
             dist.barrier()
@@ -254,69 +303,93 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
 
     n = s.n_cells
     st = bm.State.from_scenario(s, mesh=mesh, precision=prec)
+    snaps = floodplain_snapshots(s, st, args.t_end)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     st.set_stream(stream.cuda_stream)
-    st.step(args.warmup)
-    H0, _, _, _ = st.download()
-    wet0 = float(np.mean(H0 - s.z > 1e-6))
-    clocks = ClockSampler(torch.cuda.current_device())
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    st.step_async(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    st.sync()
-    ms_max, value = replica_aggregate(dist, n, args.steps, e0.elapsed_time(e1), device="cuda")
-    stats = st.stats()
-    H1, _, _, _ = st.download()
-    wet1 = float(np.mean(H1 - s.z > 1e-6))
-
-    # dominant kernel: average duration of the step kernel, events around each launch
-    nk = min(args.steps, 200)
-    k_ms, _ = st.step_timed(nk)
-    kern_s = k_ms / nk / 1e3
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
-    bytes_launch = BYTES_PER_CELL[prec] * n + BYTES_PER_EDGE[prec] * mesh.info["n_edges"]
-    hbm_gbs = bytes_launch / kern_s / 1e9
-    traffic = ncu_traffic(prec)
-    roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm,
-            "traffic": traffic, "kernel": KERNEL_NAME[prec], "kernel_ms": kern_s * 1e3,
-            "algorithmic_bytes_per_launch": bytes_launch,
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    windows, ms_list = [], []
+    for sn in snaps:
+        st.upload(sn["H"], sn["qx"], sn["qy"], sn["t"])
+        st.step(args.warmup)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.step_async(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        st.sync()
+        ms = allmax(e0.elapsed_time(e1)) / args.steps
+        ms_list.append(ms)
+        w = {"t_s": sn["t"], "wet_fraction": sn["wet"], "ms_per_step": ms,
+             "value": n * ws / (ms / 1e3),
+             "hbm_frac": BYTES_PER_CELL_UPDATE[prec] * n / (ms / 1e3) / 1e9 / hbm}
+        if prec == "fp64":
+            w["fp64_frac"] = FP64_FLOP_PER_WET_CELL * sn["wet"] * n / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS
+        windows.append(w)
+    steps, total_ms = step_weighted(snaps, ms_list)
+    ms_run = total_ms / steps  # the run's mean time per step (= mean launch duration: one launch a step)
+    value = n * ws / (ms_run / 1e3)
 
-    # end to end through the C ABI with pinned host buffers: upload, E steps, download
-    E = args.e2e_steps
+    # dominant kernel (the step kernel, the only one in the timed windows): algorithmic
+    # bytes per launch over the run's mean launch duration
+    bytes_launch = BYTES_PER_CELL_UPDATE[prec] * n
+    layout_bytes = LAYOUT_BYTES_PER_CELL[prec] * n + LAYOUT_BYTES_PER_EDGE[prec] * mesh.info["n_edges"]
+    roof = {"bound": "hbm", "achieved": bytes_launch / (ms_run / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": bytes_launch / (ms_run / 1e3) / 1e9 / hbm, "traffic": ncu_traffic(prec),
+            "kernel": KERNEL_NAME[prec], "kernel_ms": ms_run,
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "bytes": f"{BYTES_PER_CELL_UPDATE[prec]} B per cell-update (every cell every step)",
+            "layout_bytes_per_launch": layout_bytes,
+            "layout_frac": layout_bytes / (ms_run / 1e3) / 1e9 / hbm,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
+    if prec == "fp64":
+        wet_steps = sum((snaps[a + 1]["steps"] - snaps[a]["steps"]) * 0.5 * (snaps[a]["wet"] + snaps[a + 1]["wet"])
+                        for a in range(len(snaps) - 1)) or snaps[0]["wet"]
+        flop = FP64_FLOP_PER_WET_CELL * n * wet_steps / max(steps, 1)  # per launch, run mean
+        roof_fp64 = {"bound": "alu", "achieved": flop / (ms_run / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": flop / (ms_run / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                     "flop_per_launch": flop,
+                     "flops": f"{FP64_FLOP_PER_WET_CELL} FP64 FLOP per wet cell-update",
+                     "peak_source": "ncu peak: 296 DFMA per cycle x 2 x 2.031 GHz"}
+    else:
+        roof_fp64 = None
+
+    # end to end, the configuration as a user runs it through the C ABI: the initial
+    # state from pinned host memory, bm_run_until(t_end), the final state back
     pin = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(6)]
     Hh, qxh, qyh, Ho, qxo, qyo = [p.numpy() for p in pin]
     Hh[:], qxh[:], qyh[:] = s.H, s.qx, s.qy
-    times = []
-    for it in range(args.e2e_iters + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st.upload(Hh, qxh, qyh, 0.0)
-        st.step(E)
-        bm.bm_state_download(st.handle, n, Ho, qxo, qyo)
-        t1 = time.perf_counter()
-        if it > 0:
-            times.append(t1 - t0)
-    e2e_t = max(allmax(statistics.median(times)), 1e-12)
-    e2e = {"value": n * E * ws / e2e_t, "unit": METRIC, "h2d_bytes_per_step": 3 * 8 * n / E,
-           "d2h_bytes_per_step": 3 * 8 * n / E,
-           "call": f"bm_state_upload + bm_step({E}) + bm_state_download, pinned host arrays"}
-    final = (Ho.copy(), qxo.copy(), qyo.copy())
-    out = {"value": value, "ms_per_step": ms_max / args.steps, "roofline": roof, "e2e": e2e, "clocks": clk,
-           "gpu_launches": args.steps, "sim_time_s": stats["t"], "wet_fraction": [wet0, wet1]}
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st.upload(Hh, qxh, qyh, 0.0)
+    st.run_until(args.t_end)
+    bm.bm_state_download(st.handle, n, Ho, qxo, qyo)
+    wall = allmax(time.perf_counter() - t0)
+    clk = clocks.stop()
+    e2e_steps = st.stats(volume=False)["steps"]
+    e2e = {"value": n * e2e_steps * ws / wall, "unit": METRIC, "wall_s": wall, "steps": e2e_steps,
+           "h2d_bytes_per_step": 3 * 8 * n / e2e_steps, "d2h_bytes_per_step": 3 * 8 * n / e2e_steps,
+           "call": f"bm_state_upload + bm_run_until({args.t_end:g} s) + bm_state_download, pinned host arrays"}
+
+    # accuracy leg: the first steps from t = 0 (compared with the oracle by the caller)
+    st.upload(s.H, s.qx, s.qy, 0.0)
+    st.step(args.e2e_steps)
+    Hf, qxf, qyf, _ = st.download()
+    out = {"value": value, "ms_per_step": ms_run, "steps_run": steps, "windows": windows, "roofline": roof,
+           "windows_desc": ", ".join(f"{sn['t']:g}" for sn in snaps),
+           "roofline_fp64": roof_fp64, "e2e": e2e, "clocks": clk,
+           "gpu_launches": args.steps * len(snaps)}
     st.close()
-    return out, final
+    return out, (Hf, qxf, qyf)
 
 
 def measure_lake(args, torch, bm, W):
@@ -327,8 +400,10 @@ def measure_lake(args, torch, bm, W):
     must stay at rest)."""
     s = W.fractal_lake()
     mesh = bm.Mesh.from_scenario(s)
+    n_wet = int(np.count_nonzero(s.H - s.z > s.params["h_min"]))
+    hbm = measured_peaks().get("hbm_gbs", HBM_FALLBACK_GBS)
     out = {"workload": "lake at rest, 1,000,000 triangles, z = 400 m + fractal relief (5 m), surface 403 m",
-           "cells": s.n_cells, "wet_fraction": float(np.mean(s.H - s.z > 1e-6)), "steps": args.lake_steps}
+           "cells": s.n_cells, "wet_fraction": n_wet / s.n_cells, "steps": args.lake_steps}
     for prec in [p for p in args.precisions.split(",") if p]:
         st = bm.State.from_scenario(s, mesh=mesh, precision=prec)
         stream = torch.cuda.Stream()
@@ -350,11 +425,26 @@ def measure_lake(args, torch, bm, W):
         wet = h > 1e-3
         speed = float(np.max(np.hypot(qx[wet], qy[wet]) / h[wet])) if wet.any() else 0.0
         v1 = st.stats()["volume"]
-        out["fp32_bulk" if prec == "fp32" else prec] = {
-            "value": s.n_cells * args.lake_steps / (ms / 1e3), "unit": METRIC, "ms_per_step": ms / args.lake_steps,
-            "max_speed_ms": speed, "rel_volume_change": abs(v1 - v0) / abs(v0)}
+        r = {"value": s.n_cells * args.lake_steps / (ms / 1e3), "unit": METRIC, "ms_per_step": ms / args.lake_steps,
+             "max_speed_ms": speed, "rel_volume_change": abs(v1 - v0) / abs(v0),
+             "hbm_frac": BYTES_PER_CELL_UPDATE[prec] * s.n_cells / (ms / args.lake_steps / 1e3) / 1e9 / hbm}
+        if prec == "fp64":
+            flop = FP64_FLOP_PER_WET_CELL * n_wet
+            achieved = flop / (ms / args.lake_steps / 1e3) / 1e12
+            r["roofline_fp64_arith"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                                        "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                                        "flop_per_launch": flop,
+                                        "flops": f"{FP64_FLOP_PER_WET_CELL} FP64 FLOP per wet cell-update x "
+                                                 f"{n_wet} wet cells"}
+        out["fp32_bulk" if prec == "fp32" else prec] = r
         st.close()
     return out
+
+
+def run_lake(args, ws, rank, torch, bm, W):
+    """The wet-lake leg alone (its own line)."""
+    print(json.dumps(measure_lake(args, torch, bm, W)), flush=True)
+    return 0
 
 
 def measure_tracking(args, torch, bm, W):
@@ -479,6 +569,80 @@ def run_stress(args, ws, rank, torch, bm, W):
     return 0
 
 
+def ensemble_leg(args, torch, bm, W, n_members: int, steps: int) -> dict:
+    """Batched FP32-bulk ensemble: n_members floodplain-recipe meshes, log-uniform sizes in
+    [5k, 500k] triangles (member k seeded 5000 + k), stepped together by one launch per
+    step (each member with its own dt), launch shape from the autotuner; steps timed
+    with CUDA events after warm-up."""
+    scs = [W.ensemble_instance(k) for k in range(n_members)]
+    meshes = [bm.Mesh.from_scenario(x) for x in scs]
+    sts = [bm.State.from_scenario(x, mesh=m, precision="fp32") for x, m in zip(scs, meshes)]
+    b = bm.Batch(sts)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    b.set_stream(stream.cuda_stream)
+    best, _ = b.autotune(5)
+    b.step(args.warmup)
+    cells = sum(x.n_cells for x in scs)
+    clocks = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step_async(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    b.sync()
+    ms = e0.elapsed_time(e1)
+    b.close()
+    for x in sts:
+        x.close()
+    return {"workload": f"{n_members} floodplain-recipe meshes, log-uniform 5k-500k triangles ({cells} cells), "
+                        f"FP32-bulk, one launch per step, per-member dt", "members": n_members, "cells": cells,
+            "steps": steps, "value": cells * steps / (ms / 1e3), "unit": METRIC, "ms_per_step": ms / steps,
+            "ctas_per_sm": best, "clocks": clk, "gpu_launches": steps}
+
+
+def serving_leg(args, torch, bm, W, n_requests: int, rate: float = 20.0, pool: int = 6,
+                time_scale: float = 0.1, precision: str = "fp32") -> dict:
+    """Request loop: Poisson arrivals at `rate` per second of flood scenarios on a pool of
+    meshes (sizes log-uniform in [10k, 2M] triangles), each run for a duration drawn
+    from U[600, 7200] s x time_scale; a bounded trace of n_requests arrivals, then
+    drained.  p50 / p99 time-to-result (submission to result) and the throughput."""
+    rng = np.random.default_rng(6)
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(2e6), pool)).astype(int)
+    scs = [W.ensemble_instance(1000 + k, size_override=int(n)) for k, n in enumerate(sizes)]
+    meshes = [bm.Mesh.from_scenario(x) for x in scs]
+    sv = bm.Server(precision=precision, steps_per_round=32)
+    gaps = rng.exponential(1.0 / rate, n_requests)
+    picks = rng.integers(0, pool, n_requests)
+    t_ends = rng.uniform(600.0, 7200.0, n_requests) * time_scale
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    tickets = []
+    t_start = time.perf_counter()
+    next_t = t_start
+    for k in range(n_requests):
+        next_t += gaps[k]
+        while time.perf_counter() < next_t:
+            time.sleep(min(0.001, max(0.0, next_t - time.perf_counter())))
+        x = scs[picks[k]]
+        tickets.append(sv.submit(meshes[picks[k]], x.H, x.qx, x.qy, t_end=float(t_ends[k]), **x.params))
+    lat = [sv.wait(tk, 3600.0)[3] for tk in tickets]
+    wall = time.perf_counter() - t_start
+    clk = clocks.stop()
+    stt = sv.stats()
+    sv.close()
+    return {"workload": f"{n_requests} Poisson arrivals at {rate:g}/s, {pool}-mesh pool log-uniform 10k-2M "
+                        f"triangles ({', '.join(str(int(n)) for n in sizes)}), durations U[600, 7200] s x {time_scale:g}, "
+                        f"{precision.upper()}", "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "throughput": stt["cell_updates"] / wall, "unit": METRIC,
+            "wall_s": wall, "completed": stt["completed"], "clocks": clk}
+
+
 def run_ensemble(args, ws, rank, torch, bm, W):
     """Batched ensemble: args.instances floodplain-recipe meshes, log-uniform sizes in
     [5k, 500k] triangles (member k seeded 5000 + k), stepped together by one launch
@@ -579,7 +743,7 @@ def main():
         from paper_2102_12862_b300 import bm
         from paper_2102_12862_b300 import workloads as W
         torch.cuda.set_device(local)
-        fn = {"ensemble": run_ensemble, "serve": run_serve, "stress": run_stress}[args.workload]
+        fn = {"ensemble": run_ensemble, "serve": run_serve, "stress": run_stress, "lake": run_lake}[args.workload]
         return fn(args, ws, rank, torch, bm, W) if rank == 0 or ws == 1 else 0
 
     import torch
@@ -600,6 +764,9 @@ def main():
         res[p], finals[p] = measure(args, p, s, mesh, torch, bm, dist, ws, rank)
 
     lake = measure_lake(args, torch, bm, W) if (rank == 0 and args.lake_steps > 0) else None
+    ens = (ensemble_leg(args, torch, bm, W, args.ensemble_members, args.steps)
+           if (rank == 0 and args.ensemble_members > 0) else None)
+    serve = serving_leg(args, torch, bm, W, args.serve_requests) if (rank == 0 and args.serve_requests > 0) else None
     tracking = measure_tracking(args, torch, bm, W) if (rank == 0 and args.track_steps > 0) else None
 
     cpu, acc = None, {}
@@ -619,25 +786,35 @@ def main():
     if rank == 0:
         main_p = precs[0]
         r = res[main_p]
+        windows_desc = r["windows_desc"]
         line = {"metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_p == "fp64" else "f32+f64",
                 "data": "synthetic",
-                "config": {"workload": f"floodplain 2,000,000 triangles, {main_p.upper()}, K steps from t = 0 after "
-                                       f"{args.warmup} warm-up steps", "cells": s.n_cells,
-                           "edges": mesh.info["n_edges"], "precision": main_p,
+                "config": {"workload": f"floodplain 2,000,000 triangles, {main_p.upper()}, the {args.t_end:g} s run: "
+                                       f"windows of K steps after {args.warmup} warm-up steps from its states at "
+                                       f"t = {windows_desc} s (a GPU run of the same precision made them), value = the run's "
+                                       f"{r['steps_run']} steps over their step-weighted time",
+                           "cells": s.n_cells, "edges": mesh.info["n_edges"], "precision": main_p,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                           "l2": "working set > 126 MB L2, no flush", "sim_time_s": r["sim_time_s"],
-                           "wet_fraction_first_last": r["wet_fraction"], "e2e_steps_per_call": args.e2e_steps},
-                "roofline": r["roofline"], "e2e": r["e2e"], "gpu_launches": r["gpu_launches"],
-                "clocks": r["clocks"], "cpu_baseline": cpu, "accuracy_vs_oracle": acc.get(main_p)}
+                           "l2": "working set > 126 MB L2, no flush", "sim_time_s": args.t_end,
+                           "oracle_check_steps": args.e2e_steps},
+                "windows": r["windows"], "at_t0": r["windows"][0],
+                "roofline": r["roofline"], "roofline_fp64_arith": r["roofline_fp64"],
+                "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "cpu_baseline": cpu,
+                "accuracy_vs_oracle": acc.get(main_p)}
         for p in precs[1:]:
             q = res[p]
             key = "fp32_bulk" if p == "fp32" else p
             line[key] = {"value": q["value"], "unit": METRIC, "ms_per_step": q["ms_per_step"],
-                         "dtype": "f32+f64" if p == "fp32" else "f64", "roofline": q["roofline"], "e2e": q["e2e"],
-                         "clocks": q["clocks"], "gpu_launches": q["gpu_launches"], "sim_time_s": q["sim_time_s"],
-                         "wet_fraction_first_last": q["wet_fraction"], "accuracy_vs_oracle": acc.get(p)}
+                         "dtype": "f32+f64" if p == "fp32" else "f64", "windows": q["windows"],
+                         "roofline": q["roofline"], "e2e": q["e2e"], "clocks": q["clocks"],
+                         "gpu_launches": q["gpu_launches"], "accuracy_vs_oracle": acc.get(p)}
+        if ens is not None:
+            ens["vs_fp64_plain"] = ens["value"] / r["value"] if main_p == "fp64" else None
+            line["ensemble_fp32_bulk"] = ens
+        if serve is not None:
+            line["serving"] = serve
         if lake is not None:
             line["wet_lake"] = lake
         if tracking is not None:

@@ -126,7 +126,10 @@ void bm_mesh_destroy(bm_mesh* m);
  * Create a device-resident state on a mesh (Section "Initial conditions",
  * region-defined: free-surface elevation H and discharge q per cell).
  *   H, qx, qy  n_tri doubles each; qx/qy may be NULL for zeros.  H < z_bed is
- *              rejected (a dry cell is H = z_bed).  The time starts at 0.
+ *              rejected (a dry cell is H = z_bed); FP32_BULK accepts a surface down
+ *              to its own bed, the datum plus the bed's FP32 offset (what it returns
+ *              for a dry cell), so a downloaded state uploads again.  The time starts
+ *              at 0.
  * The mesh must outlive the state.  Allocates device memory.
  */
 bm_status bm_state_init(const bm_mesh* m, const bm_params* p, const double* H, const double* qx,
@@ -324,10 +327,28 @@ bm_status bm_state_test_timeout(bm_state* s);
 bm_status bm_state_set_launch(bm_state* s, int ctas_per_sm);
 
 /*
- * Autotuner: time steps_per_trial steps for each launch shape (as many CTAs per SM
- * as fit, and 1, 2, 3, 4 CTAs per SM), undo the trial steps (the state is
- * snapshotted in device memory and restored), keep the fastest shape and report it
- * and its time per step.  Allocates a temporary device copy of the state.
+ * The step kernel's schedule: the launch shape (as bm_state_set_launch) and the static
+ * share of the work tickets, static_sixteenths / 16 of them handed to the CTAs in a
+ * fixed round-robin (known a step ahead, no atomic), the rest from a launch-wide
+ * counter (balancing uneven tiles); -1 = the precision's default (FP64 4/16, FP32-bulk
+ * 10/16), at least two tickets per CTA are static.  Results do not depend on it (the
+ * reductions are order-free).  BM_EINVAL outside [-1, 16].  get returns both.
+ */
+bm_status bm_state_set_schedule(bm_state* s, int ctas_per_sm, int static_sixteenths);
+bm_status bm_state_get_schedule(bm_state* s, int* ctas_per_sm, int* static_sixteenths);
+
+/*
+ * Autotuner: time steps_per_trial steps for each schedule, in two rounds -- the launch
+ * shapes (as many CTAs per SM as fit, and 1, 2, 3, 4 CTAs per SM; shapes giving the
+ * same grid are timed once) at the current static share, then the static shares 0, 2,
+ * ..., 16 sixteenths and the default at the best shape -- undo the trial steps (the
+ * state is snapshotted in device memory and restored), keep the fastest schedule and
+ * report its shape and time per step (bm_state_get_schedule gives the share).
+ * Allocates a temporary device copy of the state.  Results do not depend on it.  The
+ * step kernel's other shape parameters are fixed at compile time: 256-cell tiles of
+ * one cell per thread (8 compute warps and 1 copy warp; the tile records are built
+ * for that size) and 3 shared-memory slots (the size that lets 2 FP64 / 3 FP32 CTAs
+ * share an SM).
  */
 bm_status bm_state_autotune(bm_state* s, int steps_per_trial, int* best_ctas_per_sm, double* ms_per_step);
 
@@ -347,6 +368,8 @@ bm_status bm_batch_info(const bm_batch* b, int32_t* n_members, int64_t* n_cells,
 bm_status bm_batch_set_stream(bm_batch* b, void* cuda_stream);
 /* Launch shape, as bm_state_set_launch; the autotuner as bm_state_autotune. */
 bm_status bm_batch_set_launch(bm_batch* b, int ctas_per_sm);
+bm_status bm_batch_set_schedule(bm_batch* b, int ctas_per_sm, int static_sixteenths);
+bm_status bm_batch_get_schedule(bm_batch* b, int* ctas_per_sm, int* static_sixteenths);
 bm_status bm_batch_autotune(bm_batch* b, int steps_per_trial, int* best_ctas_per_sm, double* ms_per_step);
 /* Every member takes n_steps steps with its own dt (Eq. 21); blocks; returns the
  * first member's BM_ENONFINITE / BM_ENEGDEPTH if any. */

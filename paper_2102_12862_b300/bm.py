@@ -64,6 +64,10 @@ SIGNATURES = {
     "bm_step_timed": (C.c_int, [_vp, _i64, _P(_d), _P(_d)]),
     "bm_state_test_timeout": (C.c_int, [_vp]),
     "bm_state_set_launch": (C.c_int, [_vp, C.c_int]),
+    "bm_state_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "bm_state_get_schedule": (C.c_int, [_vp, _P(C.c_int), _P(C.c_int)]),
+    "bm_batch_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "bm_batch_get_schedule": (C.c_int, [_vp, _P(C.c_int), _P(C.c_int)]),
     "bm_batch_create": (C.c_int, [_P(_vp), C.c_int32, _P(_vp)]),
     "bm_batch_destroy": (None, [_vp]),
     "bm_batch_info": (C.c_int, [_vp, _P(C.c_int32), _P(_i64), _P(_i64)]),
@@ -376,6 +380,26 @@ def bm_batch_set_stream(batch: int, stream_ptr: int):
     _check(load_library().bm_batch_set_stream(batch, stream_ptr or None))
 
 
+def bm_state_set_schedule(state: int, ctas_per_sm: int, static_sixteenths: int = -1):
+    _check(load_library().bm_state_set_schedule(state, int(ctas_per_sm), int(static_sixteenths)))
+
+
+def bm_state_get_schedule(state: int) -> tuple[int, int]:
+    c, s = C.c_int(), C.c_int()
+    _check(load_library().bm_state_get_schedule(state, C.byref(c), C.byref(s)))
+    return c.value, s.value
+
+
+def bm_batch_set_schedule(batch: int, ctas_per_sm: int, static_sixteenths: int = -1):
+    _check(load_library().bm_batch_set_schedule(batch, int(ctas_per_sm), int(static_sixteenths)))
+
+
+def bm_batch_get_schedule(batch: int) -> tuple[int, int]:
+    c, s = C.c_int(), C.c_int()
+    _check(load_library().bm_batch_get_schedule(batch, C.byref(c), C.byref(s)))
+    return c.value, s.value
+
+
 def bm_batch_set_launch(batch: int, ctas_per_sm: int):
     _check(load_library().bm_batch_set_launch(batch, int(ctas_per_sm)))
 
@@ -534,6 +558,13 @@ class State:
     def set_launch(self, ctas_per_sm: int):
         bm_state_set_launch(self.handle, ctas_per_sm)
 
+    def set_schedule(self, ctas_per_sm: int, static_sixteenths: int = -1):
+        bm_state_set_schedule(self.handle, ctas_per_sm, static_sixteenths)
+
+    def schedule(self) -> tuple[int, int]:
+        """(CTAs per SM, static share of the tickets in sixteenths; -1 = default)."""
+        return bm_state_get_schedule(self.handle)
+
     def autotune(self, steps_per_trial: int = 20) -> tuple[int, float]:
         return bm_state_autotune(self.handle, steps_per_trial)
 
@@ -575,6 +606,12 @@ class Batch:
 
     def set_launch(self, ctas_per_sm: int):
         bm_batch_set_launch(self.handle, ctas_per_sm)
+
+    def set_schedule(self, ctas_per_sm: int, static_sixteenths: int = -1):
+        bm_batch_set_schedule(self.handle, ctas_per_sm, static_sixteenths)
+
+    def schedule(self) -> tuple[int, int]:
+        return bm_batch_get_schedule(self.handle)
 
     def autotune(self, steps_per_trial: int = 10) -> tuple[int, float]:
         return bm_batch_autotune(self.handle, steps_per_trial)

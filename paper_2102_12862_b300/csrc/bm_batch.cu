@@ -47,8 +47,10 @@ struct bm_batch {
 };
 
 namespace bm {
-bm_status autotune_shape(std::vector<bm_state*> states, int steps, int* best, double* best_ms,
-                         const std::function<bm_status(int)>& set_shape,
+bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_ctas, int start_static, int* best,
+                         int* best_static,
+                         double* best_ms, const std::function<bm_status(int, int)>& set_shape,
+                         const std::function<int(int)>& grid_of,
                          const std::function<bm_status(int)>& run_steps, cudaStream_t st);
 namespace {
 
@@ -125,6 +127,7 @@ bm_status use_active_members(bm_batch* b) {
   if (!l) return fail(BM_ENOMEM, "bm_batch_run_until: out of host memory");
   bm_status st = build_step_list(act, dptr, l.get());
   if (st != BM_OK) return st;
+  l->static16 = b->list.static16;
   b->sub_grid = step_grid(*l, b->shape);
   b->sub = std::move(l);
   return BM_OK;
@@ -294,6 +297,28 @@ bm_status bm_batch_set_launch(bm_batch* b, int ctas_per_sm) {
   return BM_OK;
 }
 
+bm_status bm_batch_set_schedule(bm_batch* b, int ctas_per_sm, int static_sixteenths) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_set_schedule: batch is NULL");
+  if (static_sixteenths < -1 || static_sixteenths > 16)
+    return fail(BM_EINVAL, "bm_batch_set_schedule: static_sixteenths in [-1, 16]");
+  if (static_sixteenths != b->list.static16) {
+    BM_CUDA(cudaStreamSynchronize(b->stream));
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);  // they carry the old share
+    b->graphs.clear();
+    b->list.static16 = static_sixteenths;
+  }
+  return bm_batch_set_launch(b, ctas_per_sm);
+}
+
+bm_status bm_batch_get_schedule(bm_batch* b, int* ctas_per_sm, int* static_sixteenths) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_get_schedule: batch is NULL");
+  if (ctas_per_sm) *ctas_per_sm = b->shape;
+  if (static_sixteenths) *static_sixteenths = b->list.static16;
+  return BM_OK;
+}
+
 bm_status bm_batch_step_async(bm_batch* b, int64_t n_steps) {
   clear_error();
   if (!b) return fail(BM_EINVAL, "bm_batch_step: batch is NULL");
@@ -381,8 +406,9 @@ bm_status bm_batch_autotune(bm_batch* b, int steps_per_trial, int* best_ctas_per
     if (st != BM_OK) return st;
   }
   bm_status st = autotune_shape(
-      b->members, steps_per_trial, best_ctas_per_sm, ms_per_step, [&](int c) { return bm_batch_set_launch(b, c); },
-      [&](int n) { return batch_enqueue(b, n); }, b->stream);
+      b->members, steps_per_trial, b->shape, b->list.static16, best_ctas_per_sm, nullptr, ms_per_step,
+      [&](int c, int s16) { return bm_batch_set_schedule(b, c, s16); },
+      [&](int c) { return step_grid(b->list, c); }, [&](int n) { return batch_enqueue(b, n); }, b->stream);
   if (st == BM_OK && finite) st = batch_set_end(b, keep.data());
   return st;
 }

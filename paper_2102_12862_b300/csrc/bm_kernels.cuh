@@ -176,6 +176,41 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// Comparisons, minima and maxima of FP64 values on the integer pipes: B300 issues FP64
+// instructions at 2 lanes per SM and cycle and integer ones at 64, and the wet-cell
+// step is bound by its FP64 pipe, so every FP64 comparison or min / max moved off it
+// is time saved.  okey is an order-preserving integer key of a double (for x, y not
+// NaN: key(x) <= key(y) exactly when x <= y, except that -0 sorts below +0).  For
+// non-NaN arguments the helpers equal the IEEE operations, up to which zero of a
+// (-0, +0) pair fmin / fmax return; the float overloads are the FP32 operations.
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }  // x > 0
+__device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+__device__ __forceinline__ bool ge0(double x) { return okey(x) >= -1; }  // x >= 0, -0 included
+__device__ __forceinline__ bool ge0(float x) { return x >= 0.0f; }
+__device__ __forceinline__ bool le0(double x) { return okey(x) <= 0; }  // x <= 0
+__device__ __forceinline__ bool le0(float x) { return x <= 0.0f; }
+__device__ __forceinline__ bool gt(double x, double y) { return okey(x) > okey(y); }  // x > y
+__device__ __forceinline__ bool gt(float x, float y) { return x > y; }
+__device__ __forceinline__ double pos(double x) { return gt0(x) ? x : 0.0; }  // max(0, x)
+__device__ __forceinline__ float pos(float x) { return fmaxf(0.0f, x); }
+__device__ __forceinline__ double dmax(double x, double y) { return okey(x) >= okey(y) ? x : y; }
+__device__ __forceinline__ float dmax(float x, float y) { return fmaxf(x, y); }
+__device__ __forceinline__ double dmin(double x, double y) { return okey(x) <= okey(y) ? x : y; }
+__device__ __forceinline__ float dmin(float x, float y) { return fminf(x, y); }
+// the larger of two non-negative values (their bit patterns order like the values)
+__device__ __forceinline__ double nmax(double x, double y) {
+  return __double_as_longlong(x) >= __double_as_longlong(y) ? x : y;
+}
+__device__ __forceinline__ float nmax(float x, float y) { return fmaxf(x, y); }
+__device__ __forceinline__ bool finite(double x) {
+  return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool finite(float x) { return isfinite(x); }
+
 // Elementary functions.  FP64: the IEEE-rounded library square root; division as a
 // times the Newton-refined reciprocal f_rcp below; cube roots through f_rcbrt below.
 // FP32-bulk: the hardware approximations (MUFU reciprocal square root, reciprocal,
@@ -212,7 +247,7 @@ __device__ __forceinline__ float f_exp2(float x) {
 // outside [1e-30, 1e30] (beyond the estimate's range) it falls back to 1 / cbrt(x).
 __device__ __forceinline__ float f_rcbrt(float x) { return f_exp2(__log2f(x) * (-1.0f / 3.0f)); }
 __device__ __forceinline__ double f_rcbrt(double x) {
-  if (!(x >= 1e-30 && x <= 1e30)) return 1.0 / cbrt(x);
+  if (!(okey(x) >= okey(1e-30) && okey(x) <= okey(1e30))) return 1.0 / cbrt(x);
   double r = static_cast<double>(f_rcbrt(static_cast<float>(x)));
   constexpr double kThird = 1.0 / 3.0;
   r = r * fma(-x, r * r * r, 4.0) * kThird;
@@ -244,9 +279,9 @@ __device__ __forceinline__ void hllc(T hL, T unL, T utL, T cL, T hR, T unR, T ut
   const T half = T(0.5), quarter = T(0.25), two = T(2), zero = T(0);
   const T us = half * (unL + unR) + cL - cR;
   const T cs = half * (cL + cR) + quarter * (unL - unR);
-  T SL = fmin(unL - cL, us - cs);
-  T SR = fmax(unR + cR, us + cs);
-  const bool ldry = !(hL > zero), rdry = !(hR > zero);
+  T SL = dmin(unL - cL, us - cs);
+  T SR = dmax(unR + cR, us + cs);
+  const bool ldry = !gt0(hL), rdry = !gt0(hR);
   SL = ldry ? unR - two * cR : (rdry ? unL - cL : SL);
   SR = ldry ? unR + cR : (rdry ? unL + two * cL : SR);
   pL = hg * hL * hL;
@@ -258,12 +293,12 @@ __device__ __forceinline__ void hllc(T hL, T unL, T utL, T cL, T hR, T unR, T ut
   const T H1 = FL1 - SL * ((FR1 - FL1) - SR * (FR0 - FL0)) * rd;
   // sign of the contact speed S* = num / den with den < 0 whenever a side is wet
   const T num = SL * hR * (unR - SR) - SR * hL * (unL - SL);
-  const T H2 = H0 * (num <= zero ? utL : utR);
+  const T H2 = H0 * (le0(num) ? utL : utR);
   // the side whose tangential velocity (and passive species) the flux carries
-  right = SL >= zero ? false : (SR <= zero ? true : !(num <= zero));
-  if (SL >= zero) {
+  right = ge0(SL) ? false : (le0(SR) ? true : !le0(num));
+  if (ge0(SL)) {
     F0 = FL0; F1 = FL1; F2 = FL2;
-  } else if (SR <= zero) {
+  } else if (le0(SR)) {
     F0 = FR0; F1 = FR1; F2 = FR2;
   } else {
     F0 = H0; F1 = H1; F2 = H2;
@@ -278,12 +313,12 @@ template <typename T>
 __device__ __forceinline__ void cell_derived(T h, T qx, T qy, T hmin, T g, T& u, T& v, T& c) {
   u = T(0);
   v = T(0);
-  if (h > hmin) {
+  if (gt(h, hmin)) {
     const T rh = f_div(T(1), h);
     u = qx * rh;
     v = qy * rh;
   }
-  c = f_sqrt(g * fmax(T(0), h));
+  c = f_sqrt(g * pos(h));
 }
 
 // The free surface H of an FP32-bulk cell is the unevaluated sum hi + lo of two
@@ -319,10 +354,40 @@ __device__ __forceinline__ T cell_rate(const T* nxs, const T* nys, const T* ls, 
   for (int k = 0; k < 3; ++k) {
     const T lam = fabs(u * nxs[idx[k]] + v * nys[idx[k]]) + c;  // |u.n| does not depend on the side
     const T ll = lam * ls[idx[k]];
-    rmax = fmax(rmax, T(0.75) * ll * ia);
+    rmax = nmax(rmax, T(0.75) * ll * ia);
     ssum += ll;
   }
   return cfl_mode == 1 ? ssum * ia : rmax;
+}
+
+// FP64 -> FP32 by integer operations (the mantissa truncated, magnitudes below the FP32
+// normal range to 0, above it and NaN to infinity): relative error below 2^-23 with no
+// conversion instruction, for the rate screen below.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned hi = static_cast<unsigned>(b >> 32);
+  const int e = static_cast<int>((hi >> 20) & 0x7ffu) - 896;  // the FP32 biased exponent
+  const unsigned m = static_cast<unsigned>(b >> 29) & 0x7fffffu;
+  const unsigned mag = e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : (static_cast<unsigned>(e) << 23) | m);
+  return __uint_as_float((hi & 0x80000000u) | mag);
+}
+
+// A single-precision screen of a wet FP64 cell's Eq. 21 rate (cell_rate of its depth
+// h and discharge (qx, qy)): inputs truncated to FP32, the hardware reciprocal and
+// reciprocal square root; relative error below 1e-5 of the FP64 rate.
+__device__ __forceinline__ float cell_rate_screen(const double* nxs, const double* nys, const double* ls,
+                                                  const int (&idx)[3], double h, double qx, double qy, double ia,
+                                                  float g, int cfl_mode) {
+  const float hf = f32_trunc(h), rh = __frcp_rn(hf);
+  const float u = f32_trunc(qx) * rh, v = f32_trunc(qy) * rh, c = f_sqrt(g * hf), iaf = f32_trunc(ia);
+  float rmax = 0.0f, ssum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float ll = (fabsf(u * f32_trunc(nxs[idx[k]]) + v * f32_trunc(nys[idx[k]])) + c) * f32_trunc(ls[idx[k]]);
+    rmax = fmaxf(rmax, 0.75f * ll * iaf);
+    ssum += ll;
+  }
+  return cfl_mode == 1 ? ssum * iaf : rmax;
 }
 
 // ------------------------------------------------------------------ flood tracking
@@ -843,8 +908,13 @@ __global__ void gather_surface_pair(const double* user, const int32_t* perm, int
   if (i >= n) return;
   const double H = user[perm[i]];
   if (!isfinite(H)) atomicOr(bad, 1);
-  if (H < zd[i]) atomicOr(bad, 2);
-  if (H <= zd[i]) {
+  // the state's own bed: the datum plus the bed's FP32 offset, formed as a download
+  // forms a dry cell's surface (it may round either way of the FP64 bed).  Below both
+  // beds is an error; at or below either, the cell is dry (so a downloaded dry cell
+  // uploads as dry, not as a film of the rounding)
+  const double Hb = datum + static_cast<double>(zf[i]);
+  if (H < zd[i] && H < Hb) atomicOr(bad, 2);
+  if (H <= zd[i] || H <= Hb) {
     hi[i] = zf[i];
     lo[i] = 0.0f;
   } else {

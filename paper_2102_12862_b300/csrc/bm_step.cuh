@@ -123,12 +123,6 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Order-preserving integer key of a double (for x, y not NaN: key(x) <= key(y)
-// implies x <= y), so wet/dry tests of FP64 cells need no FP64 instruction.
-__device__ __forceinline__ long long okey(double x) {
-  const long long b = __double_as_longlong(x);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
 __device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
 __device__ __forceinline__ bool is_zero(float x) { return (__float_as_uint(x) << 1) == 0u; }
 // h = H - z <= 0 for a cell (FP64: exact, from the keys; FP32-bulk: the pair's depth).
@@ -548,6 +542,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
   // precision (FP32-bulk: no FP64 instruction per cell; the max of the floats, converted
   // once, equals the max of the converted values)
   T rrun = T(0);
+  float smax = 0.0f;  // FP64: the largest rate screen this lane's warp has seen for the instance
   unsigned cnt = 0;   // tiles of the current instance this CTA completed
   int n_done = 0;     // FP64: tiles this CTA completed in the launch
   for (int k = 0;; ++k) {
@@ -634,10 +629,10 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
             zR = sZ[lR];
           }
           // modified states (hydrostatic reconstruction on the higher bed)
-          const T zs = fmax(zL, zR);
-          const T h1 = fmax(zero, depth_of(HLh, HLl, zs));
-          const T h2 = fmax(zero, depth_of(HRh, HRl, zs));
-          if (h1 > zero || h2 > zero || inflow) {
+          const T zs = dmax(zL, zR);
+          const T h1 = pos(depth_of(HLh, HLl, zs));
+          const T h2 = pos(depth_of(HRh, HRl, zs));
+          if (gt0(h1) || gt0(h2) || inflow) {
             skipped = 0;
             const T nx = sNx[k2], ny = sNy[k2], l = sLn[k2];
             const T uL = U[lL], vL = V[lL], cL = C[lL];
@@ -646,7 +641,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
             if (R >= 0) {
               const T uR = U[lR], vR = V[lR], cR = C[lR];
               // the side with the higher bed keeps its own depth, hence its own celerity
-              const bool lhi = zL >= zR;
+              const bool lhi = !gt(zR, zL);  // zL >= zR
               const T clo = f_sqrt(g * (lhi ? h2 : h1));
               c1 = lhi ? cL : clo;
               c2 = lhi ? clo : cR;
@@ -829,7 +824,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
             }
           }
           h = depth_of(Hh, Hl, zi);
-          if (h > hmin && gn2 > zero) {
+          if (gt(h, hmin) && gt0(gn2)) {
             // split friction: two semi-implicit stages, Heun average.  With
             // a = dt k(q*), k(q) = g n^2 |q| / h^(7/3): q1 = q* / (1 + a), and since
             // |q1| = |q*| / (1 + a), q2 = q1 / (1 + dt k(q1)) = q* / (1 + 2a); so
@@ -850,7 +845,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
             ux = ux * fr;
             uy = uy * fr;
           }
-          if (!(h > hmin)) {
+          if (!gt(h, hmin)) {
             ux = zero;
             uy = zero;
           }
@@ -858,17 +853,32 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           if constexpr (kPair) a.Hlo[dst][i] = Hl;
           a.qx[dst][i] = ux;
           a.qy[dst][i] = uy;
-          if (!isfinite(Hh) || !isfinite(ux) || !isfinite(uy)) atomicOr(&a.ctl->status, 1);
+          if (!finite(Hh) || !finite(ux) || !finite(uy)) atomicOr(&a.ctl->status, 1);
           // negative depth: below -h_min, beyond the rounding of the FP32 bed offset in FP32-bulk
           const T negtol = kPair ? hmin + T(4) * static_cast<T>(FLT_EPSILON) * fabs(zi) : hmin;
-          if (h < -negtol) atomicOr(&a.ctl->status, 2);
+          if (gt(-negtol, h)) atomicOr(&a.ctl->status, 2);
           if constexpr (kExtra) {
             if (trk) track_update<T, kFull>(a, i, rec, h, ux, uy, gn2, hmin, new_time(cs, 1));
           }
         }
-        T u, v, c;
-        cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
-        if (h > hmin) rrun = fmax(rrun, cell_rate<T>(sNx, sNy, sLn, idx, u, v, c, ia, a.p.cfl_mode));
+        T u = zero, v = zero, c = zero;
+        const bool wet = gt(h, hmin);
+        if constexpr (SL::k64) {
+          // Eq. 21's rate: a single-precision screen of every wet cell, and the exact
+          // FP64 rate only where the screen comes within 1e-4 of the largest screen the
+          // warp has seen for this instance (the screen is within 1e-5 of the rate, so a
+          // cell below that cannot hold the instance's maximum, which stays exactly the
+          // FP64 value); after the first tiles few cells pass
+          const float scr = wet ? cell_rate_screen(sNx, sNy, sLn, idx, h, ux, uy, ia, a.p.g_f, a.p.cfl_mode) : 0.0f;
+          smax = fmaxf(smax, __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(scr))));
+          if (wet && scr >= smax * 0.9999f) {
+            cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
+            rrun = nmax(rrun, cell_rate<T>(sNx, sNy, sLn, idx, u, v, c, ia, a.p.cfl_mode));
+          }
+        } else {
+          cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
+          if (wet) rrun = nmax(rrun, cell_rate<T>(sNx, sNy, sLn, idx, u, v, c, ia, a.p.cfl_mode));
+        }
         // inflow cells: conveyance weight and depth of the new state; weir cells: the
         // weir edges' rates of Eq. 21 at the new state (h-Q edges: finalize_hq)
 #pragma unroll
@@ -883,7 +893,10 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           }
         }
         if constexpr (kFull) {
-          if (inf.flags & 16u) rrun = fmax(rrun, weir_rate<T>(a, sLR, sNx, sNy, sLn, idx, Hh, Hl, zi, h, u, v, ia));
+          if (inf.flags & 16u) {
+            cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
+            rrun = fmax(rrun, weir_rate<T>(a, sLR, sNx, sNy, sLn, idx, Hh, Hl, zi, h, u, v, ia));
+          }
         }
       }
     }
@@ -949,6 +962,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
         finalize_step<T>(a, cs, prime ? 0 : 1);
       }
       rrun = T(0);
+      smax = 0.0f;
       cnt = 0;
     }
     // FP64: boundary, inflow and wet tiles are taken early in the next launch (only the

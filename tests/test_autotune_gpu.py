@@ -33,3 +33,66 @@ def test_batch_autotune_keeps_end_times():
     assert best in (0, 1, 2, 3, 4, 6, 8)
     b.run_until([5.0, 9.0, 3.0])
     assert [st.stats()["t"] for st in sts] == [5.0, 9.0, 3.0]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_schedule_does_not_change_results(precision):
+    """Every launch shape and static share of the tickets gives bitwise the same run
+    (the reductions are order-free), also after changing it mid-run."""
+    s = W.floodplain(nx=200, ny=80, Lx=2000.0, Ly=800.0, seed=72)
+    ref = bm.State.from_scenario(s, precision=precision)
+    ref.step(60)
+    R = ref.download()
+    for ctas, s16 in [(0, 0), (1, 16), (2, 6), (0, 12)]:
+        st = bm.State.from_scenario(s, precision=precision)
+        st.set_schedule(ctas, s16)
+        assert st.schedule() == (ctas, s16)
+        st.step(30)
+        st.set_schedule(1, -1)
+        st.step(30)
+        for x, y in zip(st.download(), R):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_set_schedule_rejects_bad_share():
+    s = W.dam_break()
+    st = bm.State.from_scenario(s)
+    for bad in (-2, 17):
+        with pytest.raises(bm.BMError):
+            st.set_schedule(0, bad)
+
+
+def _ms_per_step(st, n=200, reps=3):
+    import torch
+    stream = torch.cuda.Stream()
+    st.set_stream(stream.cuda_stream)
+    best = float("inf")
+    for _ in range(reps):
+        st.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.step_async(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st.sync()
+        best = min(best, e0.elapsed_time(e1) / n)
+    return best
+
+
+@pytest.mark.parametrize("workload,precision", [("floodplain", "fp32"), ("lake", "fp64")])
+def test_tuned_schedule_is_at_least_as_fast_as_the_default(workload, precision):
+    """On two workloads (a 500,000-cell floodplain in FP32-bulk, a 250,000-cell wet lake
+    in FP64) the autotuner's schedule steps at least as fast as the default (best of 3
+    windows of 200 steps each; 5 % for timing noise)."""
+    if workload == "floodplain":
+        s = W.floodplain(nx=800, ny=312, Lx=5000.0, Ly=2000.0, seed=73)
+    else:
+        s = W.fractal_lake(nx=500, ny=250)
+    tuned = bm.State.from_scenario(s, precision=precision)
+    best, ms = tuned.autotune(20)
+    ctas, s16 = tuned.schedule()
+    assert best == ctas and -1 <= s16 <= 16
+    default = bm.State.from_scenario(s, precision=precision)
+    t_def, t_tun = _ms_per_step(default), _ms_per_step(tuned)
+    assert t_tun <= 1.05 * t_def, (t_tun, t_def, (ctas, s16))

@@ -90,3 +90,30 @@ def test_fp32_auto_datum_and_roundtrip():
     st = bm.State.from_scenario(s, precision="fp32")  # datum NaN -> min(z) = 400
     H, qx, qy, t = st.download()
     assert np.max(np.abs(H - s.H)) <= 1e-7  # offsets 1 and 0.1 round to FP32 near 1e-8
+
+
+def test_fp32_downloaded_state_uploads_again():
+    """A dry cell of an FP32-bulk state downloads as the datum plus its bed's FP32
+    offset, which can lie below the FP64 bed by that rounding; uploading the download
+    (a checkpoint resume) is accepted, keeps every dry cell's surface exactly and the
+    wet ones to the rounding of the datum-plus-pair sum (1e-12 m), and continues as
+    the run that never left the device (FP32-bulk accuracy)."""
+    s = W.floodplain(nx=160, ny=64, Lx=1600.0, Ly=640.0, seed=23, q_peak=150.0, ramp=120.0)
+    a = bm.State.from_scenario(s, precision="fp32")
+    b = bm.State.from_scenario(s, precision="fp32")
+    H0 = a.download()[0]  # a dry cell: the datum plus its bed's FP32 offset
+    a.step(40)
+    b.step(40)
+    H, qx, qy, t = a.download()
+    dry = (s.H - s.z <= 0.0) & (H == H0)  # dry at t = 0 and untouched since
+    assert np.any(H[dry] < s.z[dry])  # the case under test occurs on this bed
+    a.upload(H, qx, qy, t)
+    H2, qx2, qy2, _ = a.download()
+    assert np.array_equal(H2[dry], H[dry])
+    assert np.max(np.abs(H2 - H)) <= 1e-12
+    assert np.array_equal(qx2, qx) and np.array_equal(qy2, qy)
+    a.step(30)
+    b.step(30)
+    A, B = a.download(), b.download()
+    assert np.max(np.abs(A[0] - B[0])) <= 1e-5
+    assert A[3] == B[3] or abs(A[3] - B[3]) <= 1e-9 * B[3]
