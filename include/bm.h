@@ -128,8 +128,9 @@ void bm_mesh_destroy(bm_mesh* m);
  *   H, qx, qy  n_tri doubles each; qx/qy may be NULL for zeros.  H < z_bed is
  *              rejected (a dry cell is H = z_bed); FP32_BULK accepts a surface down
  *              to its own bed, the datum plus the bed's FP32 offset (what it returns
- *              for a dry cell), so a downloaded state uploads again.  The time starts
- *              at 0.
+ *              for a dry cell), so a downloaded state uploads again: a cell exactly on
+ *              the FP64 bed or at or below its own bed is dry, a film above its own
+ *              bed keeps its depth.  The time starts at 0.
  * The mesh must outlive the state.  Allocates device memory.
  */
 bm_status bm_state_init(const bm_mesh* m, const bm_params* p, const double* H, const double* qx,

@@ -910,11 +910,13 @@ __global__ void gather_surface_pair(const double* user, const int32_t* perm, int
   if (!isfinite(H)) atomicOr(bad, 1);
   // the state's own bed: the datum plus the bed's FP32 offset, formed as a download
   // forms a dry cell's surface (it may round either way of the FP64 bed).  Below both
-  // beds is an error; at or below either, the cell is dry (so a downloaded dry cell
-  // uploads as dry, not as a film of the rounding)
+  // beds is an error.  Dry: exactly on the FP64 bed (an FP64 dry cell) or at or below
+  // the state's own bed (a downloaded dry cell uploads as dry, not as a film of the
+  // rounding); a film between the two beds (a downloaded wet cell thinner than the
+  // bed's rounding) stays the film it was
   const double Hb = datum + static_cast<double>(zf[i]);
   if (H < zd[i] && H < Hb) atomicOr(bad, 2);
-  if (H <= zd[i] || H <= Hb) {
+  if (H == zd[i] || H <= Hb) {
     hi[i] = zf[i];
     lo[i] = 0.0f;
   } else {
