@@ -316,6 +316,7 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
     for sn in snaps:
         st.upload(sn["H"], sn["qx"], sn["qy"], sn["t"])
         st.step(args.warmup)
+        taken0, n_tiles = st.work()
         barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -328,9 +329,11 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
         st.sync()
         ms = allmax(e0.elapsed_time(e1)) / args.steps
         ms_list.append(ms)
-        w = {"t_s": sn["t"], "wet_fraction": sn["wet"], "ms_per_step": ms,
+        # the share of the tiles the launches take (mean of the window's first and last)
+        sn["taken"] = 0.5 * (taken0 + st.work()[0]) / n_tiles
+        w = {"t_s": sn["t"], "wet_fraction": sn["wet"], "tiles_taken": sn["taken"], "ms_per_step": ms,
              "value": n * ws / (ms / 1e3),
-             "hbm_frac": BYTES_PER_CELL_UPDATE[prec] * n / (ms / 1e3) / 1e9 / hbm}
+             "hbm_frac": BYTES_PER_CELL_UPDATE[prec] * n * sn["taken"] / (ms / 1e3) / 1e9 / hbm}
         if prec == "fp64":
             w["fp64_frac"] = FP64_FLOP_PER_WET_CELL * sn["wet"] * n / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS
         windows.append(w)
@@ -339,14 +342,20 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
     value = n * ws / (ms_run / 1e3)
 
     # dominant kernel (the step kernel, the only one in the timed windows): algorithmic
-    # bytes per launch over the run's mean launch duration
-    bytes_launch = BYTES_PER_CELL_UPDATE[prec] * n
-    layout_bytes = LAYOUT_BYTES_PER_CELL[prec] * n + LAYOUT_BYTES_PER_EDGE[prec] * mesh.info["n_edges"]
+    # bytes per launch over the run's mean launch duration.  A launch moves the bytes of
+    # the tiles it takes; a skipped tile (dry, at rest, no changed neighbour: its step is
+    # a copy-through) moves none, so the units of a launch are the cells of its tiles
+    taken = sum((snaps[a + 1]["steps"] - snaps[a]["steps"]) * 0.5 * (snaps[a]["taken"] + snaps[a + 1]["taken"])
+                for a in range(len(snaps) - 1)) / max(steps, 1) if len(snaps) > 1 else snaps[0]["taken"]
+    bytes_launch = BYTES_PER_CELL_UPDATE[prec] * n * taken
+    layout_bytes = (LAYOUT_BYTES_PER_CELL[prec] * n + LAYOUT_BYTES_PER_EDGE[prec] * mesh.info["n_edges"]) * taken
     roof = {"bound": "hbm", "achieved": bytes_launch / (ms_run / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
             "frac": bytes_launch / (ms_run / 1e3) / 1e9 / hbm, "traffic": ncu_traffic(prec),
             "kernel": KERNEL_NAME[prec], "kernel_ms": ms_run,
             "algorithmic_bytes_per_launch": bytes_launch,
-            "bytes": f"{BYTES_PER_CELL_UPDATE[prec]} B per cell-update (every cell every step)",
+            "tiles_taken": taken,
+            "bytes": f"{BYTES_PER_CELL_UPDATE[prec]} B per cell-update of the tiles a launch takes (the run's "
+                     f"step-weighted share {taken:.3f} of the tiles; the others are dry, at rest and unchanged)",
             "layout_bytes_per_launch": layout_bytes,
             "layout_frac": layout_bytes / (ms_run / 1e3) / 1e9 / hbm,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}

@@ -291,6 +291,28 @@ bm_status bm_state_set_outflow(bm_state* s, const double* hq_stage, const double
 bm_status bm_state_download_bed(bm_state* s, double* z);
 
 /*
+ * The work of the state's last step launch: the tiles (of 256 cells) it took (0 before
+ * the first launch, or when the state changed since) and the state's tiles in all.  A
+ * launch takes the tiles with boundary edges that carry mass, inflow, outflow or source
+ * cells, and those the previous launch listed (the tiles that were not quiet, and the
+ * tiles next to them); a skipped tile is dry and at rest, with no changed neighbour, so
+ * its step would copy it through unchanged.  The first launch after the state or its
+ * features changed, or after it was stepped in a batch, takes every tile, and so does
+ * every launch of a state with passive species or bed evolution, and a launch after one
+ * that listed most tiles.  Results do not depend on it.  Blocks (waits for the state's
+ * stream).
+ */
+bm_status bm_state_work(bm_state* s, int64_t* tiles_last, int64_t* tiles_total);
+
+/*
+ * Tile skipping (on = 1, the default) or not (on = 0: every launch takes every tile, as
+ * a state with passive species does).  Results are bitwise the same either way; the
+ * switch exists to show that, and to time the step without it.  on must be 0 or 1
+ * (BM_EINVAL).  Takes effect from the next launch.
+ */
+bm_status bm_state_set_tile_skipping(bm_state* s, int32_t on);
+
+/*
  * Scalars of the state: time, the dt the next step will take, steps taken,
  * water volume V = sum |Omega_i| (H_i - z_i) (FP64, fixed summation order), and
  * the net volume that entered through the boundary since init/upload.

@@ -61,6 +61,8 @@ SIGNATURES = {
     "bm_state_upload": (C.c_int, [_vp, _P(_d), _P(_d), _P(_d), _d]),
     "bm_state_download": (C.c_int, [_vp, _P(_d), _P(_d), _P(_d), _P(_d)]),
     "bm_state_stats": (C.c_int, [_vp, _P(_d), _P(_d), _P(_i64), _P(_d), _P(_d)]),
+    "bm_state_work": (C.c_int, [_vp, _P(_i64), _P(_i64)]),
+    "bm_state_set_tile_skipping": (C.c_int, [_vp, C.c_int32]),
     "bm_step_timed": (C.c_int, [_vp, _i64, _P(_d), _P(_d)]),
     "bm_state_test_timeout": (C.c_int, [_vp]),
     "bm_state_set_launch": (C.c_int, [_vp, C.c_int]),
@@ -312,6 +314,17 @@ def bm_state_stats(state: int, volume: bool = True) -> dict:
             "boundary_volume": bv.value}
 
 
+def bm_state_work(state: int) -> tuple[int, int]:
+    """(tiles the last step launch took, tiles of the state)."""
+    nxt, tot = _i64(), _i64()
+    _check(load_library().bm_state_work(state, C.byref(nxt), C.byref(tot)))
+    return nxt.value, tot.value
+
+
+def bm_state_set_tile_skipping(state: int, on: bool) -> None:
+    _check(load_library().bm_state_set_tile_skipping(state, 1 if on else 0))
+
+
 def bm_step_timed(state: int, n_steps: int) -> tuple[float, float]:
     """(summed step-kernel ms, total ms) of n_steps steps launched with per-kernel events."""
     k, t = _d(), _d()
@@ -548,6 +561,13 @@ class State:
 
     def step_timed(self, n: int) -> tuple[float, float]:
         return bm_step_timed(self.handle, n)
+
+    def work(self) -> tuple[int, int]:
+        """(tiles the last step launch took, tiles of the state)."""
+        return bm_state_work(self.handle)
+
+    def set_tile_skipping(self, on: bool):
+        bm_state_set_tile_skipping(self.handle, on)
 
     def test_timeout(self):
         bm_state_test_timeout(self.handle)

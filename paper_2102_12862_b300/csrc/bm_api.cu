@@ -164,26 +164,15 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
   const int prec = members.at(0)->prec;
   const int r = prec == BM_FP64 ? 0 : 1;
   std::vector<PipeItem> items;
+  std::vector<int> fixed, first;
   uint32_t ne4 = 4, nh4 = 4;
   for (size_t k = 0; k < members.size(); ++k) {
     const bm_mesh* m = members[k]->mesh;
     const TileRecords& R = m->rec[r];
     if (!m->rec_built[r] || !m->rec_dev[r].p) return fail(BM_EINVAL, "internal: tile records missing");
-    // boundary ranks in tile order; items in the order inflow tiles, other boundary
-    // tiles, interior tiles, so the per-instance inflow and boundary work (done by the
-    // CTA that completes the last such tile) happens early in the launch
-    std::vector<uint32_t> brank_of(m->h.n_tiles, 0);
-    for (int64_t t = 0, b = 0; t < m->h.n_tiles; ++t)
-      if (R.flags[t] & 1u) brank_of[t] = static_cast<uint32_t>(b++);
-    std::vector<int64_t> order;
-    order.reserve(m->h.n_tiles);
-    for (int pass = 0; pass < 3; ++pass)
-      for (int64_t t = 0; t < m->h.n_tiles; ++t) {
-        const uint8_t f = R.flags[t];
-        const int cls = (f & 2u) ? 0 : ((f & 1u) ? 1 : 2);
-        if (cls == pass) order.push_back(t);
-      }
-    for (int64_t t : order) {
+    // items in tile order (a launch takes the fixed ones first); boundary ranks in tile order
+    first.push_back(static_cast<int>(items.size()));
+    for (int64_t t = 0, b = 0; t < m->h.n_tiles; ++t) {
       PipeItem it{};
       it.rec = m->rec_dev[r].p + R.off[t];
       it.desc = descs[k];
@@ -194,28 +183,56 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
       it.inst = static_cast<int32_t>(k);
       it.flags = R.flags[t];
       if (!members[k]->src_tile.empty() && members[k]->src_tile[t]) it.flags |= 4u;  // source cells
-      it.bidx = brank_of[t];
+      it.bidx = (R.flags[t] & 1u) ? static_cast<uint32_t>(b++) : 0u;
+      if ((it.flags & kFixedFlags) || items.empty()) fixed.push_back(static_cast<int>(items.size()));
       items.push_back(it);
     }
     ne4 = std::max(ne4, R.ne4_max);
     nh4 = std::max(nh4, R.nh4_max);
   }
   cudaError_t e = out->items.upload(items);
-  if (e == cudaSuccess) e = out->sched.alloc(8);
-  if (e == cudaSuccess) e = cudaMemset(out->sched.p, 0, 8 * sizeof(int));
+  if (e == cudaSuccess) e = out->sched.alloc(kSchedInts);
   if (e == cudaSuccess) e = out->early.alloc(2 * items.size());
-  if (e == cudaSuccess) e = out->mark.alloc(items.size());
-  if (e == cudaSuccess) e = cudaMemset(out->mark.p, 0xff, items.size() * sizeof(int));  // stamp -1: none
+  if (e == cudaSuccess) e = out->mark.alloc(2 * items.size());
+  if (e == cudaSuccess) e = out->fixed.upload(fixed);
+  if (e == cudaSuccess) e = out->inst_item.upload(first);
   if (e != cudaSuccess) return dev_fail(e, "work list upload");
+  out->members = members;
   out->n = static_cast<int>(items.size());
+  out->n_fixed = static_cast<int>(fixed.size());
   out->ne4 = ne4;
   out->nh4 = nh4;
+  for (bm_state* m : members) m->last_list = nullptr;  // the first launch resets the list
   out->smem = prec == BM_FP64 ? StepLayout<double>(ne4, nh4).total : StepLayout<float>(ne4, nh4).total;
+  {
+    // every bulk-copy destination in a slot must be 16-byte aligned
+    const StepLayout<double> l64(ne4, nh4);
+    const StepLayout<float> l32(ne4, nh4);
+    const uint32_t offs[] = {l64.desc, l64.ctl, l64.arr, l64.gn2, l64.slot, l32.desc, l32.ctl, l32.arr, l32.gn2,
+                             l32.slot};
+    for (uint32_t o : offs)
+      if (o % 16u != 0u) return fail(BM_EINVAL, "internal: step layout not 16-byte aligned");
+  }
   const int lim = prec == BM_FP64 ? step_smem_limit<double>() : step_smem_limit<float>();
   if (out->smem > static_cast<size_t>(lim)) return fail(BM_EINVAL, "tile layout exceeds the device's shared memory");
   out->extra = 0;
   for (bm_state* m : members) out->extra = std::max(out->extra, state_extra_level(m));
   return list_occupancy(prec, out);
+}
+
+bool state_listed_ok(const bm_state* s) { return s->n_species == 0 && !s->morpho && !s->no_skip; }
+
+void ensure_list(StepList* l, cudaStream_t st) {
+  bool stale = false, ok = true;
+  for (bm_state* m : l->members) {
+    stale = stale || m->last_list != l;
+    ok = ok && state_listed_ok(m);
+  }
+  if (!stale || l->n <= 0) return;
+  const int n = std::max(l->n, kSchedInts);
+  list_reset<<<(n + 255) / 256, 256, 0, st>>>(static_cast<const PipeItem*>(l->items.p), l->n, l->mark.p, l->sched.p,
+                                               ok ? 1 : 0);
+  for (bm_state* m : l->members) m->last_list = l;
 }
 
 int state_extra_level(const bm_state* s) {
@@ -272,14 +289,22 @@ void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const int ne4 = static_cast<int>(l.ne4), nh4 = static_cast<int>(l.nh4);
-  const PipeItem* items = static_cast<const PipeItem*>(l.items.p);
+  ListArgs a;
+  a.items = static_cast<const PipeItem*>(l.items.p);
+  a.n_items = l.n;
+  a.sched = l.sched.p;
+  a.early = l.early.p;
+  a.mark = l.mark.p;
+  a.fixed = l.fixed.p;
+  a.n_fixed = l.n_fixed;
+  a.inst_item = l.inst_item.p;
+  a.n_inst = static_cast<int>(l.members.size());
+  a.ne4max = static_cast<int>(l.ne4);
+  a.nh4max = static_cast<int>(l.nh4);
   if (prec == BM_FP64)
-    (void)cudaLaunchKernelEx(&cfg, step_kernel<double>(l.extra), items, l.n,
-                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime, withhold, l.static16);
+    (void)cudaLaunchKernelEx(&cfg, step_kernel<double>(l.extra), a, prime, withhold, l.static16);
   else
-    (void)cudaLaunchKernelEx(&cfg, step_kernel<float>(l.extra), items, l.n,
-                             l.sched.p, l.early.p, l.mark.p, ne4, nh4, prime, withhold, l.static16);
+    (void)cudaLaunchKernelEx(&cfg, step_kernel<float>(l.extra), a, prime, withhold, l.static16);
 }
 
 namespace {
@@ -287,6 +312,7 @@ namespace {
 bm_status read_status(bm_state* s) {
   BM_CUDA(cudaMemcpyAsync(s->hctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
   BM_CUDA(cudaStreamSynchronize(s->stream));
+  if (s->hctl->status & 4) s->last_list = nullptr;  // a launch gave up: its lists are incomplete
   return status_of(*s->hctl);
 }
 
@@ -363,6 +389,7 @@ void launch_morpho(bm_state* s, cudaStream_t st) {
 }
 
 void launch_state(bm_state* s, cudaStream_t st, int prime) {
+  if (prime) ensure_list(&s->list, st);  // (prime launches are never captured)
   if (!prime && s->morpho) morpho_save_dt<<<1, 32, 0, st>>>(s->ctl, s->mo_dt.p);
   if (!prime && s->n_src > 0) {
     if (s->prec == BM_FP64)
@@ -408,6 +435,7 @@ void drop_graphs(bm_state* s) {
 bm_status enqueue_steps(bm_state* s, int64_t n) {
   constexpr int kChunk = 32;
   if (n <= 0) return BM_OK;
+  ensure_list(&s->list, s->stream);
   cudaGraphExec_t gbig = nullptr, gone = nullptr;
   if (n >= kChunk) {
     bm_status st = get_graph(s, kChunk, &gbig);
@@ -534,9 +562,9 @@ bm_status load_state(bm_state* s, const double* H, const double* qx, const doubl
   const int nb = (n + 255) / 256;
   const int32_t* perm = s->mesh->perm.p;
   BM_CUDA(cudaMemsetAsync(s->bad.p, 0, sizeof(int), s->stream));
-  // a fresh scheduling state (a launch that gave up may have left it inconsistent)
-  BM_CUDA(cudaMemsetAsync(s->list.sched.p, 0, s->list.sched.bytes(), s->stream));
-  BM_CUDA(cudaMemsetAsync(s->list.mark.p, 0xff, s->list.mark.bytes(), s->stream));
+  // a fresh scheduling state (a launch that gave up may have left it inconsistent; the
+  // new state's tiles all need a step)
+  s->last_list = nullptr;
   if (s->prec == BM_FP64) {
     Buffers<double>& b = s->b64;
     gather_from_user<double><<<nb, 256, 0, s->stream>>>(s->stage[0].p, perm, n, b.H[0].p);
@@ -937,6 +965,7 @@ bm_status bm_state_track(bm_state* s, double h_arrival) {
     if (st != BM_OK) return st;
     s->grid = step_grid(s->list, s->ctas_per_sm);
     drop_graphs(s);
+    s->last_list = nullptr;  // the state's features changed: the next launch takes every tile
   }
   return BM_OK;
 }
@@ -1024,6 +1053,7 @@ bm_status bm_state_set_scalars(bm_state* s, int32_t n_species, const double* hc,
     s->grid = step_grid(s->list, s->ctas_per_sm);
   }
   drop_graphs(s);
+  s->last_list = nullptr;  // the state's features changed: the next launch takes every tile
   return BM_OK;
 }
 
@@ -1119,6 +1149,7 @@ bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* re
   BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
   BM_CUDA(cudaStreamSynchronize(s->stream));
   drop_graphs(s);
+  s->last_list = nullptr;  // the state's features changed: the next launch takes every tile
   bm_status st = build_step_list({s}, {static_cast<const void*>(s->desc.p)}, &s->list);
   if (st != BM_OK) return st;
   s->grid = step_grid(s->list, s->ctas_per_sm);
@@ -1150,6 +1181,7 @@ bm_status bm_state_set_morpho(bm_state* s, int32_t on, double porosity, double s
   }
   s->morpho = on != 0;
   drop_graphs(s);  // the launch sequence changes
+  s->last_list = nullptr;  // the state's features changed: the next launch takes every tile
   return BM_OK;
 }
 
@@ -1186,6 +1218,7 @@ bm_status bm_state_set_outflow(bm_state* s, const double* hq_stage, const double
     s->grid = step_grid(s->list, s->ctas_per_sm);
   }
   drop_graphs(s);
+  s->last_list = nullptr;  // the state's features changed: the next launch takes every tile
   // the next step's dt and h-Q split follow the new laws: prime again (time unchanged)
   launch_state(s, s->stream, 1);
   BM_CUDA(cudaGetLastError());
@@ -1226,6 +1259,7 @@ bm_status bm_state_set_friction(bm_state* s, int32_t law, const double* coef) {
     s->grid = step_grid(s->list, s->ctas_per_sm);
   }
   drop_graphs(s);
+  s->last_list = nullptr;  // the state's features changed: the next launch takes every tile
   return BM_OK;
 }
 
@@ -1244,6 +1278,27 @@ bm_status bm_state_download_bed(bm_state* s, double* z) {
   BM_CUDA(cudaMemcpyAsync(z, s->stage[0].p, static_cast<size_t>(n) * sizeof(double), cudaMemcpyDeviceToHost,
                           s->stream));
   BM_CUDA(cudaStreamSynchronize(s->stream));
+  return BM_OK;
+}
+
+bm_status bm_state_set_tile_skipping(bm_state* s, int32_t on) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_set_tile_skipping: state is NULL");
+  if (on != 0 && on != 1) return fail(BM_EINVAL, "bm_state_set_tile_skipping: on must be 0 or 1");
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  s->no_skip = on == 0;
+  s->last_list = nullptr;  // the next launch resets the list with the new setting
+  return BM_OK;
+}
+
+bm_status bm_state_work(bm_state* s, int64_t* tiles_last, int64_t* tiles_total) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_work: state is NULL");
+  int sc[kSchedInts];
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  BM_CUDA(cudaMemcpy(sc, s->list.sched.p, sizeof(sc), cudaMemcpyDeviceToHost));
+  if (tiles_last) *tiles_last = s->last_list == &s->list ? sc[12] : 0;
+  if (tiles_total) *tiles_total = s->list.n;
   return BM_OK;
 }
 
@@ -1279,8 +1334,10 @@ bm_status bm_state_test_timeout(bm_state* s) {
   clear_error();
   if (!s) return fail(BM_EINVAL, "bm_state_test_timeout: state is NULL");
   BM_CUDA(cudaStreamSynchronize(s->stream));
+  ensure_list(&s->list, s->stream);
   launch_work(s->prec, s->list, s->grid, 0, s->stream, 1);
   BM_CUDA(cudaGetLastError());
+  s->last_list = nullptr;  // the launch gave up: its lists are incomplete
   return read_status(s);
 }
 
@@ -1300,6 +1357,7 @@ bm_status bm_step_timed(bm_state* s, int64_t n, double* step_kernel_ms, double* 
       return fail(BM_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(r));
     }
   }
+  ensure_list(&s->list, s->stream);
   for (int64_t k = 0; k < n; ++k) {
     cudaEventRecord(ev[2 * k], s->stream);
     launch_state(s, s->stream, 0);
@@ -1464,6 +1522,7 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
       cudaEventElapsedTime(&ms, e0, e1);
       tmin = std::min(tmin, ms);
       if (sn.restore(st) != cudaSuccess) return fail(BM_ECUDA, "autotune: restore failed");
+      for (bm_state* m : states) m->last_list = nullptr;  // restored arrays: the next launch takes every tile
     }
     if (first || tmin < 0.98 * bms) {
       bms = tmin;

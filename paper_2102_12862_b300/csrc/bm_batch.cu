@@ -1,8 +1,8 @@
 // bm_batch.cu -- batches of independent states stepped by one launch per step.
 //
 // The launch's work list packs every member's tiles; each CTA reads its member's
-// descriptor (pointers, sizes, parameters) and the CTA that completes a member's
-// last tile finalizes that member, so every member advances with its own dt.
+// descriptor (pointers, sizes, parameters) and the CTA that completes the launch
+// finalizes every member, so every member advances with its own dt.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -137,6 +137,8 @@ bm_status use_active_members(bm_batch* b) {
 
 bm_status batch_enqueue(bm_batch* b, int64_t n) {
   constexpr int kChunk = 16;
+  if (n <= 0) return BM_OK;
+  ensure_list(b->sub ? b->sub.get() : &b->list, b->stream);
   cudaGraphExec_t gbig = nullptr, gone = nullptr;
   if (n >= kChunk) {
     bm_status st = batch_graph(b, kChunk, &gbig);
@@ -172,6 +174,8 @@ bm_status batch_member_flags(bm_batch* b, std::vector<int>* flags) {
   batch_flags<<<(n + 127) / 128, 128, 0, b->stream>>>(b->ctlp.p, n, b->flags.p);
   BM_CUDA(cudaMemcpyAsync(b->hflags, b->flags.p, n * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   BM_CUDA(cudaStreamSynchronize(b->stream));
+  for (int k = 0; k < n; ++k)
+    if ((b->hflags[k] >> 1) & 4) b->members[k]->last_list = nullptr;  // a launch gave up
   flags->assign(b->hflags, b->hflags + n);
   return BM_OK;
 }
@@ -187,6 +191,7 @@ bm_status batch_read(bm_batch* b, int* n_active) {
   for (int k = 0; k < n; ++k) {
     act += b->hflags[k] & 1;
     const int st = b->hflags[k] >> 1;
+    if (st & 4) b->members[k]->last_list = nullptr;  // a launch gave up: its lists are incomplete
     if (worst == BM_OK && (st & 1)) worst = fail(BM_ENONFINITE, "batch member " + std::to_string(k) +
                                                      ": the step produced a non-finite value");
     if (worst == BM_OK && (st & 2)) worst = fail(BM_ENEGDEPTH, "batch member " + std::to_string(k) +

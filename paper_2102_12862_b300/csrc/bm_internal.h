@@ -2,6 +2,7 @@
 // the C ABI and the CUDA kernels of the shallow-water step.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -49,7 +50,8 @@ struct HostMesh {
   // normal (outward)
   std::vector<int32_t> in_cell;
   std::vector<double> in_len, in_nx, in_ny;
-  // tiles whose edge list holds at least one boundary edge (ascending)
+  // tiles whose edge list holds at least one boundary edge that can carry mass
+  // (transmissive or listed; ascending)
   std::vector<int32_t> btiles;
   double inflow_len = 0;
   double z_min = 0;
@@ -99,8 +101,9 @@ struct TileRecords {
   std::vector<uint64_t> off;         // byte offset of tile t's record
   std::vector<uint32_t> bytes;       // its size (multiple of 16)
   std::vector<uint32_t> ne_nh;       // edges | halo cells << 16
-  std::vector<uint8_t> flags;        // bit 0: boundary edges, bit 1: inflow edges, bit 3: h-Q edges,
-                                     // bit 4: weir edges
+  std::vector<uint8_t> flags;        // bit 0: boundary edges that can carry mass (transmissive or
+                                     // listed; walls do not count), bit 1: inflow edges, bit 3: h-Q
+                                     // edges, bit 4: weir edges
   uint32_t ne4_max = 0, nh4_max = 0;
 };
 
@@ -119,7 +122,7 @@ struct Ctl {
   double dt_cfl;   // dt^n before clipping to t_end
   long long steps;
   unsigned long long rmax_bits;  // max over cells of the Eq. 21 rate (bits of a double >= 0)
-  unsigned int done;             // tiles of the current launch that finished
+  unsigned int done;             // (unused)
   int parity;      // which state buffer holds U^n
   int active;      // 0 once t reached t_end
   int clipped;     // dt^n was clipped to t_end - t^n
@@ -128,17 +131,21 @@ struct Ctl {
   float dt_f;      // dt and quni rounded once for FP32-bulk steps
   float quni_f;
   double rb;            // max inflow-edge rate of Eq. 21 at t^{n+1} (written mid-launch)
-  unsigned int in_done; // inflow tiles of the current launch that finished
-  unsigned int b_done;  // boundary tiles of the current launch that finished
+  // (in_done, b_done: 8-byte aligned, counted together by a 64-bit atomicAdd)
+  unsigned int in_done; // inflow tiles of the current launch that finished  } one 64-bit word
+  unsigned int b_done;  // boundary tiles of the current launch that finished } (one atomic)
   double rb_out;        // max h-Q-edge rate of Eq. 21 at t^{n+1} (written mid-launch)
   unsigned int hq_done; // h-Q tiles of the current launch that finished
   unsigned int pad_u;
 };
 
 static_assert(sizeof(Ctl) % 16 == 0, "Ctl is bulk-copied: its size must be a multiple of 16");
+static_assert(offsetof(Ctl, in_done) % 8 == 0 && offsetof(Ctl, b_done) == offsetof(Ctl, in_done) + 4,
+              "in_done and b_done form one 8-byte word");
 
 // One work item of a step launch: a tile of an instance, with the addresses its bulk
-// copies read (items of one instance are consecutive; 48 bytes, 16-byte aligned).
+// copies read (the items of one instance are consecutive and in tile order, so item
+// index = the instance's first item + tile; 48 bytes, 16-byte aligned).
 struct PipeItem {
   const unsigned char* rec;  // the tile's record
   const void* desc;          // the instance's descriptor (InstDesc<T>)
@@ -147,11 +154,22 @@ struct PipeItem {
   int32_t tile;
   uint32_t ne_nh;            // edges | halo cells << 16
   int32_t inst;              // instance index within the launch
-  uint32_t flags;            // bit 0: the tile has boundary edges, bit 1: inflow edges,
-                             // bit 2: source cells, bit 3: h-Q edges, bit 4: weir edges
+  uint32_t flags;            // bit 0: the tile has boundary edges that can carry mass, bit 1:
+                             // inflow edges, bit 2: source cells, bit 3: h-Q edges, bit 4: weir edges
   uint32_t bidx;             // boundary tiles: rank among the instance's boundary tiles
 };
 static_assert(sizeof(PipeItem) == 48, "PipeItem layout");
+
+// Work items every launch takes (the "fixed" items): those with any of these flags, and
+// item 0 of a work list.  The others are taken only when the previous launch listed
+// them (see step_pipe).  kFixedMark: their entries in the list marks.
+constexpr uint32_t kFixedFlags = 31u;
+constexpr int kFixedMark = 0x7fffffff;
+// Launch stamps restart (with a full launch) before they reach this value (marks hold
+// 2 x stamp + 1 at most, below kFixedMark).
+constexpr int kStampMax = 1 << 29;
+// Scheduling counters of a work list (int entries).
+constexpr int kSchedInts = 16;
 
 // Per-tile reduction slot written by the step kernel.
 struct TilePartial {

@@ -497,124 +497,188 @@ __device__ __noinline__ void finalize_boundary(const InstDesc<T>& a, const Ctl& 
     bs = warp_sum(bs);
     if (tid == 0) {
       a.ctl->bvol = cs.bvol - cs.dt * bs;
-      a.ctl->b_done = 0u;
+      atomicAnd(reinterpret_cast<unsigned long long*>(&a.ctl->in_done), 0x00000000ffffffffull);  // b_done = 0
     }
   }
   nbar<kTile>();
 }
 
+// Knuth's TwoSum: s = a + b rounded, e its rounding error (s + e == a + b exactly).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // Inflow at the new time: Q(t), the conveyance-weighted split of Q (sum of l h^(5/3))
 // and the largest inflow-edge rate lambda_b l / |Omega| of Eq. 21.  Run by the CTA that
 // completes the instance's last inflow tile (only inflow tiles read the split, and
-// they are all done).  sred: 9 doubles, sbc: 3, scratch: kTile.
+// they are all done).  B300 runs FP64 on two lanes per SM and cycle, and this runs on
+// one SM, so the FP64 work is only what the result needs.  FP64: the weight sum in
+// FP64, the split's two divisions once, and the exact rate of the few edges whose
+// single-precision screen (inputs truncated by integer operations) can reach the
+// maximum, which is therefore the exact FP64 maximum.  FP32-bulk (whose cell rates are
+// single precision): the weight sum as an exact FP32 pair sum (products split by FMA,
+// TwoSum), the rate the largest single-precision edge rate.  Every global load is
+// issued first.  sred: 9 doubles, sbc: 4, scratch: kTile.
 template <typename T>
 __device__ __noinline__ void finalize_inflow(const InstDesc<T>& a, const Ctl& cs, int advance, double* sred,
                                              double* sbc, double* scratch) {
+  constexpr bool k64 = sizeof(T) == 8;
   Ctl* ctl = a.ctl;
   const int tid = threadIdx.x;
   const double g = a.p.g;
-  const double t = new_time(cs, advance);
   unsigned long long* ured = reinterpret_cast<unsigned long long*>(sred);
-  // all global loads first, four elements per thread and array at a time
+  auto f32 = [](T x) -> float {
+    if constexpr (k64) return f32_trunc(x);
+    else return x;
+  };
   constexpr int U = 4;
   const int ni = a.n_inflow;
-  double pwv[U], lv[U];
-  float hsv[U], liav[U];
+  T pwv[U], lv[U], hsv[U];
+  double liad[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int j = tid + u * kTile;
     const bool in = j < ni;
-    pwv[u] = in ? static_cast<double>(__ldcg(&a.in_pw[j])) : 0.0;
-    lv[u] = in ? static_cast<double>(a.in_len[j]) : 0.0;
-    hsv[u] = in ? static_cast<float>(__ldcg(&a.in_hs[j])) : 0.0f;
-    liav[u] = in ? static_cast<float>(a.in_lia[j]) : 0.0f;
+    pwv[u] = in ? __ldcg(&a.in_pw[j]) : T(0);
+    lv[u] = in ? a.in_len[j] : T(0);
+    hsv[u] = in ? __ldcg(&a.in_hs[j]) : T(0);
+    liad[u] = in ? a.in_lia[j] : 0.0;
   }
   // Q(t): the thread of the hydrograph segment that contains t evaluates it
   const int nq = a.p.hydro_n;
-  if (nq <= 0 && tid == 0) sbc[0] = 0.0;
-  for (int i = tid; i <= nq && nq > 0; i += kTile) {
+  if (tid == 0 && nq <= 0) sbc[0] = 0.0;
+  if (tid <= nq && nq > 0) {
+    const double t = new_time(cs, advance);
     const double* ht = a.p.hydro_t;
     const double* hq = a.p.hydro_q;
-    if (i == 0) {
-      if (t <= ht[0]) sbc[0] = hq[0];
-    } else if (i == nq) {
-      if (t > ht[nq - 1]) sbc[0] = hq[nq - 1];
-    } else if (t > ht[i - 1] && t <= ht[i]) {
-      const double wgt = (t - ht[i - 1]) / (ht[i] - ht[i - 1]);
-      sbc[0] = hq[i - 1] + wgt * (hq[i] - hq[i - 1]);
+    for (int i = tid; i <= nq; i += kTile) {
+      if (i == 0) {
+        if (t <= ht[0]) sbc[0] = hq[0];
+      } else if (i == nq) {
+        if (t > ht[nq - 1]) sbc[0] = hq[nq - 1];
+      } else if (t > ht[i - 1] && t <= ht[i]) {
+        const double wgt = (t - ht[i - 1]) / (ht[i] - ht[i - 1]);
+        sbc[0] = hq[i - 1] + wgt * (hq[i] - hq[i - 1]);
+      }
     }
   }
-  {
+  // the weight sum W = sum of l h^(5/3), thread 0 then the split: q_e = qscale h_e^(5/3)
+  // where some inflow cell is wet, else the uniform quni on every inflow edge
+  if constexpr (k64) {
     double wsum = 0.0;
 #pragma unroll
     for (int u = 0; u < U; ++u) wsum += lv[u] * pwv[u];
-    for (int j = tid + U * kTile; j < ni; j += kTile)
-      wsum += static_cast<double>(a.in_len[j]) * static_cast<double>(__ldcg(&a.in_pw[j]));
+    for (int j = tid + U * kTile; j < ni; j += kTile) wsum += a.in_len[j] * __ldcg(&a.in_pw[j]);
     scratch[tid] = wsum;
     nbar<kTile>();
     if (tid < 32) {
       wsum = 0.0;
       for (int k = tid; k < kTile; k += 32) wsum += scratch[k];
-      wsum = warp_sum(wsum);
-      if (tid == 0) sbc[1] = wsum;
+      scratch[tid] = warp_sum(wsum);  // (lane 0's is the sum)
+    }
+  } else {
+    float hi = 0.0f, lo = 0.0f;
+    auto add = [&](float x, float y) {  // (hi, lo) += x * y, exactly up to the pair's rounding
+      const float p = x * y, e = fmaf(x, y, -p);
+      float s2, e2;
+      two_sum(hi, p, s2, e2);
+      hi = s2;
+      lo += e2 + e;
+    };
+#pragma unroll
+    for (int u = 0; u < U; ++u) add(lv[u], pwv[u]);
+    for (int j = tid + U * kTile; j < ni; j += kTile) add(a.in_len[j], __ldcg(&a.in_pw[j]));
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+      float s2, e2;
+      two_sum(hi, h2, s2, e2);
+      hi = s2;
+      lo += l2 + e2;
+    }
+    float* sp = reinterpret_cast<float*>(scratch);
+    if ((tid & 31) == 0) {
+      sp[2 * (tid >> 5)] = hi;
+      sp[2 * (tid >> 5) + 1] = lo;
+    }
+    nbar<kTile>();
+    if (tid == 0) {
+      hi = sp[0];
+      lo = sp[1];
+      for (int w = 1; w < kTile / 32; ++w) {
+        float s2, e2;
+        two_sum(hi, sp[2 * w], s2, e2);
+        hi = s2;
+        lo += sp[2 * w + 1] + e2;
+      }
+      scratch[0] = static_cast<double>(hi) + static_cast<double>(lo);
     }
   }
+  if (tid == 0) {
+    const double Q = sbc[0], wsum = scratch[0];
+    const bool wpos = wsum > 0.0;
+    sbc[1] = wpos ? Q / wsum : 0.0;
+    sbc[2] = (!wpos && a.inflow_len > 0.0) ? Q / a.inflow_len : 0.0;
+    reinterpret_cast<int*>(&sbc[3])[0] = wpos ? 1 : 0;
+  }
   nbar<kTile>();
-  const double Q = sbc[0], wsum = sbc[1];
-  const bool wpos = wsum > 0.0;
-  const double qscale = wpos ? Q / wsum : 0.0;
-  const double quni = (!wpos && a.inflow_len > 0.0) ? Q / a.inflow_len : 0.0;
-  // a single-precision screen of every inflow edge (relative error well below 1e-5),
-  // then exact FP64 only for the edges that can reach the maximum, which is therefore
-  // the exact FP64 maximum
-  const float gf = static_cast<float>(g), qscf = static_cast<float>(qscale), qunf = static_cast<float>(quni);
+  const float qscf = f32_trunc(sbc[1]), qunf = f32_trunc(sbc[2]);
+  const bool wpos = reinterpret_cast<const int*>(&sbc[3])[0] != 0;
+  const float gf = a.p.g_f;
   const float facf = a.p.cfl_mode == 0 ? 0.75f : 1.0f;
-  const double fac = a.p.cfl_mode == 0 ? 0.75 : 1.0;
+  // the edges' single-precision rates (FP64: a screen within 1e-5 of the rate)
   auto screen = [&](float pw, float hs, float lia) {
     const float q = wpos ? qscf * pw : qunf;
     const float hbf = fmaxf(hs, f_cbrt(fmaxf(q, 1e-30f) * q / gf));
     return q > 0.0f ? (q / hbf + sqrtf(gf * hbf)) * lia * facf : 0.0f;
   };
-  auto exact = [&](double pw, double hs, double lia) {
-    const double q = wpos ? qscale * pw : quni;
-    if (!(q > 0.0)) return 0.0;
-    const double hb = fmax(hs, f_cbrt(q * q / g));
-    return (q / hb + sqrt(g * hb)) * lia * fac;
-  };
   float scr[U];
   float rbf = 0.0f;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    scr[u] = tid + u * kTile < ni ? screen(static_cast<float>(pwv[u]), hsv[u], liav[u]) : 0.0f;
+    scr[u] = tid + u * kTile < ni ? screen(f32(pwv[u]), f32(hsv[u]), f32_trunc(liad[u])) : 0.0f;
     rbf = fmaxf(rbf, scr[u]);
   }
   for (int j = tid + U * kTile; j < ni; j += kTile)
-    rbf = fmaxf(rbf, screen(static_cast<float>(__ldcg(&a.in_pw[j])), static_cast<float>(__ldcg(&a.in_hs[j])),
-                            static_cast<float>(a.in_lia[j])));
-  const double thr = block_max_nonneg_all<kTile>(static_cast<double>(rbf), ured) * (1.0 - 1e-4);
-  double rb = 0.0;
+    rbf = fmaxf(rbf, screen(f32(__ldcg(&a.in_pw[j])), f32(__ldcg(&a.in_hs[j])), f32_trunc(a.in_lia[j])));
+  // the largest (non-negative floats order as their bits)
+  {
+    unsigned v = __reduce_max_sync(0xffffffffu, __float_as_uint(rbf));
+    if ((tid & 31) == 0) reinterpret_cast<unsigned*>(scratch)[32 + (tid >> 5)] = v;
+    nbar<kTile>();
+    v = __reduce_max_sync(0xffffffffu, reinterpret_cast<const unsigned*>(scratch)[32 + (tid & 7)]);
+    rbf = __uint_as_float(v);
+  }
+  double rb;
+  if constexpr (k64) {
+    auto exact = [&](double pw, double hs, double lia) {
+      const double q = wpos ? sbc[1] * pw : sbc[2];
+      if (!(q > 0.0)) return 0.0;
+      const double hb = fmax(hs, f_cbrt(q * q / g));
+      return (q / hb + sqrt(g * hb)) * lia * (a.p.cfl_mode == 0 ? 0.75 : 1.0);
+    };
+    const float thr = rbf * (1.0f - 1e-4f);
+    rb = 0.0;
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int j = tid + u * kTile;
-    if (j < ni && static_cast<double>(scr[u]) >= thr)
-      rb = fmax(rb, exact(pwv[u], static_cast<double>(__ldcg(&a.in_hs[j])), a.in_lia[j]));
+    for (int u = 0; u < U; ++u)
+      if (tid + u * kTile < ni && scr[u] >= thr && rbf > 0.0f) rb = fmax(rb, exact(pwv[u], hsv[u], liad[u]));
+    for (int j = tid + U * kTile; j < ni; j += kTile) {
+      const double pw = __ldcg(&a.in_pw[j]), hs = __ldcg(&a.in_hs[j]), lia = a.in_lia[j];
+      if (screen(f32(pw), f32(hs), f32_trunc(lia)) >= thr && rbf > 0.0f) rb = fmax(rb, exact(pw, hs, lia));
+    }
+    rb = block_max_nonneg_all<kTile>(rb, ured);
+  } else {
+    rb = static_cast<double>(rbf);
   }
-  for (int j = tid + U * kTile; j < ni; j += kTile) {
-    const float sj = screen(static_cast<float>(__ldcg(&a.in_pw[j])), static_cast<float>(__ldcg(&a.in_hs[j])),
-                            static_cast<float>(a.in_lia[j]));
-    if (static_cast<double>(sj) >= thr)
-      rb = fmax(rb, exact(static_cast<double>(__ldcg(&a.in_pw[j])), static_cast<double>(__ldcg(&a.in_hs[j])),
-                          a.in_lia[j]));
-  }
-  rb = block_max_nonneg_all<kTile>(rb, ured);
   if (tid == 0) {
     ctl->rb = rb;
-    ctl->Q = Q;
-    ctl->qscale = qscale;
-    ctl->quni = quni;
-    ctl->quni_f = static_cast<float>(quni);
+    ctl->Q = sbc[0];
+    ctl->qscale = sbc[1];
+    ctl->quni = sbc[2];
+    ctl->quni_f = static_cast<float>(sbc[2]);
     ctl->wpos = wpos ? 1 : 0;
-    ctl->in_done = 0u;
+    atomicAnd(reinterpret_cast<unsigned long long*>(&ctl->in_done), 0xffffffff00000000ull);  // in_done = 0
   }
   nbar<kTile>();
 }

@@ -231,7 +231,7 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
           m.enx.push_back(gnx[e]);
           m.eny.push_back(gny[e]);
           m.elen.push_back(glen[e]);
-          if (code[e] < 0) has_boundary = true;
+          if (code[e] < 0 && code[e] != kWall) has_boundary = true;  // a wall carries no mass
         }
         uint64_t side_bit = (gl[e] == t) ? 0u : 1u;
         packed |= ((static_cast<uint64_t>(pos[e]) << 1) | side_bit) << (16 * k);
@@ -306,7 +306,8 @@ bm_status build_records_t(const HostMesh& m, TileRecords* out) {
         if (gR < kMinCode) return fail(BM_EINVAL, "tile records: too many listed boundary edges");
         R = gR;
         const int64_t j = kInflow - gR;  // listed edge (j >= 0) or a wall / transmissive code
-        r.flags[tile] |= j < 0 ? 1 : (j < m.n_inflow ? 3 : (j < m.n_inflow + m.n_hq ? 9 : 17));
+        if (gR != kWall)  // walls carry no mass: a tile of walls only is an interior tile
+          r.flags[tile] |= j < 0 ? 1 : (j < m.n_inflow ? 3 : (j < m.n_inflow + m.n_hq ? 9 : 17));
       }
       lr[k] = local(m.eL[e]) | (static_cast<uint32_t>(R) << kLocBits);
       put<uint32_t>(r.data, at + RL::lr() + 4 * k, lr[k]);

@@ -143,10 +143,14 @@ namespace bm {
 // The work list of a step launch and the shared-memory layout it needs.
 struct StepList {
   DBuf<PipeItem> items;
-  DBuf<int> sched;  // the kernel's scheduling counters (see step_pipe)
-  DBuf<int> early;  // 2 x n: items a launch takes first (written by the previous launch)
-  DBuf<int> mark;   // n: launch stamp of the early list an item is on
+  DBuf<int> sched;  // the kernel's scheduling counters (kSchedInts; see step_pipe)
+  DBuf<int> early;  // 2 x n: the items a launch lists for the next (front and back parts)
+  DBuf<int> mark;   // 2 x n: per launch parity, the stamp of the launch an item is listed for
+  DBuf<int> fixed;  // the items every launch takes (kFixedFlags, and item 0)
+  DBuf<int> inst_item;  // per instance: its first item
+  std::vector<bm_state*> members;
   int n = 0;
+  int n_fixed = 0;
   uint32_t ne4 = 4, nh4 = 4;
   size_t smem = 0;
   int occupancy = 1;  // resident CTAs per SM at this shared-memory size
@@ -173,6 +177,10 @@ struct bm_state {
   bm::DBuf<unsigned char> desc;   // one InstDesc<T> (device copy)
   std::vector<unsigned char> hdesc;  // host copy of the descriptor
   bm::StepList list;                 // the state's tiles as a work list of one instance
+  // the work list whose launches stepped the state last (null: none since the state's
+  // arrays or features changed); another list resets its scheduling state first
+  const bm::StepList* last_list = nullptr;
+  bool no_skip = false;  // bm_state_set_tile_skipping(s, 0): every launch takes every tile
   bm::Ctl* ctl = nullptr;   // device
   bm::Ctl* hctl = nullptr;  // pinned host mirror
   double* hvol = nullptr;   // pinned
@@ -242,4 +250,10 @@ bm_status list_occupancy(int prec, StepList* l);
 int state_extra_level(const bm_state* s);
 int step_grid(const StepList& l, int ctas_per_sm);
 void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t st, int withhold = 0);
+// Whether launches may skip the tiles the previous launch did not list (no member
+// carries passive species or bed evolution, whose kernels read every tile).
+bool state_listed_ok(const bm_state* s);
+// Before a launch of list l on stream st: unless every member was last stepped by l,
+// reset l's scheduling state (counters, lists, marks), so the next launch takes every tile.
+void ensure_list(StepList* l, cudaStream_t st);
 }  // namespace bm

@@ -4,13 +4,20 @@
 // CTAs take work items (tiles of 256 Hilbert-ordered cells of some instance) by
 // ticket: a share of each CTA's tickets is static (known ahead, no atomic), the rest
 // come from a launch-wide counter, so a CTA that meets expensive wet tiles simply takes
-// fewer; in FP64, where a wet tile costs many times a dry one (B300's FP64 rate), the tiles
-// the previous launch found wet, or that have boundary or inflow edges, are taken
-// first so the expensive tiles do not come last; the others (all tiles in FP32-bulk,
-// which is bound by memory traffic and profits from spatial order) follow in the work
-// list's order (each tile's arithmetic and every reduction are order-independent or
-// in a fixed order, so the result does not depend on which CTA took which tile, or
-// when).  Its copy warp streams every tile's data
+// fewer.  A launch takes the fixed items (tiles with boundary edges that carry mass,
+// inflow, source or outflow tiles, and item 0) and then the items the previous launch
+// listed: a tile that was not quiet lists itself and the tiles its halo cells lie in.
+// Every other tile was quiet or skipped in the previous launch and has no changed
+// neighbour: it is dry and at rest, both state buffers hold its values, and its step
+// would copy them through, so the launch skips it (no copy, no record, no arithmetic).
+// Where that is not allowed (passive species or bed evolution, whose kernels read
+// every tile), and in the first launch after the state or its features changed (a
+// "full" launch), every tile is taken: FP64 first the tiles the previous launch
+// listed -- wet tiles cost many times a dry one at B300's FP64 rate and must not come
+// last -- then the rest in the work list's (Hilbert) order, which FP32-bulk, bound by
+// memory traffic, takes from the start.  Each tile's arithmetic and every reduction are
+// order-independent or in a fixed order, so the result does not depend on which CTA
+// took which tile, or when, or on which tiles were skipped.  Its copy warp streams every tile's data
 // into a shared-memory slot ahead of the compute warps, in two groups completed on
 // mbarriers:
 //   group A  bulk copies (cp.async.bulk) of the tile record (inverse areas, slots,
@@ -36,9 +43,11 @@
 //            friction (Eq. 2, Table 1), U^{n+1} to HBM, the lambda/rho rate of Eq. 21;
 //            a dry cell at rest with three skipped edges (every cell of a quiet tile)
 //            is copied through unchanged;
-//   flush    when the CTA leaves an instance: max rate and tile count to the
-//            instance's control block; the CTA that completes an instance finalizes it
-//            (next dt, time, boundary volume, inflow split) -- no second launch.
+//   flush    when the CTA leaves an instance: its max rate to the instance's control
+//            block; boundary volume and inflow split by the CTA that completes the
+//            instance's last boundary / inflow tile; the next launch's lists;
+//   end      the CTA that completes the launch finalizes every instance that stepped
+//            (next dt, time, parity) and rolls the lists over -- no second launch.
 // Every wait is bounded (about a second): on timeout the CTA flags the instance
 // (status bit 2), its copy warp drains what it issued, and all warps return.
 #pragma once
@@ -135,10 +144,11 @@ __device__ __forceinline__ bool cell_dry(float hi, float lo, float z) { return !
 struct StageInfo {
   int tile, ne, nh, inst;
   uint32_t flags;
-  int next_inst;  // instance of the CTA's next tile (-1: none)
   int bidx;       // rank among the instance's tiles with boundary edges
   int item;       // index of the work item
+  int pad;
 };
+static_assert(sizeof(StageInfo) % 16 == 0, "the staged arrays after StageInfo take bulk copies (16-byte aligned)");
 
 template <typename T>
 struct StepLayout {
@@ -160,7 +170,7 @@ struct StepLayout {
     desc = align16(RecLayout<S>::bytes(ne4, nh4));
     ctl = desc + kDesc;
     info = ctl + static_cast<uint32_t>(sizeof(Ctl));
-    arr = info + static_cast<uint32_t>(sizeof(StageInfo));
+    arr = align16(info + static_cast<uint32_t>(sizeof(StageInfo)));  // bulk-copy destinations: 16-byte aligned
     gn2 = arr + kNA * nloc * S;
     slot = (gn2 + kSlice + 127u) & ~127u;
     F = kSlots * slot;
@@ -209,7 +219,7 @@ __device__ __forceinline__ const T* slice_src(const PipeItem& it, int lane) {
 // source for the tile's instance).
 template <typename T>
 __device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* sa, const PipeItem& it, int item,
-                                        int next_inst, const T* src, uint64_t* mb, int lane) {
+                                        const T* src, uint64_t* mb, int lane) {
   using SL = StepLayout<T>;
   if (lane == 0) {
     StageInfo* inf = reinterpret_cast<StageInfo*>(sa + L.info);
@@ -218,7 +228,6 @@ __device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* s
     inf->nh = static_cast<int>(it.ne_nh >> 16);
     inf->inst = it.inst;
     inf->flags = it.flags;
-    inf->next_inst = next_inst;
     inf->bidx = static_cast<int>(it.bidx);
     inf->item = item;
     // the arrival (release) orders the stores above before the phase completes
@@ -289,6 +298,43 @@ __device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* s
 
 // ------------------------------------------------------------------ the step
 
+// A work list as the step kernel sees it.  sched (kSchedInts): [0] tickets handed out
+// by the counter (after each CTA's static tickets), [1] CTAs done taking items (both
+// zero at launch; the last CTA to finish taking zeroes them), [2] launch stamp s, [3]
+// / [6] front / back items listed for launch s + 1, [4] / [7] the same listed for this
+// launch, [8] what this launch takes: 1 the
+// fixed and the listed items, 0 every item (FP64: the listed ones first), 2 every item
+// in work-list order (the list held most of them), [9] listing allowed (host-set),
+// [10] / [11] (one 64-bit word) tickets accounted (items finished plus tickets skipped)
+// / items finished in this launch, [12] items the previous launch finished.
+// early: 2 x n_items, per stamp parity the listed items (front part from index 0 up,
+// back part from the end down); mark: 2 x n_items, per stamp parity 2 s + 1 for an item
+// listed in front for launch s, 2 s for one listed in back only (kFixedMark: a fixed
+// item, never listed).  An item listed in back and then in front is in both parts; its
+// back ticket skips it.
+struct ListArgs {
+  const PipeItem* items;
+  int* sched;
+  int* early;
+  int* mark;
+  const int* fixed;      // the fixed items (tile flags in kFixedFlags, and item 0)
+  const int* inst_item;  // per instance: its first item
+  int n_items, n_fixed, n_inst;
+  int ne4max, nh4max;    // the largest record of the list (they fix the shared-memory layout)
+};
+
+// A work list's scheduling state for a full launch: counters zero, listing allowed or
+// not, no item listed, fixed items marked.
+__global__ void list_reset(const PipeItem* items, int n_items, int* mark, int* sched, int listed_ok) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kSchedInts) sched[i] = i == 9 ? listed_ok : 0;
+  if (i < n_items) {
+    const int v = (i == 0 || (items[i].flags & kFixedFlags)) ? kFixedMark : -1;
+    mark[i] = v;
+    mark[n_items + i] = v;
+  }
+}
+
 template <typename T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 3;
 // Share of a launch's tickets handed out statically: static16 / kStaticDen, by default
@@ -299,45 +345,53 @@ template <typename T>
 constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M floodplain
 
 // One step (prime = 0) or prime pass (prime = 1: no update; derived data, inflow
-// weights and the dt of the current state) over a work list.  sched: [0] tickets
-// handed out by the counter (after each CTA's static tickets), [1] CTAs done taking
-// items (both zero at launch; the last CTA to finish taking zeroes them), [2] launch
-// stamp s, [3] / [6] boundary-or-inflow / other wet items listed for launch s + 1,
-// [4] / [7] the same listed for this launch (F, W; E = F + W early items), [5] items
-// finished.  Ticket t < F takes early[s & 1][t], t < E takes
-// early[s & 1][n_items - 1 - (t - F)]; t < E + n_items takes item t - E unless
-// mark[t - E] == s (it was early).  Finished items are listed in early[(s + 1) & 1]
-// (from the front or the back) and marked s + 1; the last item to finish moves [3],
-// [6] to [4], [7], zeroes [3], [5], [6] and increments s.  early: 2 x n_items, mark:
-// n_items.  ne4max / nh4max: the largest record of the list (they fix the
-// shared-memory layout).  A single state is a list of one instance's tiles, so a run
-// executes the same machine code alone and in a batch and gives bitwise the same
-// result.  kX: which optional features the instantiation carries -- 0 none; 1 the
-// flood-tracking records and the edge mass fluxes exported for passive species; 2 also
-// external sources and the logarithmic friction closures (a list launches the lowest
-// level its members need, so the plain step carries none of that code).  withhold != 0
-// (diagnostics of the failure path only): every CTA's copy warp withholds group H of
-// its first tile, so the compute warps' bounded wait for it runs out; the launch then
-// takes the timeout path below (status bit 2, issued copies retired, no state written).
-// static16: the static share of the tickets in sixteenths (negative: kStaticNum); the
-// schedule never changes results (the reductions are order-free).
+// weights and the dt of the current state) over a work list g.  Ticket t < F takes
+// fixed[t]; F <= t < F + nf the front part of the listed items, then nb of the back
+// part; a full launch then takes item t - E (E = F + nf + nb) unless it is fixed or was
+// taken from the lists (its mark is s).  FP32-bulk full launches use no lists.  A
+// single state is a list of one instance's tiles, so a run executes the same machine
+// code alone and in a batch and gives bitwise the same result.  kX: which optional
+// features the instantiation carries -- 0 none; 1 the flood-tracking records and the
+// edge mass fluxes exported for passive species; 2 also external sources and the
+// logarithmic friction closures (a list launches the lowest level its members need,
+// so the plain step carries none of that code).  withhold != 0 (diagnostics of the
+// failure path only): every CTA's copy warp withholds group H of its first tile, so
+// the compute warps' bounded wait for it runs out; the launch then takes the timeout
+// path below (status bit 2, issued copies retired, no state written).  static16: the
+// static share of the tickets in sixteenths (negative: kStaticNum); the schedule never
+// changes results (the reductions are order-free).
 template <typename T, int kX>
-__global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const PipeItem* __restrict__ items,
-                                                                         int n_items, int* __restrict__ sched,
-                                                                         int* __restrict__ early, int* __restrict__ mark,
-                                                                         int ne4max, int nh4max, int prime,
-                                                                         int withhold, int static16) {
+__global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const ListArgs g, int prime, int withhold,
+                                                                         int static16) {
   constexpr bool kExtra = kX >= 1;  // tracking, species exports
   constexpr bool kFull = kX >= 2;   // sources, log-law friction
   using SL = StepLayout<T>;
   using RL = RecLayout<SL::S>;
   constexpr bool kPair = !SL::k64;
   constexpr int S = SL::kSlots;
+  const PipeItem* __restrict__ items = g.items;
+  int* __restrict__ sched = g.sched;
+  int* __restrict__ early = g.early;
+  int* __restrict__ mark = g.mark;
+  const int n_items = g.n_items;
   extern __shared__ __align__(128) unsigned char smem[];
   // per slot: group A landed, group H landed, slot released by the compute warps
   __shared__ __align__(8) uint64_t mb_a[S], mb_h[S], mb_e[S];
   __shared__ int s_abort;
-  const SL L(static_cast<uint32_t>(ne4max), static_cast<uint32_t>(nh4max));
+  // the launch's ticket map (written by the copy warp before its first issue, so the
+  // compute warps see it after their first wait): stamp, listing allowed, part bounds
+  // P1 <= P2 <= P3 <= tickets, whether the lists were taken; the tickets this CTA's copy
+  // warp skipped (written before its end marker)
+  __shared__ int s_stamp, s_listed_ok, s_p1, s_p2, s_p3, s_tickets, s_lists, s_skip;
+  // the compute warps' listings (item * 2 + front), flushed to the next launch's list in
+  // bulk (one round of atomics for many tiles, off the tiles' critical path); FP64 has
+  // less shared memory to spare (two CTAs of its layout fill an SM)
+  constexpr int kLstCap = SL::k64 ? 128 : 1024;
+  __shared__ int s_lst[kLstCap];
+  __shared__ int s_nlst;
+  __shared__ int s_fin;  // the finalizes a tile's CTA runs (bit 0 boundary, bit 1 inflow)
+  __shared__ __align__(16) PipeItem s_pa;  // the copy warp's next item to issue
+  const SL L(static_cast<uint32_t>(g.ne4max), static_cast<uint32_t>(g.nh4max));
   const int tid = threadIdx.x;
   auto slot = [&](int k) { return smem + (k % S) * L.slot; };
 
@@ -349,6 +403,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     }
     mbar_init_fence();
     s_abort = 0;
+    s_nlst = 0;
   }
   __syncthreads();
 
@@ -359,95 +414,163 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     // Work items reach the issue through a pipeline, so the copy warp seldom waits on a
     // value in the iteration that asked for it: the ticket (static, or requested from
     // the counter a step ahead) and its lookup -> the item read -> promotion to "next
-    // to issue" (instance pointers and halo indices read) -> issue.  FP64 tickets map
-    // through the early list first.
-    // FP64: the early list and marks are the previous step's
-    if constexpr (SL::k64) grid_dep_wait();
-    // The early list: the tiles with boundary or inflow edges (front part, in the order
-    // they finished; the per-instance boundary and inflow work follows the last of
-    // them), then the other tiles the previous launch found wet (stored from the end
-    // of the array).
-    int stamp = 0, n_front = 0, n_back = 0;
-    if (SL::k64 && lane == 0) {
-      stamp = *reinterpret_cast<volatile int*>(&sched[2]);
-      n_front = *reinterpret_cast<volatile int*>(&sched[4]);
-      n_back = *reinterpret_cast<volatile int*>(&sched[7]);
+    // to issue" (instance pointers and halo indices read) -> issue.
+    // A work item read ahead is held across the warp, one 32-bit word of it per lane
+    // (lanes 0..11; lane 12 holds its mark for a back-part item): the next to issue is
+    // in shared memory (s_pa), so the copy warp keeps few registers.
+    constexpr int kRest = 1 << 30, kBack = 1 << 29, kIdx = kBack - 1;
+    constexpr int kWords = static_cast<int>(sizeof(PipeItem) / 4), kWTile = 7, kWInst = 9, kWFlags = 10;
+    auto fetch_w = [&](int idx) -> unsigned {
+      if (idx < 0) return lane == kWTile ? 0xffffffffu : 0u;  // tile -1: no item
+      const int i = idx & kIdx;
+      if (lane < kWords) return __ldg(reinterpret_cast<const unsigned*>(items + i) + lane);
+      if (lane == kWords && (idx & kBack))
+        return static_cast<unsigned>(__ldcg(&mark[static_cast<size_t>(s_stamp & 1) * n_items + i]));
+      return 0u;
+    };
+    auto word = [&](unsigned w, int k) -> unsigned { return __shfl_sync(0xffffffffu, w, k); };
+    const PipeItem& pa = s_pa;
+    int hv_a[kHaloPre];
+    // A CTA whose first ticket (its own index) is a fixed item reads that item and its
+    // halo indices before the previous launch has ended (items and records do not
+    // change) and issues it right after the wait.
+    const int idx_early = static_cast<int>(blockIdx.x) < min(g.n_fixed, n_items) ? __ldg(&g.fixed[blockIdx.x]) : -1;
+    if (idx_early >= 0) {
+      const unsigned w = fetch_w(idx_early);
+      if (lane < kWords) reinterpret_cast<unsigned*>(&s_pa)[lane] = w;
+      __syncwarp();
+      load_halo<T>(pa, lane, hv_a);
     }
-    stamp = __shfl_sync(0xffffffffu, stamp, 0);
-    n_front = min(__shfl_sync(0xffffffffu, n_front, 0), n_items);
-    n_back = min(__shfl_sync(0xffffffffu, n_back, 0), n_items - n_front);
-    const int n_early = n_front + n_back;
-    const int* ord = early + static_cast<size_t>(stamp & 1) * n_items;
-    const int n_tickets = n_early + n_items;
-    // ticket -> work item (-1: taken in the early pass; -2: past the end), in two
-    // parts so the load can be issued a step ahead: map_load reads what the ticket
-    // needs (its early-list entry, or the item's mark), resolve decides.  An item
-    // listed with stamp s, or finished in the early pass and re-listed with s + 1, was
-    // taken early (an item only finishes after it was taken).
+    // The lists, the marks and the counters are the previous launch's.
+    grid_dep_wait();
+    if (lane == 0) {
+      const volatile int* vs = sched;
+      const int stamp = vs[2], mode = vs[8];
+      const bool listed = mode == 1;
+      const int n_fix = min(g.n_fixed, n_items);
+      // FP32-bulk full launches take the work list in order after the fixed items
+      const bool use_lists = listed || (SL::k64 && mode == 0);
+      const int nf = use_lists ? min(max(vs[4], 0), n_items - n_fix) : 0;
+      const int nb = use_lists ? min(max(vs[7], 0), n_items - n_fix - nf) : 0;
+      s_stamp = stamp;
+      s_listed_ok = vs[9];
+      s_p1 = n_fix;
+      s_p2 = n_fix + nf;
+      s_p3 = n_fix + nf + nb;
+      s_tickets = n_fix + nf + nb + (listed ? 0 : n_items);
+      s_lists = nf + nb > 0;
+    }
+    __syncwarp();
+    const int n_tickets = s_tickets;
+    int n_skip = 0;  // tickets resolved to an item taken otherwise
+    // ticket -> work item (-1: taken otherwise; -2: past the end), in two parts so the
+    // load can be issued a step ahead: map_load reads what the ticket needs (a fixed or
+    // listed item, or the item's mark), resolve decides.
     auto map_load = [&](int t) -> int {
-      if (t < n_early) return t < n_front ? ord[t] : ord[n_items - 1 - (t - n_front)];
-      if (n_early > 0 && t < n_tickets) return __ldcg(&mark[t - n_early]);
+      const int p1 = s_p1, p2 = s_p2, p3 = s_p3;
+      const size_t par = static_cast<size_t>(s_stamp & 1) * n_items;
+      if (t < p1) return __ldg(&g.fixed[t]);
+      if (t < p2) return __ldcg(&early[par + (t - p1)]);
+      if (t < p3) return __ldcg(&early[par + (n_items - 1 - (t - p2))]);
+      if constexpr (SL::k64) {
+        if (t < n_tickets) return __ldcg(&mark[par + (t - p3)]);
+      }
       return 0;
     };
+    // Index flags checked once the item is read: kRest, an FP32-bulk full launch takes
+    // item t - P3 without a lookup and skips it if it is a fixed one (taken by a ticket
+    // t < P1); kBack, an item of the list's back part is skipped if it is in the front
+    // part too (its mark, read with the item, says so)
     auto resolve = [&](int t, int v) -> int {
-      if (t < n_early) return v;
+      const int p2 = s_p2, p3 = s_p3;
+      if (t < p3) return (v >= 0 && v < n_items) ? (t < p2 ? v : v | kBack) : -1;  // (valid lists hold valid items)
       if (t >= n_tickets) return -2;
-      if (n_early > 0 && (v == stamp || v == stamp + 1)) return -1;
-      return t - n_early;
+      if constexpr (SL::k64) {
+        if (v == kFixedMark || (s_lists && (v >> 1) == s_stamp)) return -1;
+        return t - p3;
+      } else {
+        return (t - p3) | kRest;
+      }
     };
-    auto fetch = [&](int idx) -> PipeItem {
-      PipeItem it{};
-      it.tile = -1;
-      if (idx >= 0) it = items[idx];
-      return it;
+    auto taken_otherwise = [&](int idx, unsigned w) -> bool {
+      const unsigned fl = word(w, kWFlags);
+      const int m = static_cast<int>(word(w, kWords));
+      if (idx < 0) return false;
+      if (idx & kRest) return (idx & kIdx) == 0 || (fl & kFixedFlags) != 0u;
+      return (idx & kBack) != 0 && m == 2 * s_stamp + 1;
     };
     // Tickets: first this CTA's static ones, blockIdx.x + m gridDim.x for m < m_static
-    // (known without asking, so their items are looked up a step ahead without
-    // waiting; a share of all tickets, so that the counter's rest evens out the CTAs),
-    // then the launch's counter from n_static on, one ticket requested a step ahead.
+    // (known without asking, so their items are looked up ahead -- the first 32 in one
+    // round at the start -- without waiting; a share of all tickets, so that the
+    // counter's rest evens out the CTAs), then the launch's counter from n_static on,
+    // one ticket requested a step ahead.
     // A CTA's tickets increase, so once one is past the end every later one is too.
     const int G = static_cast<int>(gridDim.x);
     const int m_static = max(2, n_tickets / kStaticDen * (static16 >= 0 ? static16 : kStaticNum<T>) / G);
     const int n_static = m_static * G;
-    int m_next = 0;
+    const int pre_v = lane < m_static ? map_load(static_cast<int>(blockIdx.x) + lane * G) : 0;
+    int m_next = idx_early >= 0 ? 1 : 0;  // (the early item was ticket 0)
     int tc = 0;  // lane 0: the requested counter ticket
     bool tc_pending = false;
     auto request = [&]() {
       if (lane == 0) tc = atomicAdd(&sched[0], 1) + n_static;
       tc_pending = true;
     };
-    auto next_ticket = [&]() -> int {
-      if (m_next < m_static) return static_cast<int>(blockIdx.x) + (m_next++) * G;
+    auto next_tv = [&](int& v) -> int {  // the next ticket and its lookup
+      if (m_next < m_static) {
+        const int m = m_next++;
+        const int pv = __shfl_sync(0xffffffffu, pre_v, m & 31);
+        const int t = static_cast<int>(blockIdx.x) + m * G;
+        v = m < 32 ? pv : map_load(t);
+        return t;
+      }
       if (!tc_pending) request();
       tc_pending = false;
-      return __shfl_sync(0xffffffffu, tc, 0);
+      const int t = __shfl_sync(0xffffffffu, tc, 0);
+      v = map_load(t);
+      return t;
     };
     auto next_idx = [&]() -> int {  // the next ticket's item, past skipped tickets (waits)
       int idx;
       do {
-        const int t = next_ticket();
-        idx = resolve(t, map_load(t));
+        int v;
+        const int t = next_tv(v);
+        idx = resolve(t, v);
+        if (idx == -1) ++n_skip;
       } while (idx == -1);
       return idx;
     };
-    // start-up: item a (next to issue) and item b (read), read together
-    int idx_a = next_idx();
-    int idx_b = idx_a >= 0 ? next_idx() : -2;
-    PipeItem pa = fetch(idx_a);
-    PipeItem pb = fetch(idx_b);
-    int hv_a[kHaloPre];
-    load_halo<T>(pa, lane, hv_a);
-    // FP32-bulk: items and records are the mesh's, read before the previous step has
-    // ended; the ticket counter, control blocks and state are the previous step's
-    if constexpr (!SL::k64) grid_dep_wait();
-    bool tc_live = idx_b >= 0;
-    // the ticket after b and its lookup, resolved at the first promotion
-    int tn = -2, tv = 0;
-    if (tc_live) {
-      tn = next_ticket();
-      tv = map_load(tn);
-      if (m_next >= m_static && !tc_pending) request();
+    // start-up: item a (next to issue) and item b (read), read together -- or, after
+    // an early item a, b once a is issued
+    int idx_a = idx_early, idx_b = -2;
+    unsigned wb = fetch_w(-2);
+    bool b_pending = idx_early >= 0;  // b is still to be read
+    if (!b_pending) {
+      idx_a = next_idx();
+      idx_b = idx_a >= 0 ? next_idx() : -2;
+      unsigned wa = fetch_w(idx_a);
+      wb = fetch_w(idx_b);
+      while (taken_otherwise(idx_a, wa)) {
+        ++n_skip;
+        idx_a = idx_b;
+        wa = wb;
+        idx_b = idx_a >= 0 ? next_idx() : -2;
+        wb = fetch_w(idx_b);
+      }
+      if (lane < kWords) reinterpret_cast<unsigned*>(&s_pa)[lane] = wa;
+      __syncwarp();
+      load_halo<T>(pa, lane, hv_a);
     }
+    bool tc_live = false;
+    int tn = -2, tv = 0;  // the ticket after b and its lookup, resolved at the promotion
+    auto lookahead = [&]() {
+      tc_live = idx_b >= 0;
+      if (tc_live) {
+        tn = next_tv(tv);
+        if (m_next >= m_static && !tc_pending) request();
+      }
+    };
+    if (!b_pending) lookahead();
     const T* src = pa.tile >= 0 ? slice_src<T>(pa, lane) : nullptr;
     int a_next = 0;      // next tile (in this CTA's order) whose groups are issued
     bool ended = false;  // the end marker has been issued
@@ -460,35 +583,63 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       if (!free_slot && lane == 0) free_slot = mbar_test(&mb_e[a_next % S], ((a_next - S) / S) & 1);
       if (__shfl_sync(0xffffffffu, free_slot, 0)) {
         if (pa.tile >= 0) {
-          issue_a<T>(L, slot(a_next), pa, idx_a, pb.tile >= 0 ? pb.inst : -1, src, &mb_a[a_next % S], lane);
+          issue_a<T>(L, slot(a_next), pa, idx_a & kIdx, src, &mb_a[a_next % S], lane);
           if (!(withhold && a_next == 0)) issue_h<T>(L, slot(a_next), pa, src, hv_a, &mb_h[a_next % S], lane);
+          if (b_pending) {  // after an early item a
+            b_pending = false;
+            idx_b = next_idx();
+            wb = fetch_w(idx_b);
+            lookahead();
+          }
+          while (taken_otherwise(idx_b, wb)) {  // b was taken otherwise: the one after it
+            ++n_skip;
+            int idx = tc_live ? resolve(tn, tv) : -2;
+            if (idx == -1) {
+              ++n_skip;
+              idx = next_idx();
+            }
+            idx_b = idx;
+            wb = fetch_w(idx_b);
+            tc_live = idx_b >= 0;
+            if (tc_live) {
+              tn = next_tv(tv);
+              if (m_next >= m_static && !tc_pending) request();
+            }
+          }
+          const int b_tile = static_cast<int>(word(wb, kWTile)), b_inst = static_cast<int>(word(wb, kWInst));
           // promote b (read one iteration ago); read its instance pointers and halo
           // indices (used at the next issue)
-          if (pb.tile >= 0 && pb.inst != pa.inst) src = slice_src<T>(pb, lane);
-          pa = pb;
+          const int a_inst = pa.inst;
+          __syncwarp();  // every lane is done with a
+          if (lane < kWords) reinterpret_cast<unsigned*>(&s_pa)[lane] = wb;
+          __syncwarp();
+          if (b_tile >= 0 && b_inst != a_inst) src = slice_src<T>(pa, lane);
           idx_a = idx_b;
           load_halo<T>(pa, lane, hv_a);
           // the pending ticket becomes the next read; request a new ticket
-          if (pa.tile >= 0 && tc_live) {
+          if (b_tile >= 0 && tc_live) {
             // the ticket looked up a step ago; past a skipped one, the next ones now
             int idx = resolve(tn, tv);
-            if (idx == -1) idx = next_idx();
+            if (idx == -1) {
+              ++n_skip;
+              idx = next_idx();
+            }
             idx_b = idx;
-            pb = fetch(idx_b);  // used at the next promotion: its load is not waited for here
+            wb = fetch_w(idx_b);  // used at the next promotion: its load is not waited for here
             tc_live = idx_b >= 0;
             if (tc_live) {
-              tn = next_ticket();
-              tv = map_load(tn);
+              tn = next_tv(tv);
               if (m_next >= m_static && !tc_pending) request();
             }
           } else {
-            pb.tile = -1;
+            wb = fetch_w(-2);
             idx_b = -2;
             tc_live = false;
           }
         } else {
           if (lane == 0) {
             reinterpret_cast<StageInfo*>(slot(a_next) + L.info)->tile = -1;
+            s_skip = n_skip;  // released to the compute warps by the arrival below
             mbar_expect_tx(&mb_a[a_next % S], 0);
           }
           cp_async_arrive(&mb_h[a_next % S]);  // end marker: nothing to gather
@@ -536,15 +687,77 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
   double* red = reinterpret_cast<double*>(smem + L.red);
   const T zero = T(0);
   volatile int* abort_flag = &s_abort;
-  const int stamp = *reinterpret_cast<volatile int*>(&sched[2]);  // read before any item can finish
-  int* next_early = early + static_cast<size_t>((stamp + 1) & 1) * n_items;
+  // list an item for the next launch, once per part (its mark: 2 s1 + 1 in front, 2 s1
+  // in back; a back listing after a front one adds nothing)
+  auto list_next = [&](int item, bool front) {
+    const int s1 = s_stamp + 1;
+    const size_t par = static_cast<size_t>(s1 & 1) * n_items;
+    const int v = 2 * s1 + (front ? 1 : 0);
+    if (item < 0 || item >= n_items || atomicMax(&mark[par + item], v) >= v) return;
+    const int pos = atomicAdd(&sched[front ? 3 : 6], 1);
+    if (pos < n_items) early[par + (front ? pos : n_items - 1 - pos)] = item;
+  };
+  // note a listing in the CTA's buffer (at once when the buffer is full)
+  auto note = [&](int item, bool front) {
+    const int pos = atomicAdd(&s_nlst, 1);
+    if (pos < kLstCap) s_lst[pos] = item * 2 + (front ? 1 : 0);
+    else list_next(item, front);
+  };
+  // the buffer's listings, all compute threads: dedupe by the marks, then one counter
+  // add per warp and part
+  auto flush = [&]() {
+    nbar<kTile>();
+    const int n = min(s_nlst, kLstCap);
+    const int s1 = s_stamp + 1;
+    const size_t par = static_cast<size_t>(s1 & 1) * n_items;
+    const int lane = tid & 31;
+    for (int b0 = 0; b0 < n; b0 += kTile) {
+      const int j = b0 + tid;
+      int item = -1;
+      bool front = false, ok = false;
+      if (j < n) {
+        const int e = s_lst[j];
+        item = e >> 1;
+        front = (e & 1) != 0;
+        const int v = 2 * s1 + (front ? 1 : 0);
+        ok = item >= 0 && item < n_items && atomicMax(&mark[par + item], v) < v;
+      }
+      const unsigned mf = __ballot_sync(0xffffffffu, ok && front), mb = __ballot_sync(0xffffffffu, ok && !front);
+      int bf = 0, bb = 0;
+      if (lane == 0) {
+        if (mf) bf = atomicAdd(&sched[3], __popc(mf));
+        if (mb) bb = atomicAdd(&sched[6], __popc(mb));
+      }
+      bf = __shfl_sync(0xffffffffu, bf, 0);
+      bb = __shfl_sync(0xffffffffu, bb, 0);
+      if (ok) {
+        const unsigned lt = (1u << lane) - 1u;
+        const int pos = front ? bf + __popc(mf & lt) : bb + __popc(mb & lt);
+        if (pos < n_items) early[par + (front ? pos : n_items - 1 - pos)] = item;
+      }
+    }
+    nbar<kTile>();
+    if (tid == 0) s_nlst = 0;
+    nbar<kTile>();
+  };
   // this CTA's max Eq. 21 rate over the current instance's tiles, in the working
   // precision (FP32-bulk: no FP64 instruction per cell; the max of the floats, converted
   // once, equals the max of the converted values)
   T rrun = T(0);
   float smax = 0.0f;  // FP64: the largest rate screen this lane's warp has seen for the instance
   unsigned cnt = 0;   // tiles of the current instance this CTA completed
-  int n_done = 0;     // FP64: tiles this CTA completed in the launch
+  int cur_inst = -1;  // the instance of those tiles
+  Ctl* cur_ctl = nullptr;
+  // the CTA's rate max of an instance to its control block, when the CTA moves on to
+  // another instance's tiles or has no more (all compute threads)
+  auto flush_rate = [&]() {
+    const double r = block_max_nonneg_all<kTile>(static_cast<double>(rrun), reinterpret_cast<unsigned long long*>(red));
+    if (tid == 0 && r > 0.0) atomicMax(&cur_ctl->rmax_bits, static_cast<unsigned long long>(__double_as_longlong(r)));
+    rrun = T(0);
+    smax = 0.0f;
+    cnt = 0;
+  };
+  int n_done = 0;     // items this CTA completed in the launch
   for (int k = 0;; ++k) {
     unsigned char* sb = slot(k);
     {
@@ -581,6 +794,11 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     T* V = U + L.nloc;
     T* C = V + L.nloc;
     const bool run = prime || cs.active;
+    if (inf.inst != cur_inst) {  // (every compute thread reads the same slot)
+      if (cnt > 0) flush_rate();
+      cur_inst = inf.inst;
+      cur_ctl = a.ctl;
+    }
     T dt, quni, g, hg, hmin;
     step_consts(&cs, a.p, dt, quni, g, hg, hmin);
     const double qscale = cs.qscale;
@@ -605,6 +823,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
       }
     }
     const bool quiet = nbar_and<kTile>(tq) && !prime && !(inf.flags & 6u);  // no inflow or source
+    if (s_nlst > kLstCap / 2) flush();  // (every compute thread reads the count after the barrier)
 
     // phase F: edges
     double bsum = 0.0;
@@ -909,17 +1128,32 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
     if (run) {
       ++cnt;
       double* scratch = reinterpret_cast<double*>(smem + L.F);  // the fluxes are consumed
-      if (!prime && (inf.flags & 1u)) {
-        const double bs = quiet ? 0.0 : block_sum<kTile>(bsum, red);
-        int last_b = 0;
+      // boundary and inflow tiles: one fence and one count of both kinds (an inflow tile
+      // is a boundary tile too; the counts share a 64-bit word: inflow low, boundary high)
+      const bool bnd = !prime && (inf.flags & 1u);
+      const bool infl = (inf.flags & 2u) != 0u;
+      if (bnd || infl) {
+        const double bs = (bnd && !quiet) ? block_sum<kTile>(bsum, red) : 0.0;
+        if (infl && !(bnd && !quiet)) nbar<kTile>();  // every thread's inflow weights are stored
         if (tid == 0) {
-          a.part[inf.bidx].bflux = bs;
+          if (bnd) a.part[inf.bidx].bflux = bs;
           __threadfence();
-          last_b = atomicAdd(&a.ctl->b_done, 1u) + 1u == static_cast<unsigned>(a.n_btiles) ? 1 : 0;
+          const unsigned long long inc = (bnd ? (1ull << 32) : 0ull) | (infl ? 1ull : 0ull);
+          const unsigned long long old =
+              atomicAdd(reinterpret_cast<unsigned long long*>(&a.ctl->in_done), inc);
+          const bool lb = bnd && static_cast<unsigned>(old >> 32) + 1u == static_cast<unsigned>(a.n_btiles);
+          const bool li = infl && static_cast<unsigned>(old) + 1u == static_cast<unsigned>(a.n_in_tiles);
+          s_fin = (lb ? 1 : 0) | (li ? 2 : 0);
         }
-        if (nbar_or<kTile>(last_b)) {
+        nbar<kTile>();
+        const int fin = s_fin;
+        if (fin & 1) {
           __threadfence();
           finalize_boundary<T>(a, cs, scratch);
+        }
+        if (fin & 2) {
+          __threadfence();
+          finalize_inflow<T>(a, cs, prime ? 0 : 1, red + 4, red, scratch);
         }
       }
       if (kFull && (inf.flags & 8u)) {
@@ -934,70 +1168,78 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const P
           finalize_hq<T>(a, cs, prime ? 0 : 1, red + 4, red);
         }
       }
-      if (inf.flags & 2u) {
-        nbar<kTile>();  // every thread's inflow weights are stored
-        int last_in = 0;
-        if (tid == 0) {
-          __threadfence();
-          last_in = atomicAdd(&a.ctl->in_done, 1u) + 1u == static_cast<unsigned>(a.n_in_tiles) ? 1 : 0;
-        }
-        if (nbar_or<kTile>(last_in)) {
-          __threadfence();
-          finalize_inflow<T>(a, cs, prime ? 0 : 1, red + 4, red, scratch);
-        }
+    }
+    // the next launch's lists: a tile that was not quiet lists itself in front and the
+    // tiles its halo cells lie in behind; an instance that did not step keeps its items
+    // listed (nothing changed).  Where listing is not allowed, FP64 lists the tiles that
+    // were not quiet, to take them first.
+    const bool listed_ok = s_listed_ok != 0;
+    if (!((inf.flags & kFixedFlags) != 0u || inf.item == 0) && tid == 0) {
+      if (listed_ok ? (!run || !quiet) : (SL::k64 && run && !quiet)) note(inf.item, run);
+    }
+    if (listed_ok && run && !quiet) {
+      const int32_t* hg = reinterpret_cast<const int32_t*>(sb + RL::hidx(ne4));
+      const int base = inf.item - tile;  // the instance's first item
+      for (int j = tid; j < nh; j += kTile) {
+        const unsigned u = static_cast<unsigned>(hg[j]) / kTile;
+        if (j == 0 || static_cast<unsigned>(hg[j - 1]) / kTile != u)  // ascending: the first of each tile
+          note(base + static_cast<int>(u), false);
       }
     }
-    const bool leave = inf.next_inst != inf.inst;
-    if (leave && cnt > 0) {
-      const double r = block_max_nonneg_all<kTile>(static_cast<double>(rrun), reinterpret_cast<unsigned long long*>(red));
-      int is_last = 0;
-      if (tid == 0) {
-        if (r > 0.0) atomicMax(&a.ctl->rmax_bits, static_cast<unsigned long long>(__double_as_longlong(r)));
-        __threadfence();
-        const unsigned prev = atomicAdd(&a.ctl->done, cnt);
-        is_last = (prev + cnt == static_cast<unsigned>(a.n_tiles)) ? 1 : 0;
-      }
-      if (tid == 0 && is_last) {
-        __threadfence();
-        finalize_step<T>(a, cs, prime ? 0 : 1);
-      }
-      rrun = T(0);
-      smax = 0.0f;
-      cnt = 0;
-    }
-    // FP64: boundary, inflow and wet tiles are taken early in the next launch (only the
-    // next launch reads the list, so no fence); every item finishes once per launch, so
-    // the two parts never meet
-    if (SL::k64 && tid == 0) {
-      ++n_done;
-      if (inf.flags & 3u) {
-        const int pos = atomicAdd(&sched[3], 1);
-        if (pos < n_items) {
-          next_early[pos] = inf.item;
-          mark[inf.item] = stamp + 1;
-        }
-      } else if (!quiet) {
-        const int pos = atomicAdd(&sched[6], 1);
-        if (pos < n_items) {
-          next_early[n_items - 1 - pos] = inf.item;
-          mark[inf.item] = stamp + 1;
-        }
-      }
-    }
+    if (tid == 0) ++n_done;
     // release the tile's slot to the copy warp (each warp once it is done with it)
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(&mb_e[k % S]);
   }
-  // FP64: the CTA whose tiles complete the launch rolls the early lists over (the
-  // fence orders this CTA's list entries before its count)
-  if (SL::k64 && tid == 0 && n_done > 0) {
-    __threadfence();
-    if (atomicAdd(&sched[5], n_done) + n_done == n_items) {
+  if (cnt > 0) flush_rate();
+  flush();
+  // The CTA whose finished items (with the tickets its copy warp skipped) complete the
+  // launch finalizes every instance that stepped and rolls the lists over (the fence
+  // orders this CTA's rate maxima and list entries before its count).  A launch has at
+  // least one ticket (item 0 is fixed), so some CTA completes it.
+  int last = 0;
+  if (tid == 0) {
+    const int total = n_done + s_skip;
+    if (total > 0) {
       __threadfence();
-      atomicExch(&sched[4], atomicExch(&sched[3], 0));
-      atomicExch(&sched[7], atomicExch(&sched[6], 0));
-      atomicExch(&sched[5], 0);
-      atomicExch(&sched[2], stamp + 1);
+      const unsigned long long inc = (static_cast<unsigned long long>(n_done) << 32) | static_cast<unsigned>(total);
+      const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(&sched[10]), inc);
+      last = static_cast<int>(old & 0xffffffffull) + total == s_tickets ? 1 : 0;
+    }
+  }
+  if (nbar_or<kTile>(last)) {
+    __threadfence();
+    const int roll_tid = min(((g.n_inst + 31) / 32) * 32, kTile - 32);  // a warp with no instance (if any)
+    for (int k = tid; k < g.n_inst; k += kTile) {
+      // (the fields finalize_step reads plainly are not written during a launch)
+      const PipeItem& it = items[g.inst_item[k]];
+      const Ctl& cs = *it.ctl;
+      if (prime || cs.active) finalize_step<T>(*static_cast<const InstDesc<T>*>(it.desc), cs, prime ? 0 : 1);
+    }
+    // launch stamps restart before they overflow: the marks forget every listing and
+    // the next launch takes every item
+    const int stamp = s_stamp;
+    const bool wrap = stamp + 1 >= kStampMax;
+    if (wrap)
+      for (int j = tid; j < 2 * n_items; j += kTile)
+        if (__ldcg(&mark[j]) != kFixedMark) mark[j] = -1;
+    if (wrap) nbar<kTile>();
+    if (tid == roll_tid) {
+      // every other CTA has finished with the counters (its count came before this one)
+      volatile int* vs = sched;
+      const int nf = vs[3], nb = vs[6], ok = vs[9], done = vs[11];
+      // a list that holds most items: the next launch takes them all in work-list order
+      const bool dense = 4LL * (nf + nb) > 3LL * (n_items - g.n_fixed);
+      vs[3] = 0;
+      vs[6] = 0;
+      vs[10] = 0;
+      vs[11] = 0;
+      vs[12] = done;
+      vs[4] = wrap ? 0 : nf;
+      vs[7] = wrap ? 0 : nb;
+      vs[8] = wrap ? 0 : (ok ? (dense ? 2 : 1) : 0);
+      vs[2] = wrap ? 0 : stamp + 1;
+      __threadfence();
     }
   }
 }
