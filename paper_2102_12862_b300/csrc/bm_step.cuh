@@ -219,7 +219,7 @@ __device__ __forceinline__ const T* slice_src(const PipeItem& it, int lane) {
 // source for the tile's instance).
 template <typename T>
 __device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* sa, const PipeItem& it, int item,
-                                        const T* src, uint64_t* mb, int lane) {
+                                        const T* const* ssrc, uint64_t* mb, int lane) {
   using SL = StepLayout<T>;
   if (lane == 0) {
     StageInfo* inf = reinterpret_cast<StageInfo*>(sa + L.info);
@@ -243,7 +243,7 @@ __device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* s
   } else if (lane <= 3 + SL::kNA) {
     const int j = lane - 3;
     unsigned char* dst = j < SL::kNA ? sa + L.arr + j * L.nloc * SL::S : sa + L.gn2;
-    bulk_g2s(dst, src + static_cast<size_t>(it.tile) * kTile, SL::kSlice, mb);
+    bulk_g2s(dst, ssrc[j] + static_cast<size_t>(it.tile) * kTile, SL::kSlice, mb);
   }
 }
 
@@ -263,25 +263,22 @@ __device__ __forceinline__ void load_halo(const PipeItem& it, int lane, int (&hv
 }
 
 // Group H of a tile (all lanes of the copy warp): the halo cells' values by cp.async,
-// each lane arriving on mb when its gathers have landed.  src: this lane's slice
-// source (lane 3 + j holds array j); hv: the prefetched halo indices.
+// each lane arriving on mb when its gathers have landed.  ssrc: the instance's slice
+// sources (shared memory, array j at j); hv: the prefetched halo indices.
 template <typename T>
-__device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* sa, const PipeItem& it, const T* src,
-                                        const int (&hv)[kHaloPre], uint64_t* mb, int lane) {
+__device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* sa, const PipeItem& it,
+                                        const T* const* ssrc, const int (&hv)[kHaloPre], uint64_t* mb, int lane) {
   using SL = StepLayout<T>;
   const int nh = static_cast<int>(it.ne_nh >> 16);
-  const T* sp[SL::kNA];
-#pragma unroll
-  for (int j = 0; j < SL::kNA; ++j)
-    sp[j] = reinterpret_cast<const T*>(
-        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(src), 3 + j));
   T* arr = reinterpret_cast<T*>(sa + L.arr);
 #pragma unroll
-  for (int u = 0; u < kHaloPre; ++u) {
-    const int h = lane + 32 * u;
-    if (h < nh) {
+  for (int j = 0; j < SL::kNA; ++j) {
+    const T* sp = ssrc[j];
+    T* dst = arr + j * L.nloc + kTile;
 #pragma unroll
-      for (int j = 0; j < SL::kNA; ++j) cp_async<sizeof(T)>(arr + j * L.nloc + kTile + h, sp[j] + hv[u]);
+    for (int u = 0; u < kHaloPre; ++u) {
+      const int h = lane + 32 * u;
+      if (h < nh) cp_async<sizeof(T)>(dst + h, sp + hv[u]);
     }
   }
   if (nh > 32 * kHaloPre) {  // large halos (unusual meshes): the rest of the indices now
@@ -290,7 +287,7 @@ __device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* s
     for (int h = 32 * kHaloPre + lane; h < nh; h += 32) {
       const int gi = __ldg(hg + h);
 #pragma unroll
-      for (int j = 0; j < SL::kNA; ++j) cp_async<sizeof(T)>(arr + j * L.nloc + kTile + h, sp[j] + gi);
+      for (int j = 0; j < SL::kNA; ++j) cp_async<sizeof(T)>(arr + j * L.nloc + kTile + h, ssrc[j] + gi);
     }
   }
   cp_async_arrive(mb);
@@ -298,13 +295,19 @@ __device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* s
 
 // ------------------------------------------------------------------ the step
 
+// While the lists hold most items, every kProbe-th launch builds them again.
+constexpr int kProbe = 16;
+
 // A work list as the step kernel sees it.  sched (kSchedInts): [0] tickets handed out
 // by the counter (after each CTA's static tickets), [1] CTAs done taking items (both
 // zero at launch; the last CTA to finish taking zeroes them), [2] launch stamp s, [3]
 // / [6] front / back items listed for launch s + 1, [4] / [7] the same listed for this
 // launch, [8] what this launch takes: 1 the
 // fixed and the listed items, 0 every item (FP64: the listed ones first), 2 every item
-// in work-list order (the list held most of them), [9] listing allowed (host-set),
+// in work-list order (the lists held most of them: they are built again only every
+// kProbe-th launch, to see whether they still do), 3 every item in work-list order,
+// building the lists (after a prime pass, whose lists hold every item: only one state
+// buffer is valid then), [9] listing allowed (host-set),
 // [10] / [11] (one 64-bit word) tickets accounted (items finished plus tickets skipped)
 // / items finished in this launch, [12] items the previous launch finished.
 // early: 2 x n_items, per stamp parity the listed items (front part from index 0 up,
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
   // compute warps see it after their first wait): stamp, listing allowed, part bounds
   // P1 <= P2 <= P3 <= tickets, whether the lists were taken; the tickets this CTA's copy
   // warp skipped (written before its end marker)
-  __shared__ int s_stamp, s_listed_ok, s_p1, s_p2, s_p3, s_tickets, s_lists, s_skip;
+  __shared__ int s_stamp, s_listed_ok, s_order, s_p1, s_p2, s_p3, s_tickets, s_lists, s_skip;
   // the compute warps' listings (item * 2 + front), flushed to the next launch's list in
   // bulk (one round of atomics for many tiles, off the tiles' critical path); FP64 has
   // less shared memory to spare (two CTAs of its layout fill an SM)
@@ -391,6 +394,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
   __shared__ int s_nlst;
   __shared__ int s_fin;  // the finalizes a tile's CTA runs (bit 0 boundary, bit 1 inflow)
   __shared__ __align__(16) PipeItem s_pa;  // the copy warp's next item to issue
+  __shared__ const T* s_src[SL::kNA + 1];  // its instance's state slices' sources (arrays, then g n^2)
   const SL L(static_cast<uint32_t>(g.ne4max), static_cast<uint32_t>(g.nh4max));
   const int tid = threadIdx.x;
   auto slot = [&](int k) { return smem + (k % S) * L.slot; };
@@ -453,7 +457,9 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
       const int nf = use_lists ? min(max(vs[4], 0), n_items - n_fix) : 0;
       const int nb = use_lists ? min(max(vs[7], 0), n_items - n_fix - nf) : 0;
       s_stamp = stamp;
-      s_listed_ok = vs[9];
+      // listing: allowed, and (every item taken in work-list order) only on a probe
+      s_listed_ok = vs[9] && !(mode == 2 && stamp % kProbe != kProbe - 1);  // (modes 2, 3: in work-list order)
+      s_order = SL::k64 && !vs[9];  // FP64 without skipping: list the tiles that stepped, to take them first
       s_p1 = n_fix;
       s_p2 = n_fix + nf;
       s_p3 = n_fix + nf + nb;
@@ -571,7 +577,13 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
       }
     };
     if (!b_pending) lookahead();
-    const T* src = pa.tile >= 0 ? slice_src<T>(pa, lane) : nullptr;
+    // the slice sources of a's instance (lane 3 + j reads array j's)
+    auto set_src = [&]() {
+      const T* p = slice_src<T>(pa, lane);
+      if (lane >= 3 && lane <= 3 + SL::kNA) s_src[lane - 3] = p;
+      __syncwarp();
+    };
+    if (pa.tile >= 0) set_src();
     int a_next = 0;      // next tile (in this CTA's order) whose groups are issued
     bool ended = false;  // the end marker has been issued
     long long idle0 = clock64();
@@ -583,8 +595,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
       if (!free_slot && lane == 0) free_slot = mbar_test(&mb_e[a_next % S], ((a_next - S) / S) & 1);
       if (__shfl_sync(0xffffffffu, free_slot, 0)) {
         if (pa.tile >= 0) {
-          issue_a<T>(L, slot(a_next), pa, idx_a & kIdx, src, &mb_a[a_next % S], lane);
-          if (!(withhold && a_next == 0)) issue_h<T>(L, slot(a_next), pa, src, hv_a, &mb_h[a_next % S], lane);
+          issue_a<T>(L, slot(a_next), pa, idx_a & kIdx, s_src, &mb_a[a_next % S], lane);
+          if (!(withhold && a_next == 0)) issue_h<T>(L, slot(a_next), pa, s_src, hv_a, &mb_h[a_next % S], lane);
           if (b_pending) {  // after an early item a
             b_pending = false;
             idx_b = next_idx();
@@ -613,7 +625,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
           __syncwarp();  // every lane is done with a
           if (lane < kWords) reinterpret_cast<unsigned*>(&s_pa)[lane] = wb;
           __syncwarp();
-          if (b_tile >= 0 && b_inst != a_inst) src = slice_src<T>(pa, lane);
+          if (b_tile >= 0 && b_inst != a_inst) set_src();
           idx_a = idx_b;
           load_halo<T>(pa, lane, hv_a);
           // the pending ticket becomes the next read; request a new ticket
@@ -1175,7 +1187,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
     // were not quiet, to take them first.
     const bool listed_ok = s_listed_ok != 0;
     if (!((inf.flags & kFixedFlags) != 0u || inf.item == 0) && tid == 0) {
-      if (listed_ok ? (!run || !quiet) : (SL::k64 && run && !quiet)) note(inf.item, run);
+      if (listed_ok ? (!run || !quiet) : (s_order && run && !quiet)) note(inf.item, run);
     }
     if (listed_ok && run && !quiet) {
       const int32_t* hg = reinterpret_cast<const int32_t*>(sb + RL::hidx(ne4));
@@ -1229,7 +1241,10 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
       volatile int* vs = sched;
       const int nf = vs[3], nb = vs[6], ok = vs[9], done = vs[11];
       // a list that holds most items: the next launch takes them all in work-list order
-      const bool dense = 4LL * (nf + nb) > 3LL * (n_items - g.n_fixed);
+      // (and without lists built in this launch, so does the next); after a prime pass,
+      // every item in work-list order, building the lists
+      const bool dense = 4LL * (nf + nb) > 3LL * (n_items - g.n_fixed) || (ok && !s_listed_ok);
+      const int next_mode = !ok ? 0 : (prime ? 3 : (dense ? 2 : 1));
       vs[3] = 0;
       vs[6] = 0;
       vs[10] = 0;
@@ -1237,7 +1252,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
       vs[12] = done;
       vs[4] = wrap ? 0 : nf;
       vs[7] = wrap ? 0 : nb;
-      vs[8] = wrap ? 0 : (ok ? (dense ? 2 : 1) : 0);
+      vs[8] = wrap ? 0 : next_mode;
       vs[2] = wrap ? 0 : stamp + 1;
       __threadfence();
     }
