@@ -386,7 +386,7 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
     clk = clocks.stop()
     e2e_steps = st.stats(volume=False)["steps"]
     e2e = {"value": n * e2e_steps * ws / wall, "unit": METRIC, "wall_s": wall, "steps": e2e_steps,
-           "h2d_bytes_per_step": 3 * 8 * n / e2e_steps, "d2h_bytes_per_step": 3 * 8 * n / e2e_steps,
+           "h2d_bytes_per_step": 3 * 8 * n / max(e2e_steps, 1), "d2h_bytes_per_step": 3 * 8 * n / max(e2e_steps, 1),
            "call": f"bm_state_upload + bm_run_until({args.t_end:g} s) + bm_state_download, pinned host arrays"}
 
     # accuracy leg: the first steps from t = 0 (compared with the oracle by the caller)

@@ -838,7 +838,6 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
     if (s_nlst > kLstCap / 2) flush();  // (every compute thread reads the count after the barrier)
 
     // phase F: edges
-    double bsum = 0.0;
     if (run && !prime && !quiet) {
       for (int k2 = tid; k2 < ne; k2 += kTile) {
         const uint32_t lr = sLR[k2];
@@ -907,7 +906,6 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
               }
               F2 = zero;
             }
-            if (R < 0) bsum += static_cast<double>(l * F0);
             f0 = l * F0;
             f1 = l * (GL * nx - F2 * ny);
             f2 = l * (GL * ny + F2 * nx);
@@ -955,7 +953,6 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
             Fs[L.ne4 + k2] = l * (GL * nx - F2 * ny);
             Fs[2 * L.ne4 + k2] = l * (GL * ny + F2 * nx);
             skip[k2] = 0;
-            bsum += static_cast<double>(l * q);
             if constexpr (kExtra) {
               if (a.ex_flux != nullptr)
                 a.ex_flux[static_cast<size_t>(tile) * static_cast<size_t>(a.ex_stride) + k2] = l * q;
@@ -1145,7 +1142,14 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
       const bool bnd = !prime && (inf.flags & 1u);
       const bool infl = (inf.flags & 2u) != 0u;
       if (bnd || infl) {
-        const double bs = (bnd && !quiet) ? block_sum<kTile>(bsum, red) : 0.0;
+        double bs = 0.0;
+        if (bnd && !quiet) {
+          // the boundary edges' l F_h (stored with the fluxes; walls 0), FP64, fixed order
+          double bsum = 0.0;
+          for (int k2 = tid; k2 < ne; k2 += kTile)
+            if ((static_cast<int32_t>(sLR[k2]) >> kLocBits) < 0) bsum += static_cast<double>(Fs[k2]);
+          bs = block_sum<kTile>(bsum, red);
+        }
         if (infl && !(bnd && !quiet)) nbar<kTile>();  // every thread's inflow weights are stored
         if (tid == 0) {
           if (bnd) a.part[inf.bidx].bflux = bs;
