@@ -105,6 +105,8 @@ def _lib():
         lib.orc_morpho_speeds.restype = C.c_int
         lib.orc_set_outflow.argtypes = [C.c_void_p, i64, P(d), P(d), d, d]
         lib.orc_set_outflow.restype = C.c_int
+        lib.orc_set_level.argtypes = [C.c_void_p, i64, P(d), P(d)]
+        lib.orc_set_level.restype = C.c_int
         lib.orc_boundary_discharge.argtypes = [C.c_void_p, P(d), d, P(d), P(d)]
         lib.orc_boundary_discharge.restype = None
         _libs["serial"] = lib
@@ -233,6 +235,18 @@ class Oracle:
         rc = _lib().orc_set_outflow(self._h, len(s_), _dp(s_), _dp(q_), float(weir_crest), float(weir_poleni))
         if rc != 0:
             raise OracleError(f"orc_set_outflow failed with code {rc}")
+
+    def set_level(self, t_pts, z_pts):
+        """The water surface elevation Z_b(t) of the water-level edges (tag 5),
+        piecewise linear through (t_pts, z_pts), constant beyond the ends; no points
+        turns them back into walls."""
+        t_ = np.ascontiguousarray(t_pts, dtype=np.float64)
+        z_ = np.ascontiguousarray(z_pts, dtype=np.float64)
+        if t_.shape != z_.shape:
+            raise OracleError("set_level: times and levels differ in length")
+        rc = _lib().orc_set_level(self._h, len(t_), _dp(t_), _dp(z_))
+        if rc != 0:
+            raise OracleError(f"orc_set_level failed with code {rc}")
 
     def boundary_discharge(self):
         """Per edge, the unit discharge entering through an inflow edge and the one

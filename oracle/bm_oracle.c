@@ -19,7 +19,8 @@
  *      flux (Toro 2001 ch. 10, named in the same subsection) in the edge frame,
  *      pre-balanced pressure correction 1/2 g h*^2 of each side.
  *   2. boundary edges: wall (mirror), transmissive (zero gradient), discharge
- *      inflow, and the outflows h-Q relation (rating curve) and weir (Poleni)
+ *      inflow, the outflows h-Q relation (rating curve) and weir (Poleni), and the
+ *      water level (zhydrograph: a boundary state under an imposed surface)
  *      (Section "Boundary conditions": standard inflow / outflow / wall).
  *   3. conservative update, Eq. 12.
  *   4. Manning friction (Eq. 2, Table 1) split off and integrated with a
@@ -79,6 +80,12 @@ typedef struct {
   int64_t hq_n;
   double *hq_s, *hq_q;
   double weir_crest, weir_mu;
+  /* water-level boundary (zhydrograph, tag 5; orc_set_level): the water surface
+   * elevation Z_b(t), piecewise linear through (zh_t[k], zh_v[k]), constant beyond the
+   * ends (zh_n = 0: the level edges are walls); zh_now = Z_b at the current step */
+  int64_t zh_n;
+  double *zh_t, *zh_v;
+  double zh_now;
   double *qout;
   orc_params p;
   double *ht, *hq;
@@ -119,7 +126,7 @@ void orc_destroy(orc_mesh* m) {
   free(m->eL); free(m->eR); free(m->nx); free(m->ny); free(m->len);
   free(m->area); free(m->z); free(m->man); free(m->cedge);
   free(m->cL); free(m->cR); free(m->qin); free(m->ht); free(m->hq);
-  free(m->qout); free(m->hq_s); free(m->hq_q);
+  free(m->qout); free(m->hq_s); free(m->hq_q); free(m->zh_t); free(m->zh_v);
   free(m->src_reg); free(m->src_kind); free(m->src_mode); free(m->src_off);
   free(m->src_t); free(m->src_v); free(m->src_area); free(m->src_rate);
   free(m->qbx); free(m->qby); free(m->qbd); free(m->fb);
@@ -132,7 +139,8 @@ void orc_destroy(orc_mesh* m) {
  * cell.  Clockwise triangles are reoriented; their edge tags follow the edges.
  * edge_tag[3t+k] tags edge (v_k, v_{k+1}) of the triangle as given: 0 wall,
  * 1 transmissive, 2 inflow, 3 h-Q outflow, 4 weir outflow (their laws are set by
- * orc_set_outflow; until then they let nothing out).  Returns ORC_EINVAL on any
+ * orc_set_outflow; until then they let nothing out), 5 water level (zhydrograph; its
+ * series is set by orc_set_level, until then a wall).  Returns ORC_EINVAL on any
  * malformed input.
  */
 int orc_create(int64_t n_nodes, const double* xy, int64_t n_tri, const int32_t* tri,
@@ -231,7 +239,7 @@ int orc_create(int64_t n_nodes, const double* xy, int64_t n_tri, const int32_t* 
       m->cedge[3 * tr + kr] = e;
     } else {
       uint8_t tag = tg[3 * tl + kl];
-      if (tag > 4) rc = ORC_EINVAL;
+      if (tag > 5) rc = ORC_EINVAL;
       m->eR[e] = -1 - (int64_t)tag;
       if (tag == 2) m->inflow_len += l;
     }
@@ -386,7 +394,9 @@ static double inflow_weight(double l, double h, double h_min) {
 }
 
 /* inflow: unit discharge per inflow edge at time t, conveyance-weighted */
+static double level_at(const orc_mesh* m, double t);
 static void inflow_discharge(orc_mesh* m, const double* H, double t) {
+  if (m->zh_n > 0) m->zh_now = level_at(m, t);  /* the water level at t as well */
   double Q = orc_hydrograph(&m->p, t);
   double W = 0;
   for (int64_t e = 0; e < m->n_edges; ++e) {
@@ -540,6 +550,60 @@ void orc_boundary_discharge(orc_mesh* m, const double* H, double t, double* q_in
   memcpy(q_out, m->qout, m->n_edges * sizeof(double));
 }
 
+/*
+ * Water-level boundary (Section "Boundary conditions": zhydrograph, "water surface
+ * elevation" as input, among the standard inflows and outflows).  The paper gives no
+ * formula.  Reading: the edge's flux is the HLLC flux between the inside cell and a
+ * boundary state: depth h_b = max(0, Z_b(t^n) - z_i), the imposed surface over the
+ * inside cell's bed; normal velocity on the cell's outgoing characteristic, the
+ * Riemann invariant u_n + 2 sqrt(g h) carried from the cell, u_b = u_n + 2 sqrt(g h) -
+ * 2 sqrt(g h_b) (for h_b < h exactly the state the 1-rarefaction reaches from the
+ * cell); the cell's tangential velocity.  A dry inside cell carries no invariant: the
+ * boundary water is at rest there (u_b = 0), so the level floods the cell as a dam
+ * break.  Still water at the imposed level gives the cell's own state (no flux beyond
+ * its pressure).  Eq. 21 takes the boundary state's |u_b| + sqrt(g h_b) on the edge.
+ */
+static double level_at(const orc_mesh* m, double t) {
+  if (t <= m->zh_t[0]) return m->zh_v[0];
+  for (int64_t k = 1; k < m->zh_n; ++k)
+    if (t <= m->zh_t[k]) {
+      double w = (t - m->zh_t[k - 1]) / (m->zh_t[k] - m->zh_t[k - 1]);
+      return m->zh_v[k - 1] + w * (m->zh_v[k] - m->zh_v[k - 1]);
+    }
+  return m->zh_v[m->zh_n - 1];
+}
+
+/* the boundary state's depth and normal velocity of a level edge of cell i (depth h,
+ * outward normal velocity un) */
+static void level_state(const orc_mesh* m, int64_t i, double h, double un, double* hb, double* ub) {
+  const double g = m->p.g;
+  *hb = fmax(0.0, m->zh_now - m->z[i]);
+  *ub = h > m->p.h_min ? un + 2.0 * sqrt(g * h) - 2.0 * sqrt(g * *hb) : 0.0;
+}
+
+/* The water-level series of the level edges (tag 5): n >= 1 points (t strictly
+ * increasing, levels finite); n = 0 turns the edges back into walls.  ORC_EINVAL on
+ * malformed input. */
+int orc_set_level(orc_mesh* m, int64_t n, const double* t, const double* v) {
+  if (n < 0) return ORC_EINVAL;
+  for (int64_t k = 0; k < n; ++k) {
+    if (!isfinite(t[k]) || !isfinite(v[k])) return ORC_EINVAL;
+    if (k > 0 && !(t[k] > t[k - 1])) return ORC_EINVAL;
+  }
+  free(m->zh_t); free(m->zh_v);
+  m->zh_t = m->zh_v = NULL;
+  m->zh_n = 0;
+  if (n > 0) {
+    m->zh_t = (double*)malloc(n * sizeof(double));
+    m->zh_v = (double*)malloc(n * sizeof(double));
+    if (!m->zh_t || !m->zh_v) return ORC_ENOMEM;
+    memcpy(m->zh_t, t, n * sizeof(double));
+    memcpy(m->zh_v, v, n * sizeof(double));
+  }
+  m->zh_n = n;
+  return ORC_OK;
+}
+
 /* Eq. 21: dt = CFL * min_i min_j rho_ij / lambda_ij on wet cells (or, cfl_mode 1,
  * CFL * min_i |Omega_i| / sum_j l_ij lambda_ij); inflow and outflow edges add their
  * own boundary wave speed.  Returns +inf if nothing constrains dt.  Requires qin and
@@ -567,6 +631,21 @@ double orc_cfl(const orc_mesh* m, const double* H, const double* qx, const doubl
         } else {
           double r = m->area[i] / (m->len[e] * lb);
           if (r < best) best = r;
+        }
+      }
+      if (m->eR[e] == -6 && m->zh_n > 0) {
+        /* water-level edge: the boundary state's |u_b| + sqrt(g h_b) */
+        double hb, ub;
+        level_state(m, i, h > 0 ? h : 0.0, u * nx + w * ny, &hb, &ub);
+        double lb = fabs(ub) + sqrt(g * hb);
+        if (lb > 0) {
+          if (m->p.cfl_mode == 0) {
+            double rho = 4.0 * m->area[i] / (3.0 * m->len[e]);
+            if (rho / lb < best) best = rho / lb;
+          } else {
+            double r = m->area[i] / (m->len[e] * lb);
+            if (r < best) best = r;
+          }
         }
       }
       if ((m->eR[e] == -4 || m->eR[e] == -5) && m->qout[e] > 0) {
@@ -794,13 +873,18 @@ double orc_step(orc_mesh* m, double* H, double* qx, double* qy, double* t, doubl
       double p = 0.5 * g * hs * hs;
       double Fh, Gn, Ft;
       /* an outflow edge (h-Q, weir) lets q_e leave through its boundary state */
-      double qo = R <= -4 ? m->qout[e] : 0.0;
+      double qo = (R == -4 || R == -5) ? m->qout[e] : 0.0;
       double hbo = qo > 0 ? outflow_state(hs, unL, g, &qo) : -1.0;
-      if (R == -1 || (R <= -4 && !(hbo > 0))) {
+      if (R == -1 || ((R == -4 || R == -5) && !(hbo > 0)) || (R == -6 && m->zh_n == 0)) {
         /* wall: mirrored normal velocity, impermeable (also an outflow edge that lets
          * nothing out) */
         orc_hllc(hs, unL, utL, hs, -unL, utL, g, F);
         Fh = 0; Gn = F[1] - p; Ft = 0;
+      } else if (R == -6) { /* water level: HLLC with the boundary state */
+        double hb, ub;
+        level_state(m, L, hs, unL, &hb, &ub);
+        orc_hllc(hs, unL, utL, hb, ub, utL, g, F);
+        Fh = F[0]; Gn = F[1] - p; Ft = F[2];
       } else if (R == -2) { /* transmissive: the outside state equals the inside state */
         orc_hllc(hs, unL, utL, hs, unL, utL, g, F);
         Fh = F[0]; Gn = F[1] - p; Ft = F[2];
@@ -993,6 +1077,18 @@ int64_t orc_run_scalars(orc_mesh* m, double* H, double* qx, double* qy, double* 
         } else if (R == -3) {
           double q = m->qin[e];
           f = q > 0 ? -q * c_in[c] : 0.0;
+        } else if (R == -6) {
+          /* water level: the step's HLLC with the boundary state, upwinded at the contact;
+           * the water outside carries no species */
+          double hs = fmax(0.0, H[L] - m->z[L]), hb, ub;
+          if (m->zh_n > 0) {
+            m->zh_now = level_at(m, *t);
+            level_state(m, L, hs, unL, &hb, &ub);
+            orc_hllc(hs, unL, pL, hb, ub, 0.0, g, F);
+            f = F[2];
+          } else {
+            f = 0; /* a wall until its series is set */
+          }
         } else { /* outflow: the inside cell's scalar leaves with the edge's mass flux */
           double q = m->qout[e];
           double hs = fmax(0.0, H[L] - m->z[L]);

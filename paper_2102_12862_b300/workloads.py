@@ -18,7 +18,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-WALL, TRANSMISSIVE, INFLOW, HQ_OUTFLOW, WEIR = 0, 1, 2, 3, 4
+WALL, TRANSMISSIVE, INFLOW, HQ_OUTFLOW, WEIR, WATER_LEVEL = 0, 1, 2, 3, 4, 5
 
 
 @dataclass

@@ -109,6 +109,15 @@ OUTFLOW_MUTANTS = [
      "double w = (S - m->hq_s[k - 1]) / (m->hq_s[k] - m->hq_s[0]);"),
 ]
 
+# water-level boundary, caught by tests/test_oracle_level.py
+LEVEL_MUTANTS = [
+    ("level_invariant_factor", "un + 2.0 * sqrt(g * h) - 2.0 * sqrt(g * *hb)", "un + sqrt(g * h) - sqrt(g * *hb)"),
+    ("level_invariant_sign", "un + 2.0 * sqrt(g * h) - 2.0 * sqrt(g * *hb)", "un - 2.0 * sqrt(g * h) + 2.0 * sqrt(g * *hb)"),
+    ("level_not_over_bed", "*hb = fmax(0.0, m->zh_now - m->z[i]);", "*hb = fmax(0.0, m->zh_now);"),
+    ("level_flux_of_cell_state", "orc_hllc(hs, unL, utL, hb, ub, utL, g, F);", "orc_hllc(hs, unL, utL, hs, unL, utL, g, F);"),
+    ("level_frozen_in_time", "m->zh_now = level_at(m, t);", "m->zh_now = level_at(m, 0.0);"),
+]
+
 FRICTION_MUTANTS = [
     ("chezy_constant", "return h > r ? 6.25 + log(h / r) : 6.25;", "return h > r ? 6.5 + log(h / r) : 6.25;"),
     ("bezzola_branch", "if (x > 2.0) return", "if (x > 1.0) return"),
@@ -125,9 +134,11 @@ FRICTION_MUTANTS = [
                          + [m + ("test_oracle_morpho.py",) for m in MORPHO_MUTANTS]
                          + [m + ("test_oracle_friction.py",) for m in FRICTION_MUTANTS]
                          + [m + ("test_oracle_inflow.py",) for m in INFLOW_MUTANTS]
-                         + [m + ("test_oracle_outflow.py",) for m in OUTFLOW_MUTANTS],
+                         + [m + ("test_oracle_outflow.py",) for m in OUTFLOW_MUTANTS]
+                         + [m + ("test_oracle_level.py",) for m in LEVEL_MUTANTS],
                          ids=[m[0] for m in MUTANTS + TRACK_MUTANTS + SCALAR_MUTANTS + SOURCE_MUTANTS
-                              + MORPHO_MUTANTS + FRICTION_MUTANTS + INFLOW_MUTANTS + OUTFLOW_MUTANTS])
+                              + MORPHO_MUTANTS + FRICTION_MUTANTS + INFLOW_MUTANTS + OUTFLOW_MUTANTS
+                              + LEVEL_MUTANTS])
 def test_pins_catch_mutant(name, orig, mut, pins, tmp_path):
     src = open(SRC).read()
     assert src.count(orig) == 1, f"mutation site for {name} not unique"
