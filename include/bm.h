@@ -94,10 +94,11 @@ const char* bm_last_error(void);
  *             tri[3t+(k+1)%3]) when it is on the boundary: 0 wall, 1 transmissive
  *             (zero gradient), 2 discharge inflow, 3 h-Q relation outflow, 4 weir
  *             outflow (the last two let nothing out until bm_state_set_outflow
- *             sets their laws).  Ignored on interior edges.
+ *             sets their laws), 5 water level (a wall until bm_state_set_level sets
+ *             its series).  Ignored on interior edges.
  * Errors: BM_EINVAL for n_tri < 1, indices out of range, area <= 0, an edge
  * shared by more than two triangles or traversed twice in one direction, a tag
- * outside {0,1,2,3,4} on a boundary edge, n < 0 or a non-finite input.
+ * outside {0,1,2,3,4,5} on a boundary edge, n < 0 or a non-finite input.
  * *out receives the handle (NULL on failure); free with bm_mesh_destroy.
  * Host work only: the mesh is copied to the device by the first state created on
  * it (and stays on that device), so this call needs no GPU.
@@ -288,6 +289,27 @@ bm_status bm_state_set_morpho(bm_state* s, int32_t on, double porosity, double s
  */
 bm_status bm_state_set_outflow(bm_state* s, const double* hq_stage, const double* hq_discharge, int64_t n_hq,
                                double weir_crest, double weir_poleni);
+
+/*
+ * The water-level series of the mesh's level edges (tag 5; Section "Boundary
+ * conditions": the zhydrograph of the standard inflows and outflows, whose input is
+ * the water surface elevation, and the appendix's parameter list).  The imposed
+ * surface Z_b(t) is piecewise linear through (t[k], z[k]), k < n, constant beyond its
+ * ends; n = 0 turns the level edges back into walls.  A level edge's flux is HLLC's
+ * between its cell (depth h, outward normal velocity u_n) and the boundary state of
+ * depth h_b = max(0, Z_b(t^n) - z_cell), normal velocity
+ * u_b = u_n + 2 sqrt(g h) - 2 sqrt(g h_b) (the cell's outgoing Riemann invariant; 0 next
+ * to a cell at or below h_min) and the cell's tangential velocity; that state's
+ * |u_b| + sqrt(g h_b) at Z_b(t^{n+1}) enters Eq. 21.  The condition fixes the state of
+ * subcritical flow; which boundary type suits the flow regime is the user's choice.
+ * Passive species leave with the cell's concentration and enter with none; bedload
+ * leaves as on a transmissive edge.  Times and levels finite, times strictly
+ * increasing, n <= 2^20 (BM_EINVAL otherwise; the arrays are copied).  Re-primes the
+ * state: the next step's dt follows the level; time and step count are kept.  Set it
+ * before bm_batch_create on a batch member (the batch reads the member's series);
+ * served requests (bm_submit) take none (their level edges are walls).  Blocks.
+ */
+bm_status bm_state_set_level(bm_state* s, const double* t, const double* z, int64_t n);
 bm_status bm_state_download_bed(bm_state* s, double* z);
 
 /*

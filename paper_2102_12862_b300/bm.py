@@ -92,6 +92,7 @@ SIGNATURES = {
     "bm_state_download_bed": (C.c_int, [_vp, _vp]),
     "bm_state_set_friction": (C.c_int, [_vp, C.c_int32, _vp]),
     "bm_state_set_outflow": (C.c_int, [_vp, _vp, _vp, _i64, _d, _d]),
+    "bm_state_set_level": (C.c_int, [_vp, _vp, _vp, _i64]),
     "bm_server_opts_default": (None, [_P(bm_server_opts)]),
     "bm_server_create": (C.c_int, [_P(bm_server_opts), _P(_vp)]),
     "bm_server_destroy": (None, [_vp]),
@@ -539,6 +540,17 @@ class State:
         _check(load_library().bm_state_set_outflow(self.handle, _dp(st) if len(st) else None,
                                                    _dp(dq) if len(dq) else None, len(st), float(weir_crest),
                                                    float(weir_poleni)))
+
+    def set_level(self, t=(), z=()):
+        """Water-level series of the level edges (tag 5): the imposed surface Z_b(t),
+        piecewise linear through (t[k], z[k]); empty: the edges are walls. See
+        bm_state_set_level."""
+        tt = np.ascontiguousarray(t, dtype=np.float64)
+        zz = np.ascontiguousarray(z, dtype=np.float64)
+        if tt.shape != zz.shape or tt.ndim != 1:
+            raise ValueError("set_level: t and z must be 1-D and of equal length")
+        _check(load_library().bm_state_set_level(self.handle, _dp(tt) if len(tt) else None,
+                                                 _dp(zz) if len(zz) else None, len(tt)))
 
     def download_bed(self) -> np.ndarray:
         """The bed elevation z (caller cell order)."""

@@ -237,7 +237,8 @@ void ensure_list(StepList* l, cudaStream_t st) {
 
 int state_extra_level(const bm_state* s) {
   const HostMesh& h = s->mesh->h;
-  const bool outflow = (h.n_hq > 0 && s->hq_n > 0) || (h.n_weir > 0 && s->weir_mu > 0.0);
+  const bool outflow =
+      (h.n_hq > 0 && s->hq_n > 0) || (h.n_weir > 0 && s->weir_mu > 0.0) || (h.n_level > 0 && s->zh_n > 0);
   if (s->n_src > 0 || s->fr_law != 0 || outflow) return 2;
   const bool trk = s->prec == BM_FP64 ? s->b64.trk_t.p != nullptr : s->b32.trk_t.p != nullptr;
   return (trk || s->n_species > 0) ? 1 : 0;
@@ -343,6 +344,7 @@ void launch_species(bm_state* s, cudaStream_t st) {
   a.ex_stride = static_cast<int>(R.ne4_max);
   a.n_species = s->n_species;
   a.n_inflow = static_cast<int>(s->mesh->h.n_inflow);
+  a.n_level0 = static_cast<int>(s->mesh->h.n_inflow + s->mesh->h.n_hq + s->mesh->h.n_weir);
   a.n_cells = static_cast<int>(s->mesh->h.n_cells);
   const int nloc = kTile + static_cast<int>(R.nh4_max);
   const size_t smem = (2 * static_cast<size_t>(nloc) + R.ne4_max) * sizeof(T);
@@ -528,6 +530,10 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
   d.datum = s->prec == BM_FP64 ? 0.0 : s->datum;
   d.weir_crest = static_cast<T>(s->weir_crest - d.datum);
   d.weir_k = static_cast<T>(2.0 / 3.0 * s->weir_mu * std::sqrt(2.0 * s->prm.g));
+  d.n_level = static_cast<int>(h.n_level);
+  d.zh_n = s->zh_n;
+  d.zh_t = s->zh_t.p;
+  d.zh_v = s->zh_v.p;
   d.n_cells = static_cast<int>(h.n_cells);
   d.n_tiles = static_cast<int>(h.n_tiles);
 }
@@ -1220,6 +1226,41 @@ bm_status bm_state_set_outflow(bm_state* s, const double* hq_stage, const double
   drop_graphs(s);
   s->last_list = nullptr;  // the state's features changed: the next launch takes every tile
   // the next step's dt and h-Q split follow the new laws: prime again (time unchanged)
+  launch_state(s, s->stream, 1);
+  BM_CUDA(cudaGetLastError());
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  return read_status(s);
+}
+
+bm_status bm_state_set_level(bm_state* s, const double* t, const double* z, int64_t n) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_set_level: state is NULL");
+  if (n < 0) return fail(BM_EINVAL, "bm_state_set_level: n must be >= 0");
+  if (n > 0 && (!t || !z)) return fail(BM_EINVAL, "bm_state_set_level: series is NULL");
+  if (n > (1 << 20)) return fail(BM_EINVAL, "bm_state_set_level: at most 2^20 points");
+  for (int64_t k = 0; k < n; ++k) {
+    if (!std::isfinite(t[k]) || !std::isfinite(z[k]))
+      return fail(BM_EINVAL, "bm_state_set_level: times and levels must be finite");
+    if (k > 0 && !(t[k] > t[k - 1])) return fail(BM_EINVAL, "bm_state_set_level: times must increase strictly");
+  }
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  std::vector<double> tt(t, t + n), zz(z, z + n);
+  cudaError_t e = s->zh_t.upload(tt);
+  if (e == cudaSuccess) e = s->zh_v.upload(zz);
+  if (e != cudaSuccess) return dev_fail(e, "bm_state_set_level");
+  s->zh_n = static_cast<int>(n);
+  state_desc_bytes(s, &s->hdesc);
+  BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
+  const int extra = state_extra_level(s);  // a level series: the full instantiation
+  if (extra != s->list.extra) {
+    s->list.extra = extra;
+    bm_status lst = list_occupancy(s->prec, &s->list);
+    if (lst != BM_OK) return lst;
+    s->grid = step_grid(s->list, s->ctas_per_sm);
+  }
+  drop_graphs(s);
+  s->last_list = nullptr;  // the state's features changed: the next launch takes every tile
+  // the next step's dt follows the level: prime again (time unchanged)
   launch_state(s, s->stream, 1);
   BM_CUDA(cudaGetLastError());
   BM_CUDA(cudaStreamSynchronize(s->stream));

@@ -22,12 +22,13 @@ constexpr int kMaxTileEdges = 3 * kTile;
 
 // Boundary codes stored in place of the right cell of an edge.  Edges with a boundary
 // law are listed -- the inflow edges first, then the h-Q outflow edges, then the weir
-// outflow edges -- and listed edge j is stored as kInflow - j.
+// outflow edges, then the water-level edges -- and listed edge j is stored as kInflow - j.
 constexpr int32_t kWall = -1;
 constexpr int32_t kTransmissive = -2;
 constexpr int32_t kInflow = -3;
 constexpr int32_t kHqTag = -4;    // h-Q and weir edges before they are listed (mesh
 constexpr int32_t kWeirTag = -5;  // preparation only)
+constexpr int32_t kLevelTag = -6; // water-level edges before they are listed
 
 // Set the thread-local error message and return the status.
 bm_status fail(bm_status st, const std::string& msg);
@@ -37,6 +38,7 @@ void clear_error();
 struct HostMesh {
   int64_t n_cells = 0, n_edges = 0, n_boundary = 0, n_inflow = 0;
   int64_t n_hq = 0, n_weir = 0;  // listed h-Q and weir outflow edges (after the inflow edges)
+  int64_t n_level = 0;           // listed water-level edges (after the weir edges)
   int64_t n_tiles = 0;
   // per cell, new numbering (padded to n_tiles * kTile with inert cells)
   std::vector<int32_t> perm;        // new -> caller index (n_cells entries)
@@ -46,7 +48,7 @@ struct HostMesh {
   std::vector<int64_t> eoff;
   std::vector<int32_t> eL, eR;      // left cell (new id), right cell (new id) or boundary code
   std::vector<double> enx, eny, elen;
-  // listed edges (inflow, h-Q, weir; one entry each): cell (new id), length, unit
+  // listed edges (inflow, h-Q, weir, level; one entry each): cell (new id), length, unit
   // normal (outward)
   std::vector<int32_t> in_cell;
   std::vector<double> in_len, in_nx, in_ny;
@@ -103,7 +105,7 @@ struct TileRecords {
   std::vector<uint32_t> ne_nh;       // edges | halo cells << 16
   std::vector<uint8_t> flags;        // bit 0: boundary edges that can carry mass (transmissive or
                                      // listed; walls do not count), bit 1: inflow edges, bit 3: h-Q
-                                     // edges, bit 4: weir edges
+                                     // edges, bit 4: weir edges, bit 5: water-level edges
   uint32_t ne4_max = 0, nh4_max = 0;
 };
 
@@ -155,7 +157,8 @@ struct PipeItem {
   uint32_t ne_nh;            // edges | halo cells << 16
   int32_t inst;              // instance index within the launch
   uint32_t flags;            // bit 0: the tile has boundary edges that can carry mass, bit 1:
-                             // inflow edges, bit 2: source cells, bit 3: h-Q edges, bit 4: weir edges
+                             // inflow edges, bit 2: source cells, bit 3: h-Q edges, bit 4: weir edges,
+                             // bit 5: water-level edges
   uint32_t bidx;             // boundary tiles: rank among the instance's boundary tiles
 };
 static_assert(sizeof(PipeItem) == 48, "PipeItem layout");
@@ -163,7 +166,7 @@ static_assert(sizeof(PipeItem) == 48, "PipeItem layout");
 // Work items every launch takes (the "fixed" items): those with any of these flags, and
 // item 0 of a work list.  The others are taken only when the previous launch listed
 // them (see step_pipe).  kFixedMark: their entries in the list marks.
-constexpr uint32_t kFixedFlags = 31u;
+constexpr uint32_t kFixedFlags = 63u;
 constexpr int kFixedMark = 0x7fffffff;
 // Launch stamps restart (with a full launch) before they reach this value (marks hold
 // 2 x stamp + 1 at most, below kFixedMark).

@@ -33,7 +33,7 @@ struct alignas(16) InstDesc {
   const T* z;
   const T* gn2;       // g n^2
   const T* inv_area;  // 1 / |Omega_i|
-  const int32_t* in_cell;  // listed edge j (inflow, h-Q, weir): its cell
+  const int32_t* in_cell;  // listed edge j (inflow, h-Q, weir, level): its cell
   const double* in_lia;    //                l_j / |Omega| of its cell
   const T* in_len;         //                its length
   const double* in_nx;     //                its outward unit normal
@@ -81,6 +81,12 @@ struct alignas(16) InstDesc {
   double datum;            // FP32-bulk: the surface and the bed are offsets from it
   T weir_crest;
   T weir_k;
+  // water-level edges: listed edges [n_inflow + n_hq + n_weir, + n_level).  The series
+  // of the imposed surface Z_b(t) (absolute; zh_n = 0: the edges are walls)
+  int n_level;
+  int zh_n;
+  const double* zh_t;
+  const double* zh_v;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -745,10 +751,76 @@ __device__ __noinline__ T weir_rate(const InstDesc<T>& a, const uint32_t* sLR, c
   for (int k = 0; k < 3; ++k) {
     const int e = idx[k];
     const int code = static_cast<int32_t>(sLR[e]) >> kLocBits;
-    if (code > kInflow || kInflow - code < a.n_inflow + a.n_hq) continue;
+    if (code > kInflow || kInflow - code < a.n_inflow + a.n_hq ||
+        kInflow - code >= a.n_inflow + a.n_hq + a.n_weir)
+      continue;
     T q = weir_discharge<T>(a, Hh, Hl, z, h, hmin);
     const T hb = q > T(0) ? outflow_state<T>(h, u * sNx[e] + v * sNy[e], g, q) : T(-1);
     if (hb > T(0)) r = fmax(r, (q / hb + sqrt(g * hb)) * sLn[e] * ia * (a.p.cfl_mode == 0 ? T(0.75) : T(1)));
+  }
+  return r;
+}
+
+// ------------------------------------------------------------------ water-level edges
+
+// The imposed water surface Z_b(t) of the level edges (Section "Boundary conditions",
+// the zhydrograph of the standard inflows and outflows): piecewise linear through
+// (zh_t, zh_v), constant beyond its ends (zh_n >= 1).
+template <typename T>
+__device__ __forceinline__ double level_at(const InstDesc<T>& a, double t) {
+  const int n = a.zh_n;
+  if (t <= a.zh_t[0]) return a.zh_v[0];
+  for (int k = 1; k < n; ++k)
+    if (t <= a.zh_t[k]) {
+      const double w = (t - a.zh_t[k - 1]) / (a.zh_t[k] - a.zh_t[k - 1]);
+      return a.zh_v[k - 1] + w * (a.zh_v[k] - a.zh_v[k - 1]);
+    }
+  return a.zh_v[n - 1];
+}
+
+// Z_b(t) as the state stores a surface: FP64 as is (lo = 0); FP32-bulk as the pair of
+// floats (hi, lo) of its offset from the datum, rounded the way an uploaded surface is,
+// so still water at the imposed level has exactly the boundary's depth.
+template <typename T>
+__device__ __forceinline__ void level_pair(const InstDesc<T>& a, double t, T& hi, T& lo) {
+  const double v = level_at(a, t) - a.datum;
+  hi = static_cast<T>(v);
+  lo = static_cast<T>(v - static_cast<double>(hi));
+}
+
+// The boundary state of a level edge of a cell with bed z, depth h >= 0 and outward
+// normal velocity un: the imposed surface over the cell's bed, h_b = max(0, Z_b - z),
+// with the normal velocity that keeps the cell's outgoing Riemann invariant,
+// u_b = un + 2 sqrt(g h) - 2 sqrt(g h_b) (u_b = 0 next to a cell at or below h_min: the
+// boundary water floods it as a dam break); c_b = sqrt(g h_b).  The tangential
+// velocity is the cell's.
+template <typename T>
+__device__ __forceinline__ void level_state(T zh_hi, T zh_lo, T z, T h, T un, T g, T hmin, T& hb, T& ub, T& cb) {
+  hb = fmax(T(0), depth_of(zh_hi, zh_lo, z));
+  cb = sqrt(g * hb);
+  ub = h > hmin ? un + T(2) * sqrt(g * h) - T(2) * cb : T(0);
+}
+
+// The largest Eq. 21 rate of a cell's level edges at its new state (bed z, depth h,
+// velocity (u, v)) under the surface pair (zh_hi, zh_lo) of the new time: the boundary
+// state's |u_b| + sqrt(g h_b), times l / |Omega| (and 3/4 for Eq. 21's
+// rho = 4 |Omega| / (3 l)); dry cells count too (u_b = 0 there).
+template <typename T>
+__device__ __noinline__ T level_rate(const InstDesc<T>& a, const uint32_t* sLR, const T* sNx, const T* sNy,
+                                     const T* sLn, const int (&idx)[3], T zh_hi, T zh_lo, T z, T h, T u, T v,
+                                     T ia) {
+  const T g = static_cast<T>(a.p.g), hmin = static_cast<T>(a.p.h_min);
+  const int j0 = a.n_inflow + a.n_hq + a.n_weir;
+  T r = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int e = idx[k];
+    const int code = static_cast<int32_t>(sLR[e]) >> kLocBits;
+    if (code > kInflow || kInflow - code < j0) continue;
+    T hb, ub, cb;
+    level_state<T>(zh_hi, zh_lo, z, fmax(T(0), h), u * sNx[e] + v * sNy[e], g, hmin, hb, ub, cb);
+    const T lb = fabs(ub) + cb;
+    if (lb > T(0)) r = fmax(r, lb * sLn[e] * ia * (a.p.cfl_mode == 0 ? T(0.75) : T(1)));
   }
   return r;
 }

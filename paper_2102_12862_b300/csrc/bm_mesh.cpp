@@ -128,8 +128,8 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
       gr.push_back(tR);
     } else {
       uint8_t tt = tg[tkL];
-      if (tt > 4) return fail(BM_EINVAL, "bm_mesh_create: boundary edge tag outside {0,1,2,3,4}");
-      static const int32_t kOfTag[5] = {kWall, kTransmissive, kInflow, kHqTag, kWeirTag};
+      if (tt > 5) return fail(BM_EINVAL, "bm_mesh_create: boundary edge tag outside {0,1,2,3,4,5}");
+      static const int32_t kOfTag[6] = {kWall, kTransmissive, kInflow, kHqTag, kWeirTag, kLevelTag};
       gr.push_back(kOfTag[tt]);
     }
     i = j;
@@ -179,8 +179,8 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
     m.z_min = std::min(m.z_min, z[t]);
   }
 
-  // 4. boundary lists: the inflow, then the h-Q, then the weir edges; listed edge j is
-  // coded kInflow - j
+  // 4. boundary lists: the inflow, then the h-Q, then the weir, then the water-level
+  // edges; listed edge j is coded kInflow - j
   std::vector<int32_t> code(E);
   for (int64_t e = 0; e < E; ++e) {
     if (gr[e] >= 0) {
@@ -190,7 +190,7 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
       code[e] = static_cast<int32_t>(gr[e]);
     }
   }
-  for (int32_t kind : {kInflow, kHqTag, kWeirTag}) {
+  for (int32_t kind : {kInflow, kHqTag, kWeirTag, kLevelTag}) {
     for (int64_t e = 0; e < E; ++e) {
       if (gr[e] != kind) continue;
       code[e] = kInflow - static_cast<int32_t>(m.in_cell.size());
@@ -203,8 +203,10 @@ bm_status prepare_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, in
         ++m.n_inflow;
       } else if (kind == kHqTag) {
         ++m.n_hq;
-      } else {
+      } else if (kind == kWeirTag) {
         ++m.n_weir;
+      } else {
+        ++m.n_level;
       }
     }
   }
@@ -307,7 +309,10 @@ bm_status build_records_t(const HostMesh& m, TileRecords* out) {
         R = gR;
         const int64_t j = kInflow - gR;  // listed edge (j >= 0) or a wall / transmissive code
         if (gR != kWall)  // walls carry no mass: a tile of walls only is an interior tile
-          r.flags[tile] |= j < 0 ? 1 : (j < m.n_inflow ? 3 : (j < m.n_inflow + m.n_hq ? 9 : 17));
+          r.flags[tile] |= j < 0 ? 1
+                                 : (j < m.n_inflow ? 3
+                                                   : (j < m.n_inflow + m.n_hq ? 9
+                                                                              : (j < m.n_inflow + m.n_hq + m.n_weir ? 17 : 33)));
       }
       lr[k] = local(m.eL[e]) | (static_cast<uint32_t>(R) << kLocBits);
       put<uint32_t>(r.data, at + RL::lr() + 4 * k, lr[k]);

@@ -9,7 +9,8 @@
 // upwind side; this kernel, launched after each step, applies
 //   q_c^{n+1} = q_c^n - dt / |Omega| sum_j (+-) l F_h phi_c,upwind
 // with phi_c = q_c / h on U^n (0 where h <= 0), the inflow concentration on inflow
-// edges, nothing through walls, and q_c = 0 in a cell that ends the step dry.
+// edges, none from outside through water-level edges, nothing through walls, and
+// q_c = 0 in a cell that ends the step dry.
 #pragma once
 
 #include "bm_kernels.cuh"
@@ -35,6 +36,7 @@ struct SpeciesArgs {
   int n_species;
   int n_cells;
   int n_inflow;                   // listed edges below n_inflow are inflow edges (outflow above)
+  int n_level0;                   // listed edges from n_level0 on are water-level edges
 };
 
 // One CTA per work item (a 256-cell tile).  Dynamic shared memory: (2 nloc_max +
@@ -107,6 +109,9 @@ __global__ void __launch_bounds__(kTile) species_step(const SpeciesArgs<T> a, in
           const int R = static_cast<int32_t>(w) >> kLocBits;
           if (R <= kInflow && kInflow - R < a.n_inflow) {
             f = fh * a.c_in[c];  // the inflow brings its concentration
+          } else if (R <= kInflow && kInflow - R >= a.n_level0) {
+            // a water-level edge: the contact's upwind side, the water outside carrying none
+            f = a.ex_right[o] ? T(0) : fh * ph[lL];
           } else {  // an outflow edge takes the inside cell's
             const int lR = R >= 0 ? R : lL;  // transmissive: the outside equals the inside
             f = fh * (a.ex_right[o] ? ph[lR] : ph[lL]);

@@ -213,6 +213,10 @@ struct bm_state {
   bm::DBuf<double> hq_s, hq_q;
   int hq_n = 0;
   double weir_crest = 0.0, weir_mu = 0.0;
+  // the water-level series of the level edges (bm_state_set_level): times, absolute
+  // surface elevations; zh_n = 0: the level edges are walls
+  bm::DBuf<double> zh_t, zh_v;
+  int zh_n = 0;
   int n_species = 0;                    // passive species carried (0: none)
   double c_in[bm::kMaxSpecies] = {};    // their concentration in the inflow
   template <typename T>

@@ -834,7 +834,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
         C[j] = c;
       }
     }
-    const bool quiet = nbar_and<kTile>(tq) && !prime && !(inf.flags & 6u);  // no inflow or source
+    // (no inflow or source; a level edge under a series may flood a dry tile)
+    const bool quiet = nbar_and<kTile>(tq) && !prime && !(inf.flags & 6u) && !(kFull && (inf.flags & 32u) && a.zh_n > 0);
     if (s_nlst > kLstCap / 2) flush();  // (every compute thread reads the count after the barrier)
 
     // phase F: edges
@@ -929,21 +930,48 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
           }
         }
       }
-      if (kFull && (inf.flags & 24u)) {
-        // outflow edges (h-Q relation, weir), walls above: where the law lets water out,
-        // the flux of the boundary state on the cell's outgoing characteristic that
-        // carries it (each thread revisits its own edges; states whose outflow laws let
-        // something out run the full instantiation)
+      if (kFull && (inf.flags & 56u)) {
+        // outflow edges (h-Q relation, weir) and water-level edges, walls above: where
+        // the law lets water out, the flux of the boundary state on the cell's outgoing
+        // characteristic that carries it; under a level series, HLLC between the cell
+        // and the level's boundary state (each thread revisits its own edges; states
+        // with such laws run the full instantiation)
+        const int j_level = a.n_inflow + a.n_hq + a.n_weir;
+        T zh_hi = zero, zh_lo = zero;  // Z_b(t^n)
+        if ((inf.flags & 32u) && a.zh_n > 0) level_pair<T>(a, cs.t, zh_hi, zh_lo);
         for (int k2 = tid; k2 < ne; k2 += kTile) {
           const uint32_t lr = sLR[k2];
           const int R = static_cast<int32_t>(lr) >> kLocBits;
           const int lL = static_cast<int>(lr & (kMaxLocal - 1));
-          if (R > kInflow || kInflow - R < a.n_inflow || dry[lL]) continue;
+          if (R > kInflow || kInflow - R < a.n_inflow) continue;
           const int j = kInflow - R;
           const T HLh = sH[lL], HLl = kPair ? sHl[lL] : zero, zL = sZ[lL];
           const T h1 = fmax(zero, depth_of(HLh, HLl, zL));
           const T nx = sNx[k2], ny = sNy[k2], l = sLn[k2];
           const T unL = U[lL] * nx + V[lL] * ny, utL = -U[lL] * ny + V[lL] * nx;
+          if (j >= j_level) {
+            if (a.zh_n == 0) continue;  // a wall until a series is set
+            T hb, ub, cb;
+            level_state<T>(zh_hi, zh_lo, zL, h1, unL, g, hmin, hb, ub, cb);
+            if (!(gt0(h1) || gt0(hb))) continue;  // dry on both sides: no flux
+            T F0, F1, F2, pL, pR;
+            bool right = false;
+            hllc<T>(h1, unL, utL, C[lL], hb, ub, utL, cb, hg, F0, F1, F2, pL, pR, right);
+            const T GL = F1 - pL;
+            Fs[k2] = l * F0;
+            Fs[L.ne4 + k2] = l * (GL * nx - F2 * ny);
+            Fs[2 * L.ne4 + k2] = l * (GL * ny + F2 * nx);
+            skip[k2] = 0;
+            if constexpr (kExtra) {
+              if (a.ex_flux != nullptr) {
+                const size_t o = static_cast<size_t>(tile) * static_cast<size_t>(a.ex_stride) + k2;
+                a.ex_flux[o] = l * F0;
+                a.ex_right[o] = right ? 1 : 0;
+              }
+            }
+            continue;
+          }
+          if (dry[lL]) continue;
           T q = j < a.n_inflow + a.n_hq ? a.in_pw[j] : weir_discharge<T>(a, HLh, HLl, zL, h1, hmin);
           const T hb = q > zero ? outflow_state<T>(h1, unL, g, q) : T(-1);
           if (hb > zero) {
@@ -995,6 +1023,16 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
         if constexpr (kPair) a.Hlo[dst][i] = Hl;
         a.qx[dst][i] = zero;
         a.qy[dst][i] = zero;
+        if constexpr (kFull) {
+          // a level edge's rate of Eq. 21 under the level of t^{n+1} (it may have risen
+          // above the bed)
+          if ((inf.flags & 32u) && a.zh_n > 0) {
+            T zh_hi, zh_lo;
+            level_pair<T>(a, prime ? cs.t : new_time(cs, 1), zh_hi, zh_lo);
+            rrun = fmax(rrun, level_rate<T>(a, sLR, sNx, sNy, sLn, idx, zh_hi, zh_lo, zi, depth_of(Hh, Hl, zi), zero,
+                                            zero, ia));
+          }
+        }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int code = static_cast<int32_t>(sLR[idx[q]]) >> kLocBits;
@@ -1124,6 +1162,13 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
           if (inf.flags & 16u) {
             cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
             rrun = fmax(rrun, weir_rate<T>(a, sLR, sNx, sNy, sLn, idx, Hh, Hl, zi, h, u, v, ia));
+          }
+          if ((inf.flags & 32u) && a.zh_n > 0) {
+            // level edges: the boundary state's rate under the level of t^{n+1}
+            cell_derived<T>(h, ux, uy, hmin, g, u, v, c);
+            T zh_hi, zh_lo;
+            level_pair<T>(a, prime ? cs.t : new_time(cs, 1), zh_hi, zh_lo);
+            rrun = fmax(rrun, level_rate<T>(a, sLR, sNx, sNy, sLn, idx, zh_hi, zh_lo, zi, h, u, v, ia));
           }
         }
       }

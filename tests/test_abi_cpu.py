@@ -51,7 +51,7 @@ def _mesh_args():
     (lambda a: a[1].__setitem__((0, 0), 10_000), "out of range"),
     (lambda a: a[1].__setitem__((0, 1), a[1][0, 0]), "degenerate"),
     (lambda a: a[4].fill(7), "tag"),
-    (lambda a: a[4].fill(5), "tag"),
+    (lambda a: a[4].fill(6), "tag"),
     (lambda a: a[3].__setitem__(0, -0.1), "n >= 0"),
     (lambda a: a[2].__setitem__(1, np.nan), "finite"),
     (lambda a: a[0].__setitem__((3, 0), np.inf), "non-finite"),
@@ -74,6 +74,16 @@ def test_mesh_lists_outflow_edges_after_the_inflow_edges():
     info = m.info
     assert info["n_inflow"] == 4  # the x = 0 side
     assert info["n_boundary"] == 4 + 4 + 20 + 20
+
+
+def test_mesh_takes_water_level_edges():
+    """Tag 5 (water level) is a listed boundary edge too, after the outflow edges."""
+    xy, tri, tag = W.rect_mesh(20, 4, 100.0, 20.0, jitter=0.1, seed=1,
+                               side_tags=(W.INFLOW, W.WATER_LEVEL, W.HQ_OUTFLOW, W.WALL))
+    N = len(tri)
+    m = bm.Mesh(xy, tri, np.zeros(N), np.zeros(N), tag)
+    assert m.info["n_inflow"] == 4
+    assert m.info["n_boundary"] == 4 + 4 + 20 + 20
 
 
 def test_mesh_rejects_non_manifold_and_flipped():
