@@ -67,6 +67,7 @@ FP64_FLOP_PER_WET_CELL = 321.4
 FP64_PEAK_TFLOPS = 1.2023  # 296 DFMA lanes per cycle (ncu peak) x 2 FLOP x 2.031 GHz
 HBM_FALLBACK_GBS = 6400.0
 T_WINDOWS = (0.0, 600.0, 1800.0, 3600.0)  # the floodplain run's sampled times [s]
+L2_FLUSH_STEPS = 50  # steps of the L2-flushed cross-check
 KERNEL_NAME = {"fp64": "step_pipe<double, 0>", "fp32": "step_pipe<float, 0>"}  # without flood tracking
 
 
@@ -101,6 +102,11 @@ def parse():
     return ap.parse_args()
 
 
+def len_tiles(mesh) -> int:
+    """The mesh's tiles of 256 cells."""
+    return int(mesh.info["n_tiles"])
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -122,15 +128,16 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(precision: str):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def ncu_profile(precision: str):
+    """The committed ncu summary of the step kernel on the floodplain (DRAM bytes per
+    tile a launch takes, FP64-pipe activity), if it was taken on the current kernel
+    source (else None)."""
     path = os.path.join(ROOT, "profiles", f"step_{precision}_floodplain_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("kernel_source_hash") == kernel_source_hash():
-            return float(d["dram_bytes_per_launch"])
+            return d
     except Exception:
         pass
     return None
@@ -339,6 +346,27 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
         windows.append(w)
     steps, total_ms = step_weighted(snaps, ms_list)
     ms_run = total_ms / steps  # the run's mean time per step (= mean launch duration: one launch a step)
+
+    # cross-check of the cache state: the first and last windows again with L2 flushed
+    # (a 256 MiB buffer written) before every timed step, each step timed alone
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flushed = []
+    for sn in (snaps[0], snaps[-1]) if len(snaps) > 1 else (snaps[0],):
+        st.upload(sn["H"], sn["qx"], sn["qy"], sn["t"])
+        st.step(args.warmup)
+        tot = 0.0
+        for _ in range(L2_FLUSH_STEPS):
+            flush_buf.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st.step_async(1)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        st.sync()
+        flushed.append({"t_s": sn["t"], "ms_per_step": tot / L2_FLUSH_STEPS, "steps": L2_FLUSH_STEPS})
+    del flush_buf
     value = n * ws / (ms_run / 1e3)
 
     # dominant kernel (the step kernel, the only one in the timed windows): algorithmic
@@ -349,8 +377,15 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
                 for a in range(len(snaps) - 1)) / max(steps, 1) if len(snaps) > 1 else snaps[0]["taken"]
     bytes_launch = BYTES_PER_CELL_UPDATE[prec] * n * taken
     layout_bytes = (LAYOUT_BYTES_PER_CELL[prec] * n + LAYOUT_BYTES_PER_EDGE[prec] * mesh.info["n_edges"]) * taken
+    prof = ncu_profile(prec)
+    # DRAM traffic per launch: ncu's bytes per tile taken (windows at t = 0 and the run's
+    # end, their mean) times the run's mean tiles per launch
+    traffic = (prof["dram_bytes_per_tile"] * taken * len_tiles(mesh)) if prof else None
     roof = {"bound": "hbm", "achieved": bytes_launch / (ms_run / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-            "frac": bytes_launch / (ms_run / 1e3) / 1e9 / hbm, "traffic": ncu_traffic(prec),
+            "frac": bytes_launch / (ms_run / 1e3) / 1e9 / hbm, "traffic": traffic,
+            "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {prof['dram_bytes_per_tile']:.0f} B "
+                               f"per tile taken (profiles/{prof['summary']}), x the run's mean tiles per launch")
+                              if prof else "no ncu summary of the current kernel source",
             "kernel": KERNEL_NAME[prec], "kernel_ms": ms_run,
             "algorithmic_bytes_per_launch": bytes_launch,
             "tiles_taken": taken,
@@ -365,9 +400,13 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
         flop = FP64_FLOP_PER_WET_CELL * n * wet_steps / max(steps, 1)  # per launch, run mean
         roof_fp64 = {"bound": "alu", "achieved": flop / (ms_run / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": flop / (ms_run / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                     "traffic": traffic,
+                     "kernel": KERNEL_NAME[prec], "kernel_ms": ms_run,
                      "flop_per_launch": flop,
-                     "flops": f"{FP64_FLOP_PER_WET_CELL} FP64 FLOP per wet cell-update",
-                     "peak_source": "ncu peak: 296 DFMA per cycle x 2 x 2.031 GHz"}
+                     "flops": f"{FP64_FLOP_PER_WET_CELL} FP64 FLOP (DADD + DMUL + 2 DFMA, counted by ncu) per wet "
+                              f"cell-update x the run's step-weighted wet cells",
+                     "fp64_pipe_active": prof.get("fp64_pipe_active") if prof else None,
+                     "peak_source": "296 DFMA lanes per cycle (ncu peak) x 2 FLOP x 2.031 GHz (max SM clock)"}
     else:
         roof_fp64 = None
 
@@ -394,6 +433,7 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
     st.step(args.e2e_steps)
     Hf, qxf, qyf, _ = st.download()
     out = {"value": value, "ms_per_step": ms_run, "steps_run": steps, "windows": windows, "roofline": roof,
+           "l2_flushed": flushed,
            "windows_desc": ", ".join(f"{sn['t']:g}" for sn in snaps),
            "roofline_fp64": roof_fp64, "e2e": e2e, "clocks": clk,
            "gpu_launches": args.steps * len(snaps)}
@@ -806,10 +846,16 @@ def main():
                                        f"{r['steps_run']} steps over their step-weighted time",
                            "cells": s.n_cells, "edges": mesh.info["n_edges"], "precision": main_p,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                           "l2": "working set > 126 MB L2, no flush", "sim_time_s": args.t_end,
+                           "l2": "inputs larger than L2 (state and tile records > 126 MB), no flush; the tiles a "
+                                 "launch takes stay partly in L2 between steps as in the run itself (l2_flushed: "
+                                 "the first and last windows with L2 flushed before every step)",
+                           "sim_time_s": args.t_end,
                            "oracle_check_steps": args.e2e_steps},
                 "windows": r["windows"], "at_t0": r["windows"][0],
-                "roofline": r["roofline"], "roofline_fp64_arith": r["roofline_fp64"],
+                # FP64 is bound by its FP64 arithmetic (B300: 2 lanes per SM and cycle), FP32-bulk
+                # by latency inside tiles; the HBM figure of both is reported beside
+                "roofline": r["roofline_fp64"] if main_p == "fp64" else r["roofline"],
+                "roofline_hbm": r["roofline"], "l2_flushed": r["l2_flushed"],
                 "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "cpu_baseline": cpu,
                 "accuracy_vs_oracle": acc.get(main_p)}
         for p in precs[1:]:
@@ -817,7 +863,7 @@ def main():
             key = "fp32_bulk" if p == "fp32" else p
             line[key] = {"value": q["value"], "unit": METRIC, "ms_per_step": q["ms_per_step"],
                          "dtype": "f32+f64" if p == "fp32" else "f64", "windows": q["windows"],
-                         "roofline": q["roofline"], "e2e": q["e2e"], "clocks": q["clocks"],
+                         "roofline": q["roofline"], "l2_flushed": q["l2_flushed"], "e2e": q["e2e"], "clocks": q["clocks"],
                          "gpu_launches": q["gpu_launches"], "accuracy_vs_oracle": acc.get(p)}
         if ens is not None:
             ens["vs_fp64_plain"] = ens["value"] / r["value"] if main_p == "fp64" else None
