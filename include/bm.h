@@ -375,25 +375,39 @@ bm_status bm_state_set_launch(bm_state* s, int ctas_per_sm);
  * The step kernel's schedule: the launch shape (as bm_state_set_launch) and the static
  * share of the work tickets, static_sixteenths / 16 of them handed to the CTAs in a
  * fixed round-robin (known a step ahead, no atomic), the rest from a launch-wide
- * counter (balancing uneven tiles); -1 = the precision's default (FP64 4/16, FP32-bulk
- * 10/16), at least two tickets per CTA are static.  Results do not depend on it (the
+ * counter (balancing uneven tiles); -1 = the precision's default (FP64 8/16, FP32-bulk
+ * 4/16), at least two tickets per CTA are static.  Results do not depend on it (the
  * reductions are order-free).  BM_EINVAL outside [-1, 16].  get returns both.
  */
 bm_status bm_state_set_schedule(bm_state* s, int ctas_per_sm, int static_sixteenths);
 bm_status bm_state_get_schedule(bm_state* s, int* ctas_per_sm, int* static_sixteenths);
 
 /*
- * Autotuner: time steps_per_trial steps for each schedule, in two rounds -- the launch
- * shapes (as many CTAs per SM as fit, and 1, 2, 3, 4 CTAs per SM; shapes giving the
- * same grid are timed once) at the current static share, then the static shares 0, 2,
- * ..., 16 sixteenths and the default at the best shape -- undo the trial steps (the
- * state is snapshotted in device memory and restored), keep the fastest schedule and
- * report its shape and time per step (bm_state_get_schedule gives the share).
- * Allocates a temporary device copy of the state.  Results do not depend on it.  The
- * step kernel's other shape parameters are fixed at compile time: 256-cell tiles of
- * one cell per thread (8 compute warps and 1 copy warp; the tile records are built
- * for that size) and 3 shared-memory slots (the size that lets 2 FP64 / 3 FP32 CTAs
- * share an SM).
+ * Tile slots of the step kernel's pipeline: how many 256-cell tiles a CTA's copy warp
+ * may stage in shared memory ahead of its compute warps (2, 3 or 4; default 3).  More
+ * slots hide more copy latency but take more shared memory, so fewer CTAs may fit an
+ * SM.  The plain step is compiled for each count; a state with optional features
+ * (tracking, species, sources, log-law friction, outflow or level laws) runs 3 slots
+ * whatever the setting, and get reports the count in force.  Results do not depend
+ * on it.  BM_EINVAL outside {2, 3, 4}, or when that layout does not fit the device's
+ * shared memory (the count in force is kept).  Chosen by the autotuner or by hand.
+ */
+bm_status bm_state_set_slots(bm_state* s, int slots);
+bm_status bm_state_get_slots(bm_state* s, int* slots);
+
+/*
+ * Autotuner: time steps_per_trial steps for each schedule, in two rounds -- for each
+ * tile-slot count (2, 3, 4 for the plain step, the count in force first; 3 only with
+ * optional features) the launch shapes (as many CTAs per SM as fit, and 1, 2, 3, 4 CTAs
+ * per SM; shapes giving the same grid are timed once) at the current static share,
+ * then the static shares 0, 2, ..., 16 sixteenths and the default at the best slots
+ * and shape -- undo the trial steps (the state is snapshotted in device memory and
+ * restored), keep the fastest schedule and report its shape and time per step
+ * (bm_state_get_schedule and bm_state_get_slots give the rest).  A schedule replaces
+ * the one in force only if it is 2 % faster.  Allocates a temporary device copy of the
+ * state.  Results do not depend on it.  The tile size is fixed at compile time:
+ * 256-cell tiles of one cell per thread (8 compute warps and 1 copy warp; the tile
+ * records are built for that size).
  */
 bm_status bm_state_autotune(bm_state* s, int steps_per_trial, int* best_ctas_per_sm, double* ms_per_step);
 
@@ -415,6 +429,8 @@ bm_status bm_batch_set_stream(bm_batch* b, void* cuda_stream);
 bm_status bm_batch_set_launch(bm_batch* b, int ctas_per_sm);
 bm_status bm_batch_set_schedule(bm_batch* b, int ctas_per_sm, int static_sixteenths);
 bm_status bm_batch_get_schedule(bm_batch* b, int* ctas_per_sm, int* static_sixteenths);
+bm_status bm_batch_set_slots(bm_batch* b, int slots);
+bm_status bm_batch_get_slots(bm_batch* b, int* slots);
 bm_status bm_batch_autotune(bm_batch* b, int steps_per_trial, int* best_ctas_per_sm, double* ms_per_step);
 /* Every member takes n_steps steps with its own dt (Eq. 21); blocks; returns the
  * first member's BM_ENONFINITE / BM_ENEGDEPTH if any. */

@@ -70,6 +70,10 @@ SIGNATURES = {
     "bm_state_get_schedule": (C.c_int, [_vp, _P(C.c_int), _P(C.c_int)]),
     "bm_batch_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
     "bm_batch_get_schedule": (C.c_int, [_vp, _P(C.c_int), _P(C.c_int)]),
+    "bm_state_set_slots": (C.c_int, [_vp, C.c_int]),
+    "bm_state_get_slots": (C.c_int, [_vp, _P(C.c_int)]),
+    "bm_batch_set_slots": (C.c_int, [_vp, C.c_int]),
+    "bm_batch_get_slots": (C.c_int, [_vp, _P(C.c_int)]),
     "bm_batch_create": (C.c_int, [_P(_vp), C.c_int32, _P(_vp)]),
     "bm_batch_destroy": (None, [_vp]),
     "bm_batch_info": (C.c_int, [_vp, _P(C.c_int32), _P(_i64), _P(_i64)]),
@@ -414,6 +418,26 @@ def bm_batch_get_schedule(batch: int) -> tuple[int, int]:
     return c.value, s.value
 
 
+def bm_state_set_slots(state: int, slots: int):
+    _check(load_library().bm_state_set_slots(state, int(slots)))
+
+
+def bm_state_get_slots(state: int) -> int:
+    k = C.c_int()
+    _check(load_library().bm_state_get_slots(state, C.byref(k)))
+    return k.value
+
+
+def bm_batch_set_slots(batch: int, slots: int):
+    _check(load_library().bm_batch_set_slots(batch, int(slots)))
+
+
+def bm_batch_get_slots(batch: int) -> int:
+    k = C.c_int()
+    _check(load_library().bm_batch_get_slots(batch, C.byref(k)))
+    return k.value
+
+
 def bm_batch_set_launch(batch: int, ctas_per_sm: int):
     _check(load_library().bm_batch_set_launch(batch, int(ctas_per_sm)))
 
@@ -597,6 +621,14 @@ class State:
         """(CTAs per SM, static share of the tickets in sixteenths; -1 = default)."""
         return bm_state_get_schedule(self.handle)
 
+    def set_slots(self, slots: int):
+        """Tile slots of the step kernel's pipeline (2, 3 or 4)."""
+        bm_state_set_slots(self.handle, slots)
+
+    def slots(self) -> int:
+        """The tile slots in force (3 while optional features are on)."""
+        return bm_state_get_slots(self.handle)
+
     def autotune(self, steps_per_trial: int = 20) -> tuple[int, float]:
         return bm_state_autotune(self.handle, steps_per_trial)
 
@@ -644,6 +676,12 @@ class Batch:
 
     def schedule(self) -> tuple[int, int]:
         return bm_batch_get_schedule(self.handle)
+
+    def set_slots(self, slots: int):
+        bm_batch_set_slots(self.handle, slots)
+
+    def slots(self) -> int:
+        return bm_batch_get_slots(self.handle)
 
     def autotune(self, steps_per_trial: int = 10) -> tuple[int, float]:
         return bm_batch_autotune(self.handle, steps_per_trial)

@@ -84,16 +84,22 @@ int step_smem_limit() {
     int dev = 0, optin = 48 * 1024;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, step_pipe<T, 0>);
-    const int l = optin - static_cast<int>(fa.sharedSizeBytes);
+    const auto kernels = {step_pipe<T, 0, 2>, step_pipe<T, 0, 3>, step_pipe<T, 0, 4>, step_pipe<T, 1, 3>,
+                          step_pipe<T, 2, 3>};
+    int stat = 0;  // the largest static shared memory of the instantiations
+    for (auto k : kernels) {
+      cudaFuncAttributes fa{};
+      cudaFuncGetAttributes(&fa, k);
+      stat = std::max(stat, static_cast<int>(fa.sharedSizeBytes));
+    }
+    const int l = optin - stat;
     bool ok = true;
-    for (auto k : {step_pipe<T, 0>, step_pipe<T, 1>, step_pipe<T, 2>})
+    for (auto k : kernels)
       ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, l) == cudaSuccess &&
            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
     if (!ok) {
       (void)cudaGetLastError();  // leave no sticky error behind; launches check the size
-      return 48 * 1024 - static_cast<int>(fa.sharedSizeBytes);
+      return 48 * 1024 - stat;
     }
     return l;
   }();
@@ -203,7 +209,6 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
   out->ne4 = ne4;
   out->nh4 = nh4;
   for (bm_state* m : members) m->last_list = nullptr;  // the first launch resets the list
-  out->smem = prec == BM_FP64 ? StepLayout<double>(ne4, nh4).total : StepLayout<float>(ne4, nh4).total;
   {
     // every bulk-copy destination in a slot must be 16-byte aligned
     const StepLayout<double> l64(ne4, nh4);
@@ -213,8 +218,6 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
     for (uint32_t o : offs)
       if (o % 16u != 0u) return fail(BM_EINVAL, "internal: step layout not 16-byte aligned");
   }
-  const int lim = prec == BM_FP64 ? step_smem_limit<double>() : step_smem_limit<float>();
-  if (out->smem > static_cast<size_t>(lim)) return fail(BM_EINVAL, "tile layout exceeds the device's shared memory");
   out->extra = 0;
   for (bm_state* m : members) out->extra = std::max(out->extra, state_extra_level(m));
   return list_occupancy(prec, out);
@@ -244,22 +247,49 @@ int state_extra_level(const bm_state* s) {
   return (trk || s->n_species > 0) ? 1 : 0;
 }
 
-// The step kernel of a feature level.
-template <typename T>
-auto step_kernel(int level) {
-  return level >= 2 ? step_pipe<T, 2> : (level == 1 ? step_pipe<T, 1> : step_pipe<T, 0>);
+// The tile slots a list's step kernel runs with: the count asked for at the plain
+// level, 3 at the optional-feature levels (built for that count only).
+int list_slots(const StepList& l) { return l.extra == 0 ? l.slots : 3; }
+
+// The slot counts the autotuner tries for a list: the one in force first.
+std::vector<int> slot_candidates(const StepList& l) {
+  std::vector<int> k{list_slots(l)};
+  if (l.extra == 0)
+    for (int c : {2, 3, 4})
+      if (c != k[0]) k.push_back(c);
+  return k;
 }
 
-// Resident CTAs per SM of the list's kernel (with or without tracking).
+// The step kernel of a feature level and slot count.
+template <typename T>
+auto step_kernel(int level, int slots) {
+  if (level >= 2) return step_pipe<T, 2, 3>;
+  if (level == 1) return step_pipe<T, 1, 3>;
+  return slots == 2 ? step_pipe<T, 0, 2> : (slots == 4 ? step_pipe<T, 0, 4> : step_pipe<T, 0, 3>);
+}
+
+template <typename T>
+size_t step_smem(const StepList& l) {
+  const int k = list_slots(l);
+  if (k == 2) return StepLayout<T, 2>(l.ne4, l.nh4).total;
+  if (k == 4) return StepLayout<T, 4>(l.ne4, l.nh4).total;
+  return StepLayout<T, 3>(l.ne4, l.nh4).total;
+}
+
+// The list's shared memory per CTA (its largest tile layout at its slot count) and
+// resident CTAs per SM of its kernel.
 bm_status list_occupancy(int prec, StepList* l) {
+  l->smem = prec == BM_FP64 ? step_smem<double>(*l) : step_smem<float>(*l);
+  const int lim = prec == BM_FP64 ? step_smem_limit<double>() : step_smem_limit<float>();
+  if (l->smem > static_cast<size_t>(lim)) return fail(BM_EINVAL, "tile layout exceeds the device's shared memory");
   int occ = 0;
   cudaError_t e;
   if (prec == BM_FP64)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, step_kernel<double>(l->extra), kStepThreads, l->smem);
+        &occ, step_kernel<double>(l->extra, list_slots(*l)), kStepThreads, l->smem);
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, step_kernel<float>(l->extra), kStepThreads, l->smem);
+        &occ, step_kernel<float>(l->extra, list_slots(*l)), kStepThreads, l->smem);
   if (e != cudaSuccess) return dev_fail(e, "occupancy query");
   l->occupancy = std::max(1, occ);
   return BM_OK;
@@ -303,9 +333,9 @@ void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t 
   a.ne4max = static_cast<int>(l.ne4);
   a.nh4max = static_cast<int>(l.nh4);
   if (prec == BM_FP64)
-    (void)cudaLaunchKernelEx(&cfg, step_kernel<double>(l.extra), a, prime, withhold, l.static16);
+    (void)cudaLaunchKernelEx(&cfg, step_kernel<double>(l.extra, list_slots(l)), a, prime, withhold, l.static16);
   else
-    (void)cudaLaunchKernelEx(&cfg, step_kernel<float>(l.extra), a, prime, withhold, l.static16);
+    (void)cudaLaunchKernelEx(&cfg, step_kernel<float>(l.extra, list_slots(l)), a, prime, withhold, l.static16);
 }
 
 namespace {
@@ -828,6 +858,32 @@ bm_status bm_state_set_schedule(bm_state* s, int ctas_per_sm, int static_sixteen
     s->list.static16 = static_sixteenths;
   }
   return bm_state_set_launch(s, ctas_per_sm);
+}
+
+bm_status bm_state_set_slots(bm_state* s, int slots) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_set_slots: state is NULL");
+  if (slots < 2 || slots > 4) return fail(BM_EINVAL, "bm_state_set_slots: slots in {2, 3, 4}");
+  if (slots == s->list.slots) return BM_OK;
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  const int keep = s->list.slots;
+  s->list.slots = slots;
+  bm_status st = list_occupancy(s->prec, &s->list);
+  if (st != BM_OK) {  // (the layout does not fit: keep the previous count)
+    s->list.slots = keep;
+    (void)list_occupancy(s->prec, &s->list);
+    return st;
+  }
+  drop_graphs(s);  // the captured launches carry the old kernel
+  s->grid = step_grid(s->list, s->ctas_per_sm);
+  return BM_OK;
+}
+
+bm_status bm_state_get_slots(bm_state* s, int* slots) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_get_slots: state is NULL");
+  if (slots) *slots = list_slots(s->list);
+  return BM_OK;
 }
 
 bm_status bm_state_get_schedule(bm_state* s, int* ctas_per_sm, int* static_sixteenths) {
@@ -1520,16 +1576,18 @@ cudaError_t snapshot_state(bm_state* s, Snapshot* sn, cudaStream_t st) {
 }  // namespace
 
 // Time `steps` steps for each candidate launch schedule, restore the state(s), pick
-// the fastest.  Two rounds: the CTAs per SM -- the schedule in force first, then as
-// many as fit (0) and 1..4, candidates that give the same grid timed once -- at the
-// current static share of the tickets; then that share (sixteenths 0, 2, ..., 16 and
-// the precision's default) at the best CTAs per SM.  The schedule never changes results, so every trial restores the same
-// state and the choice is by time alone.
+// the fastest.  Two rounds: for each tile-slot count (the one in force first), the CTAs
+// per SM -- the count in force first, then as many as fit (0) and 1..4, candidates that
+// give the same grid timed once -- at the current static share of the tickets; then
+// that share (sixteenths 0, 2, ..., 16 and the precision's default) at the best slots
+// and CTAs per SM.  The schedule never changes results, so every trial restores the
+// same state and the choice is by time alone.
 bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_ctas, int start_static, int* best,
                          int* best_static,
                          double* best_ms, const std::function<bm_status(int, int)>& set_shape,
                          const std::function<int(int)>& grid_of,
-                         const std::function<bm_status(int)>& run_steps, cudaStream_t st) {
+                         const std::function<bm_status(int)>& run_steps, cudaStream_t st,
+                         const std::vector<int>& slot_cands, const std::function<bm_status(int)>& set_slots) {
   Snapshot sn;
   for (bm_state* s : states) {
     cudaError_t e = snapshot_state(s, &sn, st);
@@ -1540,7 +1598,8 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
   BM_CUDA(cudaEventCreate(&e0));
   BM_CUDA(cudaEventCreate(&e1));
   double bms = std::numeric_limits<double>::infinity();
-  int bc = 0, bs = start_static;
+  int bc = 0, bs = start_static, bk = slot_cands.empty() ? 3 : slot_cands[0];
+  int cur_k = bk;  // the slot count in force during a trial
   bm_status out = BM_OK;
   // a trial: the schedule, two warm steps (graph capture), then `steps` steps timed
   // twice (the state restored after each), the faster counts; a schedule replaces the
@@ -1569,18 +1628,29 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
       bms = tmin;
       bc = c;
       bs = s16;
+      bk = cur_k;
     }
     first = false;
     return BM_OK;
   };
-  std::vector<int> grids;
-  for (int c : {start_ctas, 0, 1, 2, 3, 4}) {
-    const int g = grid_of(c);
-    if (std::find(grids.begin(), grids.end(), g) != grids.end()) continue;
-    grids.push_back(g);
-    out = trial(c, start_static);
+  for (int k : slot_cands) {
     if (out != BM_OK) break;
+    if (set_slots(k) != BM_OK) {  // a layout that does not fit this device: skip the count
+      clear_error();
+      continue;
+    }
+    cur_k = k;
+    std::vector<int> grids;
+    for (int c : {start_ctas, 0, 1, 2, 3, 4}) {
+      const int g = grid_of(c);
+      if (std::find(grids.begin(), grids.end(), g) != grids.end()) continue;
+      grids.push_back(g);
+      out = trial(c, start_static);
+      if (out != BM_OK) break;
+    }
   }
+  if (out == BM_OK) out = set_slots(bk);
+  cur_k = bk;
   const int c_best = bc;
   for (int s16 = -1; s16 <= 16 && out == BM_OK; s16 += (s16 < 0 ? 1 : 2)) {
     if (s16 == start_static) continue;
@@ -1588,6 +1658,8 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (out != BM_OK) return out;
+  out = set_slots(bk);
   if (out != BM_OK) return out;
   out = set_shape(bc, bs);
   if (out != BM_OK) return out;
@@ -1614,7 +1686,8 @@ bm_status bm_state_autotune(bm_state* s, int steps_per_trial, int* best_ctas_per
   bm_status st = autotune_shape(
       {s}, steps_per_trial, s->ctas_per_sm, s->list.static16, best_ctas_per_sm, nullptr, ms_per_step,
       [&](int c, int s16) { return bm_state_set_schedule(s, c, s16); },
-      [&](int c) { return step_grid(s->list, c); }, [&](int n) { return enqueue_steps(s, n); }, s->stream);
+      [&](int c) { return step_grid(s->list, c); }, [&](int n) { return enqueue_steps(s, n); }, s->stream,
+      slot_candidates(s->list), [&](int k) { return bm_state_set_slots(s, k); });
   if (st == BM_OK && keep_end != kInf) st = set_end(s, keep_end);
   return st;
 }

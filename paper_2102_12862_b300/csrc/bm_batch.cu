@@ -51,7 +51,8 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
                          int* best_static,
                          double* best_ms, const std::function<bm_status(int, int)>& set_shape,
                          const std::function<int(int)>& grid_of,
-                         const std::function<bm_status(int)>& run_steps, cudaStream_t st);
+                         const std::function<bm_status(int)>& run_steps, cudaStream_t st,
+                         const std::vector<int>& slot_cands, const std::function<bm_status(int)>& set_slots);
 namespace {
 
 // Set every member's end time (+inf = plain stepping) from a device array.
@@ -128,6 +129,11 @@ bm_status use_active_members(bm_batch* b) {
   bm_status st = build_step_list(act, dptr, l.get());
   if (st != BM_OK) return st;
   l->static16 = b->list.static16;
+  if (b->list.slots != l->slots) {
+    l->slots = b->list.slots;
+    st = list_occupancy(b->prec, l.get());
+    if (st != BM_OK) return st;
+  }
   b->sub_grid = step_grid(*l, b->shape);
   b->sub = std::move(l);
   return BM_OK;
@@ -316,6 +322,34 @@ bm_status bm_batch_set_schedule(bm_batch* b, int ctas_per_sm, int static_sixteen
   return bm_batch_set_launch(b, ctas_per_sm);
 }
 
+bm_status bm_batch_set_slots(bm_batch* b, int slots) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_set_slots: batch is NULL");
+  if (slots < 2 || slots > 4) return fail(BM_EINVAL, "bm_batch_set_slots: slots in {2, 3, 4}");
+  if (slots == b->list.slots) return BM_OK;
+  BM_CUDA(cudaStreamSynchronize(b->stream));
+  const int keep = b->list.slots;
+  b->list.slots = slots;
+  bm_status st = list_occupancy(b->prec, &b->list);
+  if (st != BM_OK) {  // (the layout does not fit: keep the previous count)
+    b->list.slots = keep;
+    (void)list_occupancy(b->prec, &b->list);
+    return st;
+  }
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);  // they carry the old kernel
+  b->graphs.clear();
+  drop_sub(b);  // the run_until list is built again with the new count
+  b->grid = step_grid(b->list, b->shape);
+  return BM_OK;
+}
+
+bm_status bm_batch_get_slots(bm_batch* b, int* slots) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_get_slots: batch is NULL");
+  if (slots) *slots = list_slots(b->list);
+  return BM_OK;
+}
+
 bm_status bm_batch_get_schedule(bm_batch* b, int* ctas_per_sm, int* static_sixteenths) {
   clear_error();
   if (!b) return fail(BM_EINVAL, "bm_batch_get_schedule: batch is NULL");
@@ -413,7 +447,8 @@ bm_status bm_batch_autotune(bm_batch* b, int steps_per_trial, int* best_ctas_per
   bm_status st = autotune_shape(
       b->members, steps_per_trial, b->shape, b->list.static16, best_ctas_per_sm, nullptr, ms_per_step,
       [&](int c, int s16) { return bm_batch_set_schedule(b, c, s16); },
-      [&](int c) { return step_grid(b->list, c); }, [&](int n) { return batch_enqueue(b, n); }, b->stream);
+      [&](int c) { return step_grid(b->list, c); }, [&](int n) { return batch_enqueue(b, n); }, b->stream,
+      slot_candidates(b->list), [&](int k) { return bm_batch_set_slots(b, k); });
   if (st == BM_OK && finite) st = batch_set_end(b, keep.data());
   return st;
 }

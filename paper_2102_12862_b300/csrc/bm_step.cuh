@@ -150,11 +150,14 @@ struct StageInfo {
 };
 static_assert(sizeof(StageInfo) % 16 == 0, "the staged arrays after StageInfo take bulk copies (16-byte aligned)");
 
-template <typename T>
+// Shared-memory layout of a step CTA with kS tile slots (the copy warp stages up to kS
+// tiles ahead of the compute warps).
+template <typename T, int kS = 3>
 struct StepLayout {
   static constexpr bool k64 = sizeof(T) == 8;
   static constexpr int S = sizeof(T);
-  static constexpr int kSlots = 3;
+  static constexpr int kSlots = kS;
+  static_assert(kS >= 2 && kS <= 4, "2 to 4 slots");
   static constexpr int kNA = k64 ? 4 : 5;  // staged per-cell arrays
   // array order: FP64 H qx qy z; FP32-bulk H Hlo qx qy z
   static constexpr int kH = 0, kHl = 1, kQx = k64 ? 1 : 2, kQy = k64 ? 2 : 3, kZ = k64 ? 3 : 4;
@@ -217,10 +220,10 @@ __device__ __forceinline__ const T* slice_src(const PipeItem& it, int lane) {
 
 // Group A of a tile into a slot (all lanes of the copy warp; src = this lane's slice
 // source for the tile's instance).
-template <typename T>
-__device__ __forceinline__ void issue_a(const StepLayout<T>& L, unsigned char* sa, const PipeItem& it, int item,
+template <typename T, int kS>
+__device__ __forceinline__ void issue_a(const StepLayout<T, kS>& L, unsigned char* sa, const PipeItem& it, int item,
                                         const T* const* ssrc, uint64_t* mb, int lane) {
-  using SL = StepLayout<T>;
+  using SL = StepLayout<T, kS>;
   if (lane == 0) {
     StageInfo* inf = reinterpret_cast<StageInfo*>(sa + L.info);
     inf->tile = it.tile;
@@ -265,10 +268,10 @@ __device__ __forceinline__ void load_halo(const PipeItem& it, int lane, int (&hv
 // Group H of a tile (all lanes of the copy warp): the halo cells' values by cp.async,
 // each lane arriving on mb when its gathers have landed.  ssrc: the instance's slice
 // sources (shared memory, array j at j); hv: the prefetched halo indices.
-template <typename T>
-__device__ __forceinline__ void issue_h(const StepLayout<T>& L, unsigned char* sa, const PipeItem& it,
+template <typename T, int kS>
+__device__ __forceinline__ void issue_h(const StepLayout<T, kS>& L, unsigned char* sa, const PipeItem& it,
                                         const T* const* ssrc, const int (&hv)[kHaloPre], uint64_t* mb, int lane) {
-  using SL = StepLayout<T>;
+  using SL = StepLayout<T, kS>;
   const int nh = static_cast<int>(it.ne_nh >> 16);
   T* arr = reinterpret_cast<T*>(sa + L.arr);
 #pragma unroll
@@ -341,11 +344,10 @@ __global__ void list_reset(const PipeItem* items, int n_items, int* mark, int* s
 template <typename T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 3;
 // Share of a launch's tickets handed out statically: static16 / kStaticDen, by default
-// kStaticNum (FP64, with its wide spread of tile costs, leaves more to the counter);
-// the autotuner searches it.
+// kStaticNum; the autotuner searches it.
 constexpr int kStaticDen = 16;
 template <typename T>
-constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M floodplain
+constexpr int kStaticNum = sizeof(T) == 8 ? 8 : 4;  // measured over the 2M floodplain's run
 
 // One step (prime = 0) or prime pass (prime = 1: no update; derived data, inflow
 // weights and the dt of the current state) over a work list g.  Ticket t < F takes
@@ -362,13 +364,15 @@ constexpr int kStaticNum = sizeof(T) == 8 ? 4 : 10;  // measured on the 2M flood
 // the compute warps' bounded wait for it runs out; the launch then takes the timeout
 // path below (status bit 2, issued copies retired, no state written).  static16: the
 // static share of the tickets in sixteenths (negative: kStaticNum); the schedule never
-// changes results (the reductions are order-free).
-template <typename T, int kX>
+// changes results (the reductions are order-free).  kS: the tile slots in shared memory
+// (how far the copy warp may run ahead; the plain level is built for 2, 3 and 4 slots,
+// the others for 3).
+template <typename T, int kX, int kS = 3>
 __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const ListArgs g, int prime, int withhold,
                                                                          int static16) {
   constexpr bool kExtra = kX >= 1;  // tracking, species exports
   constexpr bool kFull = kX >= 2;   // sources, log-law friction
-  using SL = StepLayout<T>;
+  using SL = StepLayout<T, kS>;
   using RL = RecLayout<SL::S>;
   constexpr bool kPair = !SL::k64;
   constexpr int S = SL::kSlots;
