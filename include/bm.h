@@ -375,8 +375,9 @@ bm_status bm_state_set_launch(bm_state* s, int ctas_per_sm);
  * The step kernel's schedule: the launch shape (as bm_state_set_launch) and the static
  * share of the work tickets, static_sixteenths / 16 of them handed to the CTAs in a
  * fixed round-robin (known a step ahead, no atomic), the rest from a launch-wide
- * counter (balancing uneven tiles); -1 = the precision's default (FP64 8/16, FP32-bulk
- * 4/16), at least two tickets per CTA are static.  Results do not depend on it (the
+ * counter (balancing uneven tiles); -1 = the precision's default (FP64 0/16, FP32-bulk
+ * 4/16), at least one ticket per CTA is static (two when claiming ahead, see
+ * bm_state_set_claim).  Results do not depend on it (the
  * reductions are order-free).  BM_EINVAL outside [-1, 16].  get returns both.
  */
 bm_status bm_state_set_schedule(bm_state* s, int ctas_per_sm, int static_sixteenths);
@@ -384,7 +385,7 @@ bm_status bm_state_get_schedule(bm_state* s, int* ctas_per_sm, int* static_sixte
 
 /*
  * Tile slots of the step kernel's pipeline: how many 256-cell tiles a CTA's copy warp
- * may stage in shared memory ahead of its compute warps (2, 3 or 4; default 3).  More
+ * may stage in shared memory ahead of its compute warps (2, 3 or 4; default 2).  More
  * slots hide more copy latency but take more shared memory, so fewer CTAs may fit an
  * SM.  The plain step is compiled for each count; a state with optional features
  * (tracking, species, sources, log-law friction, outflow or level laws) runs 3 slots
@@ -396,14 +397,27 @@ bm_status bm_state_set_slots(bm_state* s, int slots);
 bm_status bm_state_get_slots(bm_state* s, int* slots);
 
 /*
- * Autotuner: time steps_per_trial steps for each schedule, in two rounds -- for each
- * tile-slot count (2, 3, 4 for the plain step, the count in force first; 3 only with
- * optional features) the launch shapes (as many CTAs per SM as fit, and 1, 2, 3, 4 CTAs
+ * How the step kernel's CTAs claim work items: 0 ahead (the copy warp reads the next
+ * items and requests the next tickets a step or two before it needs them, hiding their
+ * latency), 1 when a slot frees (a CTA commits to no more tiles than its slots hold,
+ * so the launch's last tiles are not queued behind long ones), -1 the default (1).
+ * With mode 1 a CTA's static tickets may be one.  Results do not depend on it.
+ * BM_EINVAL outside {-1, 0, 1}; get reports the mode in force.
+ */
+bm_status bm_state_set_claim(bm_state* s, int mode);
+bm_status bm_state_get_claim(bm_state* s, int* mode);
+
+/*
+ * Autotuner: time steps_per_trial steps (rounded up to whole graphs of 32 launches, as
+ * bm_step runs them) for each schedule, in two rounds -- for each
+ * claiming mode (bm_state_set_claim, the one in force first) and tile-slot count (2, 3,
+ * 4 for the plain step, the count in force first; 3 only with optional features) the
+ * launch shapes (as many CTAs per SM as fit, and 1, 2, 3, 4 CTAs
  * per SM; shapes giving the same grid are timed once) at the current static share,
  * then the static shares 0, 2, ..., 16 sixteenths and the default at the best slots
  * and shape -- undo the trial steps (the state is snapshotted in device memory and
  * restored), keep the fastest schedule and report its shape and time per step
- * (bm_state_get_schedule and bm_state_get_slots give the rest).  A schedule replaces
+ * (bm_state_get_schedule, bm_state_get_slots and bm_state_get_claim give the rest).  A schedule replaces
  * the one in force only if it is 2 % faster.  Allocates a temporary device copy of the
  * state.  Results do not depend on it.  The tile size is fixed at compile time:
  * 256-cell tiles of one cell per thread (8 compute warps and 1 copy warp; the tile
@@ -431,6 +445,8 @@ bm_status bm_batch_set_schedule(bm_batch* b, int ctas_per_sm, int static_sixteen
 bm_status bm_batch_get_schedule(bm_batch* b, int* ctas_per_sm, int* static_sixteenths);
 bm_status bm_batch_set_slots(bm_batch* b, int slots);
 bm_status bm_batch_get_slots(bm_batch* b, int* slots);
+bm_status bm_batch_set_claim(bm_batch* b, int mode);
+bm_status bm_batch_get_claim(bm_batch* b, int* mode);
 bm_status bm_batch_autotune(bm_batch* b, int steps_per_trial, int* best_ctas_per_sm, double* ms_per_step);
 /* Every member takes n_steps steps with its own dt (Eq. 21); blocks; returns the
  * first member's BM_ENONFINITE / BM_ENEGDEPTH if any. */

@@ -74,6 +74,10 @@ SIGNATURES = {
     "bm_state_get_slots": (C.c_int, [_vp, _P(C.c_int)]),
     "bm_batch_set_slots": (C.c_int, [_vp, C.c_int]),
     "bm_batch_get_slots": (C.c_int, [_vp, _P(C.c_int)]),
+    "bm_state_set_claim": (C.c_int, [_vp, C.c_int]),
+    "bm_state_get_claim": (C.c_int, [_vp, _P(C.c_int)]),
+    "bm_batch_set_claim": (C.c_int, [_vp, C.c_int]),
+    "bm_batch_get_claim": (C.c_int, [_vp, _P(C.c_int)]),
     "bm_batch_create": (C.c_int, [_P(_vp), C.c_int32, _P(_vp)]),
     "bm_batch_destroy": (None, [_vp]),
     "bm_batch_info": (C.c_int, [_vp, _P(C.c_int32), _P(_i64), _P(_i64)]),
@@ -438,6 +442,26 @@ def bm_batch_get_slots(batch: int) -> int:
     return k.value
 
 
+def bm_state_set_claim(state: int, mode: int):
+    _check(load_library().bm_state_set_claim(state, int(mode)))
+
+
+def bm_state_get_claim(state: int) -> int:
+    k = C.c_int()
+    _check(load_library().bm_state_get_claim(state, C.byref(k)))
+    return k.value
+
+
+def bm_batch_set_claim(batch: int, mode: int):
+    _check(load_library().bm_batch_set_claim(batch, int(mode)))
+
+
+def bm_batch_get_claim(batch: int) -> int:
+    k = C.c_int()
+    _check(load_library().bm_batch_get_claim(batch, C.byref(k)))
+    return k.value
+
+
 def bm_batch_set_launch(batch: int, ctas_per_sm: int):
     _check(load_library().bm_batch_set_launch(batch, int(ctas_per_sm)))
 
@@ -629,6 +653,13 @@ class State:
         """The tile slots in force (3 while optional features are on)."""
         return bm_state_get_slots(self.handle)
 
+    def set_claim(self, mode: int):
+        """Work-item claiming: 0 ahead, 1 when a slot frees, -1 the precision's default."""
+        bm_state_set_claim(self.handle, mode)
+
+    def claim(self) -> int:
+        return bm_state_get_claim(self.handle)
+
     def autotune(self, steps_per_trial: int = 20) -> tuple[int, float]:
         return bm_state_autotune(self.handle, steps_per_trial)
 
@@ -682,6 +713,12 @@ class Batch:
 
     def slots(self) -> int:
         return bm_batch_get_slots(self.handle)
+
+    def set_claim(self, mode: int):
+        bm_batch_set_claim(self.handle, mode)
+
+    def claim(self) -> int:
+        return bm_batch_get_claim(self.handle)
 
     def autotune(self, steps_per_trial: int = 10) -> tuple[int, float]:
         return bm_batch_autotune(self.handle, steps_per_trial)

@@ -247,9 +247,17 @@ int state_extra_level(const bm_state* s) {
   return (trk || s->n_species > 0) ? 1 : 0;
 }
 
-// The tile slots a list's step kernel runs with: the count asked for at the plain
-// level, 3 at the optional-feature levels (built for that count only).
-int list_slots(const StepList& l) { return l.extra == 0 ? l.slots : 3; }
+// The tile slots a list's step kernel runs with: the count asked for (by default 2,
+// measured with items claimed when a slot frees) at the plain level, 3 at the
+// optional-feature levels (built for that count only).
+constexpr int kDefaultSlots = 2;
+int list_slots(const StepList& l) { return l.extra == 0 ? (l.slots > 0 ? l.slots : kDefaultSlots) : 3; }
+
+// Work-item claiming of a list's launches: by default a CTA claims an item only when a
+// slot frees, so no CTA commits to tiles it reaches late while others run dry (the
+// launch's end is set by its last tile); measured faster than claiming ahead over the
+// floodplain run in both precisions.
+int list_claim(int, const StepList& l) { return l.claim >= 0 ? l.claim : 1; }
 
 // The slot counts the autotuner tries for a list: the one in force first.
 std::vector<int> slot_candidates(const StepList& l) {
@@ -332,6 +340,7 @@ void launch_work(int prec, const StepList& l, int grid, int prime, cudaStream_t 
   a.n_inst = static_cast<int>(l.members.size());
   a.ne4max = static_cast<int>(l.ne4);
   a.nh4max = static_cast<int>(l.nh4);
+  a.lazy = list_claim(prec, l);
   if (prec == BM_FP64)
     (void)cudaLaunchKernelEx(&cfg, step_kernel<double>(l.extra, list_slots(l)), a, prime, withhold, l.static16);
   else
@@ -864,7 +873,7 @@ bm_status bm_state_set_slots(bm_state* s, int slots) {
   clear_error();
   if (!s) return fail(BM_EINVAL, "bm_state_set_slots: state is NULL");
   if (slots < 2 || slots > 4) return fail(BM_EINVAL, "bm_state_set_slots: slots in {2, 3, 4}");
-  if (slots == s->list.slots) return BM_OK;
+  if (slots == list_slots(s->list) && s->list.slots > 0) return BM_OK;
   BM_CUDA(cudaStreamSynchronize(s->stream));
   const int keep = s->list.slots;
   s->list.slots = slots;
@@ -876,6 +885,24 @@ bm_status bm_state_set_slots(bm_state* s, int slots) {
   }
   drop_graphs(s);  // the captured launches carry the old kernel
   s->grid = step_grid(s->list, s->ctas_per_sm);
+  return BM_OK;
+}
+
+bm_status bm_state_set_claim(bm_state* s, int mode) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_set_claim: state is NULL");
+  if (mode < -1 || mode > 1) return fail(BM_EINVAL, "bm_state_set_claim: mode in {-1, 0, 1}");
+  if (mode == s->list.claim) return BM_OK;
+  BM_CUDA(cudaStreamSynchronize(s->stream));
+  drop_graphs(s);  // the captured launches carry the old mode
+  s->list.claim = mode;
+  return BM_OK;
+}
+
+bm_status bm_state_get_claim(bm_state* s, int* mode) {
+  clear_error();
+  if (!s) return fail(BM_EINVAL, "bm_state_get_claim: state is NULL");
+  if (mode) *mode = list_claim(s->prec, s->list);
   return BM_OK;
 }
 
@@ -1576,18 +1603,19 @@ cudaError_t snapshot_state(bm_state* s, Snapshot* sn, cudaStream_t st) {
 }  // namespace
 
 // Time `steps` steps for each candidate launch schedule, restore the state(s), pick
-// the fastest.  Two rounds: for each tile-slot count (the one in force first), the CTAs
-// per SM -- the count in force first, then as many as fit (0) and 1..4, candidates that
-// give the same grid timed once -- at the current static share of the tickets; then
-// that share (sixteenths 0, 2, ..., 16 and the precision's default) at the best slots
-// and CTAs per SM.  The schedule never changes results, so every trial restores the
+// the fastest.  Two rounds: for each claiming mode and tile-slot count (those in force
+// first), the CTAs per SM -- the count in force first, then as many as fit (0) and
+// 1..4, candidates that give the same grid timed once -- at the current static share
+// of the tickets; then that share (sixteenths 0, 2, ..., 16 and the precision's
+// default) at the best mode, slots and CTAs per SM.  The schedule never changes results, so every trial restores the
 // same state and the choice is by time alone.
 bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_ctas, int start_static, int* best,
                          int* best_static,
                          double* best_ms, const std::function<bm_status(int, int)>& set_shape,
                          const std::function<int(int)>& grid_of,
                          const std::function<bm_status(int)>& run_steps, cudaStream_t st,
-                         const std::vector<int>& slot_cands, const std::function<bm_status(int)>& set_slots) {
+                         const std::vector<int>& slot_cands, const std::function<bm_status(int)>& set_slots,
+                         int start_claim, const std::function<bm_status(int)>& set_claim) {
   Snapshot sn;
   for (bm_state* s : states) {
     cudaError_t e = snapshot_state(s, &sn, st);
@@ -1598,23 +1626,26 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
   BM_CUDA(cudaEventCreate(&e0));
   BM_CUDA(cudaEventCreate(&e1));
   double bms = std::numeric_limits<double>::infinity();
-  int bc = 0, bs = start_static, bk = slot_cands.empty() ? 3 : slot_cands[0];
-  int cur_k = bk;  // the slot count in force during a trial
+  int bc = 0, bs = start_static, bk = slot_cands.empty() ? 3 : slot_cands[0], bm = start_claim;
+  int cur_k = bk, cur_m = bm;  // the slot count and claiming in force during a trial
   bm_status out = BM_OK;
   // a trial: the schedule, two warm steps (graph capture), then `steps` steps timed
   // twice (the state restored after each), the faster counts; a schedule replaces the
   // best so far only if it is 2 % faster (the first trial, the schedule in force, is
   // kept unless another clearly beats it)
   bool first = true;
+  // trials time whole graphs of 32 launches (launches in one graph overlap each other's
+  // ends and starts; separate graph launches do not, which favours other shapes)
+  const int timed = (steps + 31) / 32 * 32;
   auto trial = [&](int c, int s16) -> bm_status {
     bm_status r = set_shape(c, s16);
     if (r != BM_OK) return r;
     float tmin = std::numeric_limits<float>::infinity();
     for (int rep = 0; rep < 2; ++rep) {
-      r = run_steps(2);
+      r = run_steps(rep == 0 ? 32 : 2);  // (the first captures the graphs)
       if (r != BM_OK) return r;
       cudaEventRecord(e0, st);
-      r = run_steps(steps);
+      r = run_steps(timed);
       if (r != BM_OK) return r;
       cudaEventRecord(e1, st);
       cudaEventSynchronize(e1);
@@ -1629,28 +1660,36 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
       bc = c;
       bs = s16;
       bk = cur_k;
+      bm = cur_m;
     }
     first = false;
     return BM_OK;
   };
-  for (int k : slot_cands) {
+  for (int m : {start_claim, 1 - start_claim}) {
     if (out != BM_OK) break;
-    if (set_slots(k) != BM_OK) {  // a layout that does not fit this device: skip the count
-      clear_error();
-      continue;
-    }
-    cur_k = k;
-    std::vector<int> grids;
-    for (int c : {start_ctas, 0, 1, 2, 3, 4}) {
-      const int g = grid_of(c);
-      if (std::find(grids.begin(), grids.end(), g) != grids.end()) continue;
-      grids.push_back(g);
-      out = trial(c, start_static);
+    out = set_claim(m);
+    cur_m = m;
+    for (int k : slot_cands) {
       if (out != BM_OK) break;
+      if (set_slots(k) != BM_OK) {  // a layout that does not fit this device: skip the count
+        clear_error();
+        continue;
+      }
+      cur_k = k;
+      std::vector<int> grids;
+      for (int c : {start_ctas, 0, 1, 2, 3, 4}) {
+        const int g = grid_of(c);
+        if (std::find(grids.begin(), grids.end(), g) != grids.end()) continue;
+        grids.push_back(g);
+        out = trial(c, start_static);
+        if (out != BM_OK) break;
+      }
     }
   }
+  if (out == BM_OK) out = set_claim(bm);
   if (out == BM_OK) out = set_slots(bk);
   cur_k = bk;
+  cur_m = bm;
   const int c_best = bc;
   for (int s16 = -1; s16 <= 16 && out == BM_OK; s16 += (s16 < 0 ? 1 : 2)) {
     if (s16 == start_static) continue;
@@ -1659,13 +1698,15 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (out != BM_OK) return out;
+  out = set_claim(bm);
+  if (out != BM_OK) return out;
   out = set_slots(bk);
   if (out != BM_OK) return out;
   out = set_shape(bc, bs);
   if (out != BM_OK) return out;
   if (best) *best = bc;
   if (best_static) *best_static = bs;
-  if (best_ms) *best_ms = bms / steps;
+  if (best_ms) *best_ms = bms / timed;
   return BM_OK;
 }
 
@@ -1687,7 +1728,8 @@ bm_status bm_state_autotune(bm_state* s, int steps_per_trial, int* best_ctas_per
       {s}, steps_per_trial, s->ctas_per_sm, s->list.static16, best_ctas_per_sm, nullptr, ms_per_step,
       [&](int c, int s16) { return bm_state_set_schedule(s, c, s16); },
       [&](int c) { return step_grid(s->list, c); }, [&](int n) { return enqueue_steps(s, n); }, s->stream,
-      slot_candidates(s->list), [&](int k) { return bm_state_set_slots(s, k); });
+      slot_candidates(s->list), [&](int k) { return bm_state_set_slots(s, k); }, list_claim(s->prec, s->list),
+      [&](int m) { return bm_state_set_claim(s, m); });
   if (st == BM_OK && keep_end != kInf) st = set_end(s, keep_end);
   return st;
 }

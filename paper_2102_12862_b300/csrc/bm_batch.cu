@@ -52,7 +52,8 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
                          double* best_ms, const std::function<bm_status(int, int)>& set_shape,
                          const std::function<int(int)>& grid_of,
                          const std::function<bm_status(int)>& run_steps, cudaStream_t st,
-                         const std::vector<int>& slot_cands, const std::function<bm_status(int)>& set_slots);
+                         const std::vector<int>& slot_cands, const std::function<bm_status(int)>& set_slots,
+                         int start_claim, const std::function<bm_status(int)>& set_claim);
 namespace {
 
 // Set every member's end time (+inf = plain stepping) from a device array.
@@ -129,6 +130,7 @@ bm_status use_active_members(bm_batch* b) {
   bm_status st = build_step_list(act, dptr, l.get());
   if (st != BM_OK) return st;
   l->static16 = b->list.static16;
+  l->claim = b->list.claim;
   if (b->list.slots != l->slots) {
     l->slots = b->list.slots;
     st = list_occupancy(b->prec, l.get());
@@ -326,7 +328,7 @@ bm_status bm_batch_set_slots(bm_batch* b, int slots) {
   clear_error();
   if (!b) return fail(BM_EINVAL, "bm_batch_set_slots: batch is NULL");
   if (slots < 2 || slots > 4) return fail(BM_EINVAL, "bm_batch_set_slots: slots in {2, 3, 4}");
-  if (slots == b->list.slots) return BM_OK;
+  if (slots == list_slots(b->list) && b->list.slots > 0) return BM_OK;
   BM_CUDA(cudaStreamSynchronize(b->stream));
   const int keep = b->list.slots;
   b->list.slots = slots;
@@ -340,6 +342,26 @@ bm_status bm_batch_set_slots(bm_batch* b, int slots) {
   b->graphs.clear();
   drop_sub(b);  // the run_until list is built again with the new count
   b->grid = step_grid(b->list, b->shape);
+  return BM_OK;
+}
+
+bm_status bm_batch_set_claim(bm_batch* b, int mode) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_set_claim: batch is NULL");
+  if (mode < -1 || mode > 1) return fail(BM_EINVAL, "bm_batch_set_claim: mode in {-1, 0, 1}");
+  if (mode == b->list.claim) return BM_OK;
+  BM_CUDA(cudaStreamSynchronize(b->stream));
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);  // they carry the old mode
+  b->graphs.clear();
+  drop_sub(b);
+  b->list.claim = mode;
+  return BM_OK;
+}
+
+bm_status bm_batch_get_claim(bm_batch* b, int* mode) {
+  clear_error();
+  if (!b) return fail(BM_EINVAL, "bm_batch_get_claim: batch is NULL");
+  if (mode) *mode = list_claim(b->prec, b->list);
   return BM_OK;
 }
 
@@ -448,7 +470,8 @@ bm_status bm_batch_autotune(bm_batch* b, int steps_per_trial, int* best_ctas_per
       b->members, steps_per_trial, b->shape, b->list.static16, best_ctas_per_sm, nullptr, ms_per_step,
       [&](int c, int s16) { return bm_batch_set_schedule(b, c, s16); },
       [&](int c) { return step_grid(b->list, c); }, [&](int n) { return batch_enqueue(b, n); }, b->stream,
-      slot_candidates(b->list), [&](int k) { return bm_batch_set_slots(b, k); });
+      slot_candidates(b->list), [&](int k) { return bm_batch_set_slots(b, k); }, list_claim(b->prec, b->list),
+      [&](int m) { return bm_batch_set_claim(b, m); });
   if (st == BM_OK && finite) st = batch_set_end(b, keep.data());
   return st;
 }

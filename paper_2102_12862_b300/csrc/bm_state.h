@@ -155,7 +155,9 @@ struct StepList {
   size_t smem = 0;
   int occupancy = 1;  // resident CTAs per SM at this shared-memory size
   int static16 = -1;  // static share of the tickets in sixteenths (-1: the precision's default)
-  int slots = 3;      // tile slots of the step kernel asked for (2, 3, 4; levels 1 and 2 run 3)
+  int slots = 0;      // tile slots of the step kernel asked for (2, 3, 4; 0 the default; levels
+                      // 1 and 2 run 3)
+  int claim = -1;     // work-item claiming: 0 ahead, 1 when a slot frees, -1 the default
   int extra = 0;  // the step kernel's feature level the members need (0 none; 1 tracking or
                  // species; 2 also sources or log-law friction)
 };
@@ -253,6 +255,7 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
 bm_status list_occupancy(int prec, StepList* l);
 // The tile slots a list's kernel runs with, and the counts the autotuner tries.
 int list_slots(const StepList& l);
+int list_claim(int prec, const StepList& l);
 std::vector<int> slot_candidates(const StepList& l);
 // The step kernel's feature level a state needs (see StepList::extra).
 int state_extra_level(const bm_state* s);

@@ -327,6 +327,7 @@ struct ListArgs {
   const int* inst_item;  // per instance: its first item
   int n_items, n_fixed, n_inst;
   int ne4max, nh4max;    // the largest record of the list (they fix the shared-memory layout)
+  int lazy;              // claim the next work item only when a slot frees (no lookahead)
 };
 
 // A work list's scheduling state for a full launch: counters zero, listing allowed or
@@ -347,7 +348,7 @@ constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 3;
 // kStaticNum; the autotuner searches it.
 constexpr int kStaticDen = 16;
 template <typename T>
-constexpr int kStaticNum = sizeof(T) == 8 ? 8 : 4;  // measured over the 2M floodplain's run
+constexpr int kStaticNum = sizeof(T) == 8 ? 0 : 4;  // measured over the 2M floodplain's run
 
 // One step (prime = 0) or prime pass (prime = 1: no update; derived data, inflow
 // weights and the dt of the current state) over a work list g.  Ticket t < F takes
@@ -451,6 +452,9 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
     }
     // The lists, the marks and the counters are the previous launch's.
     grid_dep_wait();
+    // the early item's slice sources (its instance's buffer parity is the previous
+    // launch's), loaded together with the counters below: one round trip, not two
+    const T* src_early = idx_early >= 0 ? slice_src<T>(pa, lane) : nullptr;
     if (lane == 0) {
       const volatile int* vs = sched;
       const int stamp = vs[2], mode = vs[8];
@@ -516,7 +520,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
     // one ticket requested a step ahead.
     // A CTA's tickets increase, so once one is past the end every later one is too.
     const int G = static_cast<int>(gridDim.x);
-    const int m_static = max(2, n_tickets / kStaticDen * (static16 >= 0 ? static16 : kStaticNum<T>) / G);
+    const int m_static =
+        max(g.lazy ? 1 : 2, n_tickets / kStaticDen * (static16 >= 0 ? static16 : kStaticNum<T>) / G);
     const int n_static = m_static * G;
     const int pre_v = lane < m_static ? map_load(static_cast<int>(blockIdx.x) + lane * G) : 0;
     int m_next = idx_early >= 0 ? 1 : 0;  // (the early item was ticket 0)
@@ -574,7 +579,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
     bool tc_live = false;
     int tn = -2, tv = 0;  // the ticket after b and its lookup, resolved at the promotion
     auto lookahead = [&]() {
-      tc_live = idx_b >= 0;
+      tc_live = idx_b >= 0 && !g.lazy;
       if (tc_live) {
         tn = next_tv(tv);
         if (m_next >= m_static && !tc_pending) request();
@@ -587,7 +592,12 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
       if (lane >= 3 && lane <= 3 + SL::kNA) s_src[lane - 3] = p;
       __syncwarp();
     };
-    if (pa.tile >= 0) set_src();
+    if (idx_early >= 0) {
+      if (lane >= 3 && lane <= 3 + SL::kNA) s_src[lane - 3] = src_early;
+      __syncwarp();
+    } else if (pa.tile >= 0) {
+      set_src();
+    }
     int a_next = 0;      // next tile (in this CTA's order) whose groups are issued
     bool ended = false;  // the end marker has been issued
     long long idle0 = clock64();
@@ -601,7 +611,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
         if (pa.tile >= 0) {
           issue_a<T>(L, slot(a_next), pa, idx_a & kIdx, s_src, &mb_a[a_next % S], lane);
           if (!(withhold && a_next == 0)) issue_h<T>(L, slot(a_next), pa, s_src, hv_a, &mb_h[a_next % S], lane);
-          if (b_pending) {  // after an early item a
+          if (b_pending) {  // after an early item a, or (claiming lazily) every issue
             b_pending = false;
             idx_b = next_idx();
             wb = fetch_w(idx_b);
@@ -609,14 +619,14 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
           }
           while (taken_otherwise(idx_b, wb)) {  // b was taken otherwise: the one after it
             ++n_skip;
-            int idx = tc_live ? resolve(tn, tv) : -2;
+            int idx = tc_live ? resolve(tn, tv) : (g.lazy ? next_idx() : -2);
             if (idx == -1) {
               ++n_skip;
               idx = next_idx();
             }
             idx_b = idx;
             wb = fetch_w(idx_b);
-            tc_live = idx_b >= 0;
+            tc_live = idx_b >= 0 && !g.lazy;
             if (tc_live) {
               tn = next_tv(tv);
               if (m_next >= m_static && !tc_pending) request();
@@ -651,6 +661,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
             wb = fetch_w(-2);
             idx_b = -2;
             tc_live = false;
+            b_pending = g.lazy && b_tile >= 0;  // claiming lazily: the next item at the next issue
           }
         } else {
           if (lane == 0) {
