@@ -88,10 +88,15 @@ def parse():
     ap.add_argument("--track-steps", type=int, default=200,
                     help="steps of the flood-tracking and passive-species cost line (0: skip it)")
     ap.add_argument("--stress-steps", type=int, default=100000, help="stress: lake-at-rest steps")
-    ap.add_argument("--workload", choices=["floodplain", "ensemble", "serve", "stress", "lake"],
+    ap.add_argument("--workload", choices=["floodplain", "ensemble", "serve", "stress", "lake", "window"],
                     default="floodplain",
                     help="floodplain: the default line; ensemble: batched uneven meshes; serve: request loop; "
-                         "lake: the wet-lake leg alone")
+                         "lake: the wet-lake leg alone; window: a few floodplain steps from the run's state at "
+                         "--t-start (for profilers)")
+    ap.add_argument("--t-start", type=float, default=0.0, help="window: simulated time of the state stepped")
+    ap.add_argument("--state-file", default="",
+                    help="window: the state at --t-start is read from this .npz if it exists, else made by a "
+                         "GPU run from t = 0 and saved there")
     ap.add_argument("--instances", type=int, default=256, help="ensemble members")
     ap.add_argument("--requests", type=int, default=200, help="serving trace length")
     ap.add_argument("--rate", type=float, default=20.0, help="serving arrivals per second (Poisson)")
@@ -782,6 +787,41 @@ def run_serve(args, ws, rank, torch, bm, W):
     return 0
 
 
+def run_window(args, ws, rank, torch, bm, W):
+    """A few steps of the floodplain run from its state at --t-start, in --precision:
+    the command profilers capture (a short process, few launches before the captured
+    ones).  The state comes from --state-file when that exists (written by an earlier
+    run of this command), else from a run from t = 0 on the GPU (saved there if a path
+    is given).  Prints the window's time per step and the tiles its launches take."""
+    s = W.floodplain()
+    st = bm.State.from_scenario(s, precision=args.precision)
+    if args.t_start > 0:
+        if args.state_file and os.path.exists(args.state_file):
+            d = np.load(args.state_file)
+            st.upload(d["H"], d["qx"], d["qy"], float(d["t"]))
+        else:
+            st.run_until(args.t_start)
+            if args.state_file:
+                H, qx, qy, t = st.download()
+                np.savez(args.state_file, H=H, qx=qx, qy=qy, t=t)
+    stream = torch.cuda.Stream()
+    st.set_stream(stream.cuda_stream)
+    st.step(args.warmup)
+    st.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st.step_async(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    st.sync()
+    taken, total = st.work()
+    print(json.dumps({"workload": f"floodplain 2,000,000 triangles, {args.precision}, {args.steps} steps from the "
+                                  f"run's state at t = {st.stats(volume=False)['t']:.1f} s",
+                      "ms_per_step": e0.elapsed_time(e1) / max(args.steps, 1), "tiles_taken": taken,
+                      "tiles": total}))
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -792,7 +832,8 @@ def main():
         from paper_2102_12862_b300 import bm
         from paper_2102_12862_b300 import workloads as W
         torch.cuda.set_device(local)
-        fn = {"ensemble": run_ensemble, "serve": run_serve, "stress": run_stress, "lake": run_lake}[args.workload]
+        fn = {"ensemble": run_ensemble, "serve": run_serve, "stress": run_stress, "lake": run_lake,
+              "window": run_window}[args.workload]
         return fn(args, ws, rank, torch, bm, W) if rank == 0 or ws == 1 else 0
 
     import torch
