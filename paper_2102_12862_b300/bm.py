@@ -654,7 +654,8 @@ class State:
         return bm_state_get_slots(self.handle)
 
     def set_claim(self, mode: int):
-        """Work-item claiming: 0 ahead, 1 when a slot frees, -1 the precision's default."""
+        """Work-item claiming: 0 ahead, 1 right after each issue, 2 once a slot is free
+        (the default, -1)."""
         bm_state_set_claim(self.handle, mode)
 
     def claim(self) -> int:

@@ -253,11 +253,12 @@ int state_extra_level(const bm_state* s) {
 constexpr int kDefaultSlots = 2;
 int list_slots(const StepList& l) { return l.extra == 0 ? (l.slots > 0 ? l.slots : kDefaultSlots) : 3; }
 
-// Work-item claiming of a list's launches: by default a CTA claims an item only when a
-// slot frees, so no CTA commits to tiles it reaches late while others run dry (the
-// launch's end is set by its last tile); measured faster than claiming ahead over the
-// floodplain run in both precisions.
-int list_claim(int, const StepList& l) { return l.claim >= 0 ? l.claim : 1; }
+// Work-item claiming of a list's launches: by default a CTA claims each item once its
+// slot is free, so it commits to no more tiles than its slots hold and none it would
+// reach late while others run dry (the launch's end is set by its last tile); measured
+// faster than claiming ahead, or right after each issue, over the floodplain run in
+// both precisions.
+int list_claim(int, const StepList& l) { return l.claim >= 0 ? l.claim : 2; }
 
 // The slot counts the autotuner tries for a list: the one in force first.
 std::vector<int> slot_candidates(const StepList& l) {
@@ -891,7 +892,7 @@ bm_status bm_state_set_slots(bm_state* s, int slots) {
 bm_status bm_state_set_claim(bm_state* s, int mode) {
   clear_error();
   if (!s) return fail(BM_EINVAL, "bm_state_set_claim: state is NULL");
-  if (mode < -1 || mode > 1) return fail(BM_EINVAL, "bm_state_set_claim: mode in {-1, 0, 1}");
+  if (mode < -1 || mode > 2) return fail(BM_EINVAL, "bm_state_set_claim: mode in {-1, 0, 1, 2}");
   if (mode == s->list.claim) return BM_OK;
   BM_CUDA(cudaStreamSynchronize(s->stream));
   drop_graphs(s);  // the captured launches carry the old mode
@@ -1665,7 +1666,7 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
     first = false;
     return BM_OK;
   };
-  for (int m : {start_claim, 1 - start_claim}) {
+  for (int m : {start_claim, (start_claim + 1) % 3, (start_claim + 2) % 3}) {
     if (out != BM_OK) break;
     out = set_claim(m);
     cur_m = m;

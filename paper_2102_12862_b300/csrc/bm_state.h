@@ -157,7 +157,8 @@ struct StepList {
   int static16 = -1;  // static share of the tickets in sixteenths (-1: the precision's default)
   int slots = 0;      // tile slots of the step kernel asked for (2, 3, 4; 0 the default; levels
                       // 1 and 2 run 3)
-  int claim = -1;     // work-item claiming: 0 ahead, 1 when a slot frees, -1 the default
+  int claim = -1;     // work-item claiming: 0 ahead, 1 after each issue, 2 once a slot is free,
+                      // -1 the default (2)
   int extra = 0;  // the step kernel's feature level the members need (0 none; 1 tracking or
                  // species; 2 also sources or log-law friction)
 };

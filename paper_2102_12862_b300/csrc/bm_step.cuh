@@ -327,7 +327,8 @@ struct ListArgs {
   const int* inst_item;  // per instance: its first item
   int n_items, n_fixed, n_inst;
   int ne4max, nh4max;    // the largest record of the list (they fix the shared-memory layout)
-  int lazy;              // claim the next work item only when a slot frees (no lookahead)
+  int lazy;              // claiming: 0 ahead; 1 the next item right after an issue (no lookahead);
+                         // 2 each item once its slot is free
 };
 
 // A work list's scheduling state for a full launch: counters zero, listing allowed or
@@ -559,8 +560,11 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
     // an early item a, b once a is issued
     int idx_a = idx_early, idx_b = -2;
     unsigned wb = fetch_w(-2);
-    bool b_pending = idx_early >= 0;  // b is still to be read
-    if (!b_pending) {
+    // claiming on demand (lazy 2): a is claimed and read once its slot is free, so
+    // b_pending says a is still to be claimed; otherwise it says b is still to be read
+    const bool on_demand = g.lazy == 2;
+    bool b_pending = on_demand ? idx_early < 0 : idx_early >= 0;
+    if (!on_demand && !b_pending) {
       idx_a = next_idx();
       idx_b = idx_a >= 0 ? next_idx() : -2;
       unsigned wa = fetch_w(idx_a);
@@ -585,18 +589,21 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
         if (m_next >= m_static && !tc_pending) request();
       }
     };
-    if (!b_pending) lookahead();
+    if (!on_demand && !b_pending) lookahead();
     // the slice sources of a's instance (lane 3 + j reads array j's)
     auto set_src = [&]() {
       const T* p = slice_src<T>(pa, lane);
       if (lane >= 3 && lane <= 3 + SL::kNA) s_src[lane - 3] = p;
       __syncwarp();
     };
+    int src_inst = -1;  // the instance whose slice sources s_src holds
     if (idx_early >= 0) {
       if (lane >= 3 && lane <= 3 + SL::kNA) s_src[lane - 3] = src_early;
       __syncwarp();
-    } else if (pa.tile >= 0) {
+      src_inst = pa.inst;
+    } else if (!on_demand && pa.tile >= 0) {
       set_src();
+      src_inst = pa.inst;
     }
     int a_next = 0;      // next tile (in this CTA's order) whose groups are issued
     bool ended = false;  // the end marker has been issued
@@ -608,7 +615,32 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
       bool free_slot = a_next < S;
       if (!free_slot && lane == 0) free_slot = mbar_test(&mb_e[a_next % S], ((a_next - S) / S) & 1);
       if (__shfl_sync(0xffffffffu, free_slot, 0)) {
-        if (pa.tile >= 0) {
+        if (on_demand && b_pending) {
+          // the item for this slot: claimed, read and promoted now
+          b_pending = false;
+          int idx = next_idx();
+          unsigned w = fetch_w(idx);
+          while (taken_otherwise(idx, w)) {
+            ++n_skip;
+            idx = next_idx();
+            w = fetch_w(idx);
+          }
+          const int w_tile = static_cast<int>(word(w, kWTile)), w_inst = static_cast<int>(word(w, kWInst));
+          __syncwarp();  // every lane is done with the previous item
+          if (lane < kWords) reinterpret_cast<unsigned*>(&s_pa)[lane] = w;
+          __syncwarp();
+          if (w_tile >= 0 && w_inst != src_inst) {
+            set_src();
+            src_inst = w_inst;
+          }
+          idx_a = idx;
+          load_halo<T>(pa, lane, hv_a);
+        }
+        if (pa.tile >= 0 && on_demand) {
+          issue_a<T>(L, slot(a_next), pa, idx_a & kIdx, s_src, &mb_a[a_next % S], lane);
+          if (!(withhold && a_next == 0)) issue_h<T>(L, slot(a_next), pa, s_src, hv_a, &mb_h[a_next % S], lane);
+          b_pending = true;  // the next item once the next slot is free
+        } else if (pa.tile >= 0) {
           issue_a<T>(L, slot(a_next), pa, idx_a & kIdx, s_src, &mb_a[a_next % S], lane);
           if (!(withhold && a_next == 0)) issue_h<T>(L, slot(a_next), pa, s_src, hv_a, &mb_h[a_next % S], lane);
           if (b_pending) {  // after an early item a, or (claiming lazily) every issue
