@@ -401,9 +401,11 @@ bm_status bm_state_get_slots(bm_state* s, int* slots);
  * items and requests the next tickets a step or two before it needs them, hiding their
  * latency), 1 the next item right after each issue (no tickets ahead), 2 each item once
  * its slot is free (a CTA commits to no more tiles than its slots hold, so the launch's
- * last tiles are not queued behind long ones), -1 the default (2).  With modes 1 and 2
- * a CTA's static tickets may be one.  Results do not depend on it.  BM_EINVAL outside
- * {-1, 0, 1, 2}; get reports the mode in force.
+ * last tiles are not queued behind long ones), 3 as 2 and only once the tile before is
+ * past its edge phase (a CTA commits to its next tile near the end of the current one),
+ * -1 the precision's default (FP64 3, FP32-bulk 2).  With modes 1-3 a CTA's static
+ * tickets may be one.  Results do not depend on it.  BM_EINVAL outside {-1, 0, 1, 2, 3};
+ * get reports the mode in force.
  */
 bm_status bm_state_set_claim(bm_state* s, int mode);
 bm_status bm_state_get_claim(bm_state* s, int* mode);

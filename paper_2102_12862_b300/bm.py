@@ -654,8 +654,9 @@ class State:
         return bm_state_get_slots(self.handle)
 
     def set_claim(self, mode: int):
-        """Work-item claiming: 0 ahead, 1 right after each issue, 2 once a slot is free
-        (the default, -1)."""
+        """Work-item claiming: 0 ahead, 1 right after each issue, 2 once a slot is free,
+        3 also once the tile before is past its edges; -1 the precision's default (FP64 3,
+        FP32-bulk 2)."""
         bm_state_set_claim(self.handle, mode)
 
     def claim(self) -> int:

@@ -255,10 +255,11 @@ int list_slots(const StepList& l) { return l.extra == 0 ? (l.slots > 0 ? l.slots
 
 // Work-item claiming of a list's launches: by default a CTA claims each item once its
 // slot is free, so it commits to no more tiles than its slots hold and none it would
-// reach late while others run dry (the launch's end is set by its last tile); measured
-// faster than claiming ahead, or right after each issue, over the floodplain run in
-// both precisions.
-int list_claim(int, const StepList& l) { return l.claim >= 0 ? l.claim : 2; }
+// reach late while others run dry (the launch's end is set by its last tile); FP64,
+// whose wet tiles take 20-35 us, also waits until the tile before is past its edge
+// phase, so a CTA commits to its next tile only near the end of the current one.
+// Measured over the floodplain run against the other modes in both precisions.
+int list_claim(int prec, const StepList& l) { return l.claim >= 0 ? l.claim : (prec == BM_FP64 ? 3 : 2); }
 
 // The slot counts the autotuner tries for a list: the one in force first.
 std::vector<int> slot_candidates(const StepList& l) {
@@ -892,7 +893,7 @@ bm_status bm_state_set_slots(bm_state* s, int slots) {
 bm_status bm_state_set_claim(bm_state* s, int mode) {
   clear_error();
   if (!s) return fail(BM_EINVAL, "bm_state_set_claim: state is NULL");
-  if (mode < -1 || mode > 2) return fail(BM_EINVAL, "bm_state_set_claim: mode in {-1, 0, 1, 2}");
+  if (mode < -1 || mode > 3) return fail(BM_EINVAL, "bm_state_set_claim: mode in {-1, 0, 1, 2, 3}");
   if (mode == s->list.claim) return BM_OK;
   BM_CUDA(cudaStreamSynchronize(s->stream));
   drop_graphs(s);  // the captured launches carry the old mode
@@ -1666,7 +1667,7 @@ bm_status autotune_shape(std::vector<bm_state*> states, int steps, int start_cta
     first = false;
     return BM_OK;
   };
-  for (int m : {start_claim, (start_claim + 1) % 3, (start_claim + 2) % 3}) {
+  for (int m : {start_claim, (start_claim + 1) % 4, (start_claim + 2) % 4, (start_claim + 3) % 4}) {
     if (out != BM_OK) break;
     out = set_claim(m);
     cur_m = m;

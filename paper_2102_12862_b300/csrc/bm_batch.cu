@@ -348,7 +348,7 @@ bm_status bm_batch_set_slots(bm_batch* b, int slots) {
 bm_status bm_batch_set_claim(bm_batch* b, int mode) {
   clear_error();
   if (!b) return fail(BM_EINVAL, "bm_batch_set_claim: batch is NULL");
-  if (mode < -1 || mode > 2) return fail(BM_EINVAL, "bm_batch_set_claim: mode in {-1, 0, 1, 2}");
+  if (mode < -1 || mode > 3) return fail(BM_EINVAL, "bm_batch_set_claim: mode in {-1, 0, 1, 2, 3}");
   if (mode == b->list.claim) return BM_OK;
   BM_CUDA(cudaStreamSynchronize(b->stream));
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);  // they carry the old mode

@@ -158,7 +158,7 @@ struct StepList {
   int slots = 0;      // tile slots of the step kernel asked for (2, 3, 4; 0 the default; levels
                       // 1 and 2 run 3)
   int claim = -1;     // work-item claiming: 0 ahead, 1 after each issue, 2 once a slot is free,
-                      // -1 the default (2)
+                      // 3 also once the tile before is past its edges; -1 the default
   int extra = 0;  // the step kernel's feature level the members need (0 none; 1 tracking or
                  // species; 2 also sources or log-law friction)
 };

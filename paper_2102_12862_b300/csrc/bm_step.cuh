@@ -328,7 +328,8 @@ struct ListArgs {
   int n_items, n_fixed, n_inst;
   int ne4max, nh4max;    // the largest record of the list (they fix the shared-memory layout)
   int lazy;              // claiming: 0 ahead; 1 the next item right after an issue (no lookahead);
-                         // 2 each item once its slot is free
+                         // 2 each item once its slot is free; 3 also once the previous
+                         // tile is past its edge phase
 };
 
 // A work list's scheduling state for a full launch: counters zero, listing allowed or
@@ -387,6 +388,9 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
   // per slot: group A landed, group H landed, slot released by the compute warps
   __shared__ __align__(8) uint64_t mb_a[S], mb_h[S], mb_e[S];
   __shared__ int s_abort;
+  // tiles whose edge phase the compute warps have finished (claiming mode 3 claims item
+  // j only once tile j - 1 is past its edges: long tiles commit late, nearly greedily)
+  __shared__ int s_edged;
   // the launch's ticket map (written by the copy warp before its first issue, so the
   // compute warps see it after their first wait): stamp, listing allowed, part bounds
   // P1 <= P2 <= P3 <= tickets, whether the lists were taken; the tickets this CTA's copy
@@ -413,6 +417,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
     }
     mbar_init_fence();
     s_abort = 0;
+    s_edged = 0;
     s_nlst = 0;
   }
   __syncthreads();
@@ -562,7 +567,9 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
     unsigned wb = fetch_w(-2);
     // claiming on demand (lazy 2): a is claimed and read once its slot is free, so
     // b_pending says a is still to be claimed; otherwise it says b is still to be read
-    const bool on_demand = g.lazy == 2;
+    const bool on_demand = g.lazy >= 2;
+    const bool gated = g.lazy == 3;
+    const volatile int* edged = &s_edged;
     bool b_pending = on_demand ? idx_early < 0 : idx_early >= 0;
     if (!on_demand && !b_pending) {
       idx_a = next_idx();
@@ -614,6 +621,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
       // groups A and H of the next tile (or the end marker) once its slot is free
       bool free_slot = a_next < S;
       if (!free_slot && lane == 0) free_slot = mbar_test(&mb_e[a_next % S], ((a_next - S) / S) & 1);
+      if (gated && a_next > 0 && lane == 0) free_slot = free_slot && *edged >= a_next;
       if (__shfl_sync(0xffffffffu, free_slot, 0)) {
         if (on_demand && b_pending) {
           // the item for this slot: claimed, read and promoted now
@@ -1045,6 +1053,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
       }
     }
     nbar<kTile>();
+    if (tid == 0) *reinterpret_cast<volatile int*>(&s_edged) = k + 1;
 
     // phase I: cells
     const int i = tile * kTile + tid;
