@@ -199,9 +199,9 @@ bm_status bm_state_download_track(bm_state* s, double* t_arrival, double* h_max,
  * inflow concentrations (NULL: 0).  n_species in [0, 5]; 0 removes them.  It
  * allocates 2 * n_species values per cell plus, per tile edge, one exported flux and
  * one byte, and blocks.  From then on every step launches a second kernel after the
- * step kernel (one CTA per tile).  A state with species steps alone:
- * bm_batch_create refuses it (BM_EINVAL); do not set species on a state that is a
- * member of a live batch (the batch keeps a copy of its descriptor).  Uploading a
+ * step kernel (one CTA per tile); in a batch, after the batch's step launch, one such
+ * kernel per member with species.  Set species before bm_batch_create on a batch
+ * member: a batch made earlier refuses to step (BM_EINVAL).  Uploading a
  * state keeps the species' values.  bm_state_download_scalars copies q_c back
  * (n_species * n_cells, caller order); BM_EINVAL when the state carries none.
  * FP32-bulk states keep q_c in single precision.
@@ -225,8 +225,10 @@ bm_status bm_state_download_scalars(bm_state* s, double* hc);
  * Sources add mass, not momentum.  n_regions in [0, 65536]; 0 removes them.  BM_EINVAL
  * on malformed input, on a total-discharge region with no cell, and when the state
  * carries passive species (not modelled together; bm_state_set_scalars refuses the
- * converse).  A state with sources steps alone (bm_batch_create refuses it).  Blocks.
- * Every step launches a one-block kernel before the step kernel (S_h at t^n).
+ * converse).  Blocks.  Every step launches a one-block kernel before the step kernel
+ * (S_h at t^n); in a batch, one per member with sources before the batch's step launch.
+ * Set sources before bm_batch_create on a batch member (a batch made earlier refuses to
+ * step, BM_EINVAL).
  */
 bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* region, const int32_t* kind,
                                const int32_t* mode, const int64_t* offsets, const double* t, const double* v);
@@ -241,9 +243,10 @@ bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* re
  * boundary edges the inside cell's normal bedload.  The free surface moves with the
  * bed, so the water depth and volume are kept.  on = 0 stops it (the bed stays as it
  * is).  FP64 states only; 0 <= porosity < 1, s > 1, d > 0 [m], alpha >= 0, m >= 1,
- * theta_cr finite (BM_EINVAL otherwise).  A state with morphodynamics steps alone
- * (bm_batch_create refuses it).  Every step launches three more kernels (the step's
- * dt saved before it; the bed fluxes, one CTA per tile, and the update after it).
+ * theta_cr finite (BM_EINVAL otherwise).  Every step launches three more kernels (the
+ * step's dt saved before it; the bed fluxes, one CTA per tile, and the update after
+ * it), in a batch for each member with morphodynamics around the batch's step launch;
+ * set it before bm_batch_create on a batch member (a batch made earlier refuses to step).
  * Blocks.  bm_state_download_bed copies the bed elevation (caller order) to z.
  */
 /*
@@ -435,6 +438,12 @@ bm_status bm_state_autotune(bm_state* s, int steps_per_trial, int* best_ctas_per
  * the caller; while they are in a batch, step them only through the batch (their
  * stats / download may be read after bm_batch_sync).  Creating a batch allocates a
  * little device memory (descriptors, work list); the members' data is not copied.
+ * Members may carry any feature (tracking, species, sources, friction closures,
+ * outflow and level laws, bed evolution): the batch's step launch runs the lowest
+ * instantiation that serves them all, and each member's own kernels (sources' rates
+ * before, species and bed update after) run around it.  A member's features must be
+ * set before the batch is made: stepping a batch whose member changed a feature since
+ * returns BM_EINVAL ("make the batch again").
  */
 typedef struct bm_batch bm_batch;
 bm_status bm_batch_create(bm_state* const* states, int32_t n_states, bm_batch** out);

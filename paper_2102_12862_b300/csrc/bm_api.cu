@@ -431,10 +431,9 @@ void launch_morpho(bm_state* s, cudaStream_t st) {
                                    a.n_cells);
 }
 
-void launch_state(bm_state* s, cudaStream_t st, int prime) {
-  if (prime) ensure_list(&s->list, st);  // (prime launches are never captured)
-  if (!prime && s->morpho) morpho_save_dt<<<1, 32, 0, st>>>(s->ctl, s->mo_dt.p);
-  if (!prime && s->n_src > 0) {
+void pre_step(bm_state* s, cudaStream_t st) {
+  if (s->morpho) morpho_save_dt<<<1, 32, 0, st>>>(s->ctl, s->mo_dt.p);
+  if (s->n_src > 0) {
     if (s->prec == BM_FP64)
       source_rates<double><<<1, 128, 0, st>>>(s->ctl, s->n_src, s->src_kind.p, s->src_off.p, s->src_t.p, s->src_v.p,
                                                s->src_area.p, s->src_rate64.p);
@@ -442,12 +441,21 @@ void launch_state(bm_state* s, cudaStream_t st, int prime) {
       source_rates<float><<<1, 128, 0, st>>>(s->ctl, s->n_src, s->src_kind.p, s->src_off.p, s->src_t.p, s->src_v.p,
                                               s->src_area.p, s->src_rate32.p);
   }
-  launch_work(s->prec, s->list, s->grid, prime, st);
-  if (!prime && s->n_species > 0) {
+}
+
+void post_step(bm_state* s, cudaStream_t st) {
+  if (s->n_species > 0) {
     if (s->prec == BM_FP64) launch_species<double>(s, st);
     else launch_species<float>(s, st);
   }
-  if (!prime && s->morpho) launch_morpho(s, st);
+  if (s->morpho) launch_morpho(s, st);
+}
+
+void launch_state(bm_state* s, cudaStream_t st, int prime) {
+  if (prime) ensure_list(&s->list, st);  // (prime launches are never captured)
+  if (!prime) pre_step(s, st);
+  launch_work(s->prec, s->list, s->grid, prime, st);
+  if (!prime) post_step(s, st);
 }
 
 bm_status get_graph(bm_state* s, int k, cudaGraphExec_t* out) {
@@ -581,6 +589,9 @@ void fill_desc(bm_state* s, InstDesc<T>& d) {
 
 }  // namespace
 
+void state_pre_step(bm_state* s, cudaStream_t st) { pre_step(s, st); }
+void state_post_step(bm_state* s, cudaStream_t st) { post_step(s, st); }
+
 // Host copy of a state's descriptor (for batches).
 void state_desc_bytes(bm_state* s, std::vector<unsigned char>* out) {
   if (s->prec == BM_FP64) {
@@ -700,6 +711,7 @@ bm_status alloc_state(bm_state* s, const bm_params* prm) {
   p.hmin_f = static_cast<float>(prm->h_min);
   p.pad_f = 0.0f;
   state_desc_bytes(s, &s->hdesc);
+  ++s->desc_epoch;  // (a batch made before this no longer describes the state)
   e = s->desc.upload(s->hdesc);
   if (e != cudaSuccess) return dev_fail(e, "bm_state_init");
   bm_status lst = build_step_list({s}, {static_cast<const void*>(s->desc.p)}, &s->list);
@@ -1040,6 +1052,7 @@ bm_status bm_state_track(bm_state* s, double h_arrival) {
   // the step kernels read the descriptor in place: rewrite it (same size, same address)
   BM_CUDA(cudaStreamSynchronize(s->stream));
   state_desc_bytes(s, &s->hdesc);
+  ++s->desc_epoch;  // (a batch made before this no longer describes the state)
   BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
   const int n = static_cast<int>(h.n_cells);
   const int nb = (n + 255) / 256;
@@ -1133,6 +1146,7 @@ bm_status bm_state_set_scalars(bm_state* s, int32_t n_species, const double* hc,
   for (int c = 0; c < kMaxSpecies; ++c) s->c_in[c] = (c < n_species && c_in) ? c_in[c] : 0.0;
   // the step kernels read the descriptor in place: rewrite it (same size, same address)
   state_desc_bytes(s, &s->hdesc);
+  ++s->desc_epoch;  // (a batch made before this no longer describes the state)
   BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
   BM_CUDA(cudaStreamSynchronize(s->stream));
   // the launch sequence changes (kernel instantiation, species kernel after each step)
@@ -1237,6 +1251,7 @@ bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* re
   s->n_src = n_regions;
   // the descriptor (read in place) and the work list (tile flags, kernel instantiation)
   state_desc_bytes(s, &s->hdesc);
+  ++s->desc_epoch;  // (a batch made before this no longer describes the state)
   BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
   BM_CUDA(cudaStreamSynchronize(s->stream));
   drop_graphs(s);
@@ -1300,6 +1315,7 @@ bm_status bm_state_set_outflow(bm_state* s, const double* hq_stage, const double
   s->weir_crest = weir_crest;
   s->weir_mu = weir_poleni;
   state_desc_bytes(s, &s->hdesc);
+  ++s->desc_epoch;  // (a batch made before this no longer describes the state)
   BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
   const int extra = state_extra_level(s);  // laws that let water out: the full instantiation
   if (extra != s->list.extra) {
@@ -1335,6 +1351,7 @@ bm_status bm_state_set_level(bm_state* s, const double* t, const double* z, int6
   if (e != cudaSuccess) return dev_fail(e, "bm_state_set_level");
   s->zh_n = static_cast<int>(n);
   state_desc_bytes(s, &s->hdesc);
+  ++s->desc_epoch;  // (a batch made before this no longer describes the state)
   BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
   const int extra = state_extra_level(s);  // a level series: the full instantiation
   if (extra != s->list.extra) {
@@ -1375,6 +1392,7 @@ bm_status bm_state_set_friction(bm_state* s, int32_t law, const double* coef) {
   if (e != cudaSuccess) return dev_fail(e, "bm_state_set_friction");
   s->fr_law = law;
   state_desc_bytes(s, &s->hdesc);
+  ++s->desc_epoch;  // (a batch made before this no longer describes the state)
   BM_CUDA(cudaMemcpyAsync(s->desc.p, s->hdesc.data(), s->hdesc.size(), cudaMemcpyHostToDevice, s->stream));
   BM_CUDA(cudaStreamSynchronize(s->stream));
   const int extra = state_extra_level(s);

@@ -20,6 +20,7 @@
 
 struct bm_batch {
   std::vector<bm_state*> members;
+  std::vector<long long> epochs;  // the members' descriptor epochs the batch was made with
   int prec = BM_FP64;
   bm::DBuf<unsigned char> descs;  // member descriptors, one after another
   size_t dsz = 0;                 // bytes per descriptor
@@ -80,11 +81,14 @@ __global__ void batch_flags(Ctl* const* ctl, int n, int* flags) {
   if (k < n) flags[k] = ctl[k]->active | (ctl[k]->status << 1);
 }
 
+// One batch step: the members' own kernels before and after it (sources, species, bed
+// evolution) around the one step launch, for the members of the list launched (a member
+// left out of a run_until list takes no step, so its species and bed are left alone).
 void launch_batch(bm_batch* b, cudaStream_t st) {
-  if (b->sub)
-    launch_work(b->prec, *b->sub, b->sub_grid, 0, st);
-  else
-    launch_work(b->prec, b->list, b->grid, 0, st);
+  const StepList& l = b->sub ? *b->sub : b->list;
+  for (bm_state* m : l.members) state_pre_step(m, st);
+  launch_work(b->prec, l, b->sub ? b->sub_grid : b->grid, 0, st);
+  for (bm_state* m : l.members) state_post_step(m, st);
 }
 
 bm_status batch_graph(bm_batch* b, int k, cudaGraphExec_t* out) {
@@ -146,6 +150,9 @@ bm_status use_active_members(bm_batch* b) {
 bm_status batch_enqueue(bm_batch* b, int64_t n) {
   constexpr int kChunk = 16;
   if (n <= 0) return BM_OK;
+  for (size_t k = 0; k < b->members.size(); ++k)
+    if (b->members[k]->desc_epoch != b->epochs[k])
+      return fail(BM_EINVAL, "batch: a member's features changed after bm_batch_create (make the batch again)");
   ensure_list(b->sub ? b->sub.get() : &b->list, b->stream);
   cudaGraphExec_t gbig = nullptr, gone = nullptr;
   if (n >= kChunk) {
@@ -226,18 +233,13 @@ bm_status bm_batch_create(bm_state* const* states, int32_t n, bm_batch** out) {
   for (int k = 0; k < n; ++k) {
     if (!states[k]) return fail(BM_EINVAL, "bm_batch_create: NULL state");
     if (states[k]->prec != prec) return fail(BM_EINVAL, "bm_batch_create: members must share one precision");
-    if (states[k]->morpho)
-      return fail(BM_EINVAL, "bm_batch_create: a state with morphodynamics steps alone (bm_step)");
-    if (states[k]->n_src > 0)
-      return fail(BM_EINVAL, "bm_batch_create: a state with external sources steps alone (bm_step)");
-    if (states[k]->n_species > 0)
-      return fail(BM_EINVAL, "bm_batch_create: a state with passive species steps alone (bm_step)");
     for (int j = 0; j < k; ++j)
       if (states[j] == states[k]) return fail(BM_EINVAL, "bm_batch_create: a state appears twice");
   }
   bm_batch* b = new (std::nothrow) bm_batch();
   if (!b) return fail(BM_ENOMEM, "bm_batch_create: out of host memory");
   b->members.assign(states, states + n);
+  for (int k = 0; k < n; ++k) b->epochs.push_back(states[k]->desc_epoch);
   b->prec = prec;
   std::vector<unsigned char> all, one;
   std::vector<Ctl*> ctls(n);

@@ -184,6 +184,7 @@ struct bm_state {
   // the work list whose launches stepped the state last (null: none since the state's
   // arrays or features changed); another list resets its scheduling state first
   const bm::StepList* last_list = nullptr;
+  long long desc_epoch = 0;  // counts the rebuilds of the state's descriptor (feature setters)
   bool no_skip = false;  // bm_state_set_tile_skipping(s, 0): every launch takes every tile
   bm::Ctl* ctl = nullptr;   // device
   bm::Ctl* hctl = nullptr;  // pinned host mirror
@@ -254,6 +255,11 @@ bm_status build_step_list(const std::vector<bm_state*>& members, const std::vect
                           StepList* out);
 // Grid of a step launch for a launch shape (ctas_per_sm = 0: all that fit).
 bm_status list_occupancy(int prec, StepList* l);
+// The per-state kernels around a step launch: before it, the external sources' rates at
+// t^n and the bed update's copy of dt^n; after it, the passive species' advection and
+// the bed update (nothing for a state without those features).
+void state_pre_step(bm_state* s, cudaStream_t st);
+void state_post_step(bm_state* s, cudaStream_t st);
 // The tile slots a list's kernel runs with, and the counts the autotuner tries.
 int list_slots(const StepList& l);
 int list_claim(int prec, const StepList& l);

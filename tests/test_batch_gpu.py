@@ -124,3 +124,70 @@ def test_fp32_batch_members_against_the_oracle():
         stt = st.stats()
         defect = abs(stt["volume"] - v0[k] - stt["boundary_volume"]) / (v0[k] + abs(stt["boundary_volume"]))
         assert defect <= 1e-7, (k, defect)
+
+
+def featured(precision):
+    """Members with every optional feature, each on its own floodplain: two passive
+    species, rain on a disk (an external source), a log-law friction closure with flood
+    tracking, and (FP64) bed evolution; plus a plain member."""
+    scs = [W.floodplain(nx=100, ny=40, Lx=1000.0, Ly=400.0, seed=61 + k, q_peak=90.0, ramp=40.0) for k in range(5)]
+    sts = [bm.State.from_scenario(s, precision=precision) for s in scs]
+    hc = np.stack([np.maximum(scs[0].H - scs[0].z, 0.0) * 0.5, np.zeros(scs[0].n_cells)])
+    sts[0].set_scalars(hc, [0.0, 1.0])
+    sts[1].set_sources(W.disk_region(scs[1], 700.0, 120.0, 60.0), [bm.SOURCE_INTENSITY], [bm.SINK_EXACT],
+                       [(np.array([0.0, 1e6]), np.array([150.0, 150.0]))])
+    sts[2].set_friction(bm.FRICTION_CHEZY, 25.0)
+    sts[2].track(0.05)
+    if precision == "fp64":
+        sts[3].set_morpho(porosity=0.4, s=2.65, d=0.001)
+    return scs, sts
+
+
+def featured_pair(precision):
+    return featured(precision)[1], featured(precision)[1]
+
+
+def same_everything(a, b, precision, k):
+    assert equal_states(a, b), k
+    if k == 0:
+        assert np.array_equal(a.download_scalars(), b.download_scalars())
+    if k == 2:
+        ta, tb = a.download_track(), b.download_track()
+        for key in ta:
+            assert np.array_equal(np.asarray(ta[key]), np.asarray(tb[key]), equal_nan=True), key
+    if k == 3 and precision == "fp64":
+        assert np.array_equal(a.download_bed(), b.download_bed())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_with_every_feature_equals_solo(precision):
+    """Members with species, sources, a log-law closure with tracking and bed evolution
+    step in one batch: each ends bitwise equal to its solo run, for plain stepping and
+    for run_until with per-member end times (the run's later launches list only the
+    members still running, and the finished members' species and beds stay put)."""
+    solo, inb = featured_pair(precision)
+    b = bm.Batch(inb)
+    for st in solo:
+        st.step(40)
+    b.step(40)
+    for k, (x, y) in enumerate(zip(inb, solo)):
+        same_everything(x, y, precision, k)
+    ends = [30.0, 12.0, 25.0, 8.0, 40.0]
+    for st, t in zip(solo, ends):
+        st.run_until(t)
+    b.run_until(ends)
+    for k, (x, y) in enumerate(zip(inb, solo)):
+        assert x.stats()["t"] == ends[k]
+        same_everything(x, y, precision, k)
+
+
+def test_batch_refuses_a_member_changed_after_it_was_made():
+    s = W.floodplain(nx=60, ny=24, Lx=600.0, Ly=240.0, seed=66)
+    a, c = bm.State.from_scenario(s), bm.State.from_scenario(s)
+    b = bm.Batch([a, c])
+    b.step(2)
+    a.set_friction(bm.FRICTION_CHEZY, 30.0)
+    with pytest.raises(bm.BMError, match="changed after bm_batch_create"):
+        b.step(1)
+    b2 = bm.Batch([a, c])  # made again: steps
+    b2.step(2)

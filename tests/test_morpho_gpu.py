@@ -104,8 +104,6 @@ def test_morpho_api_rules():
     with pytest.raises(bm.BMError, match="porosity"):
         st.set_morpho(**dict(SAND, porosity=1.0))
     st.set_morpho(**SAND)
-    with pytest.raises(bm.BMError, match="morphodynamics"):
-        bm.Batch([st])
     st.step(20)
     z1 = st.download_bed()
     assert np.max(np.abs(z1 - s.z)) > 0

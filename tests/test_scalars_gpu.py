@@ -140,9 +140,10 @@ def test_species_follow_upload_and_removal():
     H, qx, qy, t = st.download()
     st.upload(H, qx, qy, t)
     assert np.array_equal(st.download_scalars(), before)
-    with pytest.raises(bm.BMError, match="passive species"):
-        bm.Batch([st])
+    b = bm.Batch([st])  # a batch made before the species change below
     st.set_scalars(np.zeros((0, st.n_cells)))
+    with pytest.raises(bm.BMError, match="changed after bm_batch_create"):
+        b.step(1)
     with pytest.raises(bm.BMError, match="carries no species"):
         st.download_scalars()
     with pytest.raises(bm.BMError, match="n_species"):

@@ -153,8 +153,6 @@ def test_source_api_rules():
         st.set_sources(np.full(n, 3), [INTENSITY], [EXACT], [const(1.0)])
     st.set_sources(np.zeros(n), [INTENSITY], [EXACT], [const(1.0)])
     with pytest.raises(bm.BMError, match="external sources"):
-        bm.Batch([st])
-    with pytest.raises(bm.BMError, match="external sources"):
         st.set_scalars(np.zeros((1, n)))
     st.step(3)
     st.set_sources(np.zeros(n), [], [], [])
