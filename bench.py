@@ -68,7 +68,7 @@ FP64_PEAK_TFLOPS = 1.2023  # 296 DFMA lanes per cycle (ncu peak) x 2 FLOP x 2.03
 HBM_FALLBACK_GBS = 6400.0
 T_WINDOWS = (0.0, 600.0, 1800.0, 3600.0)  # the floodplain run's sampled times [s]
 L2_FLUSH_STEPS = 50  # steps of the L2-flushed cross-check
-KERNEL_NAME = {"fp64": "step_pipe<double, 0>", "fp32": "step_pipe<float, 0>"}  # without flood tracking
+KERNEL_NAME = {"fp64": "step_pipe<double, 0, 2>", "fp32": "step_pipe<float, 0, 2>"}  # plain level, 2 slots
 
 
 def parse():
@@ -398,6 +398,10 @@ def measure(args, prec, s, mesh, torch, bm, dist, ws, rank):
                      f"step-weighted share {taken:.3f} of the tiles; the others are dry, at rest and unchanged)",
             "layout_bytes_per_launch": layout_bytes,
             "layout_frac": layout_bytes / (ms_run / 1e3) / 1e9 / hbm,
+            # the same bytes per cell-update over every cell of the mesh (as if each
+            # launch streamed all tiles): the step's rate in the metric's own units,
+            # against the copy bandwidth
+            "frac_all_cells": BYTES_PER_CELL_UPDATE[prec] * n / (ms_run / 1e3) / 1e9 / hbm,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
     if prec == "fp64":
         wet_steps = sum((snaps[a + 1]["steps"] - snaps[a]["steps"]) * 0.5 * (snaps[a]["wet"] + snaps[a + 1]["wet"])
