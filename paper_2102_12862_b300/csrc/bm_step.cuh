@@ -165,7 +165,7 @@ struct StepLayout {
   static constexpr uint32_t kSlice = kTile * S;
   uint32_t ne4, nh4, nloc;
   uint32_t desc, ctl, info, arr, gn2, slot;  // within a slot (record at 0), slot size
-  uint32_t F, uvc, dry, skip, red, total;    // from the start of shared memory
+  uint32_t F, uvc, dry, skip, red, elist, total;  // from the start of shared memory
   BM_HD StepLayout(uint32_t ne4_, uint32_t nh4_) {
     ne4 = ne4_;
     nh4 = nh4_;
@@ -182,7 +182,8 @@ struct StepLayout {
     dry = uvc + 3 * nloc * S;
     skip = dry + align16(nloc);
     red = skip + align16(ne4);
-    total = red + (4 + 24) * 8;  // finalize broadcast slots and reduction buffer
+    elist = red + (4 + 24) * 8;  // finalize broadcast slots and reduction buffer
+    total = elist + (k64 ? align16(2 * ne4) : 0u);  // FP64: phase F's list of edges with water
   }
 };
 
@@ -391,6 +392,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
   // tiles whose edge phase the compute warps have finished (claiming mode 3 claims item
   // j only once tile j - 1 is past its edges: long tiles commit late, nearly greedily)
   __shared__ int s_edged;
+  __shared__ int s_nact;  // FP64: the length of the phase F edge list
   // the launch's ticket map (written by the copy warp before its first issue, so the
   // compute warps see it after their first wait): stamp, listing allowed, part bounds
   // P1 <= P2 <= P3 <= tickets, whether the lists were taken; the tickets this CTA's copy
@@ -875,6 +877,7 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
     // phase D: wet/dry flags, velocity and celerity of tile and halo cells.
     // A tile whose cells and halo cells are all dry, whose cells are at rest and which
     // has no inflow edge is quiet: every flux is zero and U^{n+1} = U^n.
+    if (SL::k64 && tid == 0) s_nact = 0;  // the phase F edge list (read before the last barrier)
     bool tq = true;
     if (run) {
       for (int j = tid; j < kTile + nh; j += kTile) {
@@ -895,7 +898,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
 
     // phase F: edges
     if (run && !prime && !quiet) {
-      for (int k2 = tid; k2 < ne; k2 += kTile) {
+      // one edge's fluxes and its skip flag
+      auto edge_flux = [&](const int k2) {
         const uint32_t lr = sLR[k2];
         const int lL = static_cast<int>(lr & (kMaxLocal - 1));
         const int R = static_cast<int32_t>(lr) >> kLocBits;
@@ -984,6 +988,52 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
             a.ex_right[o] = right ? 1 : 0;
           }
         }
+      };
+      if constexpr (SL::k64) {
+        // FP64: the edges with water on a side, and inflow edges, are listed first and
+        // the flux loop runs over that list, so that at a wet/dry front a warp's FP64
+        // instructions run with all lanes busy (the list's order is free: each edge
+        // writes its own slots).  The other edges take their zero fluxes here.
+        uint16_t* elist = reinterpret_cast<uint16_t*>(smem + L.elist);
+        const int lane = tid & 31;
+        for (int kb = 0; kb < ne; kb += kTile) {
+          const int k2 = kb + tid;
+          bool act = false;
+          if (k2 < ne) {
+            const uint32_t lr = sLR[k2];
+            const int lL = static_cast<int>(lr & (kMaxLocal - 1));
+            const int R = static_cast<int32_t>(lr) >> kLocBits;
+            const int lR = R >= 0 ? R : lL;
+            const bool inflow = R <= kInflow && kInflow - R < a.n_inflow;
+            act = !(dry[lL] && dry[lR]) || inflow;
+            if (!act) {
+              Fs[k2] = zero;
+              Fs[L.ne4 + k2] = zero;
+              Fs[2 * L.ne4 + k2] = zero;
+              Fs[3 * L.ne4 + k2] = zero;
+              Fs[4 * L.ne4 + k2] = zero;
+              skip[k2] = 1;
+              if constexpr (kExtra) {
+                if (a.ex_flux != nullptr) {
+                  const size_t o = static_cast<size_t>(tile) * static_cast<size_t>(a.ex_stride) + k2;
+                  a.ex_flux[o] = zero;
+                  a.ex_right[o] = 0;
+                }
+              }
+            }
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, act);
+          int base = 0;
+          if (lane == 0 && m != 0u) base = atomicAdd(&s_nact, __popc(m));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (act) elist[base + __popc(m & ((1u << lane) - 1u))] = static_cast<uint16_t>(k2);
+        }
+        nbar<kTile>();
+        const int nact = *reinterpret_cast<volatile int*>(&s_nact);
+        for (int j = tid; j < nact; j += kTile) edge_flux(static_cast<int>(elist[j]));
+        if (kFull && (inf.flags & 56u)) nbar<kTile>();  // the boundary-law loop below revisits edges by owner
+      } else {
+        for (int k2 = tid; k2 < ne; k2 += kTile) edge_flux(k2);
       }
       if (kFull && (inf.flags & 56u)) {
         // outflow edges (h-Q relation, weir) and water-level edges, walls above: where
