@@ -898,8 +898,52 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
 
     // phase F: edges
     if (run && !prime && !quiet) {
-      // one edge's fluxes and its skip flag
-      auto edge_flux = [&](const int k2) {
+      int nact = ne;  // the edges the flux loop visits (FP64: the list's length)
+      const uint16_t* elist = reinterpret_cast<const uint16_t*>(smem + L.elist);
+      if constexpr (SL::k64) {
+        // FP64: the edges with water on a side, and inflow edges, are listed first and
+        // the flux loop runs over that list, so that at a wet/dry front a warp's FP64
+        // instructions run with all lanes busy (the list's order is free: each edge
+        // writes its own slots).  The other edges take their zero fluxes here.
+        uint16_t* list = reinterpret_cast<uint16_t*>(smem + L.elist);
+        const int lane = tid & 31;
+        for (int kb = 0; kb < ne; kb += kTile) {
+          const int k2 = kb + tid;
+          bool act = false;
+          if (k2 < ne) {
+            const uint32_t lr = sLR[k2];
+            const int lL = static_cast<int>(lr & (kMaxLocal - 1));
+            const int R = static_cast<int32_t>(lr) >> kLocBits;
+            const int lR = R >= 0 ? R : lL;
+            const bool inflow = R <= kInflow && kInflow - R < a.n_inflow;
+            act = !(dry[lL] && dry[lR]) || inflow;
+            if (!act) {
+              Fs[k2] = zero;
+              Fs[L.ne4 + k2] = zero;
+              Fs[2 * L.ne4 + k2] = zero;
+              Fs[3 * L.ne4 + k2] = zero;
+              Fs[4 * L.ne4 + k2] = zero;
+              skip[k2] = 1;
+              if constexpr (kExtra) {
+                if (a.ex_flux != nullptr) {
+                  const size_t o = static_cast<size_t>(tile) * static_cast<size_t>(a.ex_stride) + k2;
+                  a.ex_flux[o] = zero;
+                  a.ex_right[o] = 0;
+                }
+              }
+            }
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, act);
+          int base = 0;
+          if (lane == 0 && m != 0u) base = atomicAdd(&s_nact, __popc(m));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (act) list[base + __popc(m & ((1u << lane) - 1u))] = static_cast<uint16_t>(k2);
+        }
+        nbar<kTile>();
+        nact = *reinterpret_cast<volatile int*>(&s_nact);
+      }
+      for (int j = tid; j < nact; j += kTile) {
+        const int k2 = SL::k64 ? static_cast<int>(elist[j]) : j;
         const uint32_t lr = sLR[k2];
         const int lL = static_cast<int>(lr & (kMaxLocal - 1));
         const int R = static_cast<int32_t>(lr) >> kLocBits;
@@ -988,53 +1032,8 @@ __global__ void __launch_bounds__(kStepThreads, kMinBlocks<T>) step_pipe(const L
             a.ex_right[o] = right ? 1 : 0;
           }
         }
-      };
-      if constexpr (SL::k64) {
-        // FP64: the edges with water on a side, and inflow edges, are listed first and
-        // the flux loop runs over that list, so that at a wet/dry front a warp's FP64
-        // instructions run with all lanes busy (the list's order is free: each edge
-        // writes its own slots).  The other edges take their zero fluxes here.
-        uint16_t* elist = reinterpret_cast<uint16_t*>(smem + L.elist);
-        const int lane = tid & 31;
-        for (int kb = 0; kb < ne; kb += kTile) {
-          const int k2 = kb + tid;
-          bool act = false;
-          if (k2 < ne) {
-            const uint32_t lr = sLR[k2];
-            const int lL = static_cast<int>(lr & (kMaxLocal - 1));
-            const int R = static_cast<int32_t>(lr) >> kLocBits;
-            const int lR = R >= 0 ? R : lL;
-            const bool inflow = R <= kInflow && kInflow - R < a.n_inflow;
-            act = !(dry[lL] && dry[lR]) || inflow;
-            if (!act) {
-              Fs[k2] = zero;
-              Fs[L.ne4 + k2] = zero;
-              Fs[2 * L.ne4 + k2] = zero;
-              Fs[3 * L.ne4 + k2] = zero;
-              Fs[4 * L.ne4 + k2] = zero;
-              skip[k2] = 1;
-              if constexpr (kExtra) {
-                if (a.ex_flux != nullptr) {
-                  const size_t o = static_cast<size_t>(tile) * static_cast<size_t>(a.ex_stride) + k2;
-                  a.ex_flux[o] = zero;
-                  a.ex_right[o] = 0;
-                }
-              }
-            }
-          }
-          const unsigned m = __ballot_sync(0xffffffffu, act);
-          int base = 0;
-          if (lane == 0 && m != 0u) base = atomicAdd(&s_nact, __popc(m));
-          base = __shfl_sync(0xffffffffu, base, 0);
-          if (act) elist[base + __popc(m & ((1u << lane) - 1u))] = static_cast<uint16_t>(k2);
-        }
-        nbar<kTile>();
-        const int nact = *reinterpret_cast<volatile int*>(&s_nact);
-        for (int j = tid; j < nact; j += kTile) edge_flux(static_cast<int>(elist[j]));
-        if (kFull && (inf.flags & 56u)) nbar<kTile>();  // the boundary-law loop below revisits edges by owner
-      } else {
-        for (int k2 = tid; k2 < ne; k2 += kTile) edge_flux(k2);
       }
+      if (SL::k64 && kFull && (inf.flags & 56u)) nbar<kTile>();  // the boundary-law loop below revisits edges by owner
       if (kFull && (inf.flags & 56u)) {
         // outflow edges (h-Q relation, weir) and water-level edges, walls above: where
         // the law lets water out, the flux of the boundary state on the cell's outgoing
