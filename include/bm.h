@@ -193,7 +193,9 @@ bm_status bm_state_download_track(bm_state* s, double* t_arrival, double* h_max,
  * side of the contact wave (the step kernel's own decision), phi_c = q_c / h where
  * h > 0, else 0; walls carry nothing, a transmissive edge carries the inside value,
  * and the water entering through inflow edges carries c_in[c].  A cell that ends a
- * step dry keeps no species (q_c = 0).
+ * step dry keeps no species (q_c = 0).  External sources (bm_state_set_sources) change
+ * the water only: with Eq. 8's source term off, rain and other sources bring no species
+ * (they dilute) and sinks take none (they concentrate).
  * bm_state_set_scalars sets the species: hc holds n_species * n_cells values of q_c
  * (species-major, caller cell order, finite; BM_EINVAL otherwise), c_in n_species
  * inflow concentrations (NULL: 0).  n_species in [0, 5]; 0 removes them.  It
@@ -223,9 +225,9 @@ bm_status bm_state_download_scalars(bm_state* s, double* hc);
  * (t[k], v[k]) for k in [offsets[r], offsets[r+1]) (times strictly increasing),
  * piecewise linear and constant beyond the ends; v > 0 adds water, v < 0 takes it.
  * Sources add mass, not momentum.  n_regions in [0, 65536]; 0 removes them.  BM_EINVAL
- * on malformed input, on a total-discharge region with no cell, and when the state
- * carries passive species (not modelled together; bm_state_set_scalars refuses the
- * converse).  Blocks.  Every step launches a one-block kernel before the step kernel
+ * on malformed input and on a total-discharge region with no cell.  A state may carry
+ * passive species too: the sources' water carries none (see bm_state_set_scalars).
+ * Blocks.  Every step launches a one-block kernel before the step kernel
  * (S_h at t^n); in a batch, one per member with sources before the batch's step launch.
  * Set sources before bm_batch_create on a batch member (a batch made earlier refuses to
  * step, BM_EINVAL).

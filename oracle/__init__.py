@@ -283,8 +283,6 @@ class Oracle:
     def step(self, n: int = 1, t_end: float = math.inf) -> int:
         lib = _lib()
         if self.hc is not None:
-            if getattr(self, "n_sources", 0):
-                raise OracleError("passive species with external sources are not modelled")
             if self.tracking is not None:
                 raise OracleError("scalars and flood tracking together are not supported by the oracle")
             k = lib.orc_run_scalars(self._h, _dp(self.H), _dp(self.qx), _dp(self.qy), C.byref(self.t),

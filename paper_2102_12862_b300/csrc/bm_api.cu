@@ -1111,7 +1111,6 @@ bm_status bm_state_set_scalars(bm_state* s, int32_t n_species, const double* hc,
   const HostMesh& h = s->mesh->h;
   const int n = static_cast<int>(h.n_cells);
   if (n_species > 0 && !hc) return fail(BM_EINVAL, "bm_state_set_scalars: hc is NULL");
-  if (n_species > 0 && s->n_src > 0) return fail(BM_EINVAL, "bm_state_set_scalars: the state has external sources");
   for (int64_t i = 0; i < static_cast<int64_t>(n_species) * n; ++i)
     if (!std::isfinite(hc[i])) return fail(BM_EINVAL, "bm_state_set_scalars: hc has a non-finite value");
   for (int c = 0; c < n_species && c_in; ++c)
@@ -1197,7 +1196,6 @@ bm_status bm_state_set_sources(bm_state* s, int32_t n_regions, const int32_t* re
   const HostMesh& h = s->mesh->h;
   const int64_t n = h.n_cells;
   if (n_regions > 0) {
-    if (s->n_species > 0) return fail(BM_EINVAL, "bm_state_set_sources: the state carries passive species");
     if (!region || !kind || !mode || !offsets || !t || !v) return fail(BM_EINVAL, "bm_state_set_sources: NULL array");
     if (offsets[0] != 0) return fail(BM_EINVAL, "bm_state_set_sources: offsets[0] must be 0");
     for (int32_t r = 0; r < n_regions; ++r) {

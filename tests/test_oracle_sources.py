@@ -42,6 +42,41 @@ def test_rain_on_lake_at_rest():
     assert abs(o.volume() - v0 - o.source_volume) <= 1e-11 * v0
 
 
+def test_rain_dilutes_species_on_a_lake_at_rest():
+    """Eq. 8 with its source term off: rain brings water and no species.  On a lake at
+    rest every cell's depth grows by i t while its species mass h phi stays, so phi(t) =
+    phi0 h0 / (h0 + i t) cell by cell (closed form); a sink over part of the lake takes
+    water and leaves the species (phi rises there by h0 / (h0 - s t)), and the species
+    mass of the whole closed lake is unchanged to rounding."""
+    s = W.fractal_lake(nx=40, ny=20, Lx=400.0, Ly=200.0, seed=11, relief=5.0, level=406.0)
+    o = oracle.Oracle(s)
+    h0 = o.depth().copy()
+    assert h0.min() > 0.5
+    rng = np.random.default_rng(5)
+    phi0 = rng.uniform(0.2, 1.0, o.n_cells)
+    o.set_scalars(np.stack([phi0 * h0, 0.5 * h0]))
+    o.set_sources(np.zeros(o.n_cells), [INTENSITY], [EXACT], [const(36.0)])
+    m0 = (o.area()[None, :] * o.hc).sum(axis=1)
+    o.run_until(200.0)
+    phi = o.concentration()
+    assert np.max(np.abs(phi[0] - phi0 * h0 / (h0 + 1e-5 * 200.0))) <= 1e-12
+    assert np.max(np.abs(phi[1] - 0.5 * h0 / (h0 + 1e-5 * 200.0))) <= 1e-12
+    assert np.max(np.abs((o.area()[None, :] * o.hc).sum(axis=1) - m0) / m0) <= 1e-13
+    # a sink of 36 mm/h on the cells with x < 200 m: the rest of the lake stays at rest,
+    # so with the rain off their depth falls by s t and their phi rises accordingly
+    o2 = oracle.Oracle(s)
+    o2.set_scalars(np.stack([phi0 * h0]))
+    x = s.centroids()[:, 0]
+    region = np.where(x < 200.0, 0, -1)
+    o2.set_sources(region, [INTENSITY], [EXACT], [const(-36.0)])
+    o2.step(1)
+    hs = o2.depth()
+    # one step: the sink's cells lost dt s of water and none of their species
+    sink = region == 0
+    assert np.max(np.abs(o2.hc[0][sink] - (phi0 * h0)[sink])) <= 1e-12 * np.max(phi0 * h0)
+    assert np.all(hs[sink] < h0[sink])
+
+
 def test_total_discharge_volume():
     """A total discharge Q over a disk in a closed basin: the volume grows by Q t
     (constant Q) whatever the disk's cells; a linear ramp adds the step sum of Q(t^n),

@@ -167,3 +167,41 @@ def test_t6_three_humps_fp64():
     H, _, _, _ = st.download()
     mean = (g @ area) / np.sum(area * (H - s.z))
     assert abs(mean[0] - 0.386) <= 5e-4 and abs(mean[1] - 0.023) <= 5e-4
+
+
+@pytest.mark.parametrize("seed", [41, 42])
+def test_species_with_rain_and_a_sink_fp64(seed):
+    """Species together with external sources (Eq. 8 with its source term off: the
+    sources' water carries no species): a dam break with friction under rain on one
+    region and an Available sink on another, 300 steps; q_c and the state element-wise
+    against the oracle."""
+    s = W.dam_break(nx=150, ny=20, seed=seed, manning=0.02)
+    h0 = np.maximum(s.H - s.z, 0.0)
+    x = s.centroids()[:, 0]
+    st, o = both(s, np.stack([np.where(x < 30.0, 1.0, 0.3) * h0, 0.5 * h0]), c_in=None)
+    region = np.where(x < 20.0, 0, np.where(x > 70.0, 1, -1)).astype(np.int32)
+    series = [(np.array([0.0, 2.0]), np.array([3600.0, 720.0])), (np.array([0.0]), np.array([-1800.0]))]
+    args = (region, [bm.SOURCE_INTENSITY, bm.SOURCE_INTENSITY], [bm.SINK_EXACT, bm.SINK_AVAILABLE], series)
+    st.set_sources(*args)
+    o.set_sources(*args)
+    st.step(300)
+    o.step(300)
+    compare_fp64(st, o)
+    H, qx, qy, _ = st.download()
+    assert rel_linf(H - s.z, o.H - s.z) <= 1e-11
+    assert rel_linf(qx, o.qx) <= 1e-11 and rel_linf(qy, o.qy) <= 1e-11
+
+
+def test_rain_dilutes_species_fp32():
+    """FP32-bulk: rain on a lake at rest dilutes each cell's concentration to
+    phi0 h0 / (h0 + i t) (closed form) within that mode's accuracy."""
+    s = W.fractal_lake(nx=40, ny=20, Lx=400.0, Ly=200.0, seed=11, relief=5.0, level=406.0)
+    h0 = s.H - s.z
+    phi0 = np.random.default_rng(5).uniform(0.2, 1.0, len(h0))
+    st = bm.State.from_scenario(s, precision="fp32")
+    st.set_scalars(np.stack([phi0 * h0]))
+    st.set_sources(np.zeros(len(h0), dtype=np.int32), [bm.SOURCE_INTENSITY], [bm.SINK_EXACT],
+                   [(np.array([0.0]), np.array([36.0]))])
+    st.run_until(200.0)
+    phi = st.concentration()[0]
+    assert np.max(np.abs(phi - phi0 * h0 / (h0 + 1e-5 * 200.0))) <= 1e-5
