@@ -128,12 +128,15 @@ def test_fp32_batch_members_against_the_oracle():
 
 def featured(precision):
     """Members with every optional feature, each on its own floodplain: two passive
-    species, rain on a disk (an external source), a log-law friction closure with flood
+    species under rain on a disk, rain on a disk (an external source), a log-law friction closure with flood
     tracking, and (FP64) bed evolution; plus a plain member."""
     scs = [W.floodplain(nx=100, ny=40, Lx=1000.0, Ly=400.0, seed=61 + k, q_peak=90.0, ramp=40.0) for k in range(5)]
     sts = [bm.State.from_scenario(s, precision=precision) for s in scs]
     hc = np.stack([np.maximum(scs[0].H - scs[0].z, 0.0) * 0.5, np.zeros(scs[0].n_cells)])
     sts[0].set_scalars(hc, [0.0, 1.0])
+    # the species member also takes rain (species together with sources)
+    sts[0].set_sources(W.disk_region(scs[0], 600.0, 200.0, 80.0), [bm.SOURCE_INTENSITY], [bm.SINK_EXACT],
+                       [(np.array([0.0, 1e6]), np.array([90.0, 90.0]))])
     sts[1].set_sources(W.disk_region(scs[1], 700.0, 120.0, 60.0), [bm.SOURCE_INTENSITY], [bm.SINK_EXACT],
                        [(np.array([0.0, 1e6]), np.array([150.0, 150.0]))])
     sts[2].set_friction(bm.FRICTION_CHEZY, 25.0)
